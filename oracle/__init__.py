@@ -1,0 +1,219 @@
+"""CPU oracle of the bootstrap particle filter (arXiv 1306.3277, Algorithm 2).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The product path (``paper_1306_3277_b300``) never does, and the two
+share no code: the oracle is plain C (``pf_oracle.c``) compiled with gcc,
+the product is CUDA.
+
+What each function follows, and what pins it (tests in ``tests/test_oracle_*``):
+
+========================  =======================================  ==========================================
+function                  follows                                   pinned by
+========================  =======================================  ==========================================
+philox4x32_10             Salmon et al. SC'11 (Philox4x32-10)       published known-answer vectors
+                                                                    (tests/golden/philox4x32_10_kat.txt)
+log / logf                atanh series of log (own)                libm log, <= 2 ulp; exact special values
+sincos2pi / sincos2pif    quarter-turn reduction + Taylor (own)    libm sin/cos, exact quadrant points
+normal64 / normal32       Box-Muller                               moments, Kolmogorov-Smirnov vs scipy
+flow_table                Eq. (flow) read as a half sine           closed form with numpy.sin
+l96_rk4 / l96_rk4f        Eq. (lorenz96-ode), classic RK4          fixed point, shift equivariance, energy
+                                                                    decay exp(-2t) at F=0, 4th-order
+                                                                    convergence, scipy solve_ivp
+kalman_windkessel         Algorithm 1 (scalar)                     brute-force joint Gaussian (scipy)
+lse                       Algorithm 2 likelihood line, log space   equal / one-hot weights, shift invariance,
+                                                                    math.fsum
+systematic                Sec. 3.3 systematic resampling           integer weights (exact), brute-force
+                                                                    offspring enumeration on P <= 8
+pf_run                    Algorithm 2                              Kalman likelihood (exact special case
+                                                                    and convergence over P), closed-form
+                                                                    deterministic Lorenz '96 likelihood
+========================  =======================================  ==========================================
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+WINDKESSEL = 0
+LORENZ96 = 1
+FP64 = 0
+MIXED = 1
+PURPOSE_INIT = 1
+PURPOSE_PROP = 2
+PURPOSE_RESAMPLE = 3
+OK = 0
+EINVAL = 1
+EDEGENERATE = 4
+
+
+class Model(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32),
+        ("N", ctypes.c_int32),
+        ("substeps", ctypes.c_int32),
+        ("obs_stride", ctypes.c_int32),
+        ("prec", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+        ("dt", ctypes.c_double),
+        ("ess_threshold", ctypes.c_double),
+        ("flow_peak", ctypes.c_double),
+        ("flow_period", ctypes.c_double),
+    ]
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+_ip = ctypes.POINTER(ctypes.c_int32)
+_up = ctypes.POINTER(ctypes.c_uint32)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.or_philox4x32_10.argtypes = [_up, _up, _up]
+        L.or_normal64.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                  ctypes.c_uint32]
+        L.or_normal64.restype = ctypes.c_double
+        L.or_normal32.argtypes = L.or_normal64.argtypes
+        L.or_normal32.restype = ctypes.c_float
+        L.or_resample_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint32]
+        L.or_resample_uniform.restype = ctypes.c_double
+        L.or_fill_normals.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint32,
+                                      ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _dp]
+        L.or_log.argtypes = [ctypes.c_double]
+        L.or_log.restype = ctypes.c_double
+        L.or_logf.argtypes = [ctypes.c_float]
+        L.or_logf.restype = ctypes.c_float
+        L.or_sincos2pi.argtypes = [ctypes.c_double, _dp, _dp]
+        L.or_sincos2pif.argtypes = [ctypes.c_float, _fp, _fp]
+        L.or_flow_table.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                    _dp]
+        L.or_l96_rk4.argtypes = [_dp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32]
+        L.or_l96_rk4f.argtypes = [_fp, ctypes.c_int32, ctypes.c_float, ctypes.c_float, ctypes.c_int32]
+        L.or_kalman_windkessel.argtypes = [ctypes.POINTER(Model), _dp, _dp, ctypes.c_int32]
+        L.or_kalman_windkessel.restype = ctypes.c_double
+        L.or_lse.argtypes = [_dp, ctypes.c_int64, _dp, _dp, _dp]
+        L.or_systematic.argtypes = [_dp, ctypes.c_int64, ctypes.c_double, _ip]
+        L.or_systematic.restype = ctypes.c_int64
+        L.or_pf_run.argtypes = [ctypes.POINTER(Model), _dp, _dp, ctypes.c_uint64, ctypes.c_int64,
+                                ctypes.c_int32, ctypes.c_int32, _dp, _dp, _ip, _dp]
+        L.or_pf_run.restype = ctypes.c_int32
+        _lib = L
+    return _lib
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t)
+
+
+def model(kind, N=1, substeps=1, obs_stride=1, prec=FP64, dt=0.01, ess_threshold=1.0,
+          flow_peak=400.0, flow_period=1.0):
+    return Model(kind, N, substeps, obs_stride, prec, 0, dt, ess_threshold, flow_peak, flow_period)
+
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.zeros(4, dtype=np.uint32)
+    lib().or_philox4x32_10(_ptr(c, _up), _ptr(k, _up), _ptr(o, _up))
+    return o
+
+
+def normal64(seed, j, i, purpose, q):
+    return lib().or_normal64(seed, j, i, purpose, q)
+
+
+def normal32(seed, j, i, purpose, q):
+    return lib().or_normal32(seed, j, i, purpose, q)
+
+
+def fill_normals(seed, prec, i, purpose, nj, nq):
+    out = np.zeros((nj, nq), dtype=np.float64)
+    lib().or_fill_normals(seed, prec, i, purpose, nj, nq, _ptr(out, _dp))
+    return out
+
+
+def resample_uniform(seed, i):
+    return lib().or_resample_uniform(seed, i)
+
+
+def log(x):
+    return lib().or_log(float(x))
+
+
+def logf(x):
+    return lib().or_logf(float(np.float32(x)))
+
+
+def sincos2pi(u):
+    s = ctypes.c_double()
+    c = ctypes.c_double()
+    lib().or_sincos2pi(float(u), ctypes.byref(s), ctypes.byref(c))
+    return s.value, c.value
+
+
+def sincos2pif(u):
+    s = ctypes.c_float()
+    c = ctypes.c_float()
+    lib().or_sincos2pif(float(np.float32(u)), ctypes.byref(s), ctypes.byref(c))
+    return np.float32(s.value), np.float32(c.value)
+
+
+def flow_table(peak, period, dt, n):
+    out = np.zeros(n, dtype=np.float64)
+    lib().or_flow_table(peak, period, dt, n, _ptr(out, _dp))
+    return out
+
+
+def l96_rk4(x, F, dt, nsteps):
+    x = np.array(x, dtype=np.float64)
+    lib().or_l96_rk4(_ptr(x, _dp), len(x), F, dt, nsteps)
+    return x
+
+
+def l96_rk4f(x, F, dt, nsteps):
+    x = np.array(x, dtype=np.float32)
+    lib().or_l96_rk4f(_ptr(x, _fp), len(x), float(np.float32(F)), float(np.float32(dt)), nsteps)
+    return x
+
+
+def kalman_windkessel(m, theta, y):
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    yy = np.ascontiguousarray(y, dtype=np.float64).ravel()
+    return lib().or_kalman_windkessel(ctypes.byref(m), _ptr(th, _dp), _ptr(yy, _dp), len(yy))
+
+
+def lse(ell):
+    e = np.ascontiguousarray(ell, dtype=np.float64)
+    M, S, Q = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lib().or_lse(_ptr(e, _dp), len(e), ctypes.byref(M), ctypes.byref(S), ctypes.byref(Q))
+    return M.value, S.value, Q.value
+
+
+def systematic(ell, u):
+    e = np.ascontiguousarray(ell, dtype=np.float64)
+    anc = np.zeros(len(e), dtype=np.int32)
+    near = lib().or_systematic(_ptr(e, _dp), len(e), float(u), _ptr(anc, _ip))
+    return anc, int(near)
+
+
+def pf_run(m, theta, y, seed, P, T, nthreads=0, want_x=True, want_anc=True, want_diag=True):
+    """Run the filter; returns dict(status, loglik, x [N][P], anc [T][P], diag [T][8])."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    ll = ctypes.c_double()
+    x = np.zeros((m.N, P), dtype=np.float64) if want_x else None
+    anc = np.zeros((T, P), dtype=np.int32) if want_anc else None
+    diag = np.zeros((T, 8), dtype=np.float64) if want_diag else None
+    st = lib().or_pf_run(ctypes.byref(m), _ptr(th, _dp), _ptr(yy, _dp), seed, P, T, nthreads,
+                         ctypes.byref(ll),
+                         _ptr(x, _dp) if x is not None else None,
+                         _ptr(anc, _ip) if anc is not None else None,
+                         _ptr(diag, _dp) if diag is not None else None)
+    return dict(status=st, loglik=ll.value, x=x, anc=anc, diag=diag)

@@ -1,0 +1,87 @@
+/*
+ * pf_oracle.h -- plain, slow CPU oracle for the bootstrap particle filter of
+ * Murray, "Bayesian State-Space Modelling on High-Performance Hardware Using
+ * LibBi" (arXiv 1306.3277), Algorithm 2 (Sec. 3.1.2), with systematic
+ * resampling (Sec. 3.3) and an effective-sample-size test.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may include, link or
+ * call this library: only the tests, the smoke check and the CPU-baseline leg
+ * of the benchmark do.  It shares no code with the CUDA implementation.
+ *
+ * Every arithmetic convention (operation order, explicit fma, own log and
+ * sincos for Box-Muller, Philox counter layout) is stated next to the code
+ * that implements it, so that the CUDA side can be written independently to
+ * the same definitions and compared bit for bit.
+ *
+ * Every function here is pinned by a -m "not gpu" test against something
+ * other than itself (published known answers, libm, closed forms, a Kalman
+ * filter, brute-force enumeration); the list is in oracle/__init__.py.
+ */
+#ifndef PF_ORACLE_H
+#define PF_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { OR_WINDKESSEL = 0, OR_LORENZ96 = 1 };
+enum { OR_FP64 = 0, OR_MIXED = 1 };
+enum { OR_OK = 0, OR_EINVAL = 1, OR_EDEGENERATE = 4 };
+/* Philox counter word 2 carries (purpose << 16) | block index. */
+enum { OR_PURPOSE_INIT = 1, OR_PURPOSE_PROP = 2, OR_PURPOSE_RESAMPLE = 3 };
+
+typedef struct {
+  int32_t kind;          /* OR_WINDKESSEL or OR_LORENZ96 */
+  int32_t N;             /* state dimension (1 for the windkessel) */
+  int32_t substeps;      /* Euler / RK4 substeps per observation interval */
+  int32_t obs_stride;    /* Lorenz '96: components n with n % obs_stride == 0 are observed */
+  int32_t prec;          /* OR_FP64 or OR_MIXED (FP32 state and noise, FP64 weights) */
+  int32_t pad;
+  double dt;             /* substep length */
+  double ess_threshold;  /* >= 1: resample every step; else resample iff ESS < thr * P */
+  double flow_peak;      /* windkessel input F(t): peak of the half sine */
+  double flow_period;    /* windkessel input F(t): period */
+} or_model;
+
+/* --- random numbers ---------------------------------------------------- */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* normal number q of the stream (j, i, purpose), FP64 (2 normals per block) */
+double or_normal64(uint64_t seed, uint32_t j, uint32_t i, uint32_t purpose, uint32_t q);
+/* normal number q of the stream (j, i, purpose), FP32 (4 normals per block) */
+float or_normal32(uint64_t seed, uint32_t j, uint32_t i, uint32_t purpose, uint32_t q);
+double or_resample_uniform(uint64_t seed, uint32_t i);
+void or_fill_normals(uint64_t seed, int32_t prec, uint32_t i, uint32_t purpose, uint32_t nj,
+                     uint32_t nq, double *out);
+
+/* --- project-written elementary functions ----------------------------- */
+double or_log(double x);
+void or_sincos2pi(double u, double *s, double *c);
+float or_logf(float x);
+void or_sincos2pif(float u, float *s, float *c);
+
+/* --- model pieces ------------------------------------------------------- */
+void or_flow_table(double peak, double period, double dt, int64_t n, double *out);
+/* deterministic Lorenz '96 RK4, nsteps steps of dt, in place (FP64) */
+void or_l96_rk4(double *x, int32_t N, double F, double dt, int32_t nsteps);
+void or_l96_rk4f(float *x, int32_t N, float F, float dt, int32_t nsteps);
+/* scalar Kalman filter for the Euler-discretised windkessel */
+double or_kalman_windkessel(const or_model *m, const double *theta, const double *y, int32_t T);
+
+/* --- resampling pieces -------------------------------------------------- */
+void or_lse(const double *ell, int64_t P, double *M, double *S, double *Q);
+/* systematic resampling from log-weights; returns the number of
+ * near-boundary targets (|tau_j - C_k| <= 1e-12 * C_{P-1}) */
+int64_t or_systematic(const double *ell, int64_t P, double u, int32_t *anc);
+
+/* --- the filter --------------------------------------------------------- */
+/* diag, if not NULL, receives per step i (row i-1) 8 doubles:
+ * M, S, Q, ESS, resampled (0/1), u, log-likelihood increment, near-boundary count */
+int32_t or_pf_run(const or_model *m, const double *theta, const double *y, uint64_t seed,
+                  int64_t P, int32_t T, int32_t nthreads, double *loglik,
+                  double *xfinal, int32_t *anc, double *diag);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
