@@ -1,0 +1,163 @@
+/*
+ * pf.h -- C ABI of the B300 (sm_103a) bootstrap particle filter.
+ *
+ * The operation is the bootstrap particle filter of Murray, "Bayesian
+ * State-Space Modelling on High-Performance Hardware Using LibBi"
+ * (arXiv 1306.3277), Algorithm 2 (Sec. 3.1.2): for given parameters theta it
+ * returns an estimate of the log marginal likelihood log p(y(t_1:T) | theta)
+ * (the likelihood line of Algorithm 2, accumulated in log space), the final
+ * particle cloud and the ancestor indices.  Resampling is systematic
+ * (Sec. 3.3, one uniform per step, sorted ancestors) and is skipped on steps
+ * whose effective sample size is at or above ess_threshold * P.
+ *
+ * Models (Sec. 2.1):
+ *   PF_WINDKESSEL (Sec. 2.1.1), N = 1, theta = (R, C, Z, q, r, m0, s0):
+ *     per substep x <- x + dt (F(t_k)/C - x/(R C)) + N(0, q), F held over
+ *     [t_k, t_k + dt); observation y_i ~ N(x + Z F(t_i), r); x0 ~ N(m0, s0^2).
+ *     F(t) = flow_peak sin(2 pi t / flow_period) on the first half of each
+ *     period, else 0 (Eq. flow read as a half sine).
+ *   PF_LORENZ96 (Sec. 2.1.2, Eq. lorenz96-ode), N in {4, 8, 12, 16, 20, 24,
+ *     32, 40}, theta = (F, q, r, m0, s0): `substeps` classic RK4 steps of dt,
+ *     then x_n += N(0, q) for every n; observation y ~ N(x_n, r) for every
+ *     n with n % obs_stride == 0 (Ny = ceil(N / obs_stride));
+ *     x0_n ~ N(m0, s0^2).
+ *   Observation i is at t_i = i * substeps * dt, i = 1..T.
+ *
+ * Precision: PF_FP64 computes everything in FP64.  PF_MIXED keeps the state,
+ * the integrator and the process noise in FP32 and the observation
+ * log-weights, log-sum-exp, cumulative-weight scan and likelihood in FP64.
+ *
+ * Random numbers: Philox4x32-10 keyed by the 64-bit seed, counter
+ * (particle, step, purpose << 16 | block, 0), Box-Muller normals.  A run is a
+ * pure function of (filter configuration, theta, y, seed): the same call on
+ * any B300 returns the same bits, alone or inside a batch.
+ *
+ * Errors: every entry point returns a pf_status; on anything but PF_OK (and
+ * PF_EDEGENERATE, see pf_run) outputs are left untouched, and
+ * pf_last_error() returns a message for the calling thread.  Calls on one
+ * pf_filter must not overlap; different filters may be used from different
+ * host threads.
+ */
+#ifndef PF_B300_H
+#define PF_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PF_OK = 0,
+  PF_EINVAL = 1,       /* bad argument (message in pf_last_error)            */
+  PF_ENOMEM = 2,       /* device allocation failed / over the memory budget  */
+  PF_ECUDA = 3,        /* a CUDA runtime call failed                         */
+  PF_EDEGENERATE = 4,  /* every particle weight was zero or not a number     */
+  PF_ETIMEOUT = 5,     /* a bounded wait ran out                             */
+  PF_EBUSY = 6         /* result not ready / no capacity right now           */
+} pf_status;
+
+typedef enum { PF_WINDKESSEL = 0, PF_LORENZ96 = 1 } pf_model_kind;
+typedef enum { PF_FP64 = 0, PF_MIXED = 1 } pf_precision;
+
+typedef struct {
+  int32_t kind;          /* pf_model_kind                                       */
+  int32_t N;             /* state dimension: 1 (windkessel) or a supported L96 N */
+  int32_t substeps;      /* integrator substeps per observation interval, >= 1  */
+  int32_t obs_stride;    /* Lorenz '96: observe n % obs_stride == 0, >= 1        */
+  int32_t prec;          /* pf_precision                                        */
+  int32_t reserved;      /* must be 0                                           */
+  double ess_threshold;  /* >= 1: resample after every observation but the last;
+                            in (0, 1): resample iff ESS < ess_threshold * P;
+                            0: never resample                                  */
+  double flow_peak;      /* windkessel input: peak of the half-sine flow        */
+  double flow_period;    /* windkessel input: period of the flow, > 0           */
+} pf_model;
+
+typedef struct pf_filter pf_filter;
+
+/* Number of theta entries for a model kind (7 windkessel, 5 Lorenz '96), or 0. */
+int32_t pf_theta_size(int32_t kind);
+
+/* Create a filter for P particles (1 <= P <= 2^24) and T observations (T >= 1)
+ * with substep dt > 0, on the current CUDA device.  Allocates every device
+ * buffer the run needs (state double buffer, weights, ancestors, partials);
+ * the library owns them until pf_destroy.  *out is set only on PF_OK. */
+pf_status pf_create(const pf_model* m, int64_t P, int32_t T, double dt, pf_filter** out);
+
+/* Bytes of device memory a filter of this shape holds (ancestor history
+ * included when `history` is non-zero); 0 on invalid arguments. */
+size_t pf_device_bytes(const pf_model* m, int64_t P, int32_t T, int32_t history);
+
+#define PF_FLAG_ASYNC 1u  /* enqueue only: do not wait for the stream; outputs must be
+                             device pointers, read the status later with pf_wait */
+
+/* Run the filter over y(t_1..t_T) (Algorithm 2 with r = 0, s = T).
+ *   theta            [pf_theta_size(kind)] doubles, host or device memory.
+ *   y                [T][Ny] doubles, row i-1 = y(t_i), host or device memory.
+ *   seed             64-bit Philox key.
+ *   loglik           out: 1 double, log of the likelihood estimate, host or device.
+ *   final_particles  out or NULL: [N][P] (component-major) x(t_T), in the
+ *                    state precision (double for PF_FP64, float for PF_MIXED).
+ *   ancestors        out or NULL: [T][P] int32, row i-1 = a(t_i), the ancestor
+ *                    indices used to propagate into t_i (row 0 is the identity;
+ *                    rows of steps that did not resample are the identity).
+ *   flags            0 or PF_FLAG_ASYNC.
+ *   cuda_stream      cudaStream_t to run on, or NULL for the filter's own stream.
+ * All work runs on the GPU as one CUDA-graph launch; the inputs are copied to
+ * the filter's buffers first, so they may be reused when the call returns
+ * (host inputs) or when the stream passes this point (device inputs).
+ * Returns PF_EDEGENERATE (and loglik = -inf) if at some step every weight was
+ * zero or not a number; the other outputs are then undefined. */
+pf_status pf_run(pf_filter* f, const double* theta, const double* y, uint64_t seed,
+                 double* loglik, void* final_particles, int32_t* ancestors, uint32_t flags,
+                 void* cuda_stream);
+
+/* After a PF_FLAG_ASYNC run: wait for the filter's last run and return its
+ * status (PF_OK or PF_EDEGENERATE). */
+pf_status pf_wait(pf_filter* f);
+
+pf_status pf_destroy(pf_filter* f);
+
+/* Message describing the last error on this host thread ("" if none). */
+const char* pf_last_error(void);
+
+/* Many independent filters in one launch sequence (PMCMC proposals, SMC^2
+ * parameter particles).  Filter k runs exactly as pf_run(f[k], theta[k],
+ * y[k], seeds[k], ...) would, bit for bit; the filters may differ in model,
+ * P, T and precision.  Pointers in theta[k], y[k] may be host or device
+ * memory; logliks and per_filter_status are host arrays of nfilt entries.
+ * The launch plan (tile map, CUDA graph) is cached for a repeated filter list.
+ * Returns PF_OK if every filter ran (per-filter outcomes in
+ * per_filter_status), else the first error. */
+pf_status pf_batch_run(int32_t nfilt, pf_filter* const* f, const double* const* theta,
+                       const double* const* y, const uint64_t* seeds, double* logliks,
+                       int32_t* per_filter_status, void* cuda_stream);
+
+/* Continuous-batching request server.  Requests (model, P, T, dt, theta, y,
+ * seed) are queued on submit; a scheduler thread admits them when the device
+ * memory budget and a slot allow, advances every admitted filter one
+ * observation per iteration in shared launches, and retires finished ones, so
+ * requests that arrive while others run join the next iteration.  Results are
+ * bit-identical to pf_run of the same request. */
+typedef struct pf_server pf_server;
+pf_status pf_server_create(size_t device_mem_budget, int32_t max_slots, pf_server** out);
+/* Queue a request; theta and y are copied.  PF_ENOMEM if the request alone
+ * exceeds the budget, PF_EINVAL on bad arguments. */
+pf_status pf_server_submit(pf_server* s, const pf_model* m, int64_t P, int32_t T, double dt,
+                           const double* theta, const double* y, uint64_t seed,
+                           uint64_t* ticket);
+/* PF_EBUSY while the request is queued or running; otherwise its final status,
+ * with loglik and latency (seconds from submit to completion) filled in.  A
+ * finished ticket can be polled once. */
+pf_status pf_server_poll(pf_server* s, uint64_t ticket, double* loglik, double* latency_s);
+/* Counters: queued, running, completed requests and scheduler iterations. */
+pf_status pf_server_stats(pf_server* s, int64_t* queued, int64_t* running, int64_t* completed,
+                          int64_t* iterations);
+pf_status pf_server_destroy(pf_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PF_B300_H */

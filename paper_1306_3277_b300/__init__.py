@@ -1,0 +1,261 @@
+"""B300 (sm_103a) bootstrap particle filter -- Python binding of the C ABI in
+``include/pf.h``.
+
+This module only marshals arguments: every step of the filter runs in the
+CUDA kernels of ``libpf_b300.so``.  There is no CPU fallback; importing it
+without the built library (and a CUDA device at call time) raises.
+
+Names follow the C ABI: ``pf_create``, ``pf_run``, ``pf_wait``, ``pf_destroy``,
+``pf_batch_run``, ``pf_server_*``; arrays may be numpy arrays (host memory) or
+torch CUDA tensors (device memory, passed by pointer).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_EDEGENERATE, PF_ETIMEOUT, PF_EBUSY = range(7)
+PF_WINDKESSEL, PF_LORENZ96 = 0, 1
+PF_FP64, PF_MIXED = 0, 1
+PF_FLAG_ASYNC = 1
+STATUS_NAMES = {0: "PF_OK", 1: "PF_EINVAL", 2: "PF_ENOMEM", 3: "PF_ECUDA", 4: "PF_EDEGENERATE",
+                5: "PF_ETIMEOUT", 6: "PF_EBUSY"}
+L96_SIZES = (4, 8, 12, 16, 20, 24, 32, 40)
+
+
+class PFError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+class pf_model(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("N", ctypes.c_int32), ("substeps", ctypes.c_int32),
+                ("obs_stride", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("ess_threshold", ctypes.c_double),
+                ("flow_peak", ctypes.c_double), ("flow_period", ctypes.c_double)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def lib():
+    """Load (building if stale) libpf_b300.so."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.pf_theta_size.argtypes = [ctypes.c_int32]
+        L.pf_theta_size.restype = ctypes.c_int32
+        L.pf_create.argtypes = [ctypes.POINTER(pf_model), ctypes.c_int64, ctypes.c_int32,
+                                ctypes.c_double, ctypes.POINTER(_vp)]
+        L.pf_device_bytes.argtypes = [ctypes.POINTER(pf_model), ctypes.c_int64, ctypes.c_int32,
+                                      ctypes.c_int32]
+        L.pf_device_bytes.restype = ctypes.c_size_t
+        L.pf_run.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp, ctypes.c_uint32, _vp]
+        L.pf_wait.argtypes = [_vp]
+        L.pf_destroy.argtypes = [_vp]
+        L.pf_last_error.restype = ctypes.c_char_p
+        L.pf_batch_run.argtypes = [ctypes.c_int32, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                   ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_uint64),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
+                                   _vp]
+        for name in ("pf_run", "pf_wait", "pf_destroy", "pf_create", "pf_batch_run"):
+            getattr(L, name).restype = ctypes.c_int
+        if hasattr(L, "pf_server_create"):
+            L.pf_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(_vp)]
+            L.pf_server_submit.argtypes = [_vp, ctypes.POINTER(pf_model), ctypes.c_int64,
+                                           ctypes.c_int32, ctypes.c_double, _vp, _vp,
+                                           ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
+            L.pf_server_poll.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double)]
+            L.pf_server_stats.argtypes = [_vp] + [ctypes.POINTER(ctypes.c_int64)] * 4
+            L.pf_server_destroy.argtypes = [_vp]
+            for name in ("pf_server_create", "pf_server_submit", "pf_server_poll",
+                         "pf_server_stats", "pf_server_destroy"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def library_path():
+    return _build.LIB
+
+
+def pf_last_error():
+    return lib().pf_last_error().decode()
+
+
+def _check(st, ok=(PF_OK,)):
+    if st not in ok:
+        raise PFError(st, pf_last_error())
+    return st
+
+
+def model(kind, N=1, substeps=1, obs_stride=1, prec=PF_FP64, ess_threshold=1.0, flow_peak=400.0,
+          flow_period=1.0):
+    return pf_model(kind, N, substeps, obs_stride, prec, 0, ess_threshold, flow_peak, flow_period)
+
+
+def model_from_workload(w):
+    return model(w.kind, w.N, w.substeps, w.obs_stride, w.prec, w.ess_threshold, w.flow_peak,
+                 w.flow_period)
+
+
+def pf_theta_size(kind):
+    return lib().pf_theta_size(kind)
+
+
+def pf_device_bytes(m, P, T, history=False):
+    return lib().pf_device_bytes(ctypes.byref(m), P, T, 1 if history else 0)
+
+
+def _ptr(a):
+    """Pointer of a numpy array (host) or a torch tensor (host or device)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Filter:
+    """A created filter (owns its device buffers until destroy())."""
+
+    def __init__(self, m, P, T, dt):
+        h = _vp()
+        _check(lib().pf_create(ctypes.byref(m), P, T, dt, ctypes.byref(h)))
+        self.h = h
+        self.model = m
+        self.P, self.T, self.dt = P, T, dt
+        self.N = m.N
+        self.Ny = 1 if m.kind == PF_WINDKESSEL else (m.N + m.obs_stride - 1) // m.obs_stride
+        self.state_dtype = np.float64 if m.prec == PF_FP64 else np.float32
+
+    def run(self, theta, y, seed, want_particles=False, want_ancestors=False, stream=None):
+        """Host-side convenience: returns (status, loglik, particles [N][P] or None,
+        ancestors [T][P] or None).  PF_EDEGENERATE is returned, not raised."""
+        theta = np.ascontiguousarray(theta, dtype=np.float64) if not hasattr(theta, "data_ptr") else theta
+        y = np.ascontiguousarray(y, dtype=np.float64) if not hasattr(y, "data_ptr") else y
+        ll = np.zeros(1, dtype=np.float64)
+        x = np.zeros((self.N, self.P), dtype=self.state_dtype) if want_particles else None
+        anc = np.zeros((self.T, self.P), dtype=np.int32) if want_ancestors else None
+        st = pf_run(self, theta, y, seed, ll, x, anc, 0, stream)
+        return st, float(ll[0]), x, anc
+
+    def destroy(self):
+        if self.h:
+            lib().pf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def pf_create(m, P, T, dt):
+    return Filter(m, P, T, dt)
+
+
+def pf_run(f, theta, y, seed, loglik, final_particles=None, ancestors=None, flags=0, stream=None):
+    """Raw call: every array argument is passed by pointer (numpy or torch)."""
+    st = lib().pf_run(f.h, _ptr(theta), _ptr(y), ctypes.c_uint64(seed), _ptr(loglik),
+                      _ptr(final_particles), _ptr(ancestors), flags, _stream_ptr(stream))
+    return _check(st, ok=(PF_OK, PF_EDEGENERATE))
+
+
+def pf_wait(f):
+    return _check(lib().pf_wait(f.h), ok=(PF_OK, PF_EDEGENERATE))
+
+
+def pf_destroy(f):
+    f.destroy()
+
+
+def pf_batch_run(filters, thetas, ys, seeds, stream=None):
+    """Run many filters in one launch plan; returns (logliks, statuses) numpy arrays."""
+    n = len(filters)
+    keep = []
+    th = []
+    yy = []
+    for t, y in zip(thetas, ys):
+        t = np.ascontiguousarray(t, dtype=np.float64) if not hasattr(t, "data_ptr") else t
+        y = np.ascontiguousarray(y, dtype=np.float64) if not hasattr(y, "data_ptr") else y
+        keep += [t, y]
+        th.append(_ptr(t))
+        yy.append(_ptr(y))
+    fa = (_vp * n)(*[f.h for f in filters])
+    ta = (_vp * n)(*th)
+    ya = (_vp * n)(*yy)
+    sa = (ctypes.c_uint64 * n)(*[int(s) for s in seeds])
+    lls = np.zeros(n, dtype=np.float64)
+    sts = np.zeros(n, dtype=np.int32)
+    st = lib().pf_batch_run(n, fa, ta, ya, sa, lls.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                            sts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream_ptr(stream))
+    _check(st)
+    return lls, sts
+
+
+class Server:
+    """Continuous-batching request server (pf_server_* of the C ABI)."""
+
+    def __init__(self, device_mem_budget, max_slots=64):
+        h = _vp()
+        _check(lib().pf_server_create(device_mem_budget, max_slots, ctypes.byref(h)))
+        self.h = h
+
+    def submit(self, m, P, T, dt, theta, y, seed):
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        t = ctypes.c_uint64()
+        _check(lib().pf_server_submit(self.h, ctypes.byref(m), P, T, dt, _ptr(theta), _ptr(y),
+                                      ctypes.c_uint64(seed), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else (status, loglik, latency_s)."""
+        ll = ctypes.c_double()
+        lat = ctypes.c_double()
+        st = lib().pf_server_poll(self.h, ticket, ctypes.byref(ll), ctypes.byref(lat))
+        if st == PF_EBUSY:
+            return None
+        _check(st, ok=(PF_OK, PF_EDEGENERATE))
+        return st, ll.value, lat.value
+
+    def stats(self):
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(lib().pf_server_stats(self.h, *[ctypes.byref(x) for x in v]))
+        return dict(queued=v[0].value, running=v[1].value, completed=v[2].value,
+                    iterations=v[3].value)
+
+    def destroy(self):
+        if self.h:
+            lib().pf_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def pf_server_create(device_mem_budget, max_slots=64):
+    return Server(device_mem_budget, max_slots)

@@ -1,0 +1,521 @@
+// pf_api.cu -- host runtime behind the C ABI of include/pf.h: filter
+// creation, launch plans (descriptor tables, tile maps and one captured CUDA
+// graph per plan), single and batched runs.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pf.h"
+#include "pf_internal.h"
+#include "pf_runtime.h"
+
+using namespace pfb;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+pf_status pfb::fail(pf_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+extern "C" const char* pf_last_error(void) { return g_err.c_str(); }
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(PF_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// shapes
+// ---------------------------------------------------------------------------
+extern "C" int32_t pf_theta_size(int32_t kind) {
+  return kind == PF_WINDKESSEL ? 7 : kind == PF_LORENZ96 ? 5 : 0;
+}
+
+pf_status pfb::check_shape(const pf_model* m, int64_t P, int32_t T, double dt, Shape* sh) {
+  if (!m) return fail(PF_EINVAL, "model is NULL");
+  if (m->reserved != 0) return fail(PF_EINVAL, "pf_model.reserved must be 0");
+  if (!supported(m->kind, m->N, m->prec))
+    return fail(PF_EINVAL, "unsupported model: kind %d, N %d, precision %d", m->kind, m->N,
+                m->prec);
+  if (P < 1 || P > MAX_P) return fail(PF_EINVAL, "P = %lld outside [1, 2^24]", (long long)P);
+  if (T < 1) return fail(PF_EINVAL, "T = %d must be >= 1", T);
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(PF_EINVAL, "dt must be finite and > 0");
+  if (m->substeps < 1) return fail(PF_EINVAL, "substeps must be >= 1");
+  if (!(m->ess_threshold >= 0.0) || !std::isfinite(m->ess_threshold))
+    return fail(PF_EINVAL, "ess_threshold must be finite and >= 0");
+  int Ny = 1;
+  uint64_t mask = 1;
+  if (m->kind == PF_LORENZ96) {
+    if (m->obs_stride < 1) return fail(PF_EINVAL, "obs_stride must be >= 1");
+    Ny = (m->N + m->obs_stride - 1) / m->obs_stride;
+    mask = 0;
+    for (int n = 0; n < m->N; n += m->obs_stride) mask |= (1ull << n);
+  } else {
+    if (!(m->flow_period > 0.0) || !std::isfinite(m->flow_period) || !std::isfinite(m->flow_peak))
+      return fail(PF_EINVAL, "flow_period must be finite and > 0, flow_peak finite");
+  }
+  if (double(T) * double(m->substeps) > 2.0e9) return fail(PF_EINVAL, "T * substeps too large");
+  sh->Ny = Ny;
+  sh->obs_mask = mask;
+  sh->ntiles = int((P + TILE - 1) / TILE);
+  sh->ngroups = (sh->ntiles + GROUP - 1) / GROUP;
+  sh->mode = m->ess_threshold >= 1.0 ? MODE_ALWAYS : (m->ess_threshold == 0.0 ? MODE_NEVER
+                                                                              : MODE_ADAPTIVE);
+  sh->state_bytes = size_t(m->prec == PF_FP64 ? 8 : 4);
+  sh->nflow = m->kind == PF_WINDKESSEL ? int64_t(T) * m->substeps + 1 : 0;
+  return PF_OK;
+}
+
+static size_t bytes_for(const pf_model* m, const Shape& sh, int64_t P, int32_t T, int hist) {
+  size_t b = 2 * size_t(m->N) * size_t(P) * sh.state_bytes;
+  b += size_t(P) * 8;                                     // ctil
+  if (sh.mode != MODE_ALWAYS) b += 2 * size_t(P) * 8;     // ell, lam
+  b += size_t(P) * 4;                                     // anc
+  if (hist) b += size_t(T) * size_t(P) * 4;               // history
+  b += size_t(sh.nflow) * 8;                              // flow
+  b += size_t(sh.ntiles) * sizeof(TilePart) + size_t(sh.ngroups) * sizeof(GroupPart);
+  b += sizeof(Ctl);
+  b += size_t(T) * size_t(sh.Ny) * 8;                     // observations (plan side)
+  return b;
+}
+
+extern "C" size_t pf_device_bytes(const pf_model* m, int64_t P, int32_t T, int32_t history) {
+  Shape sh;
+  // dt does not change the size
+  if (check_shape(m, P, T, 1.0, &sh) != PF_OK) return 0;
+  return bytes_for(m, sh, P, T, history);
+}
+
+// ---------------------------------------------------------------------------
+// filters
+// ---------------------------------------------------------------------------
+static void free_filter_buffers(pf_filter* f) {
+  void* ptrs[] = {f->x[0], f->x[1], f->ctil, f->ell, f->lam, f->anc, f->hist,
+                  f->flow, f->tp, f->gp, f->ctl};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (f->h_res) cudaFreeHost(f->h_res);
+  if (f->own) cudaStreamDestroy(f->own);
+}
+
+extern "C" pf_status pf_create(const pf_model* m, int64_t P, int32_t T, double dt,
+                               pf_filter** out) {
+  if (!out) return fail(PF_EINVAL, "out is NULL");
+  Shape sh;
+  pf_status st = check_shape(m, P, T, dt, &sh);
+  if (st != PF_OK) return st;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(PF_ECUDA, "no CUDA device");
+  }
+  pf_filter* f = new pf_filter();
+  f->m = *m;
+  f->P = P;
+  f->T = T;
+  f->dt = dt;
+  f->sh = sh;
+  cudaGetDevice(&f->device);
+  auto alloc = [&](void** p, size_t n) -> bool {
+    if (n == 0) return true;
+    return cudaMalloc(p, n) == cudaSuccess;
+  };
+  bool ok = cudaStreamCreateWithFlags(&f->own, cudaStreamNonBlocking) == cudaSuccess;
+  const size_t xs = size_t(m->N) * size_t(P) * sh.state_bytes;
+  ok = ok && alloc(&f->x[0], xs) && alloc(&f->x[1], xs);
+  ok = ok && alloc((void**)&f->ctil, size_t(P) * 8);
+  if (sh.mode != MODE_ALWAYS)
+    ok = ok && alloc((void**)&f->ell, size_t(P) * 8) && alloc((void**)&f->lam, size_t(P) * 8);
+  ok = ok && alloc((void**)&f->anc, size_t(P) * 4);
+  ok = ok && alloc((void**)&f->flow, size_t(sh.nflow) * 8);
+  ok = ok && alloc((void**)&f->tp, size_t(sh.ntiles) * sizeof(TilePart));
+  ok = ok && alloc((void**)&f->gp, size_t(sh.ngroups) * sizeof(GroupPart));
+  ok = ok && alloc((void**)&f->ctl, sizeof(Ctl));
+  ok = ok && cudaMallocHost((void**)&f->h_res, 64) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_filter_buffers(f);
+    delete f;
+    return fail(PF_ENOMEM, "device allocation failed for P = %lld, T = %d", (long long)P, T);
+  }
+  cudaError_t e = cudaMemsetAsync(f->gp, 0, size_t(sh.ngroups) * sizeof(GroupPart), f->own);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f->ctl, 0, sizeof(Ctl), f->own);
+  if (e == cudaSuccess && sh.nflow > 0)
+    e = launch_flow(f->flow, sh.nflow, m->flow_peak, m->flow_period, dt, f->own);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(f->own);
+  if (e != cudaSuccess) {
+    free_filter_buffers(f);
+    delete f;
+    return fail(PF_ECUDA, "filter set-up: %s", cudaGetErrorString(e));
+  }
+  FilterDev& d = f->desc;
+  memset(&d, 0, sizeof d);
+  d.kind = m->kind;
+  d.N = m->N;
+  d.s = m->substeps;
+  d.stride = m->kind == PF_LORENZ96 ? m->obs_stride : 1;
+  d.prec = m->prec;
+  d.Ny = sh.Ny;
+  d.P = int32_t(P);
+  d.T = T;
+  d.ntiles = sh.ntiles;
+  d.ngroups = sh.ngroups;
+  d.hist = 0;
+  d.mode = sh.mode;
+  d.obs_mask = sh.obs_mask;
+  d.dt = dt;
+  d.thr = m->ess_threshold;
+  d.x[0] = f->x[0];
+  d.x[1] = f->x[1];
+  d.ctil = f->ctil;
+  d.ell = f->ell;
+  d.lam = f->lam;
+  d.anc = f->anc;
+  d.flow = f->flow;
+  d.tp = f->tp;
+  d.gp = f->gp;
+  d.ctl = f->ctl;
+  f->bytes = bytes_for(m, sh, P, T, 0);
+  *out = f;
+  return PF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// plans
+// ---------------------------------------------------------------------------
+static std::mutex g_plan_mu;
+static std::map<std::vector<pf_filter*>, Plan*> g_plans;  // cached batch plans
+
+static void destroy_plan(Plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->st) cudaStreamSynchronize(p->st);
+  void* dptrs[] = {p->d_fds, p->d_tmap, p->d_ycat, p->d_res};
+  for (void* q : dptrs)
+    if (q) cudaFree(q);
+  void* hptrs[] = {p->h_fds, p->h_ycat, p->h_res};
+  for (void* q : hptrs)
+    if (q) cudaFreeHost(q);
+  if (p->ev_staged) cudaEventDestroy(p->ev_staged);
+  if (p->ev_done) cudaEventDestroy(p->ev_done);
+  if (p->st) cudaStreamDestroy(p->st);
+  delete p;
+}
+
+// Tile maps sorted by T descending so that the filters still running at step
+// i own a prefix of every map.
+pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out) {
+  Plan* p = new Plan();
+  p->filters = fl;
+  const int nf = int(fl.size());
+  std::vector<int> order(nf);
+  for (int k = 0; k < nf; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return fl[a]->T > fl[b]->T; });
+  // classes: (kind, N, prec)
+  std::map<std::tuple<int, int, int>, int> cls_index;
+  std::vector<std::vector<int2>> cls_tiles;
+  std::vector<std::vector<int>> cls_T;
+  std::vector<int2> all_tiles;
+  std::vector<int> all_T;
+  int maxT = 0;
+  size_t ytot = 0;
+  p->yoff.resize(nf);
+  for (int k = 0; k < nf; ++k) {
+    p->yoff[k] = ytot;
+    ytot += size_t(fl[k]->T) * size_t(fl[k]->sh.Ny);
+  }
+  for (int k : order) {
+    pf_filter* f = fl[k];
+    auto key = std::make_tuple(f->m.kind, f->m.N, f->m.prec);
+    auto it = cls_index.find(key);
+    int c;
+    if (it == cls_index.end()) {
+      c = int(cls_tiles.size());
+      cls_index[key] = c;
+      cls_tiles.emplace_back();
+      cls_T.emplace_back();
+      p->classes.push_back({f->m.kind, f->m.N, f->m.prec, 0, 0});
+    } else {
+      c = it->second;
+    }
+    for (int t = 0; t < f->sh.ntiles; ++t) {
+      cls_tiles[c].push_back(make_int2(k, t));
+      cls_T[c].push_back(f->T);
+      all_tiles.push_back(make_int2(k, t));
+      all_T.push_back(f->T);
+    }
+    maxT = std::max(maxT, f->T);
+  }
+  // one device array: all tiles, then each class's tiles
+  std::vector<int2> tm(all_tiles);
+  for (size_t c = 0; c < cls_tiles.size(); ++c) {
+    p->classes[c].offset = int(tm.size());
+    p->classes[c].ntiles = int(cls_tiles[c].size());
+    tm.insert(tm.end(), cls_tiles[c].begin(), cls_tiles[c].end());
+  }
+  p->nf = nf;
+  p->maxT = maxT;
+  p->ntiles_all = int(all_tiles.size());
+  // per-step counts: tiles of filters with T >= i
+  auto counts = [&](const std::vector<int>& Ts, std::vector<int>& cnt) {
+    cnt.assign(maxT + 2, 0);
+    for (int i = 1; i <= maxT + 1; ++i) {
+      int n = 0;
+      while (n < int(Ts.size()) && Ts[n] >= i) ++n;
+      cnt[i] = n;
+    }
+  };
+  counts(all_T, p->cnt_all);
+  p->cnt_cls.resize(cls_tiles.size());
+  for (size_t c = 0; c < cls_tiles.size(); ++c) counts(cls_T[c], p->cnt_cls[c]);
+
+  cudaError_t e = cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_staged, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_fds, sizeof(FilterDev) * nf);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_fds, sizeof(FilterDev) * nf);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_tmap, sizeof(int2) * tm.size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_ycat, sizeof(double) * std::max<size_t>(ytot, 1));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_ycat, sizeof(double) * std::max<size_t>(ytot, 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_res, sizeof(double) * 3 * nf);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_res, sizeof(double) * 3 * nf);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->d_tmap, tm.data(), sizeof(int2) * tm.size(), cudaMemcpyHostToDevice,
+                        p->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+  if (e != cudaSuccess) {
+    destroy_plan(p);
+    return fail(e == cudaErrorMemoryAllocation ? PF_ENOMEM : PF_ECUDA, "plan set-up: %s",
+                cudaGetErrorString(e));
+  }
+  for (int k = 0; k < nf; ++k) {
+    p->h_fds[k] = fl[k]->desc;
+    p->h_fds[k].y = p->d_ycat + p->yoff[k];
+  }
+  // capture the whole run: init, then T x (propagate per class, resample)
+  cudaGraph_t g = nullptr;
+  e = cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t le = cudaSuccess;
+    for (size_t c = 0; c < p->classes.size() && le == cudaSuccess; ++c) {
+      const PlanClass& pc = p->classes[c];
+      le = launch_init(pc.kind, pc.N, pc.prec, p->d_fds, p->d_tmap + pc.offset, pc.ntiles, p->st);
+    }
+    for (int i = 1; i <= maxT && le == cudaSuccess; ++i) {
+      for (size_t c = 0; c < p->classes.size() && le == cudaSuccess; ++c) {
+        const PlanClass& pc = p->classes[c];
+        le = launch_propagate(pc.kind, pc.N, pc.prec, p->d_fds, p->d_tmap + pc.offset,
+                              p->cnt_cls[c][i], p->st);
+      }
+      if (le == cudaSuccess) le = launch_resample(p->d_fds, p->d_tmap, p->cnt_all[i + 1], p->st);
+    }
+    if (le == cudaSuccess) le = launch_results(p->d_fds, nf, p->d_res, p->st);
+    e = cudaStreamEndCapture(p->st, &g);
+    if (e == cudaSuccess) e = le;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    destroy_plan(p);
+    return fail(PF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  }
+  *out = p;
+  return PF_OK;
+}
+
+static bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Stage theta, seed and y of every filter of the plan and launch its graph on st.
+pf_status pfb::run_plan(Plan* p, const double* const* theta, const double* const* y,
+                        const uint64_t* seeds, const int32_t* hist_on, cudaStream_t st) {
+  CK(cudaEventSynchronize(p->ev_staged));  // pinned staging of the previous run consumed
+  std::vector<int> dev_theta, dev_y;
+  for (int k = 0; k < p->nf; ++k) {
+    pf_filter* f = p->filters[k];
+    FilterDev& d = p->h_fds[k];
+    d = f->desc;
+    d.y = p->d_ycat + p->yoff[k];
+    d.seed = seeds[k];
+    if (hist_on && hist_on[k]) {
+      d.hist = 1;
+      d.anc = f->hist;
+    }
+    const int nth = pf_theta_size(f->m.kind);
+    if (!theta[k] || !y[k]) return fail(PF_EINVAL, "theta / y of filter %d is NULL", k);
+    if (is_device_ptr(theta[k])) dev_theta.push_back(k);
+    else memcpy(d.theta, theta[k], sizeof(double) * nth);
+    const size_t ny = size_t(f->T) * size_t(f->sh.Ny);
+    if (is_device_ptr(y[k])) dev_y.push_back(k);
+    else memcpy(p->h_ycat + p->yoff[k], y[k], sizeof(double) * ny);
+  }
+  CK(cudaMemcpyAsync(p->d_fds, p->h_fds, sizeof(FilterDev) * p->nf, cudaMemcpyHostToDevice, st));
+  size_t ytot = 0;
+  for (int k = 0; k < p->nf; ++k) ytot += size_t(p->filters[k]->T) * p->filters[k]->sh.Ny;
+  if (dev_y.size() < size_t(p->nf))
+    CK(cudaMemcpyAsync(p->d_ycat, p->h_ycat, sizeof(double) * ytot, cudaMemcpyHostToDevice, st));
+  for (int k : dev_y) {
+    const size_t ny = size_t(p->filters[k]->T) * p->filters[k]->sh.Ny;
+    CK(cudaMemcpyAsync(p->d_ycat + p->yoff[k], y[k], sizeof(double) * ny,
+                       cudaMemcpyDeviceToDevice, st));
+  }
+  for (int k : dev_theta) {
+    const int nth = pf_theta_size(p->filters[k]->m.kind);
+    CK(cudaMemcpyAsync(p->d_fds[k].theta, theta[k], sizeof(double) * nth,
+                       cudaMemcpyDeviceToDevice, st));
+  }
+  CK(cudaEventRecord(p->ev_staged, st));
+  CK(cudaGraphLaunch(p->exec, st));
+  CK(cudaMemcpyAsync(p->h_res, p->d_res, sizeof(double) * 3 * p->nf, cudaMemcpyDeviceToHost, st));
+  CK(cudaEventRecord(p->ev_done, st));
+  return PF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// single filter
+// ---------------------------------------------------------------------------
+extern "C" pf_status pf_run(pf_filter* f, const double* theta, const double* y, uint64_t seed,
+                            double* loglik, void* final_particles, int32_t* ancestors,
+                            uint32_t flags, void* cuda_stream) {
+  if (!f) return fail(PF_EINVAL, "filter is NULL");
+  if (!theta || !y || !loglik) return fail(PF_EINVAL, "theta, y and loglik are required");
+  if (flags & ~PF_FLAG_ASYNC) return fail(PF_EINVAL, "unknown flags 0x%x", flags);
+  const bool async = (flags & PF_FLAG_ASYNC) != 0;
+  if (async) {
+    if (!is_device_ptr(loglik) || (final_particles && !is_device_ptr(final_particles)) ||
+        (ancestors && !is_device_ptr(ancestors)))
+      return fail(PF_EINVAL, "PF_FLAG_ASYNC needs device output pointers");
+  }
+  cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : f->own;
+  if (ancestors && !f->hist) {
+    if (cudaMalloc((void**)&f->hist, size_t(f->T) * size_t(f->P) * 4) != cudaSuccess) {
+      cudaGetLastError();
+      f->hist = nullptr;
+      return fail(PF_ENOMEM, "ancestor history of %lld bytes",
+                  (long long)(size_t(f->T) * size_t(f->P) * 4));
+    }
+  }
+  if (!f->plan) {
+    std::vector<pf_filter*> one{f};
+    pf_status ps = build_plan(one, &f->plan);
+    if (ps != PF_OK) return ps;
+  }
+  Plan* p = f->plan;
+  const int32_t hist_on = ancestors ? 1 : 0;
+  pf_status ps = run_plan(p, &theta, &y, &seed, &hist_on, st);
+  if (ps != PF_OK) return ps;
+  const int64_t P = f->P;
+  if (final_particles)
+    CK(cudaMemcpyAsync(final_particles, f->x[f->T & 1], size_t(f->m.N) * P * f->sh.state_bytes,
+                       cudaMemcpyDefault, st));
+  if (ancestors)
+    CK(cudaMemcpyAsync(ancestors, f->hist, size_t(f->T) * P * 4, cudaMemcpyDefault, st));
+  if (async) {
+    CK(cudaMemcpyAsync(loglik, p->d_res, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaEventRecord(p->ev_done, st));
+    f->pending = true;
+    return PF_OK;
+  }
+  CK(cudaEventRecord(p->ev_done, st));
+  CK(cudaEventSynchronize(p->ev_done));
+  const double ll = p->h_res[0];
+  const int status = int(p->h_res[1]);
+  if (is_device_ptr(loglik)) CK(cudaMemcpy(loglik, &ll, sizeof(double), cudaMemcpyHostToDevice));
+  else *loglik = ll;
+  return status == ST_OK ? PF_OK : PF_EDEGENERATE;
+}
+
+extern "C" pf_status pf_wait(pf_filter* f) {
+  if (!f) return fail(PF_EINVAL, "filter is NULL");
+  if (!f->plan) return PF_OK;
+  CK(cudaEventSynchronize(f->plan->ev_done));
+  f->pending = false;
+  return int(f->plan->h_res[1]) == ST_OK ? PF_OK : PF_EDEGENERATE;
+}
+
+extern "C" pf_status pf_destroy(pf_filter* f) {
+  if (!f) return PF_OK;
+  cudaDeviceSynchronize();
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    for (auto it = g_plans.begin(); it != g_plans.end();) {
+      if (std::find(it->first.begin(), it->first.end(), f) != it->first.end()) {
+        destroy_plan(it->second);
+        it = g_plans.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  destroy_plan(f->plan);
+  free_filter_buffers(f);
+  delete f;
+  return PF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched
+// ---------------------------------------------------------------------------
+extern "C" pf_status pf_batch_run(int32_t nfilt, pf_filter* const* f, const double* const* theta,
+                                  const double* const* y, const uint64_t* seeds, double* logliks,
+                                  int32_t* per_filter_status, void* cuda_stream) {
+  if (nfilt < 1 || !f || !theta || !y || !seeds || !logliks || !per_filter_status)
+    return fail(PF_EINVAL, "pf_batch_run: bad arguments");
+  std::vector<pf_filter*> key(f, f + nfilt);
+  for (int k = 0; k < nfilt; ++k)
+    if (!key[k]) return fail(PF_EINVAL, "filter %d is NULL", k);
+  {
+    std::vector<pf_filter*> sorted(key);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+      return fail(PF_EINVAL, "a filter appears twice in the batch");
+  }
+  Plan* p = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) p = it->second;
+  }
+  if (!p) {
+    pf_status ps = build_plan(key, &p);
+    if (ps != PF_OK) return ps;
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    if (g_plans.size() >= 8) {
+      destroy_plan(g_plans.begin()->second);
+      g_plans.erase(g_plans.begin());
+    }
+    g_plans[key] = p;
+  }
+  cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : p->st;
+  pf_status ps = run_plan(p, theta, y, seeds, nullptr, st);
+  if (ps != PF_OK) return ps;
+  CK(cudaEventSynchronize(p->ev_done));
+  for (int k = 0; k < nfilt; ++k) {
+    logliks[k] = p->h_res[3 * k];
+    per_filter_status[k] = int(p->h_res[3 * k + 1]) == ST_OK ? PF_OK : PF_EDEGENERATE;
+  }
+  return PF_OK;
+}

@@ -1,0 +1,337 @@
+// pf_dev.cuh -- device-side building blocks of the B300 bootstrap particle
+// filter (arXiv 1306.3277, Algorithm 2): descriptors, Philox4x32-10,
+// project-written log / sincos(2 pi u) for Box-Muller, and the canonical
+// block reductions and scans that fix the summation order of every run.
+//
+// The whole library is compiled with -fmad=false: a fused multiply-add
+// happens only where the code calls fma()/fmaf(); every other operation is
+// rounded on its own, so results are reproducible bit for bit.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pfb {
+
+constexpr int TILE = 256;        // particles per tile == threads per block
+constexpr int GROUP = 256;       // tiles per group (two-level combine)
+constexpr int WARPS = TILE / 32;
+constexpr int64_t MAX_P = int64_t(1) << 24;  // GROUP * GROUP * TILE
+
+enum { KIND_WK = 0, KIND_L96 = 1 };
+enum { PREC_FP64 = 0, PREC_MIXED = 1 };
+enum { MODE_ALWAYS = 0, MODE_ADAPTIVE = 1, MODE_NEVER = 2 };
+enum { PURPOSE_INIT = 1, PURPOSE_PROP = 2, PURPOSE_RESAMPLE = 3 };
+enum { ST_OK = 0, ST_DEGENERATE = 4 };
+
+// Per tile of TILE particles: written by the propagate kernel (M, S, Q) and
+// by the group combine (g, base).
+struct alignas(16) TilePart {
+  double M;     // max log-weight in the tile
+  double S;     // sum exp(ell - M) over the tile (inclusive-scan total)
+  double Q;     // sum exp(2 (ell - M)) (adaptive resampling only)
+  double g;     // exp(M - M_group)
+  double base;  // exclusive prefix of the scaled tile sums inside the group
+  double pad;
+};
+
+struct alignas(16) GroupPart {
+  double M, S, Q;   // group max, scaled sum, scaled square sum
+  double G;         // exp(M_group - M_filter)
+  double B;         // exclusive prefix of the scaled group sums
+  unsigned ticket;  // tiles of this group finished in the current step
+  unsigned pad0;
+  double pad1, pad2;
+};
+
+// Per-filter control block, written by the last block of each propagate
+// kernel and read by the next launches.
+struct alignas(16) Ctl {
+  int32_t step;          // next observation to propagate to (1..T; T+1 = done)
+  int32_t rs_step;       // step whose resampling the resample kernel performs
+  int32_t rs_flag;       // 1: resample at rs_step, 0: carry the weights
+  int32_t anc_identity;  // propagate kernel: identity ancestors
+  int32_t lam_zero;      // propagate kernel: carried log-weights are all zero
+  int32_t status;        // ST_OK / ST_DEGENERATE
+  uint32_t gticket;      // groups finished in the current step
+  int32_t pad;
+  double ll;             // log-likelihood accumulated so far
+  double L;              // log sum_j exp(lam_j) of the carried log-weights
+  double M, S;           // max and scaled sum of the current step
+  double u;              // resampling uniform of the current step
+  double step_size;      // S / P
+  double c_obs;          // -Ny/2 log(2 pi r)
+  double logP;           // log P
+};
+
+// Descriptor of one filter (device copy read by every kernel).
+struct alignas(16) FilterDev {
+  int32_t kind, N, s, stride, prec, Ny;
+  int32_t P, T, ntiles, ngroups, hist, mode;
+  uint64_t obs_mask;  // Lorenz '96: bit n set iff component n is observed
+  uint64_t seed;
+  double dt, thr;
+  double theta[8];
+  void* x[2];         // state double buffer, component-major [N][P]
+  double* ctil;       // in-tile inclusive prefix of exp(ell - M_tile) [P]
+  double* ell;        // log-weights (adaptive / never modes) [P]
+  double* lam;        // carried log-weights [P]
+  int32_t* anc;       // ancestors: [P], or [T][P] history when hist != 0
+  const double* y;    // observations [T][Ny]
+  const double* flow; // windkessel input F(k dt), k = 0..T*s
+  TilePart* tp;       // [ntiles]
+  GroupPart* gp;      // [ngroups]
+  Ctl* ctl;
+};
+
+// -------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies and xors, key bumped by the Weyl increments between
+// rounds.
+// -------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo_a = 0xD2511F53u * c.x;
+    const uint32_t hi_a = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo_b = 0xCD9E8D57u * c.z;
+    const uint32_t hi_b = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Block of the stream (particle j, step i, purpose): counter (j, i, purpose<<16 | b, 0).
+__device__ __forceinline__ uint4 rng_block(uint64_t seed, uint32_t j, uint32_t i, uint32_t purpose,
+                                           uint32_t b) {
+  return philox4x32_10(make_uint4(j, i, (purpose << 16) | b, 0u), uint32_t(seed),
+                       uint32_t(seed >> 32));
+}
+
+// 53-bit uniforms from the 64-bit word hi:lo.
+__device__ __forceinline__ double u53_closed_open(uint32_t lo, uint32_t hi) {  // [0,1)
+  const unsigned long long v = ((static_cast<unsigned long long>(hi) << 32) | lo) >> 11;
+  return __dmul_rn(__ull2double_rn(v), 0x1.0p-53);
+}
+__device__ __forceinline__ double u53_open_closed(uint32_t lo, uint32_t hi) {  // (0,1]
+  const unsigned long long v = ((static_cast<unsigned long long>(hi) << 32) | lo) >> 11;
+  return __dmul_rn(__ull2double_rn(v + 1ull), 0x1.0p-53);
+}
+
+// -------------------------------------------------------------------------
+// Natural logarithm, FP64, for positive normal x: x = m 2^e with m in
+// [1/sqrt2, sqrt2) read off the bits, log m = 2 atanh((m-1)/(m+1)) by the
+// odd series to the 23rd power, plus e ln 2 with ln 2 in two parts.
+// -------------------------------------------------------------------------
+__device__ __forceinline__ double log_pos(double x) {
+  const long long bits = __double_as_longlong(x);
+  int e = int((bits >> 52) & 0x7ff) - 1022;
+  double m = __longlong_as_double((bits & 0x000fffffffffffffLL) | 0x3fe0000000000000LL);
+  if (m < 0x1.6a09e667f3bcdp-1) {
+    m = __dadd_rn(m, m);
+    e -= 1;
+  }
+  const double f = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+  const double two_f = __dadd_rn(f, f);
+  const double f2 = __dmul_rn(f, f);
+  double p = 1.0 / 23.0;
+  p = fma(p, f2, 1.0 / 21.0);
+  p = fma(p, f2, 1.0 / 19.0);
+  p = fma(p, f2, 1.0 / 17.0);
+  p = fma(p, f2, 1.0 / 15.0);
+  p = fma(p, f2, 1.0 / 13.0);
+  p = fma(p, f2, 1.0 / 11.0);
+  p = fma(p, f2, 1.0 / 9.0);
+  p = fma(p, f2, 1.0 / 7.0);
+  p = fma(p, f2, 1.0 / 5.0);
+  p = fma(p, f2, 1.0 / 3.0);
+  const double lm = fma(__dmul_rn(two_f, f2), p, two_f);
+  const double de = double(e);
+  return fma(de, 0x1.62e42fefa39efp-1, fma(de, 0x1.abc9e3b39803fp-56, lm));
+}
+
+// sin(2 pi u), cos(2 pi u), FP64, u in [0,1): quarter turns q = rint(4u),
+// remainder r = 4u - q (exact), angle r pi/2 with pi/2 in two parts, Taylor
+// series of sin to x^19 and cos to x^20, then rotation by q quarter turns.
+__device__ __forceinline__ void sincos_2pi(double u, double* sn, double* cs) {
+  const double v = __dmul_rn(4.0, u);
+  const double q = rint(v);
+  const double r = __dsub_rn(v, q);
+  const double x = fma(r, 0x1.921fb54442d18p+0, __dmul_rn(r, 0x1.1a62633145c07p-54));
+  const double x2 = __dmul_rn(x, x);
+  double s = -1.0 / 121645100408832000.0;
+  s = fma(s, x2, 1.0 / 355687428096000.0);
+  s = fma(s, x2, -1.0 / 1307674368000.0);
+  s = fma(s, x2, 1.0 / 6227020800.0);
+  s = fma(s, x2, -1.0 / 39916800.0);
+  s = fma(s, x2, 1.0 / 362880.0);
+  s = fma(s, x2, -1.0 / 5040.0);
+  s = fma(s, x2, 1.0 / 120.0);
+  s = fma(s, x2, -1.0 / 6.0);
+  const double sinx = fma(__dmul_rn(x, x2), s, x);
+  double c = 1.0 / 2432902008176640000.0;
+  c = fma(c, x2, -1.0 / 6402373705728000.0);
+  c = fma(c, x2, 1.0 / 20922789888000.0);
+  c = fma(c, x2, -1.0 / 87178291200.0);
+  c = fma(c, x2, 1.0 / 479001600.0);
+  c = fma(c, x2, -1.0 / 3628800.0);
+  c = fma(c, x2, 1.0 / 40320.0);
+  c = fma(c, x2, -1.0 / 720.0);
+  c = fma(c, x2, 1.0 / 24.0);
+  c = fma(c, x2, -0.5);
+  const double cosx = fma(x2, c, 1.0);
+  const int quarter = int(q) & 3;
+  *sn = quarter == 0 ? sinx : quarter == 1 ? cosx : quarter == 2 ? -sinx : -cosx;
+  *cs = quarter == 0 ? cosx : quarter == 1 ? -sinx : quarter == 2 ? -cosx : sinx;
+}
+
+// FP32 versions of the same two methods, series cut for single precision.
+__device__ __forceinline__ float log_posf(float x) {
+  const int bits = __float_as_int(x);
+  int e = ((bits >> 23) & 0xff) - 126;
+  float m = __int_as_float((bits & 0x007fffff) | 0x3f000000);
+  if (m < 0x1.6a09e6p-1f) {
+    m = __fadd_rn(m, m);
+    e -= 1;
+  }
+  const float f = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+  const float two_f = __fadd_rn(f, f);
+  const float f2 = __fmul_rn(f, f);
+  float p = 1.0f / 11.0f;
+  p = fmaf(p, f2, 1.0f / 9.0f);
+  p = fmaf(p, f2, 1.0f / 7.0f);
+  p = fmaf(p, f2, 1.0f / 5.0f);
+  p = fmaf(p, f2, 1.0f / 3.0f);
+  const float lm = fmaf(__fmul_rn(two_f, f2), p, two_f);
+  const float de = float(e);
+  return fmaf(de, 0x1.62e430p-1f, fmaf(de, -0x1.05c610p-29f, lm));
+}
+
+__device__ __forceinline__ void sincos_2pif(float u, float* sn, float* cs) {
+  const float v = __fmul_rn(4.0f, u);
+  const float q = rintf(v);
+  const float r = __fsub_rn(v, q);
+  const float x = fmaf(r, 0x1.921fb6p+0f, __fmul_rn(r, -0x1.777a5cp-25f));
+  const float x2 = __fmul_rn(x, x);
+  float s = -1.0f / 39916800.0f;
+  s = fmaf(s, x2, 1.0f / 362880.0f);
+  s = fmaf(s, x2, -1.0f / 5040.0f);
+  s = fmaf(s, x2, 1.0f / 120.0f);
+  s = fmaf(s, x2, -1.0f / 6.0f);
+  const float sinx = fmaf(__fmul_rn(x, x2), s, x);
+  float c = 1.0f / 479001600.0f;
+  c = fmaf(c, x2, -1.0f / 3628800.0f);
+  c = fmaf(c, x2, 1.0f / 40320.0f);
+  c = fmaf(c, x2, -1.0f / 720.0f);
+  c = fmaf(c, x2, 1.0f / 24.0f);
+  c = fmaf(c, x2, -0.5f);
+  const float cosx = fmaf(x2, c, 1.0f);
+  const int quarter = int(q) & 3;
+  *sn = quarter == 0 ? sinx : quarter == 1 ? cosx : quarter == 2 ? -sinx : -cosx;
+  *cs = quarter == 0 ? cosx : quarter == 1 ? -sinx : quarter == 2 ? -cosx : sinx;
+}
+
+// Box-Muller pair from one Philox block (FP64): u1 in (0,1] from w1:w0,
+// u2 in [0,1) from w3:w2; z0 = rho cos, z1 = rho sin.
+__device__ __forceinline__ void normal_pair64(uint4 w, double* z0, double* z1) {
+  const double u1 = u53_open_closed(w.x, w.y);
+  const double u2 = u53_closed_open(w.z, w.w);
+  const double rho = __dsqrt_rn(__dmul_rn(-2.0, log_pos(u1)));
+  double sn, cs;
+  sincos_2pi(u2, &sn, &cs);
+  *z0 = __dmul_rn(rho, cs);
+  *z1 = __dmul_rn(rho, sn);
+}
+
+// FP32: one 32-bit word pair (a, b) gives one pair: u1 = ((a>>8)+1) 2^-24,
+// u2 = (b>>8) 2^-24.
+__device__ __forceinline__ void normal_pair32(uint32_t a, uint32_t b, float* z0, float* z1) {
+  const float u1 = __fmul_rn(float((a >> 8) + 1u), 0x1.0p-24f);
+  const float u2 = __fmul_rn(float(b >> 8), 0x1.0p-24f);
+  const float rho = __fsqrt_rn(__fmul_rn(-2.0f, log_posf(u1)));
+  float sn, cs;
+  sincos_2pif(u2, &sn, &cs);
+  *z0 = __fmul_rn(rho, cs);
+  *z1 = __fmul_rn(rho, sn);
+}
+
+// -------------------------------------------------------------------------
+// Order-preserving int64 key of a double (for max by integer compare).
+// -------------------------------------------------------------------------
+__device__ __forceinline__ long long dkey(double v) {
+  const long long b = __double_as_longlong(v);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dunkey(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+
+// Scratch for the canonical block operations (TILE threads).
+struct BlockScratch {
+  long long kmax[WARPS];
+  double wsum[WARPS];
+  double wsum2[WARPS];
+  int flag;
+};
+
+// Max over the block; every thread receives it.
+__device__ __forceinline__ double block_max(double v, BlockScratch& sm) {
+  long long k = dkey(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) k = max(k, __shfl_xor_sync(0xffffffffu, k, o));
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) sm.kmax[w] = k;
+  __syncthreads();
+  long long r = sm.kmax[0];
+#pragma unroll
+  for (int q = 1; q < WARPS; ++q) r = max(r, sm.kmax[q]);
+  __syncthreads();
+  return dunkey(r);
+}
+
+// Canonical sum: xor-butterfly inside each warp, then the eight warp totals
+// combined as ((w0+w1)+(w2+w3))+((w4+w5)+(w6+w7)).  Every thread receives it.
+__device__ __forceinline__ double block_sum(double v, BlockScratch& sm) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) sm.wsum2[w] = v;
+  __syncthreads();
+  const double* t = sm.wsum2;
+  const double r = __dadd_rn(__dadd_rn(__dadd_rn(t[0], t[1]), __dadd_rn(t[2], t[3])),
+                             __dadd_rn(__dadd_rn(t[4], t[5]), __dadd_rn(t[6], t[7])));
+  __syncthreads();
+  return r;
+}
+
+// Canonical inclusive scan: Kogge-Stone inside each warp (shfl_up 1..16),
+// then the exclusive prefix of the warp totals added left to right.
+// Returns the thread's inclusive prefix; *total receives the block total.
+__device__ __forceinline__ double block_scan(double v, BlockScratch& sm, double* total) {
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v = __dadd_rn(n, v);
+  }
+  if (lane == 31) sm.wsum[w] = v;
+  __syncthreads();
+  double pre = 0.0;
+  for (int q = 0; q < w; ++q) pre = __dadd_rn(pre, sm.wsum[q]);
+  double tot = 0.0;
+#pragma unroll
+  for (int q = 0; q < WARPS; ++q) tot = __dadd_rn(tot, sm.wsum[q]);
+  __syncthreads();
+  *total = tot;
+  return w == 0 ? v : __dadd_rn(pre, v);
+}
+
+// L2-coherent loads for data written by other blocks of the same launch.
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) {
+  return __ldcg(p);
+}
+
+}  // namespace pfb

@@ -1,0 +1,19 @@
+// pf_internal.h -- host-side launchers shared by the runtime translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "pf_dev.cuh"
+
+namespace pfb {
+
+bool supported(int kind, int N, int prec);
+cudaError_t launch_init(int kind, int N, int prec, const FilterDev* fds, const int2* tmap,
+                        int nblocks, cudaStream_t st);
+cudaError_t launch_propagate(int kind, int N, int prec, const FilterDev* fds, const int2* tmap,
+                             int nblocks, cudaStream_t st);
+cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks, cudaStream_t st);
+cudaError_t launch_flow(double* flow, int64_t n, double peak, double period, double dt,
+                        cudaStream_t st);
+cudaError_t launch_results(const FilterDev* fds, int nf, double* out, cudaStream_t st);
+
+}  // namespace pfb

@@ -1,0 +1,569 @@
+// pf_kernels.cu -- sm_103a kernels of the bootstrap particle filter
+// (arXiv 1306.3277, Algorithm 2) and their host-side launchers.
+//
+// One step i of one filter is two launches over its tiles of TILE particles:
+//   k_propagate  gather x(t_{i-1}) at the ancestors, propagate to t_i
+//                (windkessel Euler substeps or Lorenz '96 RK4 substeps plus
+//                noise), weight with y(t_i) in FP64, then per tile the max,
+//                the inclusive prefix of exp(ell - M_tile) and its total.  The
+//                last tile of each group of GROUP tiles combines the group;
+//                the last group combines the filter: max, scaled sums,
+//                likelihood increment, ESS test, resampling uniform.
+//   k_resample   per tile: cumulative weights C_k = base + scale * prefix,
+//                the systematic targets that fall in [base, next base), and a
+//                binary search of each target among the tile's C_k.
+// Any number of filters share a launch: the tile map lists (filter, tile)
+// pairs, and every reduction is per tile / group / filter in a fixed order,
+// so a filter's result does not depend on what else is in the launch.
+#include <cmath>
+#include <cstdio>
+
+#include "pf_dev.cuh"
+#include "pf_internal.h"
+
+namespace pfb {
+
+static_assert(TILE == GROUP, "the group combine maps one tile partial per thread");
+
+__device__ __forceinline__ double fmaR(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaR(float a, float b, float c) { return fmaf(a, b, c); }
+
+// One classic RK4 step of dt for dx_n/dt = (x_{n+1} - x_{n-2}) x_{n-1} - x_n + F
+// (cyclic), the right-hand side evaluated as fma(x_{n+1} - x_{n-2}, x_{n-1}, F - x_n)
+// and the update accumulated as x + h/6 k1 + h/3 k2 + h/3 k3 + h/6 k4.
+template <int N, typename R>
+__device__ __forceinline__ void l96_rk4_step(R (&x)[N], R F, R dt, R h2, R h3, R h6) {
+  R acc[N], xa[N], xb[N];
+#pragma unroll
+  for (int n = 0; n < N; ++n) {
+    const R k = fmaR(x[(n + 1) % N] - x[(n + N - 2) % N], x[(n + N - 1) % N], F - x[n]);
+    acc[n] = fmaR(h6, k, x[n]);
+    xa[n] = fmaR(h2, k, x[n]);
+  }
+#pragma unroll
+  for (int n = 0; n < N; ++n) {
+    const R k = fmaR(xa[(n + 1) % N] - xa[(n + N - 2) % N], xa[(n + N - 1) % N], F - xa[n]);
+    acc[n] = fmaR(h3, k, acc[n]);
+    xb[n] = fmaR(h2, k, x[n]);
+  }
+#pragma unroll
+  for (int n = 0; n < N; ++n) {
+    const R k = fmaR(xb[(n + 1) % N] - xb[(n + N - 2) % N], xb[(n + N - 1) % N], F - xb[n]);
+    acc[n] = fmaR(h3, k, acc[n]);
+    xa[n] = fmaR(dt, k, x[n]);
+  }
+#pragma unroll
+  for (int n = 0; n < N; ++n) {
+    const R k = fmaR(xa[(n + 1) % N] - xa[(n + N - 2) % N], xa[(n + N - 1) % N], F - xa[n]);
+    x[n] = fmaR(h6, k, acc[n]);
+  }
+}
+
+// Normals number 0..N-1 of the stream (j, i, purpose) into z (N a multiple of 4
+// for Lorenz '96; the windkessel uses its own loop).
+template <int N>
+__device__ __forceinline__ void normals(double (&z)[N], uint64_t seed, uint32_t j, uint32_t i,
+                                        uint32_t purpose) {
+#pragma unroll
+  for (int b = 0; b < (N + 1) / 2; ++b) {
+    double z0, z1;
+    normal_pair64(rng_block(seed, j, i, purpose, b), &z0, &z1);
+    z[2 * b] = z0;
+    if (2 * b + 1 < N) z[2 * b + 1] = z1;
+  }
+}
+template <int N>
+__device__ __forceinline__ void normals(float (&z)[N], uint64_t seed, uint32_t j, uint32_t i,
+                                        uint32_t purpose) {
+#pragma unroll
+  for (int b = 0; b < (N + 3) / 4; ++b) {
+    const uint4 w = rng_block(seed, j, i, purpose, b);
+    float z0, z1, z2, z3;
+    normal_pair32(w.x, w.y, &z0, &z1);
+    normal_pair32(w.z, w.w, &z2, &z3);
+    z[4 * b] = z0;
+    if (4 * b + 1 < N) z[4 * b + 1] = z1;
+    if (4 * b + 2 < N) z[4 * b + 2] = z2;
+    if (4 * b + 3 < N) z[4 * b + 3] = z3;
+  }
+}
+
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(float v) { return double(v); }
+template <typename R> __device__ __forceinline__ R from_double(double v);
+template <> __device__ __forceinline__ double from_double<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_double<float>(double v) { return __double2float_rn(v); }
+
+// Windkessel: s Euler substeps x <- x + dt (F_k/C - x/(RC)) + sqrt(q) z_mm
+// (normal number mm of stream (j, i, PROP)), then log N(y; x + Z F(t_i), r)
+// without its constant.
+template <typename R>
+__device__ __forceinline__ double wk_prop_weight(const FilterDev& fd, uint32_t j, int i, R& xv,
+                                                 double yi) {
+  const int s = fd.s;
+  const R Rr = from_double<R>(fd.theta[0]);
+  const R Cc = from_double<R>(fd.theta[1]);
+  const R dt = from_double<R>(fd.dt);
+  const R sq = sqrt(from_double<R>(fd.theta[3]));
+  const double* fl = fd.flow + int64_t(i - 1) * s;
+  if constexpr (sizeof(R) == 8) {
+    for (int mm = 0; mm < s; mm += 2) {
+      double z[2];
+      normal_pair64(rng_block(fd.seed, j, uint32_t(i), PURPOSE_PROP, uint32_t(mm >> 1)), &z[0], &z[1]);
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        if (mm + e < s) {
+          const R Fk = fl[mm + e];
+          const R drift = Fk / Cc - xv / (Rr * Cc);
+          xv = fmaR(dt, drift, xv);
+          xv = fmaR(sq, R(z[e]), xv);
+        }
+      }
+    }
+  } else {
+    for (int mm = 0; mm < s; mm += 4) {
+      const uint4 w = rng_block(fd.seed, j, uint32_t(i), PURPOSE_PROP, uint32_t(mm >> 2));
+      float z[4];
+      normal_pair32(w.x, w.y, &z[0], &z[1]);
+      normal_pair32(w.z, w.w, &z[2], &z[3]);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (mm + e < s) {
+          const R Fk = from_double<R>(fl[mm + e]);
+          const R drift = Fk / Cc - xv / (Rr * Cc);
+          xv = fmaR(dt, drift, xv);
+          xv = fmaR(sq, R(z[e]), xv);
+        }
+      }
+    }
+  }
+  const double h = fma(fd.theta[2], fd.flow[int64_t(i) * s], to_double(xv));
+  const double d = yi - h;
+  const double acc = fma(d, d, 0.0);
+  return -0.5 * (acc / fd.theta[4]);
+}
+
+// Lorenz '96: s RK4 substeps, additive sqrt(q) z_n on every component, then
+// sum over observed components of (y - x_n)^2 accumulated by fma in FP64.
+template <int N, typename R>
+__device__ __forceinline__ double l96_prop_weight(const FilterDev& fd, uint32_t j, int i,
+                                                  R (&x)[N], const double* ys) {
+  const R F = from_double<R>(fd.theta[0]);
+  const R dt = from_double<R>(fd.dt);
+  const R h2 = R(0.5) * dt, h3 = dt / R(3.0), h6 = dt / R(6.0);
+  for (int mm = 0; mm < fd.s; ++mm) l96_rk4_step<N, R>(x, F, dt, h2, h3, h6);
+  {
+    R z[N];
+    normals<N>(z, fd.seed, j, uint32_t(i), PURPOSE_PROP);
+    const R sx = sqrt(from_double<R>(fd.theta[1]));
+#pragma unroll
+    for (int n = 0; n < N; ++n) x[n] = fmaR(sx, z[n], x[n]);
+  }
+  const uint64_t mask = fd.obs_mask;
+  double acc = 0.0;
+  int k = 0;
+#pragma unroll
+  for (int n = 0; n < N; ++n) {
+    if ((mask >> n) & 1ull) {
+      const double d = ys[k] - to_double(x[n]);
+      acc = fma(d, d, acc);
+      ++k;
+    }
+  }
+  return -0.5 * (acc / fd.theta[2]);
+}
+
+// ---------------------------------------------------------------------------
+// Group and filter combines (run by the last block to finish).
+// ---------------------------------------------------------------------------
+struct CombineScratch {
+  BlockScratch b;
+  double incl[TILE];
+  int last;
+};
+
+// Combine the tile partials of group g: group max, tile scales g_t =
+// exp(M_t - M_g), inclusive scan of S_t g_t (tile bases = exclusive prefix),
+// group sum = scan total.  Returns true in every thread of the block that
+// finished the filter's last group.
+__device__ bool combine_group(const FilterDev& fd, int g, CombineScratch& cs) {
+  const int tid = threadIdx.x;
+  const int t0 = g * GROUP;
+  const int ntg = min(GROUP, fd.ntiles - t0);
+  double Mt = -INFINITY, St = 0.0, Qt = 0.0;
+  if (tid < ntg) {
+    Mt = ldcg(&fd.tp[t0 + tid].M);
+    St = ldcg(&fd.tp[t0 + tid].S);
+    Qt = ldcg(&fd.tp[t0 + tid].Q);
+  }
+  const double Mg = block_max(Mt, cs.b);
+  const double gt = (Mt == -INFINITY) ? 0.0 : exp(Mt - Mg);
+  const double Wt = St * gt;
+  double Sg;
+  const double incl = block_scan(Wt, cs.b, &Sg);
+  cs.incl[tid] = incl;
+  double Qg = 0.0;
+  if (fd.mode == MODE_ADAPTIVE) Qg = block_sum(Qt * (gt * gt), cs.b);
+  __syncthreads();
+  if (tid < ntg) {
+    fd.tp[t0 + tid].g = gt;
+    fd.tp[t0 + tid].base = tid == 0 ? 0.0 : cs.incl[tid - 1];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    GroupPart& gp = fd.gp[g];
+    gp.M = Mg;
+    gp.S = Sg;
+    gp.Q = Qg;
+    gp.ticket = 0u;
+    __threadfence();
+    const unsigned old = atomicAdd(&fd.ctl->gticket, 1u);
+    cs.last = (old == unsigned(fd.ngroups - 1));
+  }
+  __syncthreads();
+  const bool last = cs.last != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+// Combine the groups of the filter and take the step's decisions.
+__device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs) {
+  const int tid = threadIdx.x;
+  const int ng = fd.ngroups;
+  double Mg = -INFINITY, Sg = 0.0, Qg = 0.0;
+  if (tid < ng) {
+    Mg = ldcg(&fd.gp[tid].M);
+    Sg = ldcg(&fd.gp[tid].S);
+    Qg = ldcg(&fd.gp[tid].Q);
+  }
+  const double M = block_max(Mg, cs.b);
+  const double G = (Mg == -INFINITY) ? 0.0 : exp(Mg - M);
+  const double W = Sg * G;
+  double S;
+  const double incl = block_scan(W, cs.b, &S);
+  cs.incl[tid] = incl;
+  double Q = 0.0;
+  if (fd.mode == MODE_ADAPTIVE) Q = block_sum(Qg * (G * G), cs.b);
+  __syncthreads();
+  if (tid < ng) {
+    fd.gp[tid].G = G;
+    fd.gp[tid].B = tid == 0 ? 0.0 : cs.incl[tid - 1];
+  }
+  if (tid == 0) {
+    Ctl* c = fd.ctl;
+    c->gticket = 0u;
+    c->rs_step = i;
+    if (!(M > -INFINITY) || M == INFINITY || !(S > 0.0)) {
+      c->status = ST_DEGENERATE;
+      c->ll = -INFINITY;
+      c->rs_flag = 0;
+      c->step = fd.T + 1;
+    } else {
+      const double incr = ((M + log(S)) - c->L) + c->c_obs;
+      c->ll = c->ll + incr;
+      bool resample = false;
+      if (i < fd.T) {
+        if (fd.mode == MODE_ALWAYS) resample = true;
+        else if (fd.mode == MODE_ADAPTIVE) resample = (S * S) / Q < fd.thr * double(fd.P);
+      }
+      c->M = M;
+      c->S = S;
+      if (resample) {
+        const uint4 w = rng_block(fd.seed, 0u, uint32_t(i), PURPOSE_RESAMPLE, 0u);
+        c->u = u53_closed_open(w.x, w.y);
+        c->step_size = S / double(fd.P);
+        c->rs_flag = 1;
+        c->anc_identity = 0;
+        c->lam_zero = 1;
+        c->L = c->logP;
+      } else {
+        c->rs_flag = 0;
+        if (i < fd.T) {
+          c->anc_identity = 1;
+          c->lam_zero = 0;
+          c->L = log(S);
+        }
+      }
+      c->step = i + 1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+template <int KIND, int N, typename R>
+__global__ void __launch_bounds__(TILE) k_init(const FilterDev* __restrict__ fds,
+                                               const int2* __restrict__ tmap) {
+  const int2 ft = tmap[blockIdx.x];
+  const FilterDev& fd = fds[ft.x];
+  const int t = ft.y;
+  const int j = t * TILE + threadIdx.x;
+  const int P = fd.P;
+  const double m0 = KIND == KIND_WK ? fd.theta[5] : fd.theta[3];
+  const double s0 = KIND == KIND_WK ? fd.theta[6] : fd.theta[4];
+  if (j < P) {
+    R z[N];
+    normals<N>(z, fd.seed, uint32_t(j), 0u, PURPOSE_INIT);
+    R* x0 = static_cast<R*>(fd.x[0]);
+#pragma unroll
+    for (int n = 0; n < N; ++n)
+      x0[int64_t(n) * P + j] = fmaR(from_double<R>(s0), z[n], from_double<R>(m0));
+    if (fd.hist) fd.anc[j] = j;
+  }
+  if (threadIdx.x == 0 && (t % GROUP) == 0) fd.gp[t / GROUP].ticket = 0u;
+  if (threadIdx.x == 0 && t == 0) {
+    Ctl* c = fd.ctl;
+    const double r = KIND == KIND_WK ? fd.theta[4] : fd.theta[2];
+    c->step = 1;
+    c->rs_step = 0;
+    c->rs_flag = 0;
+    c->anc_identity = 1;
+    c->lam_zero = 1;
+    c->status = ST_OK;
+    c->gticket = 0u;
+    c->ll = 0.0;
+    c->logP = log(double(P));
+    c->L = c->logP;
+    c->c_obs = -0.5 * double(fd.Ny) * log(2.0 * 3.141592653589793 * r);
+    c->M = 0.0;
+    c->S = 0.0;
+    c->u = 0.0;
+    c->step_size = 0.0;
+  }
+}
+
+template <int KIND, int N, typename R>
+__global__ void __launch_bounds__(TILE) k_propagate(const FilterDev* __restrict__ fds,
+                                                    const int2* __restrict__ tmap) {
+  __shared__ CombineScratch cs;
+  __shared__ double ys[64];
+  const int2 ft = tmap[blockIdx.x];
+  const FilterDev& fd = fds[ft.x];
+  Ctl* ctl = fd.ctl;
+  const int i = ldcg(&ctl->step);
+  if (i > fd.T || ldcg(&ctl->status) != ST_OK) return;
+  const int anc_identity = ldcg(&ctl->anc_identity);
+  const int lam_zero = ldcg(&ctl->lam_zero);
+  const int P = fd.P;
+  const int t = ft.y;
+  const int tid = threadIdx.x;
+  const int j = t * TILE + tid;
+  if (tid < fd.Ny) ys[tid] = fd.y[int64_t(i - 1) * fd.Ny + tid];
+  __syncthreads();
+
+  double ell = -INFINITY;
+  if (j < P) {
+    int a = j;
+    if (!anc_identity) a = fd.anc[(fd.hist ? int64_t(i - 1) * P : 0) + j];
+    const R* xin = static_cast<const R*>(fd.x[(i - 1) & 1]);
+    R* xout = static_cast<R*>(fd.x[i & 1]);
+    double lw;
+    if constexpr (KIND == KIND_WK) {
+      R xv = xin[a];
+      lw = wk_prop_weight<R>(fd, uint32_t(j), i, xv, ys[0]);
+      xout[j] = xv;
+    } else {
+      R x[N];
+#pragma unroll
+      for (int n = 0; n < N; ++n) x[n] = xin[int64_t(n) * P + a];
+      lw = l96_prop_weight<N, R>(fd, uint32_t(j), i, x, ys);
+#pragma unroll
+      for (int n = 0; n < N; ++n) xout[int64_t(n) * P + j] = x[n];
+    }
+    double e = lam_zero ? lw : fd.lam[j] + lw;
+    if (e != e) e = -INFINITY;
+    ell = e;
+    if (fd.mode != MODE_ALWAYS) fd.ell[j] = e;
+  }
+
+  // tile partials: max, inclusive prefix of exp(ell - M_t), total
+  const double Mt = block_max(ell, cs.b);
+  const double w = (Mt == -INFINITY) ? 0.0 : exp(ell - Mt);
+  double St;
+  const double c = block_scan(w, cs.b, &St);
+  if (j < P) fd.ctil[j] = c;
+  double Qt = 0.0;
+  if (fd.mode == MODE_ADAPTIVE) Qt = block_sum(w * w, cs.b);
+  if (tid == 0) {
+    TilePart& tp = fd.tp[t];
+    tp.M = Mt;
+    tp.S = St;
+    tp.Q = Qt;
+    __threadfence();
+    const int g = t / GROUP;
+    const int ntg = min(GROUP, fd.ntiles - g * GROUP);
+    const unsigned old = atomicAdd(&fd.gp[g].ticket, 1u);
+    cs.last = (old == unsigned(ntg - 1));
+  }
+  __syncthreads();
+  if (!cs.last) return;
+  __threadfence();
+  if (combine_group(fd, t / GROUP, cs)) combine_filter(fd, i, cs);
+}
+
+// Smallest j in [0, P] with (j + u) * step >= b (the first systematic target
+// at or above b).  Start from the closed-form guess and correct it by exact
+// comparisons with the same expression the search uses; bounded loops.
+__device__ __forceinline__ int first_target(double b, double u, double step, int P) {
+  if (!(b > 0.0)) return 0;
+  double guess = ceil(b / step - u);
+  int jj = guess < 0.0 ? 0 : (guess > double(P) ? P : int(guess));
+  for (int it = 0; it < 64 && jj > 0 && (double(jj - 1) + u) * step >= b; ++it) --jj;
+  for (int it = 0; it < 64 && jj < P && (double(jj) + u) * step < b; ++it) ++jj;
+  return jj;
+}
+
+__global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__ fds,
+                                                   const int2* __restrict__ tmap) {
+  __shared__ long long ck[TILE];
+  const int2 ft = tmap[blockIdx.x];
+  const FilterDev& fd = fds[ft.x];
+  const Ctl* ctl = fd.ctl;
+  const int i = ldcg(&ctl->rs_step);
+  if (ldcg(&ctl->status) != ST_OK || i < 1 || i >= fd.T || ldcg(&ctl->step) != i + 1) return;
+  const int P = fd.P;
+  const int t = ft.y;
+  const int tid = threadIdx.x;
+  const int j0 = t * TILE;
+  if (!ldcg(&ctl->rs_flag)) {
+    const int j = j0 + tid;
+    if (j < P && fd.mode != MODE_ALWAYS) {
+      fd.lam[j] = fd.ell[j] - ldcg(&ctl->M);
+      if (fd.hist) fd.anc[int64_t(i) * P + j] = j;
+    }
+    return;
+  }
+  const int g = t / GROUP;
+  const double base = fma(fd.gp[g].G, fd.tp[t].base, fd.gp[g].B);
+  const double scale = fd.gp[g].G * fd.tp[t].g;
+  double nb;
+  if (t + 1 < fd.ntiles) {
+    const int g1 = (t + 1) / GROUP;
+    nb = fma(fd.gp[g1].G, fd.tp[t + 1].base, fd.gp[g1].B);
+  } else {
+    nb = ldcg(&ctl->S);
+  }
+  const int nvalid = min(TILE, P - j0);
+  if (tid < nvalid) ck[tid] = __double_as_longlong(fma(scale, fd.ctil[j0 + tid], base));
+  const double u = ldcg(&ctl->u);
+  const double step = ldcg(&ctl->step_size);
+  const int jlo = first_target(base, u, step, P);
+  const int jhi = first_target(nb, u, step, P);
+  __syncthreads();
+  int32_t* aout = fd.anc + (fd.hist ? int64_t(i) * P : 0);
+  for (int jj = jlo + tid; jj < jhi; jj += TILE) {
+    const double tau = (double(jj) + u) * step;
+    const long long key = __double_as_longlong(tau);
+    int pos = 0;  // number of C_k <= tau, i.e. the first k with C_k > tau
+#pragma unroll
+    for (int half = TILE / 2; half > 0; half >>= 1)
+      if (pos + half <= nvalid && ck[pos + half - 1] <= key) pos += half;
+    aout[jj] = j0 + (pos < nvalid ? pos : nvalid - 1);
+  }
+}
+
+// Windkessel input table F(k dt), k < n: half sine of the given peak and period.
+__global__ void k_flow(double* __restrict__ flow, int64_t n, double peak, double period,
+                       double dt) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double t = double(k) * dt;
+  const double ph = t / period;
+  const double fr = ph - floor(ph);
+  double v = 0.0;
+  if (fr < 0.5) {
+    double sn, cs;
+    sincos_2pi(fr, &sn, &cs);
+    v = peak * sn;
+  }
+  flow[k] = v;
+}
+
+// Copy (loglik, status, next step) of nf filters into out[3k .. 3k+2];
+// descriptors without a control block (empty server slots) give NaNs.
+__global__ void k_results(const FilterDev* __restrict__ fds, int nf, double* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nf) return;
+  const Ctl* c = fds[k].ctl;
+  if (c == nullptr) {
+    out[3 * k] = out[3 * k + 1] = out[3 * k + 2] = NAN;
+    return;
+  }
+  out[3 * k] = ldcg(&c->ll);
+  out[3 * k + 1] = double(ldcg(&c->status));
+  out[3 * k + 2] = double(ldcg(&c->step));
+}
+
+// ---------------------------------------------------------------------------
+// Host-side dispatch
+// ---------------------------------------------------------------------------
+#define PF_L96_SIZES(X) X(4) X(8) X(12) X(16) X(20) X(24) X(32) X(40)
+
+bool supported(int kind, int N, int prec) {
+  if (prec != PREC_FP64 && prec != PREC_MIXED) return false;
+  if (kind == KIND_WK) return N == 1;
+  if (kind != KIND_L96) return false;
+#define PF_CASE(n) if (N == n) return true;
+  PF_L96_SIZES(PF_CASE)
+#undef PF_CASE
+  return false;
+}
+
+template <int KIND, int N, typename R>
+static cudaError_t launch_pair(bool init, const FilterDev* fds, const int2* tmap, int nblocks,
+                               cudaStream_t st) {
+  if (nblocks <= 0) return cudaSuccess;
+  if (init) k_init<KIND, N, R><<<nblocks, TILE, 0, st>>>(fds, tmap);
+  else k_propagate<KIND, N, R><<<nblocks, TILE, 0, st>>>(fds, tmap);
+  return cudaGetLastError();
+}
+
+static cudaError_t dispatch(bool init, int kind, int N, int prec, const FilterDev* fds,
+                            const int2* tmap, int nblocks, cudaStream_t st) {
+  const bool dp = prec == PREC_FP64;
+  if (kind == KIND_WK) {
+    return dp ? launch_pair<KIND_WK, 1, double>(init, fds, tmap, nblocks, st)
+              : launch_pair<KIND_WK, 1, float>(init, fds, tmap, nblocks, st);
+  }
+#define PF_CASE(n)                                                                       \
+  if (N == n)                                                                            \
+    return dp ? launch_pair<KIND_L96, n, double>(init, fds, tmap, nblocks, st)           \
+              : launch_pair<KIND_L96, n, float>(init, fds, tmap, nblocks, st);
+  PF_L96_SIZES(PF_CASE)
+#undef PF_CASE
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_init(int kind, int N, int prec, const FilterDev* fds, const int2* tmap,
+                        int nblocks, cudaStream_t st) {
+  return dispatch(true, kind, N, prec, fds, tmap, nblocks, st);
+}
+
+cudaError_t launch_propagate(int kind, int N, int prec, const FilterDev* fds, const int2* tmap,
+                             int nblocks, cudaStream_t st) {
+  return dispatch(false, kind, N, prec, fds, tmap, nblocks, st);
+}
+
+cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks,
+                            cudaStream_t st) {
+  if (nblocks <= 0) return cudaSuccess;
+  k_resample<<<nblocks, TILE, 0, st>>>(fds, tmap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flow(double* flow, int64_t n, double peak, double period, double dt,
+                        cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int bs = 256;
+  k_flow<<<int((n + bs - 1) / bs), bs, 0, st>>>(flow, n, peak, period, dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_results(const FilterDev* fds, int nf, double* out, cudaStream_t st) {
+  if (nf <= 0) return cudaSuccess;
+  k_results<<<(nf + 127) / 128, 128, 0, st>>>(fds, nf, out);
+  return cudaGetLastError();
+}
+
+}  // namespace pfb

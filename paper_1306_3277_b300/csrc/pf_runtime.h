@@ -1,0 +1,83 @@
+// pf_runtime.h -- host runtime objects shared by pf_api.cu and pf_server.cu.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "pf.h"
+#include "pf_internal.h"
+
+namespace pfb {
+
+struct Shape {
+  int Ny = 1;
+  uint64_t obs_mask = 1;
+  int ntiles = 0, ngroups = 0, mode = MODE_ALWAYS;
+  size_t state_bytes = 8;
+  int64_t nflow = 0;
+};
+
+struct PlanClass {
+  int kind, N, prec;
+  int offset;   // first entry of the class's tiles in Plan::d_tmap
+  int ntiles;
+};
+
+struct Plan;
+
+}  // namespace pfb
+
+struct pf_filter {
+  pf_model m{};
+  int64_t P = 0;
+  int32_t T = 0;
+  double dt = 0.0;
+  int device = 0;
+  pfb::Shape sh;
+  cudaStream_t own = nullptr;
+  void* x[2] = {nullptr, nullptr};
+  double* ctil = nullptr;
+  double* ell = nullptr;
+  double* lam = nullptr;
+  int32_t* anc = nullptr;
+  int32_t* hist = nullptr;
+  double* flow = nullptr;
+  pfb::TilePart* tp = nullptr;
+  pfb::GroupPart* gp = nullptr;
+  pfb::Ctl* ctl = nullptr;
+  double* h_res = nullptr;
+  pfb::FilterDev desc{};
+  pfb::Plan* plan = nullptr;
+  bool pending = false;
+  size_t bytes = 0;
+};
+
+namespace pfb {
+
+// A launch plan: descriptors of its filters, tile maps sorted by T
+// (descending) and one instantiated CUDA graph covering the whole run.
+struct Plan {
+  std::vector<pf_filter*> filters;
+  int nf = 0, maxT = 0, ntiles_all = 0;
+  std::vector<PlanClass> classes;
+  std::vector<int> cnt_all;                 // [i]: tiles of filters with T >= i
+  std::vector<std::vector<int>> cnt_cls;    // per class
+  std::vector<size_t> yoff;                 // offset of each filter's y in d_ycat
+  FilterDev* d_fds = nullptr;
+  FilterDev* h_fds = nullptr;               // pinned
+  int2* d_tmap = nullptr;
+  double* d_ycat = nullptr;
+  double* h_ycat = nullptr;                 // pinned
+  double* d_res = nullptr;
+  double* h_res = nullptr;                  // pinned
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev_staged = nullptr, ev_done = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+pf_status fail(pf_status st, const char* fmt, ...);
+pf_status check_shape(const pf_model* m, int64_t P, int32_t T, double dt, Shape* sh);
+pf_status build_plan(const std::vector<pf_filter*>& fl, Plan** out);
+pf_status run_plan(Plan* p, const double* const* theta, const double* const* y,
+                   const uint64_t* seeds, const int32_t* hist_on, cudaStream_t st);
+
+}  // namespace pfb

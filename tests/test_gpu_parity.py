@@ -1,0 +1,155 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the oracle on
+the same seeded inputs.  FP64 and mixed precision; ancestors and final
+particles bit-exact (outside near-boundary targets), log-likelihood within
+1e-9 relative."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from pf_parity import compare, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1306_3277_b300 as pf
+    pf.lib()
+
+
+CASES = [
+    # name, workload factory, seeds
+    ("windkessel P=1024 T=100 FP64", lambda: W.windkessel(), (1, 2, 3)),
+    ("windkessel P=1000 T=60 s=3 FP64", lambda: W.windkessel(P=1000, T=60, substeps=3), (4,)),
+    ("windkessel P=1000 T=60 s=3 mixed", lambda: W.windkessel(P=1000, T=60, substeps=3,
+                                                              prec=W.MIXED), (5,)),
+    ("windkessel P=777 T=80 ESS 0.5 FP64", lambda: W.windkessel(P=777, T=80, ess_threshold=0.5),
+     (6, 7)),
+    ("windkessel P=300 T=30 never resample", lambda: W.windkessel(P=300, T=30, ess_threshold=0.0),
+     (8,)),
+    ("lorenz96 N=8 P=2^14 T=200 FP64", lambda: W.lorenz96_8(), (1,)),
+    ("lorenz96 N=8 P=2^14 T=200 mixed", lambda: W.lorenz96_8(prec=W.MIXED), (2,)),
+    ("lorenz96 N=8 P=5000 T=40 ESS 0.5 mixed", lambda: W.lorenz96_8(P=5000, T=40, prec=W.MIXED,
+                                                                    ess_threshold=0.5), (3,)),
+    ("lorenz96 N=40 P=3000 T=20 mixed", lambda: W.lorenz96_large(P=3000, T=20), (4,)),
+    ("lorenz96 N=40 P=2^16+5 T=6 FP64", lambda: W.lorenz96_large(P=(1 << 16) + 5, T=6,
+                                                                 prec=W.FP64), (5,)),
+]
+
+
+@pytest.mark.parametrize("name,factory,seeds", CASES, ids=[c[0] for c in CASES])
+def test_parity(name, factory, seeds):
+    w = factory()
+    for seed in seeds:
+        o = run_oracle(w, seed)
+        g = run_gpu(w, seed)
+        rows, first_near = compare(w, g, o)
+        assert rows >= 1
+
+
+def test_parity_large_config_full_particle_count():
+    """Large shape (N=40, every 2nd component observed, s=10, dt=0.005) at the
+    full 2^20 particles, over the first 3 observations (the oracle's budget)."""
+    w = W.lorenz96_large(T=3)
+    o = run_oracle(w, 11)
+    g = run_gpu(w, 11)
+    compare(w, g, o)
+
+
+@pytest.mark.parametrize("P,T", [(1, 1), (1, 5), (2, 3), (255, 2), (256, 2), (257, 2)])
+def test_edge_sizes(P, T):
+    w = W.windkessel(P=P, T=T)
+    o = run_oracle(w, 3)
+    g = run_gpu(w, 3)
+    compare(w, g, o)
+    w = W.lorenz96_8(P=P, T=T, prec=W.MIXED)
+    compare(w, run_gpu(w, 4), run_oracle(w, 4))
+
+
+def test_degenerate_status():
+    import paper_1306_3277_b300 as pf
+    w = W.windkessel(P=512, T=10)
+    th = list(w.theta)
+    th[4] = 0.0
+    g = run_gpu(w, 1, theta=th)
+    o = run_oracle(w, 1, theta=th)
+    assert g["status"] == pf.PF_EDEGENERATE == o["status"]
+    assert g["loglik"] == -math.inf
+    th = list(w.theta)
+    th[0] = float("nan")
+    g = run_gpu(w, 1, theta=th)
+    assert g["status"] == pf.PF_EDEGENERATE and g["loglik"] == -math.inf
+
+
+def test_device_pointers_match_host_pointers():
+    import torch
+    import paper_1306_3277_b300 as pf
+    w = W.lorenz96_8(P=4096, T=30, prec=W.MIXED)
+    f = pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt)
+    st, ll_h, x_h, anc_h = f.run(w.theta, w.y, 9, want_particles=True, want_ancestors=True)
+    th = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
+    y = torch.tensor(w.y, dtype=torch.float64, device="cuda")
+    ll = torch.zeros(1, dtype=torch.float64, device="cuda")
+    x = torch.zeros((w.N, w.P), dtype=torch.float32, device="cuda")
+    anc = torch.zeros((w.T, w.P), dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    pf.pf_run(f, th, y, 9, ll, x, anc, pf.PF_FLAG_ASYNC, s)
+    assert pf.pf_wait(f) == pf.PF_OK
+    s.synchronize()
+    assert ll.item() == ll_h
+    assert np.array_equal(x.cpu().numpy(), x_h)
+    assert np.array_equal(anc.cpu().numpy(), anc_h)
+    f.destroy()
+
+
+def test_repeat_runs_are_identical_and_seed_sensitive():
+    import paper_1306_3277_b300 as pf
+    w = W.lorenz96_8(P=2048, T=20)
+    f = pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt)
+    a = f.run(w.theta, w.y, 5)[1]
+    b = f.run(w.theta, w.y, 5)[1]
+    c = f.run(w.theta, w.y, 6)[1]
+    f.destroy()
+    assert a == b and a != c
+
+
+def test_batch_bit_identical_to_single_runs():
+    import paper_1306_3277_b300 as pf
+    ws = W.batched(n_wk=5, n_l96=5, pmin=6, pmax=12, tmin=5, tmax=60)
+    ws += [W.lorenz96_large(P=700, T=9), W.windkessel(P=333, T=17, prec=W.FP64,
+                                                      ess_threshold=0.5)]
+    fs = [pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt) for w in ws]
+    lls, sts = pf.pf_batch_run(fs, [w.theta for w in ws], [w.y for w in ws],
+                               [w.seed for w in ws])
+    lls2, _ = pf.pf_batch_run(fs, [w.theta for w in ws], [w.y for w in ws],
+                              [w.seed for w in ws])
+    for k, (w, f) in enumerate(zip(ws, fs)):
+        st, ll, _, _ = f.run(w.theta, w.y, w.seed)
+        assert sts[k] == st
+        assert lls[k] == ll and lls2[k] == ll, (k, w.name, lls[k], ll)
+    # and against the oracle for a few
+    for k in (0, 6, len(ws) - 2):
+        o = run_oracle(ws[k], ws[k].seed)
+        if not np.any(o["diag"][:, 7] > 0):
+            assert abs(lls[k] - o["loglik"]) <= 1e-9 * abs(o["loglik"])
+    for f in fs:
+        f.destroy()
+
+
+def test_invalid_arguments_rejected():
+    import paper_1306_3277_b300 as pf
+    with pytest.raises(pf.PFError) as e:
+        pf.pf_create(pf.model(pf.PF_LORENZ96, N=7), 100, 10, 0.01)
+    assert e.value.status == pf.PF_EINVAL
+    with pytest.raises(pf.PFError):
+        pf.pf_create(pf.model(pf.PF_WINDKESSEL), 0, 10, 0.01)
+    with pytest.raises(pf.PFError):
+        pf.pf_create(pf.model(pf.PF_WINDKESSEL), 10, 10, -1.0)
+    with pytest.raises(pf.PFError):
+        pf.pf_create(pf.model(pf.PF_WINDKESSEL, ess_threshold=-1.0), 10, 10, 0.01)
