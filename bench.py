@@ -1,0 +1,461 @@
+#!/usr/bin/env python
+"""Benchmark of the B300 bootstrap particle filter.
+
+Default workload: Lorenz '96, N=40, F=8, RK4 dt=0.005 x 10 substeps per
+observation, every 2nd component observed with N(0,1) noise, P=2^20
+particles, T=500 observations, FP32 propagation / FP64 weights (the Large
+configuration).  One step = one whole filter run (all T observations:
+propagate, weight, log-sum-exp, ESS test, systematic resampling) over one
+synthetic observation series; the metric is particle-steps/s (P*T per run).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: one process per GPU (torchrun); every rank runs an independent
+filter replica (different seed), no collective on the data path; value = all
+ranks' particle-steps / max-over-ranks time ("weak" scaling).
+
+--impl reference times the CPU oracle (plain C, OpenMP over particles) on the
+host cores on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+PROFILES = os.path.join(ROOT, "profiles")
+DESCRIPTOR_BYTES = 240  # per-filter descriptor the library uploads with every run
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for fn in ("pf_kernels.cu", "pf_dev.cuh"):
+        with open(os.path.join(ROOT, "paper_1306_3277_b300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(kernel_tag):
+    """Per-launch DRAM bytes of a kernel from its committed ncu summary, if the
+    summary was taken on the current kernel source (else None)."""
+    path = os.path.join(PROFILES, "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(kernel_tag)
+    if not e or e.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+        if not self.rows:
+            return None
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+        sm = [v for v in (num(r[1]) for r in self.rows) if v is not None]
+        mx = [v for v in (num(r[2]) for r in self.rows) if v is not None]
+        pw = [v for v in (num(r[3]) for r in self.rows) if v is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def l96_flops_per_particle_step(w):
+    """Algorithmic FP32 flops of one Lorenz '96 particle-step: RK4 (4
+    right-hand sides of 2 sub + 1 fma = 4 flop, 3 stage fmas, 4 combination
+    fmas = 30 flop per component and substep) plus the noise fma (2 flop per
+    component).  Random-number generation is not counted."""
+    return 30 * w.N * w.substeps + 2 * w.N
+
+
+def propagate_bytes_per_particle(w):
+    """Algorithmic HBM bytes of the propagate kernel per particle: ancestor
+    read (4), state gather read and write (2 N sizeof), in-tile weight prefix
+    write (8)."""
+    sb = 4 if w.prec == W.MIXED else 8
+    return 2 * w.N * sb + 12
+
+
+RESAMPLE_BYTES_PER_PARTICLE = 12  # weight prefix read (8) + ancestor write (4)
+
+
+def make_workload(args):
+    if args.config == "large":
+        return W.lorenz96_large(P=args.P or (1 << 20), T=args.T or 500)
+    if args.config == "l96_8":
+        return W.lorenz96_8(P=args.P or (1 << 14), T=args.T or 200, prec=W.MIXED)
+    if args.config == "l96_8_fp64":
+        return W.lorenz96_8(P=args.P or (1 << 14), T=args.T or 200, prec=W.FP64)
+    return W.windkessel(P=args.P or 1024, T=args.T or 100)
+
+
+def cpu_oracle_rate(w, P_sample, T_sample, nthreads=0):
+    """Particle-steps/s of the oracle on a bounded sample of workload w."""
+    import oracle as O
+    ws = w.with_(P=P_sample, T=T_sample, y=w.y[:T_sample].copy())
+    m = O.model(ws.kind, N=ws.N, substeps=ws.substeps, obs_stride=ws.obs_stride, prec=ws.prec,
+                dt=ws.dt, ess_threshold=ws.ess_threshold, flow_peak=ws.flow_peak,
+                flow_period=ws.flow_period)
+    t0 = time.perf_counter()
+    O.pf_run(m, ws.theta, ws.y, 1, ws.P, ws.T, nthreads=nthreads, want_x=False, want_anc=False,
+             want_diag=False)
+    dt = time.perf_counter() - t0
+    return ws.P * ws.T / dt, dt
+
+
+def oracle_sample(w):
+    """Sample sizes for the oracle: about 10-30 s of CPU work."""
+    if w.kind == W.LORENZ96 and w.N >= 40:
+        return min(w.P, 1 << 18), min(w.T, 2)
+    if w.kind == W.LORENZ96:
+        return min(w.P, 1 << 14), min(w.T, 100)
+    return min(w.P, 1 << 14), min(w.T, 100)
+
+
+def cores():
+    return len(os.sched_getaffinity(0))
+
+
+def dtype_name(w):
+    return "f64" if w.prec == W.FP64 else "f32 state / f64 weights"
+
+
+def run_reference(args):
+    """The CPU oracle as it stands, on the host cores, bounded samples."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    w = make_workload(args)
+    P_s, T_s = oracle_sample(w)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(w, max(P_s // 16, 1), 1)
+    secs = []
+    for _ in range(args.steps):
+        secs.append(cpu_oracle_rate(w, P_s, T_s)[1])
+    total = sum(secs)
+    value = P_s * T_s * args.steps / total
+    sample = "P=%d T=%d of %s per step, OpenMP over particles" % (P_s, T_s, w.name)
+    line = {"impl": "reference", "metric": "particle-steps/s", "value": value,
+            "unit": "particle-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype_name(w), "data": "synthetic",
+            "config": {"workload": w.name, "P": w.P, "T": w.T, "N": w.N,
+                       "substeps": w.substeps, "obs_stride": w.obs_stride},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": cores(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def secondary(pf, torch, dev):
+    """Quick extra numbers: the small configurations and batched vs plain."""
+    out = {}
+    st = torch.cuda.Stream(device=dev)
+
+    def time_runs(w, reps):
+        f = pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt)
+        th = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+        y = torch.tensor(w.y, dtype=torch.float64, device=dev)
+        ll = torch.zeros(1, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize(dev)
+        for r in range(3):
+            pf.pf_run(f, th, y, 100 + r, ll, None, None, pf.PF_FLAG_ASYNC, st)
+        st.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for r in range(reps):
+            pf.pf_run(f, th, y, r + 1, ll, None, None, pf.PF_FLAG_ASYNC, st)
+        e1.record(st)
+        st.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        f.destroy()
+        return ms
+
+    for name, w, reps in (("windkessel_P1024_T100_fp64", W.windkessel(), 50),
+                          ("lorenz96_N8_P16384_T200_fp64", W.lorenz96_8(), 10),
+                          ("lorenz96_N8_P16384_T200_mixed", W.lorenz96_8(prec=W.MIXED), 10)):
+        ms = time_runs(w, reps)
+        out[name] = {"ms_per_run": ms, "particle_steps_per_s": w.P * w.T / (ms * 1e-3),
+                     "runs_per_s": 1e3 / ms}
+    # batched: 256 uneven filters in one plan (CUDA graph) vs one pf_run per filter
+    ws = W.batched()
+    fs = [pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt) for w in ws]
+    ths = [w.theta for w in ws]
+    ys = [w.y for w in ws]
+    seeds = [w.seed for w in ws]
+    pf.pf_batch_run(fs, ths, ys, seeds)  # plan + graph build
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        lls_b, _ = pf.pf_batch_run(fs, ths, ys, seeds)
+    tb = (time.perf_counter() - t0) / reps
+    for f, w in zip(fs, ws):  # build the single-filter plans
+        f.run(w.theta, w.y, w.seed)
+    t0 = time.perf_counter()
+    lls_p = [f.run(w.theta, w.y, w.seed)[1] for f, w in zip(fs, ws)]
+    tp = time.perf_counter() - t0
+    maxrel = max(abs(a - b) / abs(b) for a, b in zip(lls_b, lls_p))
+    psteps = sum(w.P * w.T for w in ws)
+    out["batched_256"] = {"filters": len(ws), "batched_evals_per_s": len(ws) / tb,
+                          "plain_evals_per_s": len(ws) / tp, "speedup": tp / tb,
+                          "batched_particle_steps_per_s": psteps / tb,
+                          "max_rel_loglik_diff_vs_plain": maxrel}
+    for f in fs:
+        f.destroy()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__,
+                                 formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="large",
+                    choices=["large", "l96_8", "l96_8_fp64", "windkessel"])
+    ap.add_argument("--P", type=int, default=0, help="override the particle count")
+    ap.add_argument("--T", type=int, default=0, help="override the observation count")
+    ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-peak", action="store_true")
+    args = ap.parse_args()
+
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    import paper_1306_3277_b300 as pf
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = make_workload(args)
+    f = pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt)
+    th = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+    y = torch.tensor(w.y, dtype=torch.float64, device=dev)
+    ll = torch.zeros(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize(dev)
+    seed0 = 1000 * (rank + 1)
+
+    # warm-up: graph replays (the last one is timed and reported as graph_ms_per_step)
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    for k in range(args.warmup):
+        if k == args.warmup - 1:
+            g0.record(stream)
+        pf.pf_run(f, th, y, seed0 + k, ll, None, None, pf.PF_FLAG_ASYNC, stream)
+    g1.record(stream)
+    stream.synchronize()
+    graph_ms = g0.elapsed_time(g1)
+
+    # timed region: K whole runs, kernels launched one by one with CUDA events
+    pf.pf_profile_enable(f, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        pf.pf_run(f, th, y, seed0 + 100 + k, ll, None, None, pf.PF_FLAG_ASYNC, stream)
+    e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    prof = pf.pf_profile_read(f)
+    pf.pf_profile_enable(f, False)
+    status = pf.pf_wait(f)
+    loglik = ll.item()
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = t.item()
+
+    psteps_rank = w.P * w.T * args.steps
+    value = psteps_rank * world / (elapsed_ms * 1e-3)
+    launches = sum(n for _, n in prof.values())
+
+    # e2e: the public call with host buffers (H2D of theta and y, D2H of the result)
+    th_h = np.ascontiguousarray(w.theta, dtype=np.float64)
+    y_h = np.ascontiguousarray(w.y, dtype=np.float64)
+    f.run(th_h, y_h, seed0)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        f.run(th_h, y_h, seed0 + 200 + k)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = t.item()
+    e2e_value = psteps_rank * world / e2e_s
+
+    if rank == 0:
+        peaks, peak_src = measured_peaks()
+        prop_ms, prop_n = prof["propagate"]
+        res_ms, res_n = prof["resample"]
+        avg_prop_ms = prop_ms / max(prop_n, 1)
+        avg_res_ms = res_ms / max(res_n, 1)
+        if w.kind == W.LORENZ96:
+            flop_launch = l96_flops_per_particle_step(w) * w.P
+        else:
+            flop_launch = 6 * w.substeps * w.P
+        prop_bytes = propagate_bytes_per_particle(w) * w.P
+        res_bytes = RESAMPLE_BYTES_PER_PARTICLE * w.P
+        fp32_peak = fp64_peak = None
+        if not args.no_peak:
+            fp32_peak = pf.pf_measure_fma_peak(pf.PF_MIXED)
+            fp64_peak = pf.pf_measure_fma_peak(pf.PF_FP64)
+        achieved_tf = flop_launch / (avg_prop_ms * 1e-3) / 1e12
+        alu_peak = fp32_peak if w.prec == W.MIXED else fp64_peak
+        alu_peak_tf = alu_peak / 1e12 if alu_peak else None
+        tag = "k_propagate<%s,%d,%s>" % ("L96" if w.kind else "WK", w.N,
+                                          "f32" if w.prec else "f64")
+        res_gbs = res_bytes / (avg_res_ms * 1e-3) / 1e9 if avg_res_ms > 0 else None
+        roof = {"kernel": tag + " (fused gather, RK4, noise, FP64 weight, tile prefix sums)",
+                "bound": "alu", "achieved": achieved_tf, "peak": alu_peak_tf, "unit": "TFLOP/s",
+                "frac": (achieved_tf / alu_peak_tf) if alu_peak_tf else None,
+                "traffic": read_traffic(tag),
+                "peak_source": "measured %s FMA throughput of this GPU in this run "
+                               "(pf_measure_fma_peak)" % ("FP32" if w.prec else "FP64"),
+                "algorithmic_flop_per_launch": flop_launch,
+                "algorithmic_bytes_per_launch": prop_bytes,
+                "avg_launch_ms": avg_prop_ms, "launches": prop_n,
+                "share_of_timed_region": prop_ms / elapsed_ms,
+                "hbm_achieved_gbs": prop_bytes / (avg_prop_ms * 1e-3) / 1e9,
+                "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_source": peak_src,
+                "fp32_fma_peak_tflops": fp32_peak / 1e12 if fp32_peak else None,
+                "fp64_fma_peak_tflops": fp64_peak / 1e12 if fp64_peak else None,
+                "resample_kernel": {
+                    "avg_launch_ms": avg_res_ms, "launches": res_n,
+                    "share_of_timed_region": res_ms / elapsed_ms,
+                    "algorithmic_bytes_per_launch": res_bytes, "hbm_achieved_gbs": res_gbs,
+                    "hbm_frac": res_gbs / peaks["hbm_gbs"] if res_gbs else None,
+                    "traffic": read_traffic("k_resample")}}
+        cpu = None
+        if not args.no_cpu_baseline:
+            P_s, T_s = oracle_sample(w)
+            rate, secs = cpu_oracle_rate(w, P_s, T_s)
+            cpu = {"value": rate, "unit": "particle-steps/s", "cores": cores(), "kind": "oracle",
+                   "sample": "P=%d T=%d of the same workload, OpenMP over particles, %.1f s wall"
+                             % (P_s, T_s, secs)}
+        sec = None
+        if not args.no_secondary and world == 1:
+            sec = secondary(pf, torch, dev)
+        out = {
+            "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype_name(w),
+            "data": "synthetic (observations simulated from the model, seeded)",
+            "config": {"workload": w.name, "model": "lorenz96" if w.kind else "windkessel",
+                       "N": w.N, "P": w.P, "T": w.T, "substeps": w.substeps, "dt": w.dt,
+                       "obs_stride": w.obs_stride, "resampling": "systematic, every step",
+                       "parallelism": "%d independent replicas" % world if world > 1
+                       else "single GPU",
+                       "l2": "inputs larger than L2 (state %d MiB x 2)" % (
+                           w.N * w.P * (4 if w.prec else 8) >> 20),
+                       "launch": "timed region: kernels launched one by one with per-kernel "
+                                 "CUDA events; warm-up: one CUDA graph per run"},
+            "graph_ms_per_step": graph_ms,
+            "loglik_last": loglik, "status": pf.STATUS_NAMES[status],
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": "particle-steps/s",
+                    "h2d_bytes_per_step": int(y_h.nbytes + DESCRIPTOR_BYTES),
+                    "d2h_bytes_per_step": 3 * 8},
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+            "kernel_source_hash": kernel_source_hash(),
+            "secondary": sec,
+        }
+        print(json.dumps(out), flush=True)
+    f.destroy()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

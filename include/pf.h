@@ -157,6 +157,22 @@ pf_status pf_server_stats(pf_server* s, int64_t* queued, int64_t* running, int64
                           int64_t* iterations);
 pf_status pf_server_destroy(pf_server* s);
 
+/* ---- diagnostics (no counterpart in the paper) -------------------------- */
+
+/* Profiling mode: while enabled, pf_run launches the filter's kernels one by
+ * one instead of as one CUDA graph and brackets every launch with CUDA events
+ * on the run's stream.  Results are unchanged. */
+pf_status pf_profile_enable(pf_filter* f, int32_t on);
+/* Summed device time (ms) and launch counts of the runs since the last read,
+ * per kernel kind: [0] init, [1] propagate+weight, [2] resample, [3] results.
+ * Waits for those runs to finish. */
+pf_status pf_profile_read(pf_filter* f, double* ms, int64_t* launches);
+
+/* Measured dense fused-multiply-add throughput of the current GPU, in flop/s
+ * (2 per FMA): prec PF_FP64 or PF_MIXED (FP32).  Runs a few ~40 ms kernels;
+ * *ms receives the duration of the best one. */
+pf_status pf_measure_fma_peak(int32_t prec, double* flops_per_s, double* ms);
+
 #ifdef __cplusplus
 }
 #endif

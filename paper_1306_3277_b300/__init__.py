@@ -63,7 +63,13 @@ def lib():
                                    ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_uint64),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
                                    _vp]
-        for name in ("pf_run", "pf_wait", "pf_destroy", "pf_create", "pf_batch_run"):
+        L.pf_profile_enable.argtypes = [_vp, ctypes.c_int32]
+        L.pf_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_int64)]
+        L.pf_measure_fma_peak.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]
+        for name in ("pf_run", "pf_wait", "pf_destroy", "pf_create", "pf_batch_run",
+                     "pf_profile_enable", "pf_profile_read", "pf_measure_fma_peak"):
             getattr(L, name).restype = ctypes.c_int
         if hasattr(L, "pf_server_create"):
             L.pf_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(_vp)]
@@ -187,6 +193,29 @@ def pf_wait(f):
 
 def pf_destroy(f):
     f.destroy()
+
+
+def pf_profile_enable(f, on=True):
+    _check(lib().pf_profile_enable(f.h, 1 if on else 0))
+
+
+PROFILE_KINDS = ("init", "propagate", "resample", "results")
+
+
+def pf_profile_read(f):
+    """{kind: (total ms, launches)} for the runs since the last read."""
+    ms = (ctypes.c_double * 4)()
+    n = (ctypes.c_int64 * 4)()
+    _check(lib().pf_profile_read(f.h, ms, n))
+    return {k: (ms[i], n[i]) for i, k in enumerate(PROFILE_KINDS)}
+
+
+def pf_measure_fma_peak(prec):
+    """Measured FMA throughput (flop/s) of the current GPU for PF_FP64 or PF_MIXED (FP32)."""
+    f = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(lib().pf_measure_fma_peak(prec, ctypes.byref(f), ctypes.byref(ms)))
+    return f.value
 
 
 def pf_batch_run(filters, thetas, ys, seeds, stream=None):

@@ -218,6 +218,42 @@ static void destroy_plan(Plan* p) {
   delete p;
 }
 
+// The launch sequence of one run of a plan: init per class, then for every
+// step one propagate launch per class and one resample launch (only over the
+// filters that are still running), then the results gather.  With a profiler,
+// every launch is bracketed by CUDA events on the same stream.
+static cudaError_t enqueue_run(Plan* p, cudaStream_t st, Profiler* prof) {
+  cudaError_t le = cudaSuccess;
+  auto timed = [&](int kind, auto&& launch) {
+    if (prof) prof->begin(kind, st);
+    const cudaError_t r = launch();
+    if (prof) prof->end(st);
+    return r;
+  };
+  for (size_t c = 0; c < p->classes.size() && le == cudaSuccess; ++c) {
+    const PlanClass& pc = p->classes[c];
+    le = timed(PROF_INIT, [&] {
+      return launch_init(pc.kind, pc.N, pc.prec, p->d_fds, p->d_tmap + pc.offset, pc.ntiles, st);
+    });
+  }
+  for (int i = 1; i <= p->maxT && le == cudaSuccess; ++i) {
+    for (size_t c = 0; c < p->classes.size() && le == cudaSuccess; ++c) {
+      const PlanClass& pc = p->classes[c];
+      if (p->cnt_cls[c][i] == 0) continue;
+      le = timed(PROF_PROPAGATE, [&] {
+        return launch_propagate(pc.kind, pc.N, pc.prec, p->d_fds, p->d_tmap + pc.offset,
+                                p->cnt_cls[c][i], st);
+      });
+    }
+    if (le == cudaSuccess && p->cnt_all[i + 1] > 0)
+      le = timed(PROF_RESAMPLE,
+                 [&] { return launch_resample(p->d_fds, p->d_tmap, p->cnt_all[i + 1], st); });
+  }
+  if (le == cudaSuccess)
+    le = timed(PROF_RESULTS, [&] { return launch_results(p->d_fds, p->nf, p->d_res, st); });
+  return le;
+}
+
 // Tile maps sorted by T descending so that the filters still running at step
 // i own a prefix of every map.
 pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out) {
@@ -312,20 +348,7 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out) {
   cudaGraph_t g = nullptr;
   e = cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaError_t le = cudaSuccess;
-    for (size_t c = 0; c < p->classes.size() && le == cudaSuccess; ++c) {
-      const PlanClass& pc = p->classes[c];
-      le = launch_init(pc.kind, pc.N, pc.prec, p->d_fds, p->d_tmap + pc.offset, pc.ntiles, p->st);
-    }
-    for (int i = 1; i <= maxT && le == cudaSuccess; ++i) {
-      for (size_t c = 0; c < p->classes.size() && le == cudaSuccess; ++c) {
-        const PlanClass& pc = p->classes[c];
-        le = launch_propagate(pc.kind, pc.N, pc.prec, p->d_fds, p->d_tmap + pc.offset,
-                              p->cnt_cls[c][i], p->st);
-      }
-      if (le == cudaSuccess) le = launch_resample(p->d_fds, p->d_tmap, p->cnt_all[i + 1], p->st);
-    }
-    if (le == cudaSuccess) le = launch_results(p->d_fds, nf, p->d_res, p->st);
+    const cudaError_t le = enqueue_run(p, p->st, nullptr);
     e = cudaStreamEndCapture(p->st, &g);
     if (e == cudaSuccess) e = le;
   }
@@ -351,7 +374,8 @@ static bool is_device_ptr(const void* ptr) {
 
 // Stage theta, seed and y of every filter of the plan and launch its graph on st.
 pf_status pfb::run_plan(Plan* p, const double* const* theta, const double* const* y,
-                        const uint64_t* seeds, const int32_t* hist_on, cudaStream_t st) {
+                        const uint64_t* seeds, const int32_t* hist_on, cudaStream_t st,
+                        Profiler* prof) {
   CK(cudaEventSynchronize(p->ev_staged));  // pinned staging of the previous run consumed
   std::vector<int> dev_theta, dev_y;
   for (int k = 0; k < p->nf; ++k) {
@@ -388,7 +412,8 @@ pf_status pfb::run_plan(Plan* p, const double* const* theta, const double* const
                        cudaMemcpyDeviceToDevice, st));
   }
   CK(cudaEventRecord(p->ev_staged, st));
-  CK(cudaGraphLaunch(p->exec, st));
+  if (prof) CK(enqueue_run(p, st, prof));
+  else CK(cudaGraphLaunch(p->exec, st));
   CK(cudaMemcpyAsync(p->h_res, p->d_res, sizeof(double) * 3 * p->nf, cudaMemcpyDeviceToHost, st));
   CK(cudaEventRecord(p->ev_done, st));
   return PF_OK;
@@ -425,7 +450,7 @@ extern "C" pf_status pf_run(pf_filter* f, const double* theta, const double* y, 
   }
   Plan* p = f->plan;
   const int32_t hist_on = ancestors ? 1 : 0;
-  pf_status ps = run_plan(p, &theta, &y, &seed, &hist_on, st);
+  pf_status ps = run_plan(p, &theta, &y, &seed, &hist_on, st, f->prof);
   if (ps != PF_OK) return ps;
   const int64_t P = f->P;
   if (final_particles)
@@ -472,6 +497,7 @@ extern "C" pf_status pf_destroy(pf_filter* f) {
   }
   destroy_plan(f->plan);
   free_filter_buffers(f);
+  delete f->prof;
   delete f;
   return PF_OK;
 }
@@ -510,7 +536,7 @@ extern "C" pf_status pf_batch_run(int32_t nfilt, pf_filter* const* f, const doub
     g_plans[key] = p;
   }
   cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : p->st;
-  pf_status ps = run_plan(p, theta, y, seeds, nullptr, st);
+  pf_status ps = run_plan(p, theta, y, seeds, nullptr, st, nullptr);
   if (ps != PF_OK) return ps;
   CK(cudaEventSynchronize(p->ev_done));
   for (int k = 0; k < nfilt; ++k) {
@@ -518,4 +544,22 @@ extern "C" pf_status pf_batch_run(int32_t nfilt, pf_filter* const* f, const doub
     per_filter_status[k] = int(p->h_res[3 * k + 1]) == ST_OK ? PF_OK : PF_EDEGENERATE;
   }
   return PF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// diagnostics
+// ---------------------------------------------------------------------------
+extern "C" pf_status pf_profile_enable(pf_filter* f, int32_t on) {
+  if (!f) return fail(PF_EINVAL, "filter is NULL");
+  if (on && !f->prof) f->prof = new Profiler();
+  if (!on) {
+    delete f->prof;
+    f->prof = nullptr;
+  }
+  return PF_OK;
+}
+
+extern "C" pf_status pf_profile_read(pf_filter* f, double* ms, int64_t* launches) {
+  if (!f || !f->prof) return fail(PF_EINVAL, "profiling is not enabled on this filter");
+  return f->prof->read(ms, launches);
 }

@@ -24,6 +24,57 @@ struct PlanClass {
 
 struct Plan;
 
+enum { PROF_INIT = 0, PROF_PROPAGATE = 1, PROF_RESAMPLE = 2, PROF_RESULTS = 3, PROF_KINDS = 4 };
+
+// Per-launch CUDA-event timing of direct (non-graph) runs, summed per kernel kind.
+struct Profiler {
+  struct Pair {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Pair> pairs;
+  size_t next = 0;
+  cudaEvent_t take() {
+    if (next == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[next++];
+  }
+  void begin(int kind, cudaStream_t st) {
+    Pair pr{kind, take(), nullptr};
+    cudaEventRecord(pr.a, st);
+    pairs.push_back(pr);
+  }
+  void end(cudaStream_t st) {
+    pairs.back().b = take();
+    cudaEventRecord(pairs.back().b, st);
+  }
+  pf_status read(double* ms, int64_t* launches) {
+    double acc[PROF_KINDS] = {0, 0, 0, 0};
+    int64_t cnt[PROF_KINDS] = {0, 0, 0, 0};
+    for (const Pair& pr : pairs) {
+      if (cudaEventSynchronize(pr.b) != cudaSuccess) return PF_ECUDA;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, pr.a, pr.b);
+      acc[pr.kind] += t;
+      cnt[pr.kind] += 1;
+    }
+    for (int k = 0; k < PROF_KINDS; ++k) {
+      if (ms) ms[k] = acc[k];
+      if (launches) launches[k] = cnt[k];
+    }
+    pairs.clear();
+    next = 0;
+    return PF_OK;
+  }
+  ~Profiler() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
 }  // namespace pfb
 
 struct pf_filter {
@@ -47,6 +98,7 @@ struct pf_filter {
   double* h_res = nullptr;
   pfb::FilterDev desc{};
   pfb::Plan* plan = nullptr;
+  pfb::Profiler* prof = nullptr;
   bool pending = false;
   size_t bytes = 0;
 };
@@ -78,6 +130,7 @@ pf_status fail(pf_status st, const char* fmt, ...);
 pf_status check_shape(const pf_model* m, int64_t P, int32_t T, double dt, Shape* sh);
 pf_status build_plan(const std::vector<pf_filter*>& fl, Plan** out);
 pf_status run_plan(Plan* p, const double* const* theta, const double* const* y,
-                   const uint64_t* seeds, const int32_t* hist_on, cudaStream_t st);
+                   const uint64_t* seeds, const int32_t* hist_on, cudaStream_t st,
+                   Profiler* prof);
 
 }  // namespace pfb

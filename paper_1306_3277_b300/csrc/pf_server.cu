@@ -1,0 +1,468 @@
+// pf_server.cu -- continuous-batching likelihood server (pf_server_* of pf.h).
+//
+// A scheduler thread owns one CUDA stream and a table of slots.  Every
+// iteration it
+//   1. retires the filters that an earlier iteration reported finished (their
+//      results were copied back asynchronously), freeing slot and memory;
+//   2. admits queued requests (FIFO) while a slot is free and the request's
+//      device bytes fit in the budget; their buffers come from a private,
+//      stream-ordered memory pool, their y from a pinned staging arena;
+//   3. launches, over the tiles of every admitted filter, the init kernel for
+//      the new ones, then one propagate launch per model class and one
+//      resample launch, so every running filter advances one observation.
+// The same kernels and per-filter reduction order as pf_run are used, so a
+// request's log-likelihood is bit-identical to pf_run of the same request.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "pf.h"
+#include "pf_internal.h"
+#include "pf_runtime.h"
+
+using namespace pfb;
+
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct Request {
+  uint64_t ticket = 0;
+  pf_model m{};
+  int64_t P = 0;
+  int32_t T = 0;
+  double dt = 0.0;
+  Shape sh;
+  double theta[8] = {0};
+  std::vector<double> y;
+  uint64_t seed = 0;
+  size_t bytes = 0;
+  double t_submit = 0.0, t_done = 0.0;
+  // while running
+  int slot = -1;
+  bool fresh = false;
+  std::vector<void*> bufs;
+  FilterDev desc{};
+  // result
+  double ll = 0.0;
+  int status = PF_OK;
+};
+
+constexpr size_t ARENA_HALF = size_t(16) << 20;  // pinned staging per iteration parity
+
+}  // namespace
+
+struct pf_server {
+  size_t budget = 0;
+  int max_slots = 0;
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Request*> queue;
+  std::unordered_map<uint64_t, Request*> finished;
+  uint64_t next_ticket = 1;
+  int64_t n_running = 0, n_completed = 0, n_iter = 0;
+  bool stop = false;
+  std::thread thr;
+  // scheduler-owned
+  cudaStream_t st = nullptr;
+  cudaMemPool_t pool = nullptr;
+  std::vector<Request*> slots;
+  size_t used = 0;
+  FilterDev* d_fds = nullptr;
+  FilterDev* h_fds[2] = {nullptr, nullptr};
+  int2* d_tmap = nullptr;
+  int2* h_tmap[2] = {nullptr, nullptr};
+  size_t tmap_cap = 0;
+  double* d_res = nullptr;
+  double* h_res[2] = {nullptr, nullptr};
+  char* arena[2] = {nullptr, nullptr};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  bool ev_live[2] = {false, false};
+  std::vector<Request*> launched[2];  // requests in slots as of each in-flight iteration
+};
+
+namespace {
+
+bool alloc_request(pf_server* s, Request* r) {
+  auto get = [&](size_t n) -> void* {
+    if (n == 0) return nullptr;
+    void* p = nullptr;
+    if (cudaMallocFromPoolAsync(&p, n, s->pool, s->st) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    r->bufs.push_back(p);
+    return p;
+  };
+  const Shape& sh = r->sh;
+  const size_t xs = size_t(r->m.N) * size_t(r->P) * sh.state_bytes;
+  FilterDev& d = r->desc;
+  memset(&d, 0, sizeof d);
+  d.x[0] = get(xs);
+  d.x[1] = get(xs);
+  d.ctil = static_cast<double*>(get(size_t(r->P) * 8));
+  if (sh.mode != MODE_ALWAYS) {
+    d.ell = static_cast<double*>(get(size_t(r->P) * 8));
+    d.lam = static_cast<double*>(get(size_t(r->P) * 8));
+  }
+  d.anc = static_cast<int32_t*>(get(size_t(r->P) * 4));
+  double* flow = sh.nflow ? static_cast<double*>(get(size_t(sh.nflow) * 8)) : nullptr;
+  d.tp = static_cast<TilePart*>(get(size_t(sh.ntiles) * sizeof(TilePart)));
+  d.gp = static_cast<GroupPart*>(get(size_t(sh.ngroups) * sizeof(GroupPart)));
+  d.ctl = static_cast<Ctl*>(get(sizeof(Ctl)));
+  double* y = static_cast<double*>(get(r->y.size() * 8));
+  const bool ok = d.x[0] && d.x[1] && d.ctil && d.anc && d.tp && d.gp && d.ctl && y &&
+                  (sh.mode == MODE_ALWAYS || (d.ell && d.lam)) && (!sh.nflow || flow);
+  if (!ok) return false;
+  d.kind = r->m.kind;
+  d.N = r->m.N;
+  d.s = r->m.substeps;
+  d.stride = r->m.kind == PF_LORENZ96 ? r->m.obs_stride : 1;
+  d.prec = r->m.prec;
+  d.Ny = sh.Ny;
+  d.P = int32_t(r->P);
+  d.T = r->T;
+  d.ntiles = sh.ntiles;
+  d.ngroups = sh.ngroups;
+  d.mode = sh.mode;
+  d.obs_mask = sh.obs_mask;
+  d.dt = r->dt;
+  d.thr = r->m.ess_threshold;
+  d.seed = r->seed;
+  memcpy(d.theta, r->theta, sizeof d.theta);
+  d.flow = flow;
+  d.y = y;
+  cudaMemsetAsync(d.gp, 0, size_t(sh.ngroups) * sizeof(GroupPart), s->st);
+  cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), s->st);
+  if (flow) launch_flow(flow, sh.nflow, r->m.flow_peak, r->m.flow_period, r->dt, s->st);
+  return true;
+}
+
+void free_request_buffers(pf_server* s, Request* r) {
+  for (void* p : r->bufs) cudaFreeAsync(p, s->st);
+  r->bufs.clear();
+}
+
+void finish(pf_server* s, Request* r) {
+  r->t_done = now_s();
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->finished[r->ticket] = r;
+  s->n_completed += 1;
+  s->n_running -= 1;
+}
+
+// Wait for the iteration that used this parity, then retire the filters it
+// reported finished (degenerate, or past their last observation).
+void retire(pf_server* s, int parity) {
+  if (!s->ev_live[parity]) return;
+  cudaEventSynchronize(s->ev[parity]);
+  s->ev_live[parity] = false;
+  const double* res = s->h_res[parity];
+  for (Request* r : s->launched[parity]) {
+    const int k = r->slot;
+    if (k < 0 || s->slots[k] != r) continue;
+    const double ll = res[3 * k], stt = res[3 * k + 1], step = res[3 * k + 2];
+    if (stt != 0.0 || step > double(r->T)) {
+      r->ll = ll;
+      r->status = stt != 0.0 ? PF_EDEGENERATE : PF_OK;
+      free_request_buffers(s, r);
+      s->used -= r->bytes;
+      s->slots[k] = nullptr;
+      r->slot = -1;
+      finish(s, r);
+    }
+  }
+  s->launched[parity].clear();
+}
+
+void scheduler(pf_server* s) {
+  cudaSetDevice(s->device);
+  int parity = 0;
+  for (;;) {
+    // the pinned buffers of this parity were last used two iterations ago
+    retire(s, parity);
+    size_t arena_used = 0;
+    std::vector<Request*> admitted;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      bool any_running = false;
+      for (Request* r : s->slots) any_running = any_running || r;
+      if (!any_running && s->queue.empty() && !s->ev_live[0] && !s->ev_live[1]) {
+        if (s->stop) break;
+        s->cv.wait_for(lk, std::chrono::milliseconds(2));
+        continue;
+      }
+      while (!s->queue.empty()) {
+        Request* r = s->queue.front();
+        int free_slot = -1;
+        for (int k = 0; k < s->max_slots; ++k)
+          if (!s->slots[k]) {
+            free_slot = k;
+            break;
+          }
+        const size_t ybytes = (r->y.size() * 8 + 255) & ~size_t(255);
+        if (free_slot < 0 || s->used + r->bytes > s->budget || arena_used + ybytes > ARENA_HALF)
+          break;
+        s->queue.pop_front();
+        s->slots[free_slot] = r;
+        r->slot = free_slot;
+        s->used += r->bytes;
+        arena_used += ybytes;
+        s->n_running += 1;
+        admitted.push_back(r);
+      }
+    }
+    size_t aoff = 0;
+    for (Request* r : admitted) {
+      if (!alloc_request(s, r)) {
+        free_request_buffers(s, r);
+        s->used -= r->bytes;
+        s->slots[r->slot] = nullptr;
+        r->slot = -1;
+        r->status = PF_ENOMEM;
+        r->ll = 0.0;
+        finish(s, r);
+        continue;
+      }
+      char* stage = s->arena[parity] + aoff;
+      memcpy(stage, r->y.data(), r->y.size() * 8);
+      cudaMemcpyAsync(const_cast<double*>(r->desc.y), stage, r->y.size() * 8,
+                      cudaMemcpyHostToDevice, s->st);
+      aoff += (r->y.size() * 8 + 255) & ~size_t(255);
+      r->fresh = true;
+    }
+    // descriptors and tile map of this iteration:
+    // [running tiles by class | new tiles by class]
+    FilterDev* hf = s->h_fds[parity];
+    std::map<std::tuple<int, int, int>, std::vector<int2>> run_cls, new_cls;
+    for (int k = 0; k < s->max_slots; ++k) {
+      Request* r = s->slots[k];
+      if (!r) {
+        memset(&hf[k], 0, sizeof(FilterDev));
+        continue;
+      }
+      hf[k] = r->desc;
+      auto key = std::make_tuple(r->m.kind, r->m.N, r->m.prec);
+      for (int t = 0; t < r->sh.ntiles; ++t) {
+        run_cls[key].push_back(make_int2(k, t));
+        if (r->fresh) new_cls[key].push_back(make_int2(k, t));
+      }
+    }
+    size_t ntm = 0;
+    for (auto& kv : run_cls) ntm += kv.second.size();
+    for (auto& kv : new_cls) ntm += kv.second.size();
+    if (ntm == 0) {  // nothing running: drain the other parity and wait for work
+      retire(s, parity ^ 1);
+      continue;
+    }
+    if (ntm > s->tmap_cap) {  // grow the staging copies and the device map (rare)
+      cudaStreamSynchronize(s->st);
+      for (int q = 0; q < 2; ++q) {
+        if (s->h_tmap[q]) cudaFreeHost(s->h_tmap[q]);
+        s->h_tmap[q] = nullptr;
+        cudaMallocHost((void**)&s->h_tmap[q], sizeof(int2) * ntm * 2);
+      }
+      if (s->d_tmap) cudaFree(s->d_tmap);
+      s->d_tmap = nullptr;
+      cudaMalloc((void**)&s->d_tmap, sizeof(int2) * ntm * 2);
+      s->tmap_cap = ntm * 2;
+    }
+    int2* tm = s->h_tmap[parity];
+    struct Seg {
+      int kind, N, prec;
+      size_t off, n;
+    };
+    std::vector<Seg> run_seg, new_seg;
+    size_t off = 0;
+    for (auto& kv : run_cls) {
+      memcpy(tm + off, kv.second.data(), kv.second.size() * sizeof(int2));
+      run_seg.push_back({std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), off,
+                         kv.second.size()});
+      off += kv.second.size();
+    }
+    const size_t n_run = off;
+    for (auto& kv : new_cls) {
+      memcpy(tm + off, kv.second.data(), kv.second.size() * sizeof(int2));
+      new_seg.push_back({std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), off,
+                         kv.second.size()});
+      off += kv.second.size();
+    }
+    cudaMemcpyAsync(s->d_fds, hf, sizeof(FilterDev) * s->max_slots, cudaMemcpyHostToDevice, s->st);
+    cudaMemcpyAsync(s->d_tmap, tm, sizeof(int2) * off, cudaMemcpyHostToDevice, s->st);
+    for (const Seg& g : new_seg)
+      launch_init(g.kind, g.N, g.prec, s->d_fds, s->d_tmap + g.off, int(g.n), s->st);
+    for (const Seg& g : run_seg)
+      launch_propagate(g.kind, g.N, g.prec, s->d_fds, s->d_tmap + g.off, int(g.n), s->st);
+    launch_resample(s->d_fds, s->d_tmap, int(n_run), s->st);
+    double* dres = s->d_res + size_t(parity) * 3 * s->max_slots;
+    launch_results(s->d_fds, s->max_slots, dres, s->st);
+    cudaMemcpyAsync(s->h_res[parity], dres, sizeof(double) * 3 * s->max_slots,
+                    cudaMemcpyDeviceToHost, s->st);
+    cudaEventRecord(s->ev[parity], s->st);
+    s->ev_live[parity] = true;
+    for (Request* r : s->slots)
+      if (r) {
+        s->launched[parity].push_back(r);
+        r->fresh = false;
+      }
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->n_iter += 1;
+    }
+    parity ^= 1;
+  }
+}
+
+}  // namespace
+
+extern "C" pf_status pf_server_create(size_t device_mem_budget, int32_t max_slots,
+                                      pf_server** out) {
+  if (!out || max_slots < 1 || max_slots > 4096 || device_mem_budget == 0)
+    return fail(PF_EINVAL, "pf_server_create: bad arguments");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(PF_ECUDA, "no CUDA device");
+  }
+  pf_server* s = new pf_server();
+  s->budget = device_mem_budget;
+  s->max_slots = max_slots;
+  s->slots.assign(max_slots, nullptr);
+  cudaGetDevice(&s->device);
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof props);
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = s->device;
+  cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemPoolCreate(&s->pool, &props);
+  if (e == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_fds, sizeof(FilterDev) * max_slots);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&s->d_res, sizeof(double) * 6 * max_slots);
+  for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+    e = cudaMallocHost((void**)&s->h_fds[q], sizeof(FilterDev) * max_slots);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&s->h_res[q], sizeof(double) * 3 * max_slots);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&s->arena[q], ARENA_HALF);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev[q], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    pf_server_destroy(s);
+    return fail(PF_ECUDA, "server set-up: %s", cudaGetErrorString(e));
+  }
+  s->thr = std::thread(scheduler, s);
+  *out = s;
+  return PF_OK;
+}
+
+extern "C" pf_status pf_server_submit(pf_server* s, const pf_model* m, int64_t P, int32_t T,
+                                      double dt, const double* theta, const double* y,
+                                      uint64_t seed, uint64_t* ticket) {
+  if (!s || !theta || !y || !ticket) return fail(PF_EINVAL, "pf_server_submit: NULL argument");
+  Shape sh;
+  pf_status st = check_shape(m, P, T, dt, &sh);
+  if (st != PF_OK) return st;
+  const size_t need = pf_device_bytes(m, P, T, 0) + 256 * 16;
+  if (need > s->budget || size_t(T) * sh.Ny * 8 > ARENA_HALF)
+    return fail(PF_ENOMEM, "request needs %zu bytes, budget is %zu", need, s->budget);
+  Request* r = new Request();
+  r->m = *m;
+  r->P = P;
+  r->T = T;
+  r->dt = dt;
+  r->sh = sh;
+  memcpy(r->theta, theta, sizeof(double) * pf_theta_size(m->kind));
+  r->y.assign(y, y + size_t(T) * sh.Ny);
+  r->seed = seed;
+  r->bytes = need;
+  r->t_submit = now_s();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->ticket = s->next_ticket++;
+    s->queue.push_back(r);
+  }
+  s->cv.notify_one();
+  *ticket = r->ticket;
+  return PF_OK;
+}
+
+extern "C" pf_status pf_server_poll(pf_server* s, uint64_t ticket, double* loglik,
+                                    double* latency_s) {
+  if (!s) return fail(PF_EINVAL, "server is NULL");
+  Request* r = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->finished.find(ticket);
+    if (it == s->finished.end()) {
+      if (ticket == 0 || ticket >= s->next_ticket)
+        return fail(PF_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+      return PF_EBUSY;
+    }
+    r = it->second;
+    s->finished.erase(it);
+  }
+  if (loglik) *loglik = r->ll;
+  if (latency_s) *latency_s = r->t_done - r->t_submit;
+  const pf_status st = pf_status(r->status);
+  delete r;
+  return st;
+}
+
+extern "C" pf_status pf_server_stats(pf_server* s, int64_t* queued, int64_t* running,
+                                     int64_t* completed, int64_t* iterations) {
+  if (!s) return fail(PF_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (queued) *queued = int64_t(s->queue.size());
+  if (running) *running = s->n_running;
+  if (completed) *completed = s->n_completed;
+  if (iterations) *iterations = s->n_iter;
+  return PF_OK;
+}
+
+extern "C" pf_status pf_server_destroy(pf_server* s) {
+  if (!s) return PF_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    for (Request* r : s->queue) delete r;
+    s->queue.clear();
+  }
+  s->cv.notify_all();
+  if (s->thr.joinable()) s->thr.join();
+  if (s->st) cudaStreamSynchronize(s->st);
+  for (Request* r : s->slots)
+    if (r) {
+      free_request_buffers(s, r);
+      delete r;
+    }
+  for (auto& kv : s->finished) delete kv.second;
+  if (s->st) cudaStreamSynchronize(s->st);
+  if (s->d_fds) cudaFree(s->d_fds);
+  if (s->d_tmap) cudaFree(s->d_tmap);
+  if (s->d_res) cudaFree(s->d_res);
+  for (int q = 0; q < 2; ++q) {
+    if (s->h_fds[q]) cudaFreeHost(s->h_fds[q]);
+    if (s->h_tmap[q]) cudaFreeHost(s->h_tmap[q]);
+    if (s->h_res[q]) cudaFreeHost(s->h_res[q]);
+    if (s->arena[q]) cudaFreeHost(s->arena[q]);
+    if (s->ev[q]) cudaEventDestroy(s->ev[q]);
+  }
+  if (s->pool) cudaMemPoolDestroy(s->pool);
+  if (s->st) cudaStreamDestroy(s->st);
+  delete s;
+  return PF_OK;
+}
