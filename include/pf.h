@@ -157,6 +157,40 @@ pf_status pf_server_stats(pf_server* s, int64_t* queued, int64_t* running, int64
                           int64_t* iterations);
 pf_status pf_server_destroy(pf_server* s);
 
+/* ---- allocation-free run (no counterpart in the paper) ------------------- */
+
+/* Size of the fixed device array pf_run_noalloc works in: 32 MiB, reserved on
+ * every GPU that loads this library until the process exits. */
+#define PF_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* One run of the filter, exactly as pf_create + pf_run + pf_destroy would give
+ * (same kernels, same bits), for callers that cannot allocate device memory
+ * where they need a likelihood: code running while its own pool or arena
+ * holds the device budget, frameworks that forbid allocation on the hot path
+ * (an allocation may synchronise the device or fail under fragmentation), or
+ * real-time loops that must not enter the allocator.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine: every internal buffer is
+ * carved out of one fixed array of PF_NOALLOC_SCRATCH_BYTES.
+ *   m, P, T, dt   as for pf_create; a filter whose buffers do not fit in the
+ *                 array is rejected with PF_EINVAL and a message giving the
+ *                 bytes it needs (use pf_create/pf_run for it).
+ *   theta         device pointer, pf_theta_size(kind) doubles.
+ *   y             device pointer, [T][Ny] doubles (read during the run).
+ *   seed          as for pf_run.
+ *   loglik        device pointer, 1 double (out).
+ *   status        device pointer or NULL: 1 int32 (out), PF_OK or PF_EDEGENERATE.
+ *   final_particles device pointer or NULL: [N][P] in the state precision.
+ *   cuda_stream   stream to enqueue on (NULL: the legacy default stream).
+ * The call only enqueues work; outputs are valid once the stream reaches it.
+ * Every call on a device shares the one array, which keeps the previous
+ * call's contents (the run clears what must start at zero): calls that
+ * overlap on the GPU (different streams, or several host threads) race and
+ * must be serialised by the caller.  The first call on a device looks up the
+ * array's device address; make that first call before any stream capture. */
+pf_status pf_run_noalloc(const pf_model* m, int64_t P, int32_t T, double dt,
+                         const double* theta, const double* y, uint64_t seed, double* loglik,
+                         int32_t* status, void* final_particles, void* cuda_stream);
+
 /* ---- diagnostics (no counterpart in the paper) -------------------------- */
 
 /* Profiling mode: while enabled, pf_run launches the filter's kernels one by

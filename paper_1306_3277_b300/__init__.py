@@ -71,6 +71,10 @@ def lib():
         for name in ("pf_run", "pf_wait", "pf_destroy", "pf_create", "pf_batch_run",
                      "pf_profile_enable", "pf_profile_read", "pf_measure_fma_peak"):
             getattr(L, name).restype = ctypes.c_int
+        L.pf_run_noalloc.argtypes = [ctypes.POINTER(pf_model), ctypes.c_int64, ctypes.c_int32,
+                                     ctypes.c_double, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp,
+                                     _vp]
+        L.pf_run_noalloc.restype = ctypes.c_int
         if hasattr(L, "pf_server_create"):
             L.pf_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(_vp)]
             L.pf_server_submit.argtypes = [_vp, ctypes.POINTER(pf_model), ctypes.c_int64,
@@ -185,6 +189,20 @@ def pf_run(f, theta, y, seed, loglik, final_particles=None, ancestors=None, flag
     st = lib().pf_run(f.h, _ptr(theta), _ptr(y), ctypes.c_uint64(seed), _ptr(loglik),
                       _ptr(final_particles), _ptr(ancestors), flags, _stream_ptr(stream))
     return _check(st, ok=(PF_OK, PF_EDEGENERATE))
+
+
+PF_NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def pf_run_noalloc(m, P, T, dt, theta, y, seed, loglik, status=None, final_particles=None,
+                   stream=None):
+    """Allocation-free run: every array is a device pointer (torch CUDA tensor);
+    only enqueues on `stream`.  Raises PFError (PF_EINVAL) if the filter does not
+    fit in the library's fixed scratch array."""
+    st = lib().pf_run_noalloc(ctypes.byref(m), P, T, dt, _ptr(theta), _ptr(y),
+                              ctypes.c_uint64(seed), _ptr(loglik), _ptr(status),
+                              _ptr(final_particles), _stream_ptr(stream))
+    return _check(st)
 
 
 def pf_wait(f):
