@@ -272,6 +272,8 @@ struct BlockScratch {
   long long kmax[WARPS];
   double wsum[WARPS];
   double wsum2[WARPS];
+  double wpre[WARPS];
+  double wtot;
   int flag;
 };
 
@@ -306,7 +308,8 @@ __device__ __forceinline__ double block_sum(double v, BlockScratch& sm) {
 }
 
 // Canonical inclusive scan: Kogge-Stone inside each warp (shfl_up 1..16),
-// then the exclusive prefix of the warp totals added left to right.
+// then warp 0 scans the eight warp totals with a Kogge-Stone over lanes 0..7
+// (shfl_up 1, 2, 4) and every thread adds its warp's exclusive prefix.
 // Returns the thread's inclusive prefix; *total receives the block total.
 __device__ __forceinline__ double block_scan(double v, BlockScratch& sm, double* total) {
   const int lane = threadIdx.x & 31;
@@ -318,14 +321,20 @@ __device__ __forceinline__ double block_scan(double v, BlockScratch& sm, double*
   }
   if (lane == 31) sm.wsum[w] = v;
   __syncthreads();
-  double pre = 0.0;
-  for (int q = 0; q < w; ++q) pre = __dadd_rn(pre, sm.wsum[q]);
-  double tot = 0.0;
+  if (w == 0) {
+    double t = lane < WARPS ? sm.wsum[lane] : 0.0;
 #pragma unroll
-  for (int q = 0; q < WARPS; ++q) tot = __dadd_rn(tot, sm.wsum[q]);
+    for (int o = 1; o < WARPS; o <<= 1) {
+      const double n = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t = __dadd_rn(n, t);
+    }
+    const double ex = __shfl_up_sync(0xffffffffu, t, 1);
+    if (lane < WARPS) sm.wpre[lane] = lane == 0 ? 0.0 : ex;
+    if (lane == WARPS - 1) sm.wtot = t;
+  }
   __syncthreads();
-  *total = tot;
-  return w == 0 ? v : __dadd_rn(pre, v);
+  *total = sm.wtot;
+  return w == 0 ? v : __dadd_rn(sm.wpre[w], v);
 }
 
 // L2-coherent loads for data written by other blocks of the same launch.

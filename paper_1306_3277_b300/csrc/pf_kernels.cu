@@ -333,8 +333,16 @@ __global__ void __launch_bounds__(TILE) k_init(const FilterDev* __restrict__ fds
   }
 }
 
+// Blocks per SM the propagate kernel is compiled for: two wherever the state
+// fits in 128 registers per thread without spilling more than a few words
+// (every FP32 size, FP64 up to N = 12, the windkessel), else one.
 template <int KIND, int N, typename R>
-__global__ void __launch_bounds__(TILE) k_propagate(const FilterDev* __restrict__ fds,
+struct PropagateOccupancy {
+  static constexpr int value = (KIND == KIND_WK || sizeof(R) == 4 || N <= 12) ? 2 : 1;
+};
+
+template <int KIND, int N, typename R>
+__global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value)) k_propagate(const FilterDev* __restrict__ fds,
                                                     const int2* __restrict__ tmap) {
   __shared__ CombineScratch cs;
   __shared__ double ys[64];
