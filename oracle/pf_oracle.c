@@ -23,7 +23,12 @@
  *  - first propagation uses identity ancestors (all initial weights equal);
  *  - no resampling after the final observation;
  *  - the constant -Ny/2 log(2 pi r) of the Gaussian observation density is
- *    added to each likelihood increment, not to the particle log-weights.
+ *    added to each likelihood increment, not to the particle log-weights;
+ *  - the particle log-weight is the residual sum of squares (fma-accumulated
+ *    over the observed components in index order) times the per-run
+ *    constant cw = -0.5 / r;
+ *  - systematic targets (j + u) S / P are compared with the cumulative
+ *    weights in the scaled form C_k (P / S) - u > j.
  */
 #include "pf_oracle.h"
 
@@ -432,31 +437,36 @@ void or_lse(const double *ell, int64_t P, double *Mo, double *So, double *Qo) {
 
 /* ======================================================================
  * Systematic resampling (Sec. 3.3): cumulative weights C_k (compensated
- * inclusive prefix of w = exp(ell - M)), one uniform u, targets
- * tau_j = (j + u) (C_{P-1} / P), ancestor a_j = min{k : C_k > tau_j},
- * clamped to P-1.  Ancestors come out sorted.
+ * inclusive prefix of w = exp(ell - M)), total S = C_{P-1}, one uniform u.
+ * Target j (j = 0..P-1) sits at (j + u) S / P and takes the first particle
+ * whose cumulative weight exceeds it; the comparison is evaluated in the
+ * scaled form E_k = C_k (P / S) - u > j (ratio P / S and E_k each rounded
+ * once), so a_j = min{k : E_k > j}, clamped to P-1.  Ancestors come out
+ * sorted; particle k has offspring j in [ceil E_{k-1}, ceil E_k).
  * ==================================================================== */
 static int64_t or_systematic_from_w(const double *w, int64_t P, double u, int32_t *anc,
                                     double *Cbuf) {
-  double sum = 0.0, comp = 0.0, S, step;
+  double sum = 0.0, comp = 0.0, S, ratio;
   int64_t j, k, near = 0;
   for (k = 0; k < P; ++k) {
     or_neumaier_add(&sum, &comp, w[k]);
     Cbuf[k] = sum + comp;
   }
   S = Cbuf[P - 1];
-  step = S / (double)P;
+  ratio = (double)P / S;
+  for (k = 0; k < P; ++k) Cbuf[k] = Cbuf[k] * ratio - u; /* E_k */
   for (j = 0; j < P; ++j) {
-    double tau = ((double)j + u) * step;
-    int64_t lo = 0, hi = P; /* first k in [lo, hi) with C_k > tau */
+    const double tj = (double)j;
+    int64_t lo = 0, hi = P; /* first k in [lo, hi) with E_k > j */
     while (lo < hi) {
       int64_t mid = lo + (hi - lo) / 2;
-      if (Cbuf[mid] > tau) hi = mid;
+      if (Cbuf[mid] > tj) hi = mid;
       else lo = mid + 1;
     }
     k = lo < P ? lo : P - 1;
     anc[j] = (int32_t)k;
-    if (fabs(tau - Cbuf[k]) <= 1e-12 * S || (k > 0 && fabs(tau - Cbuf[k - 1]) <= 1e-12 * S))
+    if (fabs(tj - Cbuf[k]) <= 1e-12 * (double)P ||
+        (k > 0 && fabs(tj - Cbuf[k - 1]) <= 1e-12 * (double)P))
       ++near;
   }
   return near;
@@ -486,6 +496,7 @@ typedef struct {
   uint64_t seed;
   int32_t Ny;
   double r;
+  double cw; /* -0.5 / r: scale of the residual sum of squares */
 } or_ctx;
 
 /* FP64 path. */
@@ -521,7 +532,7 @@ static double or_prop_weight64(const or_ctx *cx, uint32_t j, int32_t i, double *
       acc = fma(d, d, acc);
     }
   }
-  return -0.5 * (acc / cx->r);
+  return acc * cx->cw;
 }
 
 /* Mixed path: FP32 state, RK4/Euler and noise; FP64 residuals and weight. */
@@ -561,7 +572,7 @@ static double or_prop_weight32(const or_ctx *cx, uint32_t j, int32_t i, float *x
       acc = fma(d, d, acc);
     }
   }
-  return -0.5 * (acc / cx->r);
+  return acc * cx->cw;
 }
 
 /* ======================================================================
@@ -628,6 +639,7 @@ int32_t or_pf_run(const or_model *m, const double *th, const double *y, uint64_t
   acur = (int32_t *)malloc(sizeof(int32_t) * (size_t)P);
 
   cx.m = m; cx.th = th; cx.flow = flow; cx.seed = seed; cx.Ny = Ny; cx.r = r;
+  cx.cw = -0.5 / r;
 
   /* initialisation (Algorithm 2, init lines) */
 #pragma omp parallel for schedule(static)

@@ -71,7 +71,7 @@ double or_kalman_windkessel(const or_model *m, const double *theta, const double
 /* --- resampling pieces -------------------------------------------------- */
 void or_lse(const double *ell, int64_t P, double *M, double *S, double *Q);
 /* systematic resampling from log-weights; returns the number of
- * near-boundary targets (|tau_j - C_k| <= 1e-12 * C_{P-1}) */
+ * near-boundary targets (|E_k - j| <= 1e-12 P, E_k = C_k P / S - u) */
 int64_t or_systematic(const double *ell, int64_t P, double u, int32_t *anc);
 
 /* --- the filter --------------------------------------------------------- */

@@ -58,9 +58,10 @@ struct alignas(16) Ctl {
   double L;              // log sum_j exp(lam_j) of the carried log-weights
   double M, S;           // max and scaled sum of the current step
   double u;              // resampling uniform of the current step
-  double step_size;      // S / P
+  double ratio;          // P / S (systematic targets compared in the scaled form)
   double c_obs;          // -Ny/2 log(2 pi r)
   double logP;           // log P
+  double cw;             // -0.5 / r: scale of the residual sum of squares
 };
 
 // Descriptor of one filter (device copy read by every kernel).

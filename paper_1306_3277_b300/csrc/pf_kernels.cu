@@ -10,8 +10,9 @@
 //                the last group combines the filter: max, scaled sums,
 //                likelihood increment, ESS test, resampling uniform.
 //   k_resample   per tile: cumulative weights C_k = base + scale * prefix,
-//                the systematic targets that fall in [base, next base), and a
-//                binary search of each target among the tile's C_k.
+//                each particle's count of systematic targets below C_k, and
+//                the targets between the tile's base and the next tile's
+//                written out by a binary search over those counts.
 // Any number of filters share a launch: the tile map lists (filter, tile)
 // pairs, and every reduction is per tile / group / filter in a fixed order,
 // so a filter's result does not depend on what else is in the launch.
@@ -96,10 +97,10 @@ template <> __device__ __forceinline__ float from_double<float>(double v) { retu
 
 // Windkessel: s Euler substeps x <- x + dt (F_k/C - x/(RC)) + sqrt(q) z_mm
 // (normal number mm of stream (j, i, PROP)), then log N(y; x + Z F(t_i), r)
-// without its constant.
+// without its constant: (y - x - Z F)^2 times cw = -0.5 / r.
 template <typename R>
 __device__ __forceinline__ double wk_prop_weight(const FilterDev& fd, uint32_t j, int i, R& xv,
-                                                 double yi) {
+                                                 double yi, double cw) {
   const int s = fd.s;
   const R Rr = from_double<R>(fd.theta[0]);
   const R Cc = from_double<R>(fd.theta[1]);
@@ -140,14 +141,14 @@ __device__ __forceinline__ double wk_prop_weight(const FilterDev& fd, uint32_t j
   const double h = fma(fd.theta[2], fd.flow[int64_t(i) * s], to_double(xv));
   const double d = yi - h;
   const double acc = fma(d, d, 0.0);
-  return -0.5 * (acc / fd.theta[4]);
+  return acc * cw;
 }
 
 // Lorenz '96: s RK4 substeps, additive sqrt(q) z_n on every component, then
 // sum over observed components of (y - x_n)^2 accumulated by fma in FP64.
 template <int N, typename R>
 __device__ __forceinline__ double l96_prop_weight(const FilterDev& fd, uint32_t j, int i,
-                                                  R (&x)[N], const double* ys) {
+                                                  R (&x)[N], const double* ys, double cw) {
   const R F = from_double<R>(fd.theta[0]);
   const R dt = from_double<R>(fd.dt);
   const R h2 = R(0.5) * dt, h3 = dt / R(3.0), h6 = dt / R(6.0);
@@ -170,7 +171,7 @@ __device__ __forceinline__ double l96_prop_weight(const FilterDev& fd, uint32_t 
       ++k;
     }
   }
-  return -0.5 * (acc / fd.theta[2]);
+  return acc * cw;
 }
 
 // ---------------------------------------------------------------------------
@@ -271,7 +272,7 @@ __device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs) {
       if (resample) {
         const uint4 w = rng_block(fd.seed, 0u, uint32_t(i), PURPOSE_RESAMPLE, 0u);
         c->u = u53_closed_open(w.x, w.y);
-        c->step_size = S / double(fd.P);
+        c->ratio = double(fd.P) / S;
         c->rs_flag = 1;
         c->anc_identity = 0;
         c->lam_zero = 1;
@@ -326,10 +327,11 @@ __global__ void __launch_bounds__(TILE) k_init(const FilterDev* __restrict__ fds
     c->logP = log(double(P));
     c->L = c->logP;
     c->c_obs = -0.5 * double(fd.Ny) * log(2.0 * 3.141592653589793 * r);
+    c->cw = -0.5 / r;
     c->M = 0.0;
     c->S = 0.0;
     c->u = 0.0;
-    c->step_size = 0.0;
+    c->ratio = 0.0;
   }
 }
 
@@ -353,6 +355,7 @@ __global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value))
   if (i > fd.T || ldcg(&ctl->status) != ST_OK) return;
   const int anc_identity = ldcg(&ctl->anc_identity);
   const int lam_zero = ldcg(&ctl->lam_zero);
+  const double cw = ldcg(&ctl->cw);
   const int P = fd.P;
   const int t = ft.y;
   const int tid = threadIdx.x;
@@ -369,13 +372,13 @@ __global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value))
     double lw;
     if constexpr (KIND == KIND_WK) {
       R xv = xin[a];
-      lw = wk_prop_weight<R>(fd, uint32_t(j), i, xv, ys[0]);
+      lw = wk_prop_weight<R>(fd, uint32_t(j), i, xv, ys[0], cw);
       xout[j] = xv;
     } else {
       R x[N];
 #pragma unroll
       for (int n = 0; n < N; ++n) x[n] = xin[int64_t(n) * P + a];
-      lw = l96_prop_weight<N, R>(fd, uint32_t(j), i, x, ys);
+      lw = l96_prop_weight<N, R>(fd, uint32_t(j), i, x, ys, cw);
 #pragma unroll
       for (int n = 0; n < N; ++n) xout[int64_t(n) * P + j] = x[n];
     }
@@ -410,21 +413,27 @@ __global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value))
   if (combine_group(fd, t / GROUP, cs)) combine_filter(fd, i, cs);
 }
 
-// Smallest j in [0, P] with (j + u) * step >= b (the first systematic target
-// at or above b).  Start from the closed-form guess and correct it by exact
-// comparisons with the same expression the search uses; bounded loops.
-__device__ __forceinline__ int first_target(double b, double u, double step, int P) {
-  if (!(b > 0.0)) return 0;
-  double guess = ceil(b / step - u);
-  int jj = guess < 0.0 ? 0 : (guess > double(P) ? P : int(guess));
-  for (int it = 0; it < 64 && jj > 0 && (double(jj - 1) + u) * step >= b; ++it) --jj;
-  for (int it = 0; it < 64 && jj < P && (double(jj) + u) * step < b; ++it) ++jj;
-  return jj;
+// Number of systematic targets j in [0, P) below cumulative weight b: target
+// j sits at (j + u) S / P, compared in the scaled form j < b (P / S) - u, so
+// the count is ceil(b ratio - u) clamped to [0, P].
+__device__ __forceinline__ int targets_below(double b, double ratio, double u, int P) {
+  const double e = b * ratio - u;
+  if (!(e > 0.0)) return 0;
+  if (e >= double(P)) return P;
+  return __double2int_ru(e);
 }
 
+// Systematic resampling of one tile.  Its particles k have cumulative weights
+// C_k = base + scale * prefix_k; the tile owns the targets [lo, hi) between
+// its base and the next tile's base (both counts computed from the same
+// values in the two tiles), particle k takes the targets [n_{k-1}, n_k) with
+// n_k = targets_below(C_k) clamped to [lo, hi] (the last particle takes the
+// rest), and the targets are written out by a binary search over n.  Only
+// the per-particle counts use FP64; the per-target work is integer.
 __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__ fds,
                                                    const int2* __restrict__ tmap) {
-  __shared__ long long ck[TILE];
+  __shared__ int nk[TILE];
+  __shared__ int range[2];
   const int2 ft = tmap[blockIdx.x];
   const FilterDev& fd = fds[ft.x];
   const Ctl* ctl = fd.ctl;
@@ -445,29 +454,36 @@ __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__
   const int g = t / GROUP;
   const double base = fma(fd.gp[g].G, fd.tp[t].base, fd.gp[g].B);
   const double scale = fd.gp[g].G * fd.tp[t].g;
-  double nb;
-  if (t + 1 < fd.ntiles) {
-    const int g1 = (t + 1) / GROUP;
-    nb = fma(fd.gp[g1].G, fd.tp[t + 1].base, fd.gp[g1].B);
-  } else {
-    nb = ldcg(&ctl->S);
-  }
-  const int nvalid = min(TILE, P - j0);
-  if (tid < nvalid) ck[tid] = __double_as_longlong(fma(scale, fd.ctil[j0 + tid], base));
   const double u = ldcg(&ctl->u);
-  const double step = ldcg(&ctl->step_size);
-  const int jlo = first_target(base, u, step, P);
-  const int jhi = first_target(nb, u, step, P);
+  const double ratio = ldcg(&ctl->ratio);
+  if (tid == 0) range[0] = targets_below(base, ratio, u, P);
+  if (tid == 32) {
+    double nb;
+    if (t + 1 < fd.ntiles) {
+      const int g1 = (t + 1) / GROUP;
+      nb = fma(fd.gp[g1].G, fd.tp[t + 1].base, fd.gp[g1].B);
+    } else {
+      nb = ldcg(&ctl->S);
+    }
+    range[1] = targets_below(nb, ratio, u, P);
+  }
+  __syncthreads();
+  const int lo = range[0];
+  const int hi = range[1];
+  const int nvalid = min(TILE, P - j0);
+  if (tid < nvalid) {
+    int n = targets_below(fma(scale, fd.ctil[j0 + tid], base), ratio, u, P);
+    n = min(max(n, lo), hi);
+    nk[tid] = tid == nvalid - 1 ? hi : n;
+  }
   __syncthreads();
   int32_t* aout = fd.anc + (fd.hist ? int64_t(i) * P : 0);
-  for (int jj = jlo + tid; jj < jhi; jj += TILE) {
-    const double tau = (double(jj) + u) * step;
-    const long long key = __double_as_longlong(tau);
-    int pos = 0;  // number of C_k <= tau, i.e. the first k with C_k > tau
+  for (int jj = lo + tid; jj < hi; jj += TILE) {
+    int pos = 0;  // number of particles whose targets all lie below jj
 #pragma unroll
     for (int half = TILE / 2; half > 0; half >>= 1)
-      if (pos + half <= nvalid && ck[pos + half - 1] <= key) pos += half;
-    aout[jj] = j0 + (pos < nvalid ? pos : nvalid - 1);
+      if (pos + half <= nvalid && nk[pos + half - 1] <= jj) pos += half;
+    aout[jj] = j0 + pos;
   }
 }
 
