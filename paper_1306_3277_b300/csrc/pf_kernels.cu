@@ -11,8 +11,8 @@
 //                likelihood increment, ESS test, resampling uniform.
 //   k_resample   per tile: cumulative weights C_k = base + scale * prefix,
 //                each particle's count of systematic targets below C_k, and
-//                the targets between the tile's base and the next tile's
-//                written out by a binary search over those counts.
+//                each particle's offspring range written out (long ranges
+//                by the whole block).
 // Any number of filters share a launch: the tile map lists (filter, tile)
 // pairs, and every reduction is per tile / group / filter in a fixed order,
 // so a filter's result does not depend on what else is in the launch.
@@ -426,14 +426,20 @@ __device__ __forceinline__ int targets_below(double b, double ratio, double u, i
 // Systematic resampling of one tile.  Its particles k have cumulative weights
 // C_k = base + scale * prefix_k; the tile owns the targets [lo, hi) between
 // its base and the next tile's base (both counts computed from the same
-// values in the two tiles), particle k takes the targets [n_{k-1}, n_k) with
-// n_k = targets_below(C_k) clamped to [lo, hi] (the last particle takes the
-// rest), and the targets are written out by a binary search over n.  Only
-// the per-particle counts use FP64; the per-target work is integer.
+// values in the two tiles), and particle k takes the targets [n_{k-1}, n_k)
+// with n_k = targets_below(C_k) clamped to [lo, hi] (the last particle takes
+// the rest).  Each particle writes its own offspring range; ranges longer
+// than SHORT_RANGE are queued and written by the whole block, so a tile that
+// owns most of the targets still writes them with coalesced stores.  Only
+// the per-particle counts use FP64.
+constexpr int SHORT_RANGE = 16;
+
 __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__ fds,
                                                    const int2* __restrict__ tmap) {
   __shared__ int nk[TILE];
   __shared__ int range[2];
+  __shared__ int nlong;
+  __shared__ int longk[TILE];
   const int2 ft = tmap[blockIdx.x];
   const FilterDev& fd = fds[ft.x];
   const Ctl* ctl = fd.ctl;
@@ -456,7 +462,10 @@ __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__
   const double scale = fd.gp[g].G * fd.tp[t].g;
   const double u = ldcg(&ctl->u);
   const double ratio = ldcg(&ctl->ratio);
-  if (tid == 0) range[0] = targets_below(base, ratio, u, P);
+  if (tid == 0) {
+    range[0] = targets_below(base, ratio, u, P);
+    nlong = 0;
+  }
   if (tid == 32) {
     double nb;
     if (t + 1 < fd.ntiles) {
@@ -478,12 +487,22 @@ __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__
   }
   __syncthreads();
   int32_t* aout = fd.anc + (fd.hist ? int64_t(i) * P : 0);
-  for (int jj = lo + tid; jj < hi; jj += TILE) {
-    int pos = 0;  // number of particles whose targets all lie below jj
-#pragma unroll
-    for (int half = TILE / 2; half > 0; half >>= 1)
-      if (pos + half <= nvalid && nk[pos + half - 1] <= jj) pos += half;
-    aout[jj] = j0 + pos;
+  if (tid < nvalid) {
+    const int a = tid == 0 ? lo : nk[tid - 1];
+    const int b = nk[tid];
+    if (b - a <= SHORT_RANGE) {
+      for (int jj = a; jj < b; ++jj) aout[jj] = j0 + tid;
+    } else {
+      longk[atomicAdd(&nlong, 1)] = tid;
+    }
+  }
+  __syncthreads();
+  const int nl = nlong;
+  for (int q = 0; q < nl; ++q) {
+    const int k = longk[q];
+    const int a = k == 0 ? lo : nk[k - 1];
+    const int b = nk[k];
+    for (int jj = a + tid; jj < b; jj += TILE) aout[jj] = j0 + k;
   }
 }
 
