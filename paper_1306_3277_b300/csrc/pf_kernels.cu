@@ -90,7 +90,18 @@ __device__ __forceinline__ void normals(float (&z)[N], uint64_t seed, uint32_t j
 }
 
 __device__ __forceinline__ double to_double(double v) { return v; }
-__device__ __forceinline__ double to_double(float v) { return double(v); }
+// Exact float -> double for finite normal floats built with integer ops
+// (rebias the exponent, shift the mantissa), leaving the FP64 unit, which
+// B300 runs at 1/64 of the FP32 rate, to the weight arithmetic itself; zero,
+// subnormal, infinite and NaN inputs take the ordinary conversion.
+__device__ __forceinline__ double to_double(float v) {
+  const unsigned b = __float_as_uint(v);
+  const unsigned e = b & 0x7f800000u;
+  if (e == 0u || e == 0x7f800000u) return double(v);
+  const unsigned hi = (b & 0x80000000u) | (((e >> 23) + 896u) << 20) | ((b & 0x007fffffu) >> 3);
+  const unsigned lo = (b & 7u) << 29;
+  return __hiloint2double(int(hi), int(lo));
+}
 template <typename R> __device__ __forceinline__ R from_double(double v);
 template <> __device__ __forceinline__ double from_double<double>(double v) { return v; }
 template <> __device__ __forceinline__ float from_double<float>(double v) { return __double2float_rn(v); }
