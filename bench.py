@@ -179,6 +179,21 @@ def cores():
     return len(os.sched_getaffinity(0))
 
 
+def max_over_ranks(x, dist=None, device=None):
+    """The largest of every rank's value (the whole job ends with its slowest rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def whole_job_rate(units_per_rank, world, elapsed_s):
+    """Units all ranks processed per second of the slowest rank (weak scaling)."""
+    return units_per_rank * world / elapsed_s
+
+
 def dtype_name(w):
     return "f64" if w.prec == W.FP64 else "f32 state / f64 weights"
 
@@ -347,13 +362,10 @@ def main():
     pf.pf_profile_enable(f, False)
     status = pf.pf_wait(f)
     loglik = ll.item()
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = t.item()
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, dev)
 
     psteps_rank = w.P * w.T * args.steps
-    value = psteps_rank * world / (elapsed_ms * 1e-3)
+    value = whole_job_rate(psteps_rank, world, elapsed_ms * 1e-3)
     launches = sum(n for _, n in prof.values())
 
     # e2e: the public call with host buffers (H2D of theta and y, D2H of the result)
@@ -365,12 +377,8 @@ def main():
     t0 = time.perf_counter()
     for k in range(args.steps):
         f.run(th_h, y_h, seed0 + 200 + k)
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = t.item()
-    e2e_value = psteps_rank * world / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e_value = whole_job_rate(psteps_rank, world, e2e_s)
 
     if rank == 0:
         peaks, peak_src = measured_peaks()
