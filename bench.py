@@ -286,6 +286,106 @@ def secondary(pf, torch, dev):
     return out
 
 
+def run_serving(args):
+    """Continuous-batching server under Poisson arrivals: a rate sweep with
+    goodput and p50/p99 latency per offered rate, and the plain form (one
+    pf_run per request, back to back) on a sample of the same requests."""
+    import torch
+    import paper_1306_3277_b300 as pf
+    torch.cuda.set_device(0)
+    rates = [float(r) for r in args.rates.split(",")]
+    sweep = []
+    for rate in rates:
+        n = max(1, int(rate * args.duration))
+        reqs = W.serving_requests(n, rate, seed=int(rate))
+        srv = pf.pf_server_create(int(args.budget_gb * (1 << 30)), args.slots)
+        pending = {}
+        lat, done_ll = [], 0
+        psteps_done = 0
+        t0 = time.perf_counter()
+        k = 0
+        while k < len(reqs) or pending:
+            now = time.perf_counter() - t0
+            while k < len(reqs) and reqs[k][0] <= now:
+                w = reqs[k][1]
+                t = srv.submit(pf.model_from_workload(w), w.P, w.T, w.dt, w.theta, w.y, w.seed)
+                pending[t] = w
+                k += 1
+            for t in list(pending):
+                r = srv.poll(t)
+                if r is not None:
+                    w = pending.pop(t)
+                    lat.append(r[2])
+                    psteps_done += w.P * w.T
+                    done_ll += 1
+            if now > args.duration + args.drain:
+                break
+            time.sleep(0.0005)
+        elapsed = time.perf_counter() - t0
+        st = srv.stats()
+        srv.destroy()
+        lat.sort()
+        q = (lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None)
+        sweep.append({"offered_per_s": rate, "submitted": k, "completed": len(lat),
+                      "unfinished": len(pending), "goodput_per_s": len(lat) / elapsed,
+                      "particle_steps_per_s": psteps_done / elapsed,
+                      "p50_s": q(0.5), "p99_s": q(0.99), "elapsed_s": elapsed,
+                      "iterations": st["iterations"]})
+        print(json.dumps({"rate": rate, **sweep[-1]}), file=sys.stderr, flush=True)
+    # plain form: the same kind of requests one pf_run at a time
+    reqs = W.serving_requests(args.plain_sample, 100.0, seed=7)
+    fs = [(pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt), w) for _, w in reqs]
+    for f, w in fs[:3]:
+        f.run(w.theta, w.y, w.seed)
+    t0 = time.perf_counter()
+    for f, w in fs:
+        f.run(w.theta, w.y, w.seed)
+    tp = time.perf_counter() - t0
+    for f, _ in fs:
+        f.destroy()
+    best = max(sweep, key=lambda d: d["goodput_per_s"])
+    out = {"metric": "requests/s (goodput) and p50/p99 latency", "value": best["goodput_per_s"],
+           "unit": "requests/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 state / f64 weights", "data": "synthetic",
+           "config": {"workload": "serving: Poisson arrivals, models windkessel / L96 N=8 / "
+                                  "L96 N=40, P=2^U{10..16}, T~U{50..1000}",
+                      "slots": args.slots, "budget_gb": args.budget_gb,
+                      "duration_s": args.duration, "drain_s": args.drain},
+           "sweep": sweep,
+           "plain_one_run_at_a_time": {"requests": len(fs), "requests_per_s": len(fs) / tp,
+                                       "note": "same request mix, one pf_run per request"}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_precision(args):
+    """Mixed (FP32 state, FP64 weights) minus FP64 log-likelihood on the same
+    seeds, per configuration: mean and standard error over seeds."""
+    import torch
+    import paper_1306_3277_b300 as pf
+    torch.cuda.set_device(0)
+    cfgs = [("windkessel_P1024_T100", lambda p: W.windkessel(prec=p), args.seeds),
+            ("lorenz96_N8_P16384_T200", lambda p: W.lorenz96_8(prec=p), args.seeds),
+            ("lorenz96_N40_P65536_T100", lambda p: W.lorenz96_large(P=1 << 16, T=100, prec=p),
+             max(8, args.seeds // 4))]
+    res = {}
+    for name, make, nseed in cfgs:
+        out = {}
+        for prec in (W.FP64, W.MIXED):
+            w = make(prec)
+            f = pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt)
+            out[prec] = np.array([f.run(w.theta, w.y, s + 1)[1] for s in range(nseed)])
+            f.destroy()
+        d = out[W.MIXED] - out[W.FP64]
+        res[name] = {"seeds": nseed, "mean_mixed_minus_fp64": float(d.mean()),
+                     "se": float(d.std(ddof=1) / np.sqrt(nseed)),
+                     "sd_fp64_over_seeds": float(out[W.FP64].std(ddof=1)),
+                     "mean_fp64": float(out[W.FP64].mean())}
+    print(json.dumps({"metric": "loglik(mixed) - loglik(fp64), same seeds", "results": res}),
+          flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__,
                                  formatter_class=argparse.RawTextHelpFormatter)
@@ -294,7 +394,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="large",
-                    choices=["large", "l96_8", "l96_8_fp64", "windkessel"])
+                    choices=["large", "l96_8", "l96_8_fp64", "windkessel", "serving",
+                             "precision"])
+    ap.add_argument("--rates", default="250,500,1000,1500,2000", help="serving: offered rates")
+    ap.add_argument("--duration", type=float, default=4.0, help="serving: seconds of arrivals")
+    ap.add_argument("--drain", type=float, default=20.0, help="serving: extra seconds to finish")
+    ap.add_argument("--slots", type=int, default=64, help="serving: concurrent filters")
+    ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: device memory budget")
+    ap.add_argument("--plain-sample", type=int, default=60, help="serving: plain-form sample")
+    ap.add_argument("--seeds", type=int, default=64, help="precision: seeds per configuration")
     ap.add_argument("--P", type=int, default=0, help="override the particle count")
     ap.add_argument("--T", type=int, default=0, help="override the observation count")
     ap.add_argument("--no-secondary", action="store_true")
@@ -304,6 +412,10 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "serving":
+        return run_serving(args)
+    if args.config == "precision":
+        return run_precision(args)
     args.warmup = max(args.warmup, 3)
 
     import torch
