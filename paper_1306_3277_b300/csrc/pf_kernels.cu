@@ -106,12 +106,10 @@ template <typename R> __device__ __forceinline__ R from_double(double v);
 template <> __device__ __forceinline__ double from_double<double>(double v) { return v; }
 template <> __device__ __forceinline__ float from_double<float>(double v) { return __double2float_rn(v); }
 
-// Windkessel: s Euler substeps x <- x + dt (F_k/C - x/(RC)) + sqrt(q) z_mm
-// (normal number mm of stream (j, i, PROP)), then log N(y; x + Z F(t_i), r)
-// without its constant: (y - x - Z F)^2 times cw = -0.5 / r.
+// Windkessel propagation: s Euler substeps x <- x + dt (F_k/C - x/(RC)) +
+// sqrt(q) z_mm (normal number mm of stream (j, i, PROP)).
 template <typename R>
-__device__ __forceinline__ double wk_prop_weight(const FilterDev& fd, uint32_t j, int i, R& xv,
-                                                 double yi, double cw) {
+__device__ __forceinline__ void wk_propagate(const FilterDev& fd, uint32_t j, int i, R& xv) {
   const int s = fd.s;
   const R Rr = from_double<R>(fd.theta[0]);
   const R Cc = from_double<R>(fd.theta[1]);
@@ -149,17 +147,23 @@ __device__ __forceinline__ double wk_prop_weight(const FilterDev& fd, uint32_t j
       }
     }
   }
-  const double h = fma(fd.theta[2], fd.flow[int64_t(i) * s], to_double(xv));
+}
+
+// Windkessel weight: log N(y; x + Z F(t_i), r) without its constant,
+// (y - x - Z F)^2 times cw = -0.5 / r.
+template <typename R>
+__device__ __forceinline__ double wk_weight(const FilterDev& fd, int i, R xv, double yi,
+                                            double cw) {
+  const double h = fma(fd.theta[2], fd.flow[int64_t(i) * fd.s], to_double(xv));
   const double d = yi - h;
   const double acc = fma(d, d, 0.0);
   return acc * cw;
 }
 
-// Lorenz '96: s RK4 substeps, additive sqrt(q) z_n on every component, then
-// sum over observed components of (y - x_n)^2 accumulated by fma in FP64.
+// Lorenz '96 propagation: s RK4 substeps, then additive sqrt(q) z_n on every
+// component.
 template <int N, typename R>
-__device__ __forceinline__ double l96_prop_weight(const FilterDev& fd, uint32_t j, int i,
-                                                  R (&x)[N], const double* ys, double cw) {
+__device__ __forceinline__ void l96_propagate(const FilterDev& fd, uint32_t j, int i, R (&x)[N]) {
   const R F = from_double<R>(fd.theta[0]);
   const R dt = from_double<R>(fd.dt);
   const R h2 = R(0.5) * dt, h3 = dt / R(3.0), h6 = dt / R(6.0);
@@ -171,6 +175,13 @@ __device__ __forceinline__ double l96_prop_weight(const FilterDev& fd, uint32_t 
 #pragma unroll
     for (int n = 0; n < N; ++n) x[n] = fmaR(sx, z[n], x[n]);
   }
+}
+
+// Lorenz '96 weight: sum over observed components (index order) of
+// (y - x_n)^2 accumulated by fma in FP64, times cw = -0.5 / r.
+template <int N, typename R>
+__device__ __forceinline__ double l96_weight(const FilterDev& fd, const R (&x)[N],
+                                             const double* ys, double cw) {
   const uint64_t mask = fd.obs_mask;
   double acc = 0.0;
   int k = 0;
@@ -362,37 +373,39 @@ __global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value))
   const int2 ft = tmap[blockIdx.x];
   const FilterDev& fd = fds[ft.x];
   Ctl* ctl = fd.ctl;
+  const int P = fd.P;
+  const int t = ft.y;
+  const int tid = threadIdx.x;
+  const int j = t * TILE + tid;
+  const bool valid = j < P;
+  // issued before the control block is read (without a history the ancestor
+  // row does not depend on the step), so the two loads overlap
+  const int a_spec = (valid && !fd.hist) ? fd.anc[j] : j;
   const int i = ldcg(&ctl->step);
   if (i > fd.T || ldcg(&ctl->status) != ST_OK) return;
   const int anc_identity = ldcg(&ctl->anc_identity);
   const int lam_zero = ldcg(&ctl->lam_zero);
   const double cw = ldcg(&ctl->cw);
-  const int P = fd.P;
-  const int t = ft.y;
-  const int tid = threadIdx.x;
-  const int j = t * TILE + tid;
-  if (tid < fd.Ny) ys[tid] = fd.y[int64_t(i - 1) * fd.Ny + tid];
-  __syncthreads();
+  if (tid < fd.Ny) ys[tid] = fd.y[int64_t(i - 1) * fd.Ny + tid];  // read after the barrier below
 
-  double ell = -INFINITY;
-  if (j < P) {
-    int a = j;
-    if (!anc_identity) a = fd.anc[(fd.hist ? int64_t(i - 1) * P : 0) + j];
+  R x[N];
+  if (valid) {
+    const int a = anc_identity ? j : (fd.hist ? fd.anc[int64_t(i - 1) * P + j] : a_spec);
     const R* xin = static_cast<const R*>(fd.x[(i - 1) & 1]);
     R* xout = static_cast<R*>(fd.x[i & 1]);
+#pragma unroll
+    for (int n = 0; n < N; ++n) x[n] = xin[int64_t(n) * P + a];
+    if constexpr (KIND == KIND_WK) wk_propagate<R>(fd, uint32_t(j), i, x[0]);
+    else l96_propagate<N, R>(fd, uint32_t(j), i, x);
+#pragma unroll
+    for (int n = 0; n < N; ++n) xout[int64_t(n) * P + j] = x[n];
+  }
+  __syncthreads();  // observation row staged
+  double ell = -INFINITY;
+  if (valid) {
     double lw;
-    if constexpr (KIND == KIND_WK) {
-      R xv = xin[a];
-      lw = wk_prop_weight<R>(fd, uint32_t(j), i, xv, ys[0], cw);
-      xout[j] = xv;
-    } else {
-      R x[N];
-#pragma unroll
-      for (int n = 0; n < N; ++n) x[n] = xin[int64_t(n) * P + a];
-      lw = l96_prop_weight<N, R>(fd, uint32_t(j), i, x, ys, cw);
-#pragma unroll
-      for (int n = 0; n < N; ++n) xout[int64_t(n) * P + j] = x[n];
-    }
+    if constexpr (KIND == KIND_WK) lw = wk_weight<R>(fd, i, x[0], ys[0], cw);
+    else lw = l96_weight<N, R>(fd, x, ys, cw);
     double e = lam_zero ? lw : fd.lam[j] + lw;
     if (e != e) e = -INFINITY;
     ell = e;
@@ -454,12 +467,16 @@ __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__
   const int2 ft = tmap[blockIdx.x];
   const FilterDev& fd = fds[ft.x];
   const Ctl* ctl = fd.ctl;
-  const int i = ldcg(&ctl->rs_step);
-  if (ldcg(&ctl->status) != ST_OK || i < 1 || i >= fd.T || ldcg(&ctl->step) != i + 1) return;
   const int P = fd.P;
   const int t = ft.y;
   const int tid = threadIdx.x;
   const int j0 = t * TILE;
+  const int g = t / GROUP;
+  // the tile's inputs are independent of the control block: issue them first
+  const double ct = j0 + tid < P ? fd.ctil[j0 + tid] : 0.0;
+  const double gG = fd.gp[g].G, gB = fd.gp[g].B, tbase = fd.tp[t].base, tg = fd.tp[t].g;
+  const int i = ldcg(&ctl->rs_step);
+  if (ldcg(&ctl->status) != ST_OK || i < 1 || i >= fd.T || ldcg(&ctl->step) != i + 1) return;
   if (!ldcg(&ctl->rs_flag)) {
     const int j = j0 + tid;
     if (j < P && fd.mode != MODE_ALWAYS) {
@@ -468,9 +485,8 @@ __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__
     }
     return;
   }
-  const int g = t / GROUP;
-  const double base = fma(fd.gp[g].G, fd.tp[t].base, fd.gp[g].B);
-  const double scale = fd.gp[g].G * fd.tp[t].g;
+  const double base = fma(gG, tbase, gB);
+  const double scale = gG * tg;
   const double u = ldcg(&ctl->u);
   const double ratio = ldcg(&ctl->ratio);
   if (tid == 0) {
@@ -492,7 +508,7 @@ __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__
   const int hi = range[1];
   const int nvalid = min(TILE, P - j0);
   if (tid < nvalid) {
-    int n = targets_below(fma(scale, fd.ctil[j0 + tid], base), ratio, u, P);
+    int n = targets_below(fma(scale, ct, base), ratio, u, P);
     n = min(max(n, lo), hi);
     nk[tid] = tid == nvalid - 1 ? hi : n;
   }
