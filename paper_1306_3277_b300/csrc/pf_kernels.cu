@@ -381,11 +381,23 @@ __global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value))
   // issued before the control block is read (without a history the ancestor
   // row does not depend on the step), so the two loads overlap
   const int a_spec = (valid && !fd.hist) ? fd.anc[j] : j;
-  const int i = ldcg(&ctl->step);
-  if (i > fd.T || ldcg(&ctl->status) != ST_OK) return;
-  const int anc_identity = ldcg(&ctl->anc_identity);
-  const int lam_zero = ldcg(&ctl->lam_zero);
-  const double cw = ldcg(&ctl->cw);
+  // one thread reads the control block (written by the previous launch) and
+  // shares it: every thread reading it would queue on one L2 line
+  __shared__ int s_step, s_ok, s_anc_identity, s_lam_zero;
+  __shared__ double s_cw;
+  if (tid == 0) {
+    s_step = ldcg(&ctl->step);
+    s_ok = ldcg(&ctl->status) == ST_OK;
+    s_anc_identity = ldcg(&ctl->anc_identity);
+    s_lam_zero = ldcg(&ctl->lam_zero);
+    s_cw = ldcg(&ctl->cw);
+  }
+  __syncthreads();
+  const int i = s_step;
+  if (i > fd.T || !s_ok) return;
+  const int anc_identity = s_anc_identity;
+  const int lam_zero = s_lam_zero;
+  const double cw = s_cw;
   if (tid < fd.Ny) ys[tid] = fd.y[int64_t(i - 1) * fd.Ny + tid];  // read after the barrier below
 
   R x[N];
@@ -475,20 +487,34 @@ __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__
   // the tile's inputs are independent of the control block: issue them first
   const double ct = j0 + tid < P ? fd.ctil[j0 + tid] : 0.0;
   const double gG = fd.gp[g].G, gB = fd.gp[g].B, tbase = fd.tp[t].base, tg = fd.tp[t].g;
-  const int i = ldcg(&ctl->rs_step);
-  if (ldcg(&ctl->status) != ST_OK || i < 1 || i >= fd.T || ldcg(&ctl->step) != i + 1) return;
-  if (!ldcg(&ctl->rs_flag)) {
+  // one thread reads the control block and shares it (see k_propagate)
+  __shared__ int s_i, s_go, s_flag;
+  __shared__ double s_u, s_ratio, s_M, s_S;
+  if (tid == 0) {
+    const int i0 = ldcg(&ctl->rs_step);
+    s_i = i0;
+    s_go = ldcg(&ctl->status) == ST_OK && i0 >= 1 && i0 < fd.T && ldcg(&ctl->step) == i0 + 1;
+    s_flag = ldcg(&ctl->rs_flag);
+    s_u = ldcg(&ctl->u);
+    s_ratio = ldcg(&ctl->ratio);
+    s_M = ldcg(&ctl->M);
+    s_S = ldcg(&ctl->S);
+  }
+  __syncthreads();
+  if (!s_go) return;
+  const int i = s_i;
+  if (!s_flag) {
     const int j = j0 + tid;
     if (j < P && fd.mode != MODE_ALWAYS) {
-      fd.lam[j] = fd.ell[j] - ldcg(&ctl->M);
+      fd.lam[j] = fd.ell[j] - s_M;
       if (fd.hist) fd.anc[int64_t(i) * P + j] = j;
     }
     return;
   }
   const double base = fma(gG, tbase, gB);
   const double scale = gG * tg;
-  const double u = ldcg(&ctl->u);
-  const double ratio = ldcg(&ctl->ratio);
+  const double u = s_u;
+  const double ratio = s_ratio;
   if (tid == 0) {
     range[0] = targets_below(base, ratio, u, P);
     nlong = 0;
@@ -499,7 +525,7 @@ __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__
       const int g1 = (t + 1) / GROUP;
       nb = fma(fd.gp[g1].G, fd.tp[t + 1].base, fd.gp[g1].B);
     } else {
-      nb = ldcg(&ctl->S);
+      nb = s_S;
     }
     range[1] = targets_below(nb, ratio, u, P);
   }
