@@ -60,6 +60,79 @@ __device__ __forceinline__ void l96_rk4_step(R (&x)[N], R F, R dt, R h2, R h3, R
   }
 }
 
+// ---------------------------------------------------------------------------
+// Packed FP32 pairs (sm_100-family f32x2 instructions): one instruction does
+// the same IEEE single-precision operation on both halves of a 64-bit
+// register, so a packed computation gives bit for bit the scalar results
+// with half the instructions issued.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk(float lo, float hi) {
+  f32x2 d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void upk(f32x2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 swp(f32x2 v) {
+  float a, b;
+  upk(v, a, b);
+  return pk(b, a);
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// Lorenz '96 right-hand side for the component pair p = (p, p + H) of a state
+// stored as H = N/2 pairs; the cyclic neighbours of the first and last pairs
+// are the swapped halves of the pairs at the other end.
+template <int H>
+__device__ __forceinline__ f32x2 l96_rhs2(const f32x2 (&Y)[H], int p, f32x2 FF) {
+  const f32x2 xp1 = p + 1 < H ? Y[(p + 1) % H] : swp(Y[0]);
+  const f32x2 xm2 = p >= 2 ? Y[(p + H - 2) % H] : swp(Y[(p + H - 2) % H]);
+  const f32x2 xm1 = p >= 1 ? Y[(p + H - 1) % H] : swp(Y[H - 1]);
+  return fma2(sub2(xp1, xm2), xm1, sub2(FF, Y[p]));
+}
+
+// The RK4 step of l96_rk4_step on the packed state (same operations per lane).
+template <int H>
+__device__ __forceinline__ void l96_rk4_step2(f32x2 (&X)[H], f32x2 FF, f32x2 dt, f32x2 h2,
+                                              f32x2 h3, f32x2 h6) {
+  f32x2 acc[H], A[H], B[H];
+#pragma unroll
+  for (int p = 0; p < H; ++p) {
+    const f32x2 k = l96_rhs2<H>(X, p, FF);
+    acc[p] = fma2(h6, k, X[p]);
+    A[p] = fma2(h2, k, X[p]);
+  }
+#pragma unroll
+  for (int p = 0; p < H; ++p) {
+    const f32x2 k = l96_rhs2<H>(A, p, FF);
+    acc[p] = fma2(h3, k, acc[p]);
+    B[p] = fma2(h2, k, X[p]);
+  }
+#pragma unroll
+  for (int p = 0; p < H; ++p) {
+    const f32x2 k = l96_rhs2<H>(B, p, FF);
+    acc[p] = fma2(h3, k, acc[p]);
+    A[p] = fma2(dt, k, X[p]);
+  }
+#pragma unroll
+  for (int p = 0; p < H; ++p) {
+    const f32x2 k = l96_rhs2<H>(A, p, FF);
+    X[p] = fma2(h6, k, acc[p]);
+  }
+}
+
 // Normals number 0..N-1 of the stream (j, i, purpose) into z (N a multiple of 4
 // for Lorenz '96; the windkessel uses its own loop).
 template <int N>
@@ -161,14 +234,32 @@ __device__ __forceinline__ double wk_weight(const FilterDev& fd, int i, R xv, do
 }
 
 // Lorenz '96 propagation: s RK4 substeps, then additive sqrt(q) z_n on every
-// component.
+// component.  In FP32 the state is integrated as N/2 packed pairs (components
+// p and p + N/2), which issues half the instructions for the same bits.
 template <int N, typename R>
 __device__ __forceinline__ void l96_propagate(const FilterDev& fd, uint32_t j, int i, R (&x)[N]) {
   const R F = from_double<R>(fd.theta[0]);
   const R dt = from_double<R>(fd.dt);
   const R h2 = R(0.5) * dt, h3 = dt / R(3.0), h6 = dt / R(6.0);
-  for (int mm = 0; mm < fd.s; ++mm) l96_rk4_step<N, R>(x, F, dt, h2, h3, h6);
-  {
+  if constexpr (sizeof(R) == 4 && N % 2 == 0) {
+    constexpr int H = N / 2;
+    f32x2 X[H];
+#pragma unroll
+    for (int p = 0; p < H; ++p) X[p] = pk(x[p], x[p + H]);
+    const f32x2 FF = pk(F, F), dt2 = pk(dt, dt), h22 = pk(h2, h2), h32 = pk(h3, h3),
+                h62 = pk(h6, h6);
+    for (int mm = 0; mm < fd.s; ++mm) l96_rk4_step2<H>(X, FF, dt2, h22, h32, h62);
+    R z[N];
+    normals<N>(z, fd.seed, j, uint32_t(i), PURPOSE_PROP);
+    const R sx = sqrt(from_double<R>(fd.theta[1]));
+    const f32x2 sx2 = pk(sx, sx);
+#pragma unroll
+    for (int p = 0; p < H; ++p) {
+      X[p] = fma2(sx2, pk(z[p], z[p + H]), X[p]);
+      upk(X[p], x[p], x[p + H]);
+    }
+  } else {
+    for (int mm = 0; mm < fd.s; ++mm) l96_rk4_step<N, R>(x, F, dt, h2, h3, h6);
     R z[N];
     normals<N>(z, fd.seed, j, uint32_t(i), PURPOSE_PROP);
     const R sx = sqrt(from_double<R>(fd.theta[1]));
