@@ -550,6 +550,15 @@ __device__ __forceinline__ int targets_below(double b, double ratio, double u, i
   return __double2int_ru(e);
 }
 
+// The same count for a particle of a tile whose cumulative weights are
+// C_k = base + scale * prefix_k, evaluated as ceil(fma(scale', prefix_k, e0))
+// with scale' = scale ratio and e0 = base ratio - u prepared once per tile
+// (one FP64 fma per particle; the conversion saturates, and the caller clamps
+// the count to the tile's own target range).
+__device__ __forceinline__ int tile_targets_below(double scale_r, double prefix, double e0) {
+  return __double2int_ru(fma(scale_r, prefix, e0));
+}
+
 // Systematic resampling of one tile.  Its particles k have cumulative weights
 // C_k = base + scale * prefix_k; the tile owns the targets [lo, hi) between
 // its base and the next tile's base (both counts computed from the same
@@ -567,6 +576,7 @@ __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__
   __shared__ int range[2];
   __shared__ int nlong;
   __shared__ int longk[TILE];
+  __shared__ double tile_e0, tile_scale_r;
   const int2 ft = tmap[blockIdx.x];
   const FilterDev& fd = fds[ft.x];
   const Ctl* ctl = fd.ctl;
@@ -602,12 +612,13 @@ __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__
     }
     return;
   }
-  const double base = fma(gG, tbase, gB);
-  const double scale = gG * tg;
   const double u = s_u;
   const double ratio = s_ratio;
   if (tid == 0) {
+    const double base = fma(gG, tbase, gB);
     range[0] = targets_below(base, ratio, u, P);
+    tile_e0 = base * ratio - u;
+    tile_scale_r = (gG * tg) * ratio;
     nlong = 0;
   }
   if (tid == 32) {
@@ -625,7 +636,7 @@ __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__
   const int hi = range[1];
   const int nvalid = min(TILE, P - j0);
   if (tid < nvalid) {
-    int n = targets_below(fma(scale, ct, base), ratio, u, P);
+    int n = tile_targets_below(tile_scale_r, ct, tile_e0);
     n = min(max(n, lo), hi);
     nk[tid] = tid == nvalid - 1 ? hi : n;
   }
