@@ -44,6 +44,7 @@ MIXED = 1
 PURPOSE_INIT = 1
 PURPOSE_PROP = 2
 PURPOSE_RESAMPLE = 3
+PURPOSE_PATH = 4
 OK = 0
 EINVAL = 1
 EDEGENERATE = 4
@@ -104,6 +105,11 @@ def lib():
         L.or_pf_run.argtypes = [ctypes.POINTER(Model), _dp, _dp, ctypes.c_uint64, ctypes.c_int64,
                                 ctypes.c_int32, ctypes.c_int32, _dp, _dp, _ip, _dp]
         L.or_pf_run.restype = ctypes.c_int32
+        L.or_pf_run_ex.argtypes = L.or_pf_run.argtypes + [_dp, _dp]
+        L.or_pf_run_ex.restype = ctypes.c_int32
+        L.or_sample_path.argtypes = [ctypes.POINTER(Model), _dp, _dp, ctypes.c_uint64,
+                                     ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _dp, _dp, _ip]
+        L.or_sample_path.restype = ctypes.c_int32
         _lib = L
     return _lib
 
@@ -217,3 +223,29 @@ def pf_run(m, theta, y, seed, P, T, nthreads=0, want_x=True, want_anc=True, want
                          _ptr(anc, _ip) if anc is not None else None,
                          _ptr(diag, _dp) if diag is not None else None)
     return dict(status=st, loglik=ll.value, x=x, anc=anc, diag=diag)
+
+
+def pf_run_ex(m, theta, y, seed, P, T, nthreads=0):
+    """Filter run with the whole state history [T+1][N][P] and final log-weights [P]."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    ll = ctypes.c_double()
+    xh = np.zeros((T + 1, m.N, P), dtype=np.float64)
+    ellT = np.zeros(P, dtype=np.float64)
+    anc = np.zeros((T, P), dtype=np.int32)
+    st = lib().or_pf_run_ex(ctypes.byref(m), _ptr(th, _dp), _ptr(yy, _dp), seed, P, T, nthreads,
+                            ctypes.byref(ll), None, _ptr(anc, _ip), None, _ptr(xh, _dp),
+                            _ptr(ellT, _dp))
+    return dict(status=st, loglik=ll.value, xhist=xh, ellT=ellT, anc=anc)
+
+
+def sample_path(m, theta, y, seed, P, T, nthreads=0):
+    """One state path by ancestry: (status, loglik, path [T+1][N], idx [T+1])."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    ll = ctypes.c_double()
+    path = np.zeros((T + 1, m.N), dtype=np.float64)
+    idx = np.zeros(T + 1, dtype=np.int32)
+    st = lib().or_sample_path(ctypes.byref(m), _ptr(th, _dp), _ptr(yy, _dp), seed, P, T, nthreads,
+                              ctypes.byref(ll), _ptr(path, _dp), _ptr(idx, _ip))
+    return st, ll.value, path, idx

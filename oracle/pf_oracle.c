@@ -593,6 +593,15 @@ static double or_prop_weight32(const or_ctx *cx, uint32_t j, int32_t i, float *x
 int32_t or_pf_run(const or_model *m, const double *th, const double *y, uint64_t seed, int64_t P,
                   int32_t T, int32_t nthreads, double *loglik, double *xfinal, int32_t *anc,
                   double *diag) {
+  return or_pf_run_ex(m, th, y, seed, P, T, nthreads, loglik, xfinal, anc, diag, NULL, NULL);
+}
+
+/* As or_pf_run, plus optionally the whole state history xhist [T+1][N][P]
+ * (row i = x(t_i), row 0 the initial draw) and the final log-weights
+ * ellT [P] (ell at t_T, including carried weights). */
+int32_t or_pf_run_ex(const or_model *m, const double *th, const double *y, uint64_t seed,
+                     int64_t P, int32_t T, int32_t nthreads, double *loglik, double *xfinal,
+                     int32_t *anc, double *diag, double *xhist, double *ellT) {
   const int32_t N = m->N, s = m->substeps;
   const int mixed = (m->prec == OR_MIXED);
   const int32_t stride = (m->kind == OR_LORENZ96) ? m->obs_stride : 1;
@@ -656,6 +665,9 @@ int32_t or_pf_run(const or_model *m, const double *th, const double *y, uint64_t
     }
   }
 
+  if (xhist) {
+    for (j = 0; j < (int64_t)N * P; ++j) xhist[j] = mixed ? (double)fa[j] : xa[j];
+  }
   for (i = 1; i <= T; ++i) {
     const double *yi = y + (int64_t)(i - 1) * Ny;
     double M, S, Q, ess, incr, u = 0.0;
@@ -690,6 +702,11 @@ int32_t or_pf_run(const or_model *m, const double *th, const double *y, uint64_t
     }
     if (mixed) { float *t = fa; fa = fb; fb = t; }
     else { double *t = xa; xa = xb; xb = t; }
+    if (xhist) {
+      double *xr = xhist + (int64_t)i * N * P;
+      for (j = 0; j < (int64_t)N * P; ++j) xr[j] = mixed ? (double)fa[j] : xa[j];
+    }
+    if (ellT && i == T) memcpy(ellT, ell, sizeof(double) * (size_t)P);
 
     or_lse(ell, P, &M, &S, &Q);
     if (!(M > -INFINITY) || !(S > 0.0) || M == INFINITY) {
@@ -732,5 +749,56 @@ int32_t or_pf_run(const or_model *m, const double *th, const double *y, uint64_t
   }
   free(flow); free(xa); free(xb); free(fa); free(fb);
   free(ell); free(lam); free(w); free(Cbuf); free(acur);
+  return status;
+}
+
+/* ======================================================================
+ * Single state path (the last lines of Algorithm 2): draw one particle j
+ * from the final weights, j = min{k : C_k (P / S) > v P} with v the path
+ * uniform of the run (block (0, T + 1, PATH, 0), 53 bits) and C_k the
+ * compensated prefix of exp(ell_T - M); then follow the ancestors back:
+ * b_T = j, b_{i-1} = a(t_i)[b_i], and return x(t_i) of particle b_i.
+ * path [T+1][N], idx [T+1].  Returns the filter's status.
+ * ==================================================================== */
+int32_t or_sample_path(const or_model *m, const double *th, const double *y, uint64_t seed,
+                       int64_t P, int32_t T, int32_t nthreads, double *loglik, double *path,
+                       int32_t *idx) {
+  const int32_t N = m->N;
+  double *xhist = (double *)malloc(sizeof(double) * (size_t)(T + 1) * (size_t)N * (size_t)P);
+  int32_t *anc = (int32_t *)malloc(sizeof(int32_t) * (size_t)T * (size_t)P);
+  double *ellT = (double *)malloc(sizeof(double) * (size_t)P);
+  double *C = (double *)malloc(sizeof(double) * (size_t)P);
+  int32_t status = or_pf_run_ex(m, th, y, seed, P, T, nthreads, loglik, NULL, anc, NULL, xhist,
+                                ellT);
+  if (status == OR_OK) {
+    double M = -INFINITY, sum = 0.0, comp = 0.0, ratio, v, vp;
+    int64_t k, j, lo, hi;
+    int32_t i, n;
+    uint32_t w[4];
+    for (k = 0; k < P; ++k)
+      if (ellT[k] > M) M = ellT[k];
+    for (k = 0; k < P; ++k) {
+      or_neumaier_add(&sum, &comp, exp(ellT[k] - M));
+      C[k] = sum + comp;
+    }
+    ratio = (double)P / C[P - 1];
+    or_block(seed, 0u, (uint32_t)(T + 1), OR_PURPOSE_PATH, 0u, w);
+    v = or_u53_half_open(w[0], w[1]);
+    vp = v * (double)P;
+    lo = 0;
+    hi = P;
+    while (lo < hi) {
+      int64_t mid = lo + (hi - lo) / 2;
+      if (C[mid] * ratio > vp) hi = mid;
+      else lo = mid + 1;
+    }
+    j = lo < P ? lo : P - 1;
+    for (i = T; i >= 0; --i) {
+      idx[i] = (int32_t)j;
+      for (n = 0; n < N; ++n) path[(int64_t)i * N + n] = xhist[((int64_t)i * N + n) * P + j];
+      if (i > 0) j = anc[(int64_t)(i - 1) * P + j];
+    }
+  }
+  free(xhist); free(anc); free(ellT); free(C);
   return status;
 }

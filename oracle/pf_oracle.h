@@ -29,7 +29,7 @@ enum { OR_WINDKESSEL = 0, OR_LORENZ96 = 1 };
 enum { OR_FP64 = 0, OR_MIXED = 1 };
 enum { OR_OK = 0, OR_EINVAL = 1, OR_EDEGENERATE = 4 };
 /* Philox counter word 2 carries (purpose << 16) | block index. */
-enum { OR_PURPOSE_INIT = 1, OR_PURPOSE_PROP = 2, OR_PURPOSE_RESAMPLE = 3 };
+enum { OR_PURPOSE_INIT = 1, OR_PURPOSE_PROP = 2, OR_PURPOSE_RESAMPLE = 3, OR_PURPOSE_PATH = 4 };
 
 typedef struct {
   int32_t kind;          /* OR_WINDKESSEL or OR_LORENZ96 */
@@ -80,6 +80,14 @@ int64_t or_systematic(const double *ell, int64_t P, double u, int32_t *anc);
 int32_t or_pf_run(const or_model *m, const double *theta, const double *y, uint64_t seed,
                   int64_t P, int32_t T, int32_t nthreads, double *loglik,
                   double *xfinal, int32_t *anc, double *diag);
+
+int32_t or_pf_run_ex(const or_model *m, const double *theta, const double *y, uint64_t seed,
+                     int64_t P, int32_t T, int32_t nthreads, double *loglik, double *xfinal,
+                     int32_t *anc, double *diag, double *xhist, double *ellT);
+/* one state path by ancestry (end of Algorithm 2); path [T+1][N], idx [T+1] */
+int32_t or_sample_path(const or_model *m, const double *theta, const double *y, uint64_t seed,
+                       int64_t P, int32_t T, int32_t nthreads, double *loglik, double *path,
+                       int32_t *idx);
 
 #ifdef __cplusplus
 }
