@@ -114,6 +114,37 @@ pf_status pf_run(pf_filter* f, const double* theta, const double* y, uint64_t se
                  double* loglik, void* final_particles, int32_t* ancestors, uint32_t flags,
                  void* cuda_stream);
 
+/* Algorithm 2 over an interval t_{r:s}: advance the filter from t_r to t_s.
+ * r = 0 starts a new run (initial draw from theta); r > 0 must be the s of
+ * the previous pf_run_range call on this filter, with no other run of it
+ * (pf_run, pf_batch_run, pf_sample_path) in between, else PF_EINVAL.
+ * Resampling after step i happens only for i < T, so splitting (0, T] into
+ * consecutive intervals gives the same bits as one pf_run.
+ *   theta      used when r = 0 (may be NULL when r > 0), host or device.
+ *   y          [s-r][Ny] doubles: y(t_{r+1}) .. y(t_s), host or device, so
+ *              observations can arrive interval by interval.
+ *   seed       used when r = 0 (the whole run draws from it).
+ *   loglik     out: log of the likelihood estimate of y(t_1..t_s).
+ *   particles  out or NULL: [N][P] x(t_s) in the state precision.
+ * Synchronous on cuda_stream (NULL: the filter's own stream).  Returns
+ * PF_EDEGENERATE (loglik = -inf) once a step has degenerated. */
+pf_status pf_run_range(pf_filter* f, const double* theta, const double* y, uint64_t seed,
+                       int32_t r, int32_t s, double* loglik, void* particles, void* cuda_stream);
+
+/* One state path drawn from the filter's approximation of the smoothing
+ * distribution p(x(t_0..t_T) | y(t_1..t_T)) (end of Algorithm 2): particle
+ * b_T is drawn from the final normalised weights with the Philox uniform of
+ * block (0, T+1, purpose 4, 0) as the first k with C_k (P / S) > v P, and
+ * b_{i-1} = a(t_i)[b_i] follows the ancestor history back to t_0.
+ *   theta, y, seed  as for pf_run; loglik as for pf_run.
+ *   path        out: [T+1][N] doubles, row i = x(t_i) of particle b_i, host or device.
+ *   path_index  out or NULL: [T+1] int32, b_0 .. b_T.
+ * Runs the filter twice (the second run regenerates the states it copies
+ * from) and holds a [T][P] int32 ancestor history on the device.
+ * Synchronous.  On PF_EDEGENERATE the path is NaN and the indices -1. */
+pf_status pf_sample_path(pf_filter* f, const double* theta, const double* y, uint64_t seed,
+                         double* loglik, double* path, int32_t* path_index, void* cuda_stream);
+
 /* After a PF_FLAG_ASYNC run: wait for the filter's last run and return its
  * status (PF_OK or PF_EDEGENERATE). */
 pf_status pf_wait(pf_filter* f);

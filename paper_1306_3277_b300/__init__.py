@@ -68,8 +68,12 @@ def lib():
                                       ctypes.POINTER(ctypes.c_int64)]
         L.pf_measure_fma_peak.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]
+        L.pf_run_range.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32,
+                                   _vp, _vp, _vp]
+        L.pf_sample_path.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp, _vp]
         for name in ("pf_run", "pf_wait", "pf_destroy", "pf_create", "pf_batch_run",
-                     "pf_profile_enable", "pf_profile_read", "pf_measure_fma_peak"):
+                     "pf_profile_enable", "pf_profile_read", "pf_measure_fma_peak",
+                     "pf_run_range", "pf_sample_path"):
             getattr(L, name).restype = ctypes.c_int
         L.pf_run_noalloc.argtypes = [ctypes.POINTER(pf_model), ctypes.c_int64, ctypes.c_int32,
                                      ctypes.c_double, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp,
@@ -168,6 +172,27 @@ class Filter:
         st = pf_run(self, theta, y, seed, ll, x, anc, 0, stream)
         return st, float(ll[0]), x, anc
 
+    def run_range(self, theta, y, seed, r, s, want_particles=False, stream=None):
+        """Advance from t_r to t_s (y = the s - r observation rows y(t_{r+1..s})):
+        returns (status, loglik of y(t_1..t_s), particles x(t_s) or None)."""
+        theta = None if theta is None else (
+            np.ascontiguousarray(theta, dtype=np.float64) if not hasattr(theta, "data_ptr") else theta)
+        y = np.ascontiguousarray(y, dtype=np.float64) if not hasattr(y, "data_ptr") else y
+        ll = np.zeros(1, dtype=np.float64)
+        x = np.zeros((self.N, self.P), dtype=self.state_dtype) if want_particles else None
+        st = pf_run_range(self, theta, y, seed, r, s, ll, x, stream)
+        return st, float(ll[0]), x
+
+    def sample_path(self, theta, y, seed, stream=None):
+        """One path by ancestry: (status, loglik, path [T+1][N], indices [T+1])."""
+        theta = np.ascontiguousarray(theta, dtype=np.float64) if not hasattr(theta, "data_ptr") else theta
+        y = np.ascontiguousarray(y, dtype=np.float64) if not hasattr(y, "data_ptr") else y
+        ll = np.zeros(1, dtype=np.float64)
+        path = np.zeros((self.T + 1, self.N), dtype=np.float64)
+        idx = np.zeros(self.T + 1, dtype=np.int32)
+        st = pf_sample_path(self, theta, y, seed, ll, path, idx, stream)
+        return st, float(ll[0]), path, idx
+
     def destroy(self):
         if self.h:
             lib().pf_destroy(self.h)
@@ -188,6 +213,20 @@ def pf_run(f, theta, y, seed, loglik, final_particles=None, ancestors=None, flag
     """Raw call: every array argument is passed by pointer (numpy or torch)."""
     st = lib().pf_run(f.h, _ptr(theta), _ptr(y), ctypes.c_uint64(seed), _ptr(loglik),
                       _ptr(final_particles), _ptr(ancestors), flags, _stream_ptr(stream))
+    return _check(st, ok=(PF_OK, PF_EDEGENERATE))
+
+
+def pf_run_range(f, theta, y, seed, r, s, loglik, particles=None, stream=None):
+    """Raw call of pf_run_range (array arguments by pointer)."""
+    st = lib().pf_run_range(f.h, _ptr(theta), _ptr(y), ctypes.c_uint64(seed), r, s, _ptr(loglik),
+                            _ptr(particles), _stream_ptr(stream))
+    return _check(st, ok=(PF_OK, PF_EDEGENERATE))
+
+
+def pf_sample_path(f, theta, y, seed, loglik, path, path_index=None, stream=None):
+    """Raw call of pf_sample_path (array arguments by pointer)."""
+    st = lib().pf_sample_path(f.h, _ptr(theta), _ptr(y), ctypes.c_uint64(seed), _ptr(loglik),
+                              _ptr(path), _ptr(path_index), _stream_ptr(stream))
     return _check(st, ok=(PF_OK, PF_EDEGENERATE))
 
 

@@ -107,7 +107,7 @@ extern "C" size_t pf_device_bytes(const pf_model* m, int64_t P, int32_t T, int32
 // ---------------------------------------------------------------------------
 static void free_filter_buffers(pf_filter* f) {
   void* ptrs[] = {f->x[0], f->x[1], f->ctil, f->ell, f->lam, f->anc, f->hist,
-                  f->flow, f->tp, f->gp, f->ctl};
+                  f->flow, f->tp, f->gp, f->ctl, f->path, f->path_idx};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (f->h_res) cudaFreeHost(f->h_res);
@@ -218,11 +218,17 @@ static void destroy_plan(Plan* p) {
   delete p;
 }
 
-// The launch sequence of one run of a plan: init per class, then for every
-// step one propagate launch per class and one resample launch (only over the
-// filters that are still running), then the results gather.  With a profiler,
-// every launch is bracketed by CUDA events on the same stream.
-static cudaError_t enqueue_run(Plan* p, cudaStream_t st, Profiler* prof) {
+// The launch sequence of steps first..last of a plan: init when first == 1,
+// then for every step one propagate launch per class and one resample launch
+// (only over the filters that are still running), then the results gather.
+// hook(i) is called after the propagate launches of step i (and hook(0)
+// after init), to enqueue work that reads x(t_i).  With a profiler, every
+// launch is bracketed by CUDA events on the same stream.
+static cudaError_t no_hook(int) { return cudaSuccess; }
+
+template <typename Hook>
+static cudaError_t enqueue_steps(Plan* p, int first, int last, cudaStream_t st, Profiler* prof,
+                                 Hook&& hook) {
   cudaError_t le = cudaSuccess;
   auto timed = [&](int kind, auto&& launch) {
     if (prof) prof->begin(kind, st);
@@ -230,13 +236,17 @@ static cudaError_t enqueue_run(Plan* p, cudaStream_t st, Profiler* prof) {
     if (prof) prof->end(st);
     return r;
   };
-  for (size_t c = 0; c < p->classes.size() && le == cudaSuccess; ++c) {
-    const PlanClass& pc = p->classes[c];
-    le = timed(PROF_INIT, [&] {
-      return launch_init(pc.kind, pc.N, pc.prec, p->d_fds, p->d_tmap + pc.offset, pc.ntiles, st);
-    });
+  if (first == 1) {
+    for (size_t c = 0; c < p->classes.size() && le == cudaSuccess; ++c) {
+      const PlanClass& pc = p->classes[c];
+      le = timed(PROF_INIT, [&] {
+        return launch_init(pc.kind, pc.N, pc.prec, p->d_fds, p->d_tmap + pc.offset, pc.ntiles,
+                           st);
+      });
+    }
+    if (le == cudaSuccess) le = hook(0);
   }
-  for (int i = 1; i <= p->maxT && le == cudaSuccess; ++i) {
+  for (int i = first; i <= last && le == cudaSuccess; ++i) {
     for (size_t c = 0; c < p->classes.size() && le == cudaSuccess; ++c) {
       const PlanClass& pc = p->classes[c];
       if (p->cnt_cls[c][i] == 0) continue;
@@ -245,6 +255,7 @@ static cudaError_t enqueue_run(Plan* p, cudaStream_t st, Profiler* prof) {
                                 p->cnt_cls[c][i], st);
       });
     }
+    if (le == cudaSuccess) le = hook(i);
     if (le == cudaSuccess && p->cnt_all[i + 1] > 0)
       le = timed(PROF_RESAMPLE,
                  [&] { return launch_resample(p->d_fds, p->d_tmap, p->cnt_all[i + 1], st); });
@@ -252,6 +263,11 @@ static cudaError_t enqueue_run(Plan* p, cudaStream_t st, Profiler* prof) {
   if (le == cudaSuccess)
     le = timed(PROF_RESULTS, [&] { return launch_results(p->d_fds, p->nf, p->d_res, st); });
   return le;
+}
+
+// The launch sequence of one whole run of a plan.
+static cudaError_t enqueue_run(Plan* p, cudaStream_t st, Profiler* prof) {
+  return enqueue_steps(p, 1, p->maxT, st, prof, no_hook);
 }
 
 // Tile maps sorted by T descending so that the filters still running at step
@@ -450,6 +466,7 @@ extern "C" pf_status pf_run(pf_filter* f, const double* theta, const double* y, 
   }
   Plan* p = f->plan;
   const int32_t hist_on = ancestors ? 1 : 0;
+  f->range_pos = -1;
   pf_status ps = run_plan(p, &theta, &y, &seed, &hist_on, st, f->prof);
   if (ps != PF_OK) return ps;
   const int64_t P = f->P;
@@ -471,6 +488,125 @@ extern "C" pf_status pf_run(pf_filter* f, const double* theta, const double* y, 
   if (is_device_ptr(loglik)) CK(cudaMemcpy(loglik, &ll, sizeof(double), cudaMemcpyHostToDevice));
   else *loglik = ll;
   return status == ST_OK ? PF_OK : PF_EDEGENERATE;
+}
+
+// ---------------------------------------------------------------------------
+// interval continuation and single-path sampling (Algorithm 2 over t_{r:s})
+// ---------------------------------------------------------------------------
+static pf_status ensure_history(pf_filter* f) {
+  if (f->hist) return PF_OK;
+  if (cudaMalloc((void**)&f->hist, size_t(f->T) * size_t(f->P) * 4) != cudaSuccess) {
+    cudaGetLastError();
+    f->hist = nullptr;
+    return fail(PF_ENOMEM, "ancestor history of %lld bytes",
+                (long long)(size_t(f->T) * size_t(f->P) * 4));
+  }
+  return PF_OK;
+}
+
+static pf_status ensure_plan(pf_filter* f) {
+  if (f->plan) return PF_OK;
+  std::vector<pf_filter*> one{f};
+  return build_plan(one, &f->plan);
+}
+
+extern "C" pf_status pf_run_range(pf_filter* f, const double* theta, const double* y,
+                                  uint64_t seed, int32_t r, int32_t s, double* loglik,
+                                  void* particles, void* cuda_stream) {
+  if (!f) return fail(PF_EINVAL, "filter is NULL");
+  if (!y || !loglik) return fail(PF_EINVAL, "y and loglik are required");
+  if (r < 0 || s <= r || s > f->T)
+    return fail(PF_EINVAL, "range (%d, %d] is not inside (0, %d]", r, s, f->T);
+  if (r == 0 && !theta) return fail(PF_EINVAL, "theta is required when r = 0");
+  if (r > 0 && r != f->range_pos)
+    return fail(PF_EINVAL, "the filter does not stand at t_%d (continue from its last s, or "
+                "start again at r = 0)", r);
+  pf_status ps = ensure_plan(f);
+  if (ps != PF_OK) return ps;
+  Plan* p = f->plan;
+  cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : f->own;
+  f->range_pos = -1;
+  CK(cudaEventSynchronize(p->ev_staged));
+  if (r == 0) {
+    FilterDev& d = p->h_fds[0];
+    d = f->desc;
+    d.y = p->d_ycat;
+    d.seed = seed;
+    const int nth = pf_theta_size(f->m.kind);
+    const bool dev_theta = is_device_ptr(theta);
+    if (!dev_theta) memcpy(d.theta, theta, sizeof(double) * nth);
+    CK(cudaMemcpyAsync(p->d_fds, p->h_fds, sizeof(FilterDev), cudaMemcpyHostToDevice, st));
+    if (dev_theta)
+      CK(cudaMemcpyAsync(p->d_fds[0].theta, theta, sizeof(double) * nth,
+                         cudaMemcpyDeviceToDevice, st));
+  }
+  const size_t off = size_t(r) * f->sh.Ny;
+  const size_t ny = size_t(s - r) * f->sh.Ny;
+  if (is_device_ptr(y)) {
+    CK(cudaMemcpyAsync(p->d_ycat + off, y, sizeof(double) * ny, cudaMemcpyDeviceToDevice, st));
+  } else {
+    memcpy(p->h_ycat + off, y, sizeof(double) * ny);
+    CK(cudaMemcpyAsync(p->d_ycat + off, p->h_ycat + off, sizeof(double) * ny,
+                       cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaEventRecord(p->ev_staged, st));
+  CK(enqueue_steps(p, r + 1, s, st, f->prof, no_hook));
+  CK(cudaMemcpyAsync(p->h_res, p->d_res, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
+  if (particles)
+    CK(cudaMemcpyAsync(particles, f->x[s & 1], size_t(f->m.N) * f->P * f->sh.state_bytes,
+                       cudaMemcpyDefault, st));
+  CK(cudaEventRecord(p->ev_done, st));
+  CK(cudaEventSynchronize(p->ev_done));
+  f->range_pos = s;
+  const double ll = p->h_res[0];
+  if (is_device_ptr(loglik)) CK(cudaMemcpy(loglik, &ll, sizeof(double), cudaMemcpyHostToDevice));
+  else *loglik = ll;
+  return int(p->h_res[1]) == ST_OK ? PF_OK : PF_EDEGENERATE;
+}
+
+extern "C" pf_status pf_sample_path(pf_filter* f, const double* theta, const double* y,
+                                    uint64_t seed, double* loglik, double* path,
+                                    int32_t* path_index, void* cuda_stream) {
+  if (!f) return fail(PF_EINVAL, "filter is NULL");
+  if (!theta || !y || !loglik || !path) return fail(PF_EINVAL, "theta, y, loglik and path are required");
+  pf_status ps = ensure_history(f);
+  if (ps == PF_OK) ps = ensure_plan(f);
+  if (ps != PF_OK) return ps;
+  const int T = f->T, N = f->m.N;
+  if (!f->path) {
+    if (cudaMalloc((void**)&f->path, sizeof(double) * size_t(T + 1) * N) != cudaSuccess ||
+        cudaMalloc((void**)&f->path_idx, sizeof(int32_t) * size_t(T + 1)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PF_ENOMEM, "path buffers");
+    }
+  }
+  Plan* p = f->plan;
+  cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : f->own;
+  f->range_pos = -1;
+  // pass 1: the filter with its ancestor history, then the pick and the trace
+  const int32_t hist_on = 1;
+  ps = run_plan(p, &theta, &y, &seed, &hist_on, st, nullptr);
+  if (ps != PF_OK) return ps;
+  CK(cudaMemsetAsync(f->path_idx + T, 0x7f, sizeof(int32_t), st));
+  CK(launch_path_pick(p->d_fds, f->sh.ntiles, f->path_idx + T, st));
+  CK(launch_path_trace(p->d_fds, f->path_idx, st));
+  // pass 2: the same run again (same descriptor, so bit-identical states),
+  // copying x(t_i) of particle b_i after each propagate
+  const int prec = f->m.prec;
+  const int P = int(f->P);
+  CK(enqueue_steps(p, 1, T, st, nullptr, [&](int i) {
+    return launch_path_copy(f->x[i & 1], prec, N, P, f->path_idx, i, f->path, st);
+  }));
+  CK(cudaMemcpyAsync(path, f->path, sizeof(double) * size_t(T + 1) * N, cudaMemcpyDefault, st));
+  if (path_index)
+    CK(cudaMemcpyAsync(path_index, f->path_idx, sizeof(int32_t) * size_t(T + 1),
+                       cudaMemcpyDefault, st));
+  CK(cudaEventRecord(p->ev_done, st));
+  CK(cudaEventSynchronize(p->ev_done));
+  const double ll = p->h_res[0];
+  if (is_device_ptr(loglik)) CK(cudaMemcpy(loglik, &ll, sizeof(double), cudaMemcpyHostToDevice));
+  else *loglik = ll;
+  return int(p->h_res[1]) == ST_OK ? PF_OK : PF_EDEGENERATE;
 }
 
 extern "C" pf_status pf_wait(pf_filter* f) {
@@ -536,6 +672,7 @@ extern "C" pf_status pf_batch_run(int32_t nfilt, pf_filter* const* f, const doub
     g_plans[key] = p;
   }
   cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : p->st;
+  for (int k = 0; k < nfilt; ++k) key[k]->range_pos = -1;
   pf_status ps = run_plan(p, theta, y, seeds, nullptr, st, nullptr);
   if (ps != PF_OK) return ps;
   CK(cudaEventSynchronize(p->ev_done));

@@ -20,7 +20,7 @@ constexpr int64_t MAX_P = int64_t(1) << 24;  // GROUP * GROUP * TILE
 enum { KIND_WK = 0, KIND_L96 = 1 };
 enum { PREC_FP64 = 0, PREC_MIXED = 1 };
 enum { MODE_ALWAYS = 0, MODE_ADAPTIVE = 1, MODE_NEVER = 2 };
-enum { PURPOSE_INIT = 1, PURPOSE_PROP = 2, PURPOSE_RESAMPLE = 3 };
+enum { PURPOSE_INIT = 1, PURPOSE_PROP = 2, PURPOSE_RESAMPLE = 3, PURPOSE_PATH = 4 };
 enum { ST_OK = 0, ST_DEGENERATE = 4 };
 
 // Per tile of TILE particles: written by the propagate kernel (M, S, Q) and

@@ -661,6 +661,79 @@ __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__
   }
 }
 
+// ---------------------------------------------------------------------------
+// Single state path (end of Algorithm 2)
+// ---------------------------------------------------------------------------
+// Draw one particle from the final weights of filter 0: the first k whose
+// scaled cumulative weight C_k (P / S) exceeds v P, with v the uniform of the
+// path purpose at step T + 1.  Each tile evaluates C_k (P / S) as the
+// resampling kernel does (with u = 0) and offers its first qualifying
+// particle to an atomic minimum in *pick (set to a large value beforehand).
+__global__ void __launch_bounds__(TILE) k_path_pick(const FilterDev* __restrict__ fds,
+                                                    int32_t* __restrict__ pick) {
+  const FilterDev& fd = fds[0];
+  const int t = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int P = fd.P;
+  const int j0 = t * TILE;
+  const int g = t / GROUP;
+  const double ct = j0 + tid < P ? fd.ctil[j0 + tid] : 0.0;
+  const double gG = fd.gp[g].G, gB = fd.gp[g].B, tbase = fd.tp[t].base, tg = fd.tp[t].g;
+  __shared__ int s_ok, s_first;
+  __shared__ double s_ratio, s_tau;
+  if (tid == 0) {
+    const Ctl* c = fd.ctl;
+    s_ok = ldcg(&c->status) == ST_OK && ldcg(&c->step) == fd.T + 1;
+    s_ratio = double(P) / ldcg(&c->S);
+    const uint4 w = rng_block(fd.seed, 0u, uint32_t(fd.T + 1), PURPOSE_PATH, 0u);
+    s_tau = u53_closed_open(w.x, w.y) * double(P);
+    s_first = TILE;
+  }
+  __syncthreads();
+  if (!s_ok) return;
+  const double ratio = s_ratio;
+  const double e0 = fma(gG, tbase, gB) * ratio;
+  const double scale_r = (gG * tg) * ratio;
+  if (j0 + tid < P && fma(scale_r, ct, e0) > s_tau) atomicMin(&s_first, tid);
+  __syncthreads();
+  if (tid == 0 && s_first < TILE) atomicMin(pick, j0 + s_first);
+}
+
+// Follow the ancestor history of filter 0 back from the picked particle:
+// b_T = pick (clamped to P - 1 when no cumulative weight exceeded the target),
+// b_{i-1} = a(t_i)[b_i].  One thread; idx[T] holds the pick on entry.  A
+// degenerate filter gives idx = -1 everywhere.
+__global__ void k_path_trace(const FilterDev* __restrict__ fds, int32_t* __restrict__ idx) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const FilterDev& fd = fds[0];
+  const int P = fd.P, T = fd.T;
+  if (ldcg(&fd.ctl->status) != ST_OK || !fd.hist) {
+    for (int i = 0; i <= T; ++i) idx[i] = -1;
+    return;
+  }
+  int b = min(idx[T], P - 1);
+  idx[T] = b;
+  for (int i = T; i >= 1; --i) {
+    b = (b >= 0 && b < P) ? fd.anc[int64_t(i - 1) * P + b] : -1;
+    idx[i - 1] = b;
+  }
+}
+
+// path[i][n] = x(t_i)[n][idx[i]] in FP64 (N threads); NaN when idx[i] is not a particle.
+__global__ void k_path_copy(const void* __restrict__ x, int prec, int N, int P,
+                            const int32_t* __restrict__ idx, int i, double* __restrict__ path) {
+  const int n = threadIdx.x;
+  if (n >= N) return;
+  const int b = idx[i];
+  double v = NAN;
+  if (b >= 0 && b < P) {
+    const int64_t at = int64_t(n) * P + b;
+    v = prec == PREC_MIXED ? double(static_cast<const float*>(x)[at])
+                         : static_cast<const double*>(x)[at];
+  }
+  path[int64_t(i) * N + n] = v;
+}
+
 // Windkessel input table F(k dt), k < n: half sine of the given peak and period.
 __global__ void k_flow(double* __restrict__ flow, int64_t n, double peak, double period,
                        double dt) {
@@ -761,6 +834,22 @@ cudaError_t launch_flow(double* flow, int64_t n, double peak, double period, dou
 cudaError_t launch_results(const FilterDev* fds, int nf, double* out, cudaStream_t st) {
   if (nf <= 0) return cudaSuccess;
   k_results<<<(nf + 127) / 128, 128, 0, st>>>(fds, nf, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_path_pick(const FilterDev* fds, int ntiles, int32_t* pick, cudaStream_t st) {
+  k_path_pick<<<ntiles, TILE, 0, st>>>(fds, pick);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_path_trace(const FilterDev* fds, int32_t* idx, cudaStream_t st) {
+  k_path_trace<<<1, 32, 0, st>>>(fds, idx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_path_copy(const void* x, int prec, int N, int P, const int32_t* idx, int i,
+                             double* path, cudaStream_t st) {
+  k_path_copy<<<1, 64, 0, st>>>(x, prec, N, P, idx, i, path);
   return cudaGetLastError();
 }
 

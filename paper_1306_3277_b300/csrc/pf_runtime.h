@@ -91,6 +91,8 @@ struct pf_filter {
   double* lam = nullptr;
   int32_t* anc = nullptr;
   int32_t* hist = nullptr;
+  double* path = nullptr;        // [T+1][N] sampled path (pf_sample_path)
+  int32_t* path_idx = nullptr;   // [T+1] its particle indices
   double* flow = nullptr;
   pfb::TilePart* tp = nullptr;
   pfb::GroupPart* gp = nullptr;
@@ -100,6 +102,7 @@ struct pf_filter {
   pfb::Plan* plan = nullptr;
   pfb::Profiler* prof = nullptr;
   bool pending = false;
+  int32_t range_pos = -1;        // t_s reached by the last pf_run_range, else -1
   size_t bytes = 0;
 };
 
