@@ -123,7 +123,9 @@ pf_status pf_run(pf_filter* f, const double* theta, const double* y, uint64_t se
  *   theta      used when r = 0 (may be NULL when r > 0), host or device.
  *   y          [s-r][Ny] doubles: y(t_{r+1}) .. y(t_s), host or device, so
  *              observations can arrive interval by interval.
- *   seed       used when r = 0 (the whole run draws from it).
+ *   seed       Philox key of this interval's steps (and of the initial draw
+ *              when r = 0); the same key in every interval reproduces pf_run,
+ *              a new key continues the filter with fresh randomness.
  *   loglik     out: log of the likelihood estimate of y(t_1..t_s).
  *   particles  out or NULL: [N][P] x(t_s) in the state precision.
  * Synchronous on cuda_stream (NULL: the filter's own stream).  Returns

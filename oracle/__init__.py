@@ -107,6 +107,10 @@ def lib():
         L.or_pf_run.restype = ctypes.c_int32
         L.or_pf_run_ex.argtypes = L.or_pf_run.argtypes + [_dp, _dp]
         L.or_pf_run_ex.restype = ctypes.c_int32
+        L.or_pf_run_sched.argtypes = [ctypes.POINTER(Model), _dp, _dp, ctypes.c_uint64,
+                                      ctypes.POINTER(ctypes.c_uint64), ctypes.c_int64,
+                                      ctypes.c_int32, ctypes.c_int32, _dp, _dp, _ip, _dp, _dp, _dp]
+        L.or_pf_run_sched.restype = ctypes.c_int32
         L.or_sample_path.argtypes = [ctypes.POINTER(Model), _dp, _dp, ctypes.c_uint64,
                                      ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _dp, _dp, _ip]
         L.or_sample_path.restype = ctypes.c_int32
@@ -249,3 +253,22 @@ def sample_path(m, theta, y, seed, P, T, nthreads=0):
     st = lib().or_sample_path(ctypes.byref(m), _ptr(th, _dp), _ptr(yy, _dp), seed, P, T, nthreads,
                               ctypes.byref(ll), _ptr(path, _dp), _ptr(idx, _ip))
     return st, ll.value, path, idx
+
+
+def pf_run_sched(m, theta, y, sched, P, T, nthreads=0, want_xhist=False):
+    """Filter run with a seed schedule sched[0..T] (initial draw, then one key
+    per step): loglik, final state, ancestors, diagnostics, optional history."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    sc = np.ascontiguousarray(sched, dtype=np.uint64)
+    assert len(sc) == T + 1
+    ll = ctypes.c_double()
+    x = np.zeros((m.N, P), dtype=np.float64)
+    anc = np.zeros((T, P), dtype=np.int32)
+    diag = np.zeros((T, 8), dtype=np.float64)
+    xh = np.zeros((T + 1, m.N, P), dtype=np.float64) if want_xhist else None
+    st = lib().or_pf_run_sched(ctypes.byref(m), _ptr(th, _dp), _ptr(yy, _dp), 0,
+                               sc.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), P, T, nthreads,
+                               ctypes.byref(ll), _ptr(x, _dp), _ptr(anc, _ip), _ptr(diag, _dp),
+                               None if xh is None else _ptr(xh, _dp), None)
+    return dict(status=st, loglik=ll.value, x=x, anc=anc, diag=diag, xhist=xh)

@@ -602,6 +602,19 @@ int32_t or_pf_run(const or_model *m, const double *th, const double *y, uint64_t
 int32_t or_pf_run_ex(const or_model *m, const double *th, const double *y, uint64_t seed,
                      int64_t P, int32_t T, int32_t nthreads, double *loglik, double *xfinal,
                      int32_t *anc, double *diag, double *xhist, double *ellT) {
+  return or_pf_run_sched(m, th, y, seed, NULL, P, T, nthreads, loglik, xfinal, anc, diag, xhist,
+                         ellT);
+}
+
+/* As or_pf_run_ex with a seed schedule: when sched is not NULL, the initial
+ * draw uses the Philox key sched[0] and step i (its propagation, weights and
+ * the resampling after it) uses sched[i], i = 1..T; this is the run that
+ * advancing a filter interval by interval with a new key per interval
+ * gives.  With sched NULL every draw uses seed. */
+int32_t or_pf_run_sched(const or_model *m, const double *th, const double *y, uint64_t seed,
+                        const uint64_t *sched, int64_t P, int32_t T, int32_t nthreads,
+                        double *loglik, double *xfinal, int32_t *anc, double *diag,
+                        double *xhist, double *ellT) {
   const int32_t N = m->N, s = m->substeps;
   const int mixed = (m->prec == OR_MIXED);
   const int32_t stride = (m->kind == OR_LORENZ96) ? m->obs_stride : 1;
@@ -647,6 +660,7 @@ int32_t or_pf_run_ex(const or_model *m, const double *th, const double *y, uint6
   Cbuf = (double *)malloc(sizeof(double) * (size_t)P);
   acur = (int32_t *)malloc(sizeof(int32_t) * (size_t)P);
 
+  if (sched) seed = sched[0];
   cx.m = m; cx.th = th; cx.flow = flow; cx.seed = seed; cx.Ny = Ny; cx.r = r;
   cx.cw = -0.5 / r;
 
@@ -673,6 +687,7 @@ int32_t or_pf_run_ex(const or_model *m, const double *th, const double *y, uint6
     double M, S, Q, ess, incr, u = 0.0;
     int resample;
     int64_t near = 0;
+    if (sched) cx.seed = sched[i];
     if (anc) {
       for (j = 0; j < P; ++j) anc[(int64_t)(i - 1) * P + j] = anc_identity ? (int32_t)j : acur[j];
     }
@@ -725,7 +740,7 @@ int32_t or_pf_run_ex(const or_model *m, const double *th, const double *y, uint6
     resample = (i < T) && (m->ess_threshold >= 1.0 || ess < m->ess_threshold * (double)P);
     if (resample) {
       for (j = 0; j < P; ++j) w[j] = exp(ell[j] - M);
-      u = or_resample_uniform(seed, (uint32_t)i);
+      u = or_resample_uniform(cx.seed, (uint32_t)i);
       near = or_systematic_from_w(w, P, u, acur, Cbuf);
       anc_identity = 0;
       lam_zero = 1;

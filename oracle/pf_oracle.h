@@ -84,6 +84,10 @@ int32_t or_pf_run(const or_model *m, const double *theta, const double *y, uint6
 int32_t or_pf_run_ex(const or_model *m, const double *theta, const double *y, uint64_t seed,
                      int64_t P, int32_t T, int32_t nthreads, double *loglik, double *xfinal,
                      int32_t *anc, double *diag, double *xhist, double *ellT);
+int32_t or_pf_run_sched(const or_model *m, const double *theta, const double *y, uint64_t seed,
+                        const uint64_t *sched, int64_t P, int32_t T, int32_t nthreads,
+                        double *loglik, double *xfinal, int32_t *anc, double *diag,
+                        double *xhist, double *ellT);
 /* one state path by ancestry (end of Algorithm 2); path [T+1][N], idx [T+1] */
 int32_t or_sample_path(const or_model *m, const double *theta, const double *y, uint64_t seed,
                        int64_t P, int32_t T, int32_t nthreads, double *loglik, double *path,

@@ -539,6 +539,10 @@ extern "C" pf_status pf_run_range(pf_filter* f, const double* theta, const doubl
     if (dev_theta)
       CK(cudaMemcpyAsync(p->d_fds[0].theta, theta, sizeof(double) * nth,
                          cudaMemcpyDeviceToDevice, st));
+  } else {
+    p->h_fds[0].seed = seed;  // the key of this interval's steps
+    CK(cudaMemcpyAsync(&p->d_fds[0].seed, &p->h_fds[0].seed, sizeof(uint64_t),
+                       cudaMemcpyHostToDevice, st));
   }
   const size_t off = size_t(r) * f->sh.Ny;
   const size_t ny = size_t(s - r) * f->sh.Ny;

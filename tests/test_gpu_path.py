@@ -66,6 +66,31 @@ def test_range_pieces_equal_whole_run_and_oracle(name, factory, cuts):
         f.destroy()
 
 
+@pytest.mark.parametrize("name,factory,cuts", RANGE_CASES[:4], ids=[c[0] for c in RANGE_CASES[:4]])
+def test_range_fresh_key_per_interval_matches_oracle_schedule(name, factory, cuts):
+    import paper_1306_3277_b300 as pf
+    w = factory()
+    keys = [1000003 * (k + 1) + 17 for k in range(len(cuts) - 1)]
+    sched = np.zeros(w.T + 1, dtype=np.uint64)
+    sched[0] = keys[0]
+    for k, (r, s) in enumerate(zip(cuts[:-1], cuts[1:])):
+        sched[r + 1:s + 1] = keys[k]
+    o = O.pf_run_sched(oracle_model(w), w.theta, w.y, sched, w.P, w.T, want_xhist=True)
+    running = np.cumsum(o["diag"][:, 6])
+    first_near = _near_step(o)
+    f = pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt)
+    try:
+        for k, (r, s) in enumerate(zip(cuts[:-1], cuts[1:])):
+            st, ll, x = f.run_range(w.theta if r == 0 else None, w.y[r:s], keys[k], r, s,
+                                    want_particles=True)
+            assert st == pf.PF_OK
+            if first_near is None or s < first_near:
+                assert np.array_equal(x, o["xhist"][s].astype(x.dtype))
+                assert abs(ll - running[s - 1]) <= 1e-9 * abs(running[s - 1])
+    finally:
+        f.destroy()
+
+
 def test_range_observations_from_device_memory():
     import torch
     import paper_1306_3277_b300 as pf
@@ -131,7 +156,7 @@ PATH_CASES = [
     ("lorenz96 N=8 P=5000 T=40 ESS 0.5 FP64", lambda: W.lorenz96_8(P=5000, T=40,
                                                                    ess_threshold=0.5), (6,)),
     ("lorenz96 N=40 P=2^16+5 T=6 FP64", lambda: W.lorenz96_large(P=(1 << 16) + 5, T=6,
-                                                                 prec=W.FP64), (7,)),
+                                                                 prec=W.FP64), (7, 8)),
     ("lorenz96 N=40 P=3000 T=20 mixed", lambda: W.lorenz96_large(P=3000, T=20), (8,)),
 ]
 

@@ -133,3 +133,20 @@ def test_seed_changes_result():
     a = O.pf_run(m, w.theta, w.y, 1, w.P, w.T)["loglik"]
     b = O.pf_run(m, w.theta, w.y, 2, w.P, w.T)["loglik"]
     assert a != b
+
+
+def test_seed_schedule_constant_is_plain_run_and_still_converges():
+    w = W.windkessel(P=1024, T=100)
+    m = _om(w)
+    a = O.pf_run(m, w.theta, w.y, 7, w.P, w.T)
+    b = O.pf_run_sched(m, w.theta, w.y, [7] * (w.T + 1), w.P, w.T)
+    assert a["loglik"] == b["loglik"] and np.array_equal(a["anc"], b["anc"])
+    # a new key at every step is still a particle filter: unbiased for the
+    # Kalman likelihood with the same Jensen offset as the plain runs
+    kf = O.kalman_windkessel(m, w.theta, w.y)
+    rng = np.random.default_rng(12)
+    lls = np.array([O.pf_run_sched(m, w.theta, w.y, rng.integers(1, 2 ** 63, w.T + 1,
+                                                                 dtype=np.uint64),
+                                   w.P, w.T)["loglik"] for _ in range(32)])
+    se = math.sqrt(lls.var(ddof=1) / 32)
+    assert abs(lls.mean() - (kf - lls.var(ddof=1) / 2)) < 4 * se + 0.02
