@@ -28,6 +28,15 @@ systematic                Sec. 3.3 systematic resampling           integer weigh
 pf_run                    Algorithm 2                              Kalman likelihood (exact special case
                                                                     and convergence over P), closed-form
                                                                     deterministic Lorenz '96 likelihood
+pf_run_sched              Algorithm 2 over t_{r:s} intervals,      constant schedule = pf_run; per-step
+                          one Philox key per step                  keys still converge to the Kalman value
+sample_path               Algorithm 2 ancestry trace (end)         exact rational pick, noiseless closed
+                                                                    form, joint-Gaussian smoothing moments
+log_prior / propose       Sec. 2.1 parameter / proposal blocks     scipy logpdf, KS of the draws, scipy
+                                                                    Hastings correction
+pmmh                      Algorithm 3, Eq. (mh)                    prior-only chains sample the prior;
+                                                                    Kalman-likelihood chains match a grid
+                                                                    posterior
 ========================  =======================================  ==========================================
 """
 import ctypes
@@ -45,6 +54,8 @@ PURPOSE_INIT = 1
 PURPOSE_PROP = 2
 PURPOSE_RESAMPLE = 3
 PURPOSE_PATH = 4
+PURPOSE_PMMH = 5
+PURPOSE_SMC2 = 6
 OK = 0
 EINVAL = 1
 EDEGENERATE = 4
@@ -111,6 +122,15 @@ def lib():
                                       ctypes.POINTER(ctypes.c_uint64), ctypes.c_int64,
                                       ctypes.c_int32, ctypes.c_int32, _dp, _dp, _ip, _dp, _dp, _dp]
         L.or_pf_run_sched.restype = ctypes.c_int32
+        L.or_pmmh.argtypes = [ctypes.POINTER(Model), _dp, ctypes.c_int64, ctypes.c_int32,
+                              ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(Param), _dp,
+                              ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32, _dp, _dp, _ip, _ip]
+        L.or_pmmh.restype = ctypes.c_int32
+        L.or_log_prior.argtypes = [ctypes.POINTER(Param), ctypes.c_int32, _dp]
+        L.or_log_prior.restype = ctypes.c_double
+        L.or_propose.argtypes = [ctypes.POINTER(Param), ctypes.c_int32, _dp, ctypes.c_uint64,
+                                 ctypes.c_uint32, ctypes.c_uint32, _dp]
+        L.or_propose.restype = ctypes.c_double
         L.or_sample_path.argtypes = [ctypes.POINTER(Model), _dp, _dp, ctypes.c_uint64,
                                      ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _dp, _dp, _ip]
         L.or_sample_path.restype = ctypes.c_int32
@@ -272,3 +292,56 @@ def pf_run_sched(m, theta, y, sched, P, T, nthreads=0, want_xhist=False):
                                ctypes.byref(ll), _ptr(x, _dp), _ptr(anc, _ip), _ptr(diag, _dp),
                                None if xh is None else _ptr(xh, _dp), None)
     return dict(status=st, loglik=ll.value, x=x, anc=anc, diag=diag, xhist=xh)
+
+
+# ---- marginal Metropolis-Hastings (Algorithm 3) ---------------------------
+PRIOR_FIXED, PRIOR_UNIFORM, PRIOR_GAUSSIAN, PRIOR_GAMMA, PRIOR_INV_GAMMA = range(5)
+PROPOSE_FIXED, PROPOSE_TRUNC_GAUSSIAN, PROPOSE_INV_GAMMA = range(3)
+LIK_PF, LIK_KALMAN, LIK_NONE = range(3)
+
+
+class Param(ctypes.Structure):
+    _fields_ = [("prior", ctypes.c_int32), ("proposal", ctypes.c_int32), ("a", ctypes.c_double),
+                ("b", ctypes.c_double), ("c", ctypes.c_double), ("d", ctypes.c_double),
+                ("e", ctypes.c_double)]
+
+
+def params(spec):
+    """spec: list of (prior, proposal, a, b, c, d, e) tuples -> ctypes array."""
+    arr = (Param * len(spec))()
+    for k, t in enumerate(spec):
+        t = tuple(t) + (0.0,) * (7 - len(t))
+        arr[k] = Param(int(t[0]), int(t[1]), *[float(v) for v in t[2:7]])
+    return arr
+
+
+def log_prior(spec, theta):
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    sp = params(spec)
+    return lib().or_log_prior(sp, len(th), _ptr(th, _dp))
+
+
+def propose(spec, theta, seed, j, i):
+    """(theta', log q(theta|theta') - log q(theta'|theta)) of chain j at iteration i."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    out = np.zeros_like(th)
+    sp = params(spec)
+    lqr = lib().or_propose(sp, len(th), _ptr(th, _dp), seed, j, i, _ptr(out, _dp))
+    return out, lqr
+
+
+def pmmh(m, y, P, T, lik, spec, theta0, niter, seed, nthreads=0):
+    """Chains of Algorithm 3: samples [niter+1][nchains][nth], logliks
+    [niter+1][nchains], accepted [nchains], near [niter+1][nchains]."""
+    th0 = np.ascontiguousarray(theta0, dtype=np.float64)
+    nc, nth = th0.shape
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    sp = params(spec)
+    samples = np.zeros((niter + 1, nc, nth))
+    lls = np.zeros((niter + 1, nc))
+    acc = np.zeros(nc, dtype=np.int32)
+    near = np.zeros((niter + 1, nc), dtype=np.int32)
+    st = lib().or_pmmh(ctypes.byref(m), _ptr(yy, _dp), P, T, lik, nc, sp, _ptr(th0, _dp), niter,
+                       seed, nthreads, _ptr(samples, _dp), _ptr(lls, _dp), _ptr(acc, _ip),
+                       _ptr(near, _ip))
+    return dict(status=st, samples=samples, logliks=lls, accepted=acc, near=near)

@@ -73,7 +73,7 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 
 /* Counter layout: (particle j, time index i, (purpose << 16) | block, 0);
  * key = (low, high) 32-bit halves of the 64-bit seed. */
-static void or_block(uint64_t seed, uint32_t j, uint32_t i, uint32_t purpose, uint32_t blk,
+void or_block(uint64_t seed, uint32_t j, uint32_t i, uint32_t purpose, uint32_t blk,
                      uint32_t w[4]) {
   uint32_t ctr[4], key[2];
   ctr[0] = j;
@@ -86,11 +86,11 @@ static void or_block(uint64_t seed, uint32_t j, uint32_t i, uint32_t purpose, ui
 }
 
 /* 53-bit uniforms from the 64-bit word (hi:lo). */
-static double or_u53_half_open(uint32_t lo, uint32_t hi) { /* [0, 1) */
+double or_u53_half_open(uint32_t lo, uint32_t hi) { /* [0, 1) */
   uint64_t v = ((((uint64_t)hi) << 32) | (uint64_t)lo) >> 11;
   return (double)v * 0x1.0p-53;
 }
-static double or_u53_open_zero(uint32_t lo, uint32_t hi) { /* (0, 1] */
+double or_u53_open_zero(uint32_t lo, uint32_t hi) { /* (0, 1] */
   uint64_t v = ((((uint64_t)hi) << 32) | (uint64_t)lo) >> 11;
   return (double)(v + 1u) * 0x1.0p-53;
 }

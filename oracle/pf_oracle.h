@@ -29,7 +29,8 @@ enum { OR_WINDKESSEL = 0, OR_LORENZ96 = 1 };
 enum { OR_FP64 = 0, OR_MIXED = 1 };
 enum { OR_OK = 0, OR_EINVAL = 1, OR_EDEGENERATE = 4 };
 /* Philox counter word 2 carries (purpose << 16) | block index. */
-enum { OR_PURPOSE_INIT = 1, OR_PURPOSE_PROP = 2, OR_PURPOSE_RESAMPLE = 3, OR_PURPOSE_PATH = 4 };
+enum { OR_PURPOSE_INIT = 1, OR_PURPOSE_PROP = 2, OR_PURPOSE_RESAMPLE = 3, OR_PURPOSE_PATH = 4,
+       OR_PURPOSE_PMMH = 5, OR_PURPOSE_SMC2 = 6 };
 
 typedef struct {
   int32_t kind;          /* OR_WINDKESSEL or OR_LORENZ96 */
@@ -46,6 +47,12 @@ typedef struct {
 
 /* --- random numbers ---------------------------------------------------- */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* Philox block of counter (j, i, (purpose << 16) | blk, 0), key = seed halves */
+void or_block(uint64_t seed, uint32_t j, uint32_t i, uint32_t purpose, uint32_t blk,
+              uint32_t w[4]);
+/* 53-bit uniforms from the 64-bit word (hi:lo): [0, 1) and (0, 1] */
+double or_u53_half_open(uint32_t lo, uint32_t hi);
+double or_u53_open_zero(uint32_t lo, uint32_t hi);
 /* normal number q of the stream (j, i, purpose), FP64 (2 normals per block) */
 double or_normal64(uint64_t seed, uint32_t j, uint32_t i, uint32_t purpose, uint32_t q);
 /* normal number q of the stream (j, i, purpose), FP32 (4 normals per block) */
@@ -92,6 +99,33 @@ int32_t or_pf_run_sched(const or_model *m, const double *theta, const double *y,
 int32_t or_sample_path(const or_model *m, const double *theta, const double *y, uint64_t seed,
                        int64_t P, int32_t T, int32_t nthreads, double *loglik, double *path,
                        int32_t *idx);
+
+/* --- marginal Metropolis-Hastings (Algorithm 3, Eq. mh) ---------------- */
+enum { OR_PRIOR_FIXED = 0, OR_PRIOR_UNIFORM = 1, OR_PRIOR_GAUSSIAN = 2, OR_PRIOR_GAMMA = 3,
+       OR_PRIOR_INV_GAMMA = 4 };
+enum { OR_PROPOSE_FIXED = 0, OR_PROPOSE_TRUNC_GAUSSIAN = 1, OR_PROPOSE_INV_GAMMA = 2 };
+enum { OR_LIK_PF = 0, OR_LIK_KALMAN = 1, OR_LIK_NONE = 2 };
+
+typedef struct {
+  int32_t prior;      /* OR_PRIOR_*: uniform (a, b); gaussian (mean a, sd b);
+                         gamma (shape a, scale b); inverse gamma (shape a, scale b) */
+  int32_t proposal;   /* OR_PROPOSE_*: truncated gaussian around the current value
+                         (sd c, bounds [d, e]); inverse gamma (integer shape c,
+                         scale d * current value) */
+  double a, b, c, d, e;
+} or_param;
+
+double or_log_prior(const or_param *spec, int32_t nth, const double *theta);
+/* One proposal theta' ~ q(. | theta) of chain j at iteration i (Philox key
+ * seed); returns log q(theta | theta') - log q(theta' | theta). */
+double or_propose(const or_param *spec, int32_t nth, const double *theta, uint64_t seed,
+                  uint32_t j, uint32_t i, double *theta_new);
+/* nchains independent chains of niter iterations; samples [niter+1][nchains][nth],
+ * logliks [niter+1][nchains], accepted [nchains], near [niter+1][nchains]. */
+int32_t or_pmmh(const or_model *m, const double *y, int64_t P, int32_t T, int32_t lik,
+                int32_t nchains, const or_param *spec, const double *theta0, int32_t niter,
+                uint64_t seed, int32_t nthreads, double *samples, double *logliks,
+                int32_t *accepted, int32_t *near);
 
 #ifdef __cplusplus
 }
