@@ -168,6 +168,57 @@ pf_status pf_batch_run(int32_t nfilt, pf_filter* const* f, const double* const* 
                        const double* const* y, const uint64_t* seeds, double* logliks,
                        int32_t* per_filter_status, void* cuda_stream);
 
+/* ---- marginal Metropolis-Hastings over the parameters (Algorithm 3) ------ */
+
+typedef enum {
+  PF_PRIOR_FIXED = 0,      /* not sampled: contributes nothing                     */
+  PF_PRIOR_UNIFORM = 1,    /* uniform on [a, b]                                    */
+  PF_PRIOR_GAUSSIAN = 2,   /* gaussian, mean a, standard deviation b              */
+  PF_PRIOR_GAMMA = 3,      /* gamma, shape a, scale b                              */
+  PF_PRIOR_INV_GAMMA = 4   /* inverse gamma, shape a, scale b                      */
+} pf_prior_kind;
+
+typedef enum {
+  PF_PROPOSE_FIXED = 0,           /* the component keeps its value                */
+  PF_PROPOSE_TRUNC_GAUSSIAN = 1,  /* N(current, c^2) truncated to [d, e] (d, e may
+                                     be -/+ infinity)                              */
+  PF_PROPOSE_INV_GAMMA = 2        /* inverse gamma, integer shape c in [1, 64],
+                                     scale d * current value                        */
+} pf_proposal_kind;
+
+/* Prior and proposal of one component of theta (the parameter and
+ * proposal_parameter blocks of the paper's model listings). */
+typedef struct {
+  int32_t prior;      /* pf_prior_kind    */
+  int32_t proposal;   /* pf_proposal_kind */
+  double a, b;        /* prior parameters */
+  double c, d, e;     /* proposal parameters */
+} pf_param;
+
+/* nchains independent marginal Metropolis-Hastings chains (Algorithm 3, the
+ * acceptance rule of Eq. mh) whose likelihoods are particle-filter estimates
+ * (the pseudo-marginal sampler).  Chain c runs its filter f[c] (all filters
+ * of one model kind and T; P, precision and resampling may differ); every
+ * iteration proposes theta' for all chains on the GPU, runs all nchains
+ * filters as one batched launch sequence, and accepts or rejects on the GPU,
+ * so the host only enqueues.
+ *   y        [T][Ny] doubles, host or device, shared by the chains.
+ *   spec     [pf_theta_size(kind)] priors / proposals, host.
+ *   theta0   [nchains][pf_theta_size(kind)] starting points, host.
+ *   niter    iterations after the starting point (>= 0).
+ *   seed     Philox key of the proposals, acceptance uniforms and filter keys:
+ *            counter (c, i, (5 << 16) | block, 0) -- block 0: uniform alpha in
+ *            (0, 1]; block 1: the filter's key; block 16 + 64 d + a: draw a of
+ *            component d (a Box-Muller normal, or the exponential -log u).
+ *   samples  out: [niter+1][nchains][pf_theta_size(kind)] doubles, host or device.
+ *   logliks  out: [niter+1][nchains] log-likelihood estimates of the samples.
+ *   accepted out or NULL: [nchains] int32 accepted-move counts.
+ * A proposal outside the prior's support or whose filter degenerates is
+ * rejected.  Synchronous on cuda_stream (NULL: the plan's stream). */
+pf_status pf_pmmh_run(int32_t nchains, pf_filter* const* f, const double* y,
+                      const pf_param* spec, const double* theta0, int32_t niter, uint64_t seed,
+                      double* samples, double* logliks, int32_t* accepted, void* cuda_stream);
+
 /* Continuous-batching request server.  Requests (model, P, T, dt, theta, y,
  * seed) are queued on submit; a scheduler thread admits them when the device
  * memory budget and a slot allow, advances every admitted filter one

@@ -68,6 +68,10 @@ def lib():
                                       ctypes.POINTER(ctypes.c_int64)]
         L.pf_measure_fma_peak.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]
+        L.pf_pmmh_run.argtypes = [ctypes.c_int32, ctypes.POINTER(_vp), _vp,
+                                  ctypes.POINTER(pf_param), _vp, ctypes.c_int32,
+                                  ctypes.c_uint64, _vp, _vp, _vp, _vp]
+        L.pf_pmmh_run.restype = ctypes.c_int
         L.pf_run_range.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32,
                                    _vp, _vp, _vp]
         L.pf_sample_path.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp, _vp]
@@ -112,6 +116,43 @@ def _check(st, ok=(PF_OK,)):
 def model(kind, N=1, substeps=1, obs_stride=1, prec=PF_FP64, ess_threshold=1.0, flow_peak=400.0,
           flow_period=1.0):
     return pf_model(kind, N, substeps, obs_stride, prec, 0, ess_threshold, flow_peak, flow_period)
+
+
+PF_PRIOR_FIXED, PF_PRIOR_UNIFORM, PF_PRIOR_GAUSSIAN, PF_PRIOR_GAMMA, PF_PRIOR_INV_GAMMA = range(5)
+PF_PROPOSE_FIXED, PF_PROPOSE_TRUNC_GAUSSIAN, PF_PROPOSE_INV_GAMMA = range(3)
+
+
+class pf_param(ctypes.Structure):
+    """Prior and proposal of one component of theta (include/pf.h)."""
+    _fields_ = [("prior", ctypes.c_int32), ("proposal", ctypes.c_int32),
+                ("a", ctypes.c_double), ("b", ctypes.c_double), ("c", ctypes.c_double),
+                ("d", ctypes.c_double), ("e", ctypes.c_double)]
+
+
+def params(spec):
+    """List of (prior, proposal, a, b, c, d, e) tuples -> pf_param array."""
+    arr = (pf_param * len(spec))()
+    for k, t in enumerate(spec):
+        t = tuple(t) + (0.0,) * (7 - len(t))
+        arr[k] = pf_param(int(t[0]), int(t[1]), *[float(v) for v in t[2:7]])
+    return arr
+
+
+def pf_pmmh_run(filters, y, spec, theta0, niter, seed, stream=None):
+    """Marginal Metropolis-Hastings chains, one per filter (Algorithm 3):
+    returns samples [niter+1][nchains][nth], logliks [niter+1][nchains],
+    accepted [nchains]."""
+    nc = len(filters)
+    th0 = np.ascontiguousarray(theta0, dtype=np.float64).reshape(nc, -1)
+    y = np.ascontiguousarray(y, dtype=np.float64) if not hasattr(y, "data_ptr") else y
+    sp = params(spec)
+    hs = (_vp * nc)(*[f.h for f in filters])
+    samples = np.zeros((niter + 1, nc, th0.shape[1]))
+    lls = np.zeros((niter + 1, nc))
+    acc = np.zeros(nc, dtype=np.int32)
+    _check(lib().pf_pmmh_run(nc, hs, _ptr(y), sp, _ptr(th0), niter, ctypes.c_uint64(seed),
+                             _ptr(samples), _ptr(lls), _ptr(acc), _stream_ptr(stream)))
+    return samples, lls, acc
 
 
 def model_from_workload(w):

@@ -388,10 +388,10 @@ static bool is_device_ptr(const void* ptr) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Stage theta, seed and y of every filter of the plan and launch its graph on st.
-pf_status pfb::run_plan(Plan* p, const double* const* theta, const double* const* y,
-                        const uint64_t* seeds, const int32_t* hist_on, cudaStream_t st,
-                        Profiler* prof) {
+// Stage theta, seed and y of every filter of the plan on st (descriptors and
+// host observations through pinned copies, device inputs device to device).
+pf_status pfb::stage_plan(Plan* p, const double* const* theta, const double* const* y,
+                          const uint64_t* seeds, const int32_t* hist_on, cudaStream_t st) {
   CK(cudaEventSynchronize(p->ev_staged));  // pinned staging of the previous run consumed
   std::vector<int> dev_theta, dev_y;
   for (int k = 0; k < p->nf; ++k) {
@@ -428,6 +428,15 @@ pf_status pfb::run_plan(Plan* p, const double* const* theta, const double* const
                        cudaMemcpyDeviceToDevice, st));
   }
   CK(cudaEventRecord(p->ev_staged, st));
+  return PF_OK;
+}
+
+// Stage the inputs of every filter of the plan and launch its graph on st.
+pf_status pfb::run_plan(Plan* p, const double* const* theta, const double* const* y,
+                        const uint64_t* seeds, const int32_t* hist_on, cudaStream_t st,
+                        Profiler* prof) {
+  pf_status ps = stage_plan(p, theta, y, seeds, hist_on, st);
+  if (ps != PF_OK) return ps;
   if (prof) CK(enqueue_run(p, st, prof));
   else CK(cudaGraphLaunch(p->exec, st));
   CK(cudaMemcpyAsync(p->h_res, p->d_res, sizeof(double) * 3 * p->nf, cudaMemcpyDeviceToHost, st));
@@ -645,6 +654,30 @@ extern "C" pf_status pf_destroy(pf_filter* f) {
 // ---------------------------------------------------------------------------
 // batched
 // ---------------------------------------------------------------------------
+// The cached launch plan of a filter list (built on first use; at most eight
+// are kept, the oldest evicted).  The filters must be distinct.
+pf_status pfb::batch_plan(const std::vector<pf_filter*>& key, Plan** out) {
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) {
+      *out = it->second;
+      return PF_OK;
+    }
+  }
+  Plan* p = nullptr;
+  pf_status ps = build_plan(key, &p);
+  if (ps != PF_OK) return ps;
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  if (g_plans.size() >= 8) {
+    destroy_plan(g_plans.begin()->second);
+    g_plans.erase(g_plans.begin());
+  }
+  g_plans[key] = p;
+  *out = p;
+  return PF_OK;
+}
+
 extern "C" pf_status pf_batch_run(int32_t nfilt, pf_filter* const* f, const double* const* theta,
                                   const double* const* y, const uint64_t* seeds, double* logliks,
                                   int32_t* per_filter_status, void* cuda_stream) {
@@ -660,21 +693,8 @@ extern "C" pf_status pf_batch_run(int32_t nfilt, pf_filter* const* f, const doub
       return fail(PF_EINVAL, "a filter appears twice in the batch");
   }
   Plan* p = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_plan_mu);
-    auto it = g_plans.find(key);
-    if (it != g_plans.end()) p = it->second;
-  }
-  if (!p) {
-    pf_status ps = build_plan(key, &p);
-    if (ps != PF_OK) return ps;
-    std::lock_guard<std::mutex> lk(g_plan_mu);
-    if (g_plans.size() >= 8) {
-      destroy_plan(g_plans.begin()->second);
-      g_plans.erase(g_plans.begin());
-    }
-    g_plans[key] = p;
-  }
+  pf_status bs = batch_plan(key, &p);
+  if (bs != PF_OK) return bs;
   cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : p->st;
   for (int k = 0; k < nfilt; ++k) key[k]->range_pos = -1;
   pf_status ps = run_plan(p, theta, y, seeds, nullptr, st, nullptr);

@@ -132,8 +132,11 @@ struct Plan {
 pf_status fail(pf_status st, const char* fmt, ...);
 pf_status check_shape(const pf_model* m, int64_t P, int32_t T, double dt, Shape* sh);
 pf_status build_plan(const std::vector<pf_filter*>& fl, Plan** out);
+pf_status stage_plan(Plan* p, const double* const* theta, const double* const* y,
+                     const uint64_t* seeds, const int32_t* hist_on, cudaStream_t st);
 pf_status run_plan(Plan* p, const double* const* theta, const double* const* y,
                    const uint64_t* seeds, const int32_t* hist_on, cudaStream_t st,
                    Profiler* prof);
+pf_status batch_plan(const std::vector<pf_filter*>& key, Plan** out);
 
 }  // namespace pfb
