@@ -37,6 +37,9 @@ log_prior / propose       Sec. 2.1 parameter / proposal blocks     scipy logpdf,
 pmmh                      Algorithm 3, Eq. (mh)                    prior-only chains sample the prior;
                                                                     Kalman-likelihood chains match a grid
                                                                     posterior
+smc2                      Algorithm 4                              exact-likelihood (Kalman) runs match
+                                                                    quadrature evidence and posterior;
+                                                                    filter runs keep the evidence
 ========================  =======================================  ==========================================
 """
 import ctypes
@@ -131,6 +134,10 @@ def lib():
         L.or_propose.argtypes = [ctypes.POINTER(Param), ctypes.c_int32, _dp, ctypes.c_uint64,
                                  ctypes.c_uint32, ctypes.c_uint32, _dp]
         L.or_propose.restype = ctypes.c_double
+        L.or_smc2.argtypes = [ctypes.POINTER(Model), _dp, ctypes.c_int64, ctypes.c_int32,
+                              ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(Param), _dp,
+                              ctypes.c_uint64, ctypes.c_int32, _dp, _dp, _dp, _dp, _ip, _ip]
+        L.or_smc2.restype = ctypes.c_int32
         L.or_sample_path.argtypes = [ctypes.POINTER(Model), _dp, _dp, ctypes.c_uint64,
                                      ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _dp, _dp, _ip]
         L.or_sample_path.restype = ctypes.c_int32
@@ -345,3 +352,23 @@ def pmmh(m, y, P, T, lik, spec, theta0, niter, seed, nthreads=0):
                        seed, nthreads, _ptr(samples, _dp), _ptr(lls, _dp), _ptr(acc, _ip),
                        _ptr(near, _ip))
     return dict(status=st, samples=samples, logliks=lls, accepted=acc, near=near)
+
+
+def smc2(m, y, P, T, lik, ntheta, spec, base, seed, nthreads=0):
+    """SMC^2 (Algorithm 4): final theta-particles, their log-weights, the log
+    evidence and its per-step increments, accepted moves and near flags."""
+    nth = 7 if m.kind == WINDKESSEL else 5
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    b = np.ascontiguousarray(base, dtype=np.float64)
+    sp = params(spec)
+    th = np.zeros((ntheta, nth))
+    logv = np.zeros(ntheta)
+    lz = ctypes.c_double()
+    incr = np.zeros(T)
+    acc = np.zeros(T, dtype=np.int32)
+    near = np.zeros(T, dtype=np.int32)
+    st = lib().or_smc2(ctypes.byref(m), _ptr(yy, _dp), P, T, lik, ntheta, sp, _ptr(b, _dp), seed,
+                       nthreads, _ptr(th, _dp), _ptr(logv, _dp), ctypes.byref(lz), _ptr(incr, _dp),
+                       _ptr(acc, _ip), _ptr(near, _ip))
+    return dict(status=st, theta=th, logv=logv, log_evidence=lz.value, incr=incr, accepted=acc,
+                near=near)

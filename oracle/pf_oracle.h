@@ -127,6 +127,16 @@ int32_t or_pmmh(const or_model *m, const double *y, int64_t P, int32_t T, int32_
                 uint64_t seed, int32_t nthreads, double *samples, double *logliks,
                 int32_t *accepted, int32_t *near);
 
+/* --- SMC^2 (Algorithm 4) ---------------------------------------------- */
+/* ntheta parameter particles; base supplies the components whose prior is
+ * OR_PRIOR_FIXED.  Outputs: theta_out [ntheta][nth], logv_out [ntheta] (the
+ * last step's log theta-weights), log_evidence, incr [T] (per-step log
+ * evidence increments), accepted [T] (rejuvenation moves accepted), near [T]. */
+int32_t or_smc2(const or_model *m, const double *y, int64_t P, int32_t T, int32_t lik,
+                int32_t ntheta, const or_param *spec, const double *base, uint64_t seed,
+                int32_t nthreads, double *theta_out, double *logv_out, double *log_evidence,
+                double *incr, int32_t *accepted, int32_t *near);
+
 #ifdef __cplusplus
 }
 #endif
