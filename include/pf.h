@@ -219,6 +219,37 @@ pf_status pf_pmmh_run(int32_t nchains, pf_filter* const* f, const double* y,
                       const pf_param* spec, const double* theta0, int32_t niter, uint64_t seed,
                       double* samples, double* logliks, int32_t* accepted, void* cuda_stream);
 
+/* SMC^2 over the parameters (Algorithm 4): ntheta parameter particles drawn
+ * from the prior, each with its own filter of P particles (model m, T, dt);
+ * for every observation i: multinomial resampling of the parameter particles
+ * on their weights, one Metropolis-Hastings move per particle (Eq. mh, its
+ * likelihood from a fresh filter over t_{0:i-1}; a rejected move keeps a
+ * copy of the ancestor's filter), then every filter continues over
+ * t_{i-1:i} and its likelihood increment is the particle's new weight.
+ *   y            [T][Ny] doubles, host or device.
+ *   spec         [pf_theta_size(kind)] priors / proposals, host; gamma and
+ *                inverse-gamma priors need integer shapes 1..64 (drawn as
+ *                sums of unit exponentials).
+ *   theta_base   [pf_theta_size(kind)] values of the PF_PRIOR_FIXED components.
+ *   seed         Philox key; counter (j, i, (6 << 16) | block, 0): block 0 the
+ *                multinomial uniform, 1 the rejuvenation filter's key, 2 the
+ *                continuation's key (step 0: the initial filter's), 3 the
+ *                acceptance uniform, 16 + 64 d + a the prior draw (step 0) or
+ *                proposal (step i) of component d.
+ *   theta_out    out: [ntheta][pf_theta_size(kind)] the particles at t_T.
+ *   logw_out     out: [ntheta] their log-weights log v^j(t_T).
+ *   log_evidence out: sum_i log((1/ntheta) sum_j v^j(t_i)), the log of the
+ *                marginal-likelihood estimate.
+ *   evidence_incr out or NULL: [T] the per-observation terms of that sum.
+ *   accepted     out or NULL: [T] moves accepted at each observation.
+ * Outputs may be host or device memory.  Allocates 2 * ntheta filters for the
+ * call (the rejuvenation population and the current one).  Synchronous;
+ * PF_EDEGENERATE if every parameter particle's weight vanished. */
+pf_status pf_smc2_run(const pf_model* m, int64_t P, int32_t T, double dt, const double* y,
+                      int32_t ntheta, const pf_param* spec, const double* theta_base,
+                      uint64_t seed, double* theta_out, double* logw_out, double* log_evidence,
+                      double* evidence_incr, int32_t* accepted, void* cuda_stream);
+
 /* Continuous-batching request server.  Requests (model, P, T, dt, theta, y,
  * seed) are queued on submit; a scheduler thread admits them when the device
  * memory budget and a slot allow, advances every admitted filter one

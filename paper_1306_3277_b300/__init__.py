@@ -72,6 +72,10 @@ def lib():
                                   ctypes.POINTER(pf_param), _vp, ctypes.c_int32,
                                   ctypes.c_uint64, _vp, _vp, _vp, _vp]
         L.pf_pmmh_run.restype = ctypes.c_int
+        L.pf_smc2_run.argtypes = [ctypes.POINTER(pf_model), ctypes.c_int64, ctypes.c_int32,
+                                  ctypes.c_double, _vp, ctypes.c_int32, ctypes.POINTER(pf_param),
+                                  _vp, ctypes.c_uint64, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.pf_smc2_run.restype = ctypes.c_int
         L.pf_run_range.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32,
                                    _vp, _vp, _vp]
         L.pf_sample_path.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp, _vp]
@@ -153,6 +157,25 @@ def pf_pmmh_run(filters, y, spec, theta0, niter, seed, stream=None):
     _check(lib().pf_pmmh_run(nc, hs, _ptr(y), sp, _ptr(th0), niter, ctypes.c_uint64(seed),
                              _ptr(samples), _ptr(lls), _ptr(acc), _stream_ptr(stream)))
     return samples, lls, acc
+
+
+def pf_smc2_run(m, P, T, dt, y, ntheta, spec, theta_base, seed, stream=None):
+    """SMC^2 (Algorithm 4): returns (status, theta [ntheta][nth], log-weights
+    [ntheta], log evidence, per-step evidence increments [T], accepted moves [T])."""
+    nth = len(theta_base)
+    y = np.ascontiguousarray(y, dtype=np.float64) if not hasattr(y, "data_ptr") else y
+    base = np.ascontiguousarray(theta_base, dtype=np.float64)
+    sp = params(spec)
+    th = np.zeros((ntheta, nth))
+    logw = np.zeros(ntheta)
+    lz = np.zeros(1)
+    incr = np.zeros(T)
+    acc = np.zeros(T, dtype=np.int32)
+    st = lib().pf_smc2_run(ctypes.byref(m), P, T, dt, _ptr(y), ntheta, sp, _ptr(base),
+                           ctypes.c_uint64(seed), _ptr(th), _ptr(logw), _ptr(lz), _ptr(incr),
+                           _ptr(acc), _stream_ptr(stream))
+    st = _check(st, ok=(PF_OK, PF_EDEGENERATE))
+    return st, th, logw, float(lz[0]), incr, acc
 
 
 def model_from_workload(w):

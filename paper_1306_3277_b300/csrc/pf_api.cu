@@ -218,17 +218,18 @@ static void destroy_plan(Plan* p) {
   delete p;
 }
 
-// The launch sequence of steps first..last of a plan: init when first == 1,
-// then for every step one propagate launch per class and one resample launch
-// (only over the filters that are still running), then the results gather.
-// hook(i) is called after the propagate launches of step i (and hook(0)
-// after init), to enqueue work that reads x(t_i).  With a profiler, every
-// launch is bracketed by CUDA events on the same stream.
+// The launch sequence of steps first..last of a plan: the initial draw when
+// `init` (normally first == 1), then for every step one propagate launch per
+// class and one resample launch (only over the filters that are still
+// running), then the results gather.  hook(i) is called after the propagate
+// launches of step i (and hook(0) after init), to enqueue work that reads
+// x(t_i).  With a profiler, every launch is bracketed by CUDA events on the
+// same stream.
 static cudaError_t no_hook(int) { return cudaSuccess; }
 
 template <typename Hook>
 static cudaError_t enqueue_steps(Plan* p, int first, int last, cudaStream_t st, Profiler* prof,
-                                 Hook&& hook) {
+                                 Hook&& hook, bool init) {
   cudaError_t le = cudaSuccess;
   auto timed = [&](int kind, auto&& launch) {
     if (prof) prof->begin(kind, st);
@@ -236,7 +237,7 @@ static cudaError_t enqueue_steps(Plan* p, int first, int last, cudaStream_t st, 
     if (prof) prof->end(st);
     return r;
   };
-  if (first == 1) {
+  if (init) {
     for (size_t c = 0; c < p->classes.size() && le == cudaSuccess; ++c) {
       const PlanClass& pc = p->classes[c];
       le = timed(PROF_INIT, [&] {
@@ -267,7 +268,11 @@ static cudaError_t enqueue_steps(Plan* p, int first, int last, cudaStream_t st, 
 
 // The launch sequence of one whole run of a plan.
 static cudaError_t enqueue_run(Plan* p, cudaStream_t st, Profiler* prof) {
-  return enqueue_steps(p, 1, p->maxT, st, prof, no_hook);
+  return enqueue_steps(p, 1, p->maxT, st, prof, no_hook, true);
+}
+
+cudaError_t pfb::enqueue_plan_steps(Plan* p, int first, int last, bool init, cudaStream_t st) {
+  return enqueue_steps(p, first, last, st, nullptr, no_hook, init);
 }
 
 // Tile maps sorted by T descending so that the filters still running at step
@@ -563,7 +568,7 @@ extern "C" pf_status pf_run_range(pf_filter* f, const double* theta, const doubl
                        cudaMemcpyHostToDevice, st));
   }
   CK(cudaEventRecord(p->ev_staged, st));
-  CK(enqueue_steps(p, r + 1, s, st, f->prof, no_hook));
+  CK(enqueue_steps(p, r + 1, s, st, f->prof, no_hook, r == 0));
   CK(cudaMemcpyAsync(p->h_res, p->d_res, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
   if (particles)
     CK(cudaMemcpyAsync(particles, f->x[s & 1], size_t(f->m.N) * f->P * f->sh.state_bytes,
@@ -607,9 +612,10 @@ extern "C" pf_status pf_sample_path(pf_filter* f, const double* theta, const dou
   // copying x(t_i) of particle b_i after each propagate
   const int prec = f->m.prec;
   const int P = int(f->P);
-  CK(enqueue_steps(p, 1, T, st, nullptr, [&](int i) {
-    return launch_path_copy(f->x[i & 1], prec, N, P, f->path_idx, i, f->path, st);
-  }));
+  CK(enqueue_steps(
+      p, 1, T, st, nullptr,
+      [&](int i) { return launch_path_copy(f->x[i & 1], prec, N, P, f->path_idx, i, f->path, st); },
+      true));
   CK(cudaMemcpyAsync(path, f->path, sizeof(double) * size_t(T + 1) * N, cudaMemcpyDefault, st));
   if (path_index)
     CK(cudaMemcpyAsync(path_index, f->path_idx, sizeof(int32_t) * size_t(T + 1),

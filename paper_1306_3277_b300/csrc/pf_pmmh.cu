@@ -25,19 +25,11 @@
 #include <cstring>
 #include <vector>
 
+#include "pf_params.cuh"
 #include "pf_runtime.h"
 
 namespace pfb {
 namespace {
-
-constexpr int MAX_THETA = 8;
-constexpr int TG_ATTEMPTS = 64;
-constexpr uint32_t PURPOSE_PMMH = 5;
-
-struct Spec {
-  pf_param p[MAX_THETA];
-  int nth;
-};
 
 struct Chains {
   double* theta;    // [nc][MAX_THETA] current parameters
@@ -49,50 +41,8 @@ struct Chains {
   int32_t* acc;     // [nc] accepted moves
 };
 
-__device__ double log_prior(const Spec& sp, const double* th) {
-  double lp = 0.0;
-  for (int d = 0; d < sp.nth; ++d) {
-    const pf_param& p = sp.p[d];
-    const double x = th[d];
-    switch (p.prior) {
-      case PF_PRIOR_UNIFORM:
-        if (!(x >= p.a && x <= p.b)) return -INFINITY;
-        lp += -log(p.b - p.a);
-        break;
-      case PF_PRIOR_GAUSSIAN: {
-        const double z = (x - p.a) / p.b;
-        lp += -0.5 * z * z - log(p.b) - 0.5 * log(2.0 * 3.141592653589793);
-        break;
-      }
-      case PF_PRIOR_GAMMA:
-        if (!(x > 0.0)) return -INFINITY;
-        lp += (p.a - 1.0) * log(x) - x / p.b - lgamma(p.a) - p.a * log(p.b);
-        break;
-      case PF_PRIOR_INV_GAMMA:
-        if (!(x > 0.0)) return -INFINITY;
-        lp += p.a * log(p.b) - lgamma(p.a) - (p.a + 1.0) * log(x) - p.b / x;
-        break;
-      default:
-        break;
-    }
-  }
-  return lp;
-}
-
-// log of the probability N(mu, sd^2) gives to [lo, hi]
-__device__ double tg_log_mass(double mu, double sd, double lo, double hi) {
-  const double up = isinf(hi) ? 1.0 : 0.5 * erfc(-(hi - mu) / sd * 0.7071067811865476);
-  const double dn = isinf(lo) ? 0.0 : 0.5 * erfc(-(lo - mu) / sd * 0.7071067811865476);
-  return log(up - dn);
-}
-
-__device__ double ig_logpdf(double x, double shape, double scale) {
-  return shape * log(scale) - lgamma(shape) - (shape + 1.0) * log(x) - scale / x;
-}
-
 __device__ uint64_t filter_key(uint64_t seed, uint32_t c, uint32_t i) {
-  const uint4 w = rng_block(seed, c, i, PURPOSE_PMMH, 1u);
-  return (uint64_t(w.y) << 32) | uint64_t(w.x);
+  return philox_key(seed, c, i, PURPOSE_PMMH, 1u);
 }
 
 __global__ void k_pmmh_start(Spec sp, FilterDev* __restrict__ fds, int nc, Chains ch,
@@ -111,40 +61,10 @@ __global__ void k_pmmh_propose(Spec sp, FilterDev* __restrict__ fds, int nc, Cha
                                uint64_t seed, int it) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
-  const double* th = ch.theta + size_t(c) * MAX_THETA;
   double* out = ch.theta_p + size_t(c) * MAX_THETA;
-  double lqr = 0.0;
-  for (int d = 0; d < sp.nth; ++d) {
-    const pf_param& p = sp.p[d];
-    const double x = th[d];
-    double xn = x;
-    if (p.proposal == PF_PROPOSE_TRUNC_GAUSSIAN) {
-      for (int a = 0; a < TG_ATTEMPTS; ++a) {
-        const uint4 w = rng_block(seed, uint32_t(c), uint32_t(it), PURPOSE_PMMH,
-                                  16u + 64u * uint32_t(d) + uint32_t(a));
-        double z0, z1;
-        normal_pair64(w, &z0, &z1);
-        const double v = fma(p.c, z0, x);
-        if (v >= p.d && v <= p.e) {
-          xn = v;
-          break;
-        }
-      }
-      lqr += tg_log_mass(x, p.c, p.d, p.e) - tg_log_mass(xn, p.c, p.d, p.e);
-    } else if (p.proposal == PF_PROPOSE_INV_GAMMA) {
-      const int k = int(p.c);
-      double sum = 0.0;
-      for (int a = 0; a < k; ++a) {
-        const uint4 w = rng_block(seed, uint32_t(c), uint32_t(it), PURPOSE_PMMH,
-                                  16u + 64u * uint32_t(d) + uint32_t(a));
-        sum = sum + -log_pos(u53_open_closed(w.x, w.y));
-      }
-      xn = (p.d * x) / sum;
-      lqr += ig_logpdf(x, p.c, p.d * xn) - ig_logpdf(xn, p.c, p.d * x);
-    }
-    out[d] = xn;
-    fds[c].theta[d] = xn;
-  }
+  const double lqr = propose(sp, ch.theta + size_t(c) * MAX_THETA, seed, uint32_t(c), uint32_t(it),
+                             PURPOSE_PMMH, out);
+  for (int d = 0; d < sp.nth; ++d) fds[c].theta[d] = out[d];
   ch.lp_p[c] = log_prior(sp, out);
   ch.lqr[c] = lqr;
   fds[c].seed = filter_key(seed, uint32_t(c), uint32_t(it));
@@ -175,32 +95,6 @@ __global__ void k_pmmh_accept(Spec sp, const FilterDev* __restrict__ fds, int nc
   }
   for (int d = 0; d < sp.nth; ++d) samples_row[size_t(c) * sp.nth + d] = th[d];
   ll_row[c] = ch.ll[c];
-}
-
-pf_status check_spec(const pf_param* spec, int nth) {
-  for (int d = 0; d < nth; ++d) {
-    const pf_param& p = spec[d];
-    bool ok = true;
-    switch (p.prior) {
-      case PF_PRIOR_FIXED: break;
-      case PF_PRIOR_UNIFORM: ok = p.a < p.b; break;
-      case PF_PRIOR_GAUSSIAN: ok = p.b > 0.0; break;
-      case PF_PRIOR_GAMMA:
-      case PF_PRIOR_INV_GAMMA: ok = p.a > 0.0 && p.b > 0.0; break;
-      default: ok = false;
-    }
-    if (!ok) return fail(PF_EINVAL, "prior of theta[%d]: bad kind or parameters", d);
-    switch (p.proposal) {
-      case PF_PROPOSE_FIXED: break;
-      case PF_PROPOSE_TRUNC_GAUSSIAN: ok = p.c > 0.0 && p.d < p.e; break;
-      case PF_PROPOSE_INV_GAMMA:
-        ok = p.c >= 1.0 && p.c <= 64.0 && p.c == std::floor(p.c) && p.d > 0.0;
-        break;
-      default: ok = false;
-    }
-    if (!ok) return fail(PF_EINVAL, "proposal of theta[%d]: bad kind or parameters", d);
-  }
-  return PF_OK;
 }
 
 }  // namespace

@@ -138,5 +138,8 @@ pf_status run_plan(Plan* p, const double* const* theta, const double* const* y,
                    const uint64_t* seeds, const int32_t* hist_on, cudaStream_t st,
                    Profiler* prof);
 pf_status batch_plan(const std::vector<pf_filter*>& key, Plan** out);
+// Direct launches of steps first..last of a plan (with the initial draw when
+// init), then the results gather; no staging, no graph.
+cudaError_t enqueue_plan_steps(Plan* p, int first, int last, bool init, cudaStream_t st);
 
 }  // namespace pfb
