@@ -25,6 +25,9 @@ lse                       Algorithm 2 likelihood line, log space   equal / one-h
                                                                     math.fsum
 systematic                Sec. 3.3 systematic resampling           integer weights (exact), brute-force
                                                                     offspring enumeration on P <= 8
+resample (stratified,     Sec. 3.3 / Algorithm 2 multinomial       exact rational targets from the
+ multinomial)             (sorted: exponential spacings)           published Philox stream; offspring
+                                                                    mean, variance, range over seeds
 pf_run                    Algorithm 2                              Kalman likelihood (exact special case
                                                                     and convergence over P), closed-form
                                                                     deterministic Lorenz '96 likelihood
@@ -60,6 +63,7 @@ PURPOSE_PATH = 4
 PURPOSE_PMMH = 5
 PURPOSE_SMC2 = 6
 OK = 0
+RESAMPLE_SYSTEMATIC, RESAMPLE_STRATIFIED, RESAMPLE_MULTINOMIAL = range(3)
 EINVAL = 1
 EDEGENERATE = 4
 
@@ -71,7 +75,7 @@ class Model(ctypes.Structure):
         ("substeps", ctypes.c_int32),
         ("obs_stride", ctypes.c_int32),
         ("prec", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("resampler", ctypes.c_int32),
         ("dt", ctypes.c_double),
         ("ess_threshold", ctypes.c_double),
         ("flow_peak", ctypes.c_double),
@@ -116,6 +120,9 @@ def lib():
         L.or_lse.argtypes = [_dp, ctypes.c_int64, _dp, _dp, _dp]
         L.or_systematic.argtypes = [_dp, ctypes.c_int64, ctypes.c_double, _ip]
         L.or_systematic.restype = ctypes.c_int64
+        L.or_resample.argtypes = [_dp, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                  ctypes.c_uint32, _ip]
+        L.or_resample.restype = ctypes.c_int64
         L.or_pf_run.argtypes = [ctypes.POINTER(Model), _dp, _dp, ctypes.c_uint64, ctypes.c_int64,
                                 ctypes.c_int32, ctypes.c_int32, _dp, _dp, _ip, _dp]
         L.or_pf_run.restype = ctypes.c_int32
@@ -150,8 +157,9 @@ def _ptr(a, t):
 
 
 def model(kind, N=1, substeps=1, obs_stride=1, prec=FP64, dt=0.01, ess_threshold=1.0,
-          flow_peak=400.0, flow_period=1.0):
-    return Model(kind, N, substeps, obs_stride, prec, 0, dt, ess_threshold, flow_peak, flow_period)
+          flow_peak=400.0, flow_period=1.0, resampler=0):
+    return Model(kind, N, substeps, obs_stride, prec, resampler, dt, ess_threshold, flow_peak,
+                 flow_period)
 
 
 def philox4x32_10(ctr, key):
@@ -237,6 +245,15 @@ def systematic(ell, u):
     e = np.ascontiguousarray(ell, dtype=np.float64)
     anc = np.zeros(len(e), dtype=np.int32)
     near = lib().or_systematic(_ptr(e, _dp), len(e), float(u), _ptr(anc, _ip))
+    return anc, int(near)
+
+
+def resample(ell, kind, seed, i):
+    """Ancestors of resampling step i (systematic, stratified or multinomial)
+    from log-weights ell; returns (ancestors, near-boundary count)."""
+    e = np.ascontiguousarray(ell, dtype=np.float64)
+    anc = np.zeros(len(e), dtype=np.int32)
+    near = lib().or_resample(_ptr(e, _dp), len(e), kind, seed, i, _ptr(anc, _ip))
     return anc, int(near)
 
 

@@ -472,6 +472,95 @@ static int64_t or_systematic_from_w(const double *w, int64_t P, double u, int32_
   return near;
 }
 
+/* ======================================================================
+ * Stratified and multinomial resampling (Sec. 3.3; Algorithm 2 draws the
+ * ancestors from a multinomial).  Both compare targets against the scaled
+ * cumulative weights E_k = C_k (P / S) (C_k compensated, ratio rounded once)
+ * and give a_j = min{k : E_k > target_j}, clamped to P-1; targets increase
+ * with j, so ancestors come out sorted.
+ *   stratified:  target_j = j + u_j, u_j in [0, 1) from Philox block
+ *                (j, i, RESAMPLE, 1), words 1:0; E_k > j + u_j is evaluated
+ *                as E_k - j > u_j, which is exact (E_k - j is exact whenever
+ *                the comparison is not decided by sign or magnitude).
+ *   multinomial: P + 1 unit exponentials e_l = -log u_l (own log; u_l in
+ *                (0, 1] from block (l, i, RESAMPLE, 2), words 1:0), partial
+ *                sums G_m = e_0 + .. + e_m (compensated); target_j =
+ *                G_j (P / G_P).  (G_0, .., G_{P-1}) / G_P are the order
+ *                statistics of P independent uniforms, so the offspring
+ *                counts are Multinomial(P, w / S).
+ * A target within 1e-12 P of E_k or E_{k-1} counts as near.
+ * ==================================================================== */
+static int64_t or_resample_other(const double *w, int64_t P, int32_t kind, uint64_t seed,
+                                 uint32_t i, int32_t *anc, double *Cbuf) {
+  double sum = 0.0, comp = 0.0, S, ratio, tscale = 0.0;
+  double *G = NULL;
+  int64_t j, k, near = 0;
+  for (k = 0; k < P; ++k) {
+    or_neumaier_add(&sum, &comp, w[k]);
+    Cbuf[k] = sum + comp;
+  }
+  S = Cbuf[P - 1];
+  ratio = (double)P / S;
+  for (k = 0; k < P; ++k) Cbuf[k] = Cbuf[k] * ratio; /* E_k */
+  if (kind == OR_RESAMPLE_MULTINOMIAL) {
+    double gs = 0.0, gc = 0.0;
+    uint32_t wd[4];
+    G = (double *)malloc(sizeof(double) * (size_t)P);
+    for (j = 0; j <= P; ++j) {
+      or_block(seed, (uint32_t)j, i, OR_PURPOSE_RESAMPLE, 2u, wd);
+      or_neumaier_add(&gs, &gc, -or_log(or_u53_open_zero(wd[0], wd[1])));
+      if (j < P) G[j] = gs + gc;
+    }
+    tscale = (double)P / (gs + gc);
+  }
+  for (j = 0; j < P; ++j) {
+    double uj = 0.0, tj;
+    int64_t lo = 0, hi = P;
+    if (kind == OR_RESAMPLE_STRATIFIED) {
+      uint32_t wd[4];
+      or_block(seed, (uint32_t)j, i, OR_PURPOSE_RESAMPLE, 1u, wd);
+      uj = or_u53_half_open(wd[0], wd[1]);
+      tj = (double)j + uj; /* for the near test only */
+      while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (Cbuf[mid] - (double)j > uj) hi = mid;
+        else lo = mid + 1;
+      }
+    } else {
+      tj = G[j] * tscale;
+      while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (Cbuf[mid] > tj) hi = mid;
+        else lo = mid + 1;
+      }
+    }
+    k = lo < P ? lo : P - 1;
+    anc[j] = (int32_t)k;
+    if (fabs(tj - Cbuf[k]) <= 1e-12 * (double)P ||
+        (k > 0 && fabs(tj - Cbuf[k - 1]) <= 1e-12 * (double)P))
+      ++near;
+  }
+  free(G);
+  return near;
+}
+
+int64_t or_resample(const double *ell, int64_t P, int32_t kind, uint64_t seed, uint32_t i,
+                    int32_t *anc) {
+  double M, S, Q;
+  double *w = (double *)malloc(sizeof(double) * (size_t)P);
+  double *C = (double *)malloc(sizeof(double) * (size_t)P);
+  int64_t j, near;
+  or_lse(ell, P, &M, &S, &Q);
+  for (j = 0; j < P; ++j) w[j] = exp(ell[j] - M);
+  if (kind == OR_RESAMPLE_SYSTEMATIC)
+    near = or_systematic_from_w(w, P, or_resample_uniform(seed, i), anc, C);
+  else
+    near = or_resample_other(w, P, kind, seed, i, anc, C);
+  free(w);
+  free(C);
+  return near;
+}
+
 int64_t or_systematic(const double *ell, int64_t P, double u, int32_t *anc) {
   double M, S, Q;
   double *w = (double *)malloc(sizeof(double) * (size_t)P);
@@ -637,6 +726,8 @@ int32_t or_pf_run_sched(const or_model *m, const double *th, const double *y, ui
   if (P <= 0 || T <= 0 || N <= 0 || s <= 0) return OR_EINVAL;
   if (m->kind == OR_WINDKESSEL && N != 1) return OR_EINVAL;
   if (m->kind == OR_LORENZ96 && (N < 4 || N > 256 || stride <= 0)) return OR_EINVAL;
+  if (m->resampler < OR_RESAMPLE_SYSTEMATIC || m->resampler > OR_RESAMPLE_MULTINOMIAL)
+    return OR_EINVAL;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
@@ -740,8 +831,12 @@ int32_t or_pf_run_sched(const or_model *m, const double *th, const double *y, ui
     resample = (i < T) && (m->ess_threshold >= 1.0 || ess < m->ess_threshold * (double)P);
     if (resample) {
       for (j = 0; j < P; ++j) w[j] = exp(ell[j] - M);
-      u = or_resample_uniform(cx.seed, (uint32_t)i);
-      near = or_systematic_from_w(w, P, u, acur, Cbuf);
+      if (m->resampler == OR_RESAMPLE_SYSTEMATIC) {
+        u = or_resample_uniform(cx.seed, (uint32_t)i);
+        near = or_systematic_from_w(w, P, u, acur, Cbuf);
+      } else {
+        near = or_resample_other(w, P, m->resampler, cx.seed, (uint32_t)i, acur, Cbuf);
+      }
       anc_identity = 0;
       lam_zero = 1;
       L = log((double)P);

@@ -28,6 +28,7 @@ extern "C" {
 enum { OR_WINDKESSEL = 0, OR_LORENZ96 = 1 };
 enum { OR_FP64 = 0, OR_MIXED = 1 };
 enum { OR_OK = 0, OR_EINVAL = 1, OR_EDEGENERATE = 4 };
+enum { OR_RESAMPLE_SYSTEMATIC = 0, OR_RESAMPLE_STRATIFIED = 1, OR_RESAMPLE_MULTINOMIAL = 2 };
 /* Philox counter word 2 carries (purpose << 16) | block index. */
 enum { OR_PURPOSE_INIT = 1, OR_PURPOSE_PROP = 2, OR_PURPOSE_RESAMPLE = 3, OR_PURPOSE_PATH = 4,
        OR_PURPOSE_PMMH = 5, OR_PURPOSE_SMC2 = 6 };
@@ -38,7 +39,7 @@ typedef struct {
   int32_t substeps;      /* Euler / RK4 substeps per observation interval */
   int32_t obs_stride;    /* Lorenz '96: components n with n % obs_stride == 0 are observed */
   int32_t prec;          /* OR_FP64 or OR_MIXED (FP32 state and noise, FP64 weights) */
-  int32_t pad;
+  int32_t resampler;     /* OR_RESAMPLE_SYSTEMATIC / _STRATIFIED / _MULTINOMIAL */
   double dt;             /* substep length */
   double ess_threshold;  /* >= 1: resample every step; else resample iff ESS < thr * P */
   double flow_peak;      /* windkessel input F(t): peak of the half sine */
@@ -80,6 +81,10 @@ void or_lse(const double *ell, int64_t P, double *M, double *S, double *Q);
 /* systematic resampling from log-weights; returns the number of
  * near-boundary targets (|E_k - j| <= 1e-12 P, E_k = C_k P / S - u) */
 int64_t or_systematic(const double *ell, int64_t P, double u, int32_t *anc);
+/* resampling of step i with any of the three schemes (systematic uses the
+ * uniform of or_resample_uniform); returns the near-boundary count */
+int64_t or_resample(const double *ell, int64_t P, int32_t kind, uint64_t seed, uint32_t i,
+                    int32_t *anc);
 
 /* --- the filter --------------------------------------------------------- */
 /* diag, if not NULL, receives per step i (row i-1) 8 doubles:

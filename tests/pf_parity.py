@@ -8,7 +8,7 @@ import oracle as O
 def oracle_model(w):
     return O.model(w.kind, N=w.N, substeps=w.substeps, obs_stride=w.obs_stride, prec=w.prec,
                    dt=w.dt, ess_threshold=w.ess_threshold, flow_peak=w.flow_peak,
-                   flow_period=w.flow_period)
+                   flow_period=w.flow_period, resampler=w.resampler)
 
 
 def run_oracle(w, seed, theta=None, nthreads=0):

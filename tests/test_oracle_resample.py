@@ -109,3 +109,90 @@ def test_systematic_offspring_brute_force(P):
                 integral[k] += Fraction(b - a) * int(o[k])
         for k in range(P):
             assert float(integral[k]) == pytest.approx(float(P * w[k] / S), abs=1e-8)
+
+
+# ---- stratified and multinomial resampling --------------------------------
+def _uniform(seed, j, i, blk, open_zero=False):
+    w = O.philox4x32_10([j, i, (O.PURPOSE_RESAMPLE << 16) | blk, 0],
+                        [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF])
+    v = ((int(w[1]) << 32) | int(w[0])) >> 11
+    return Fraction(v + (1 if open_zero else 0), 1 << 53)
+
+
+def test_stratified_matches_exact_rational():
+    rng = np.random.default_rng(7)
+    for trial in range(150):
+        P = int(rng.integers(1, 48))
+        ell = rng.normal(0, 2, P)
+        seed, i = int(rng.integers(1, 2 ** 40)), int(rng.integers(1, 50))
+        anc, near = O.resample(ell, O.RESAMPLE_STRATIFIED, seed, i)
+        M = ell.max()
+        w = [Fraction(math.exp(e - M)) for e in ell]
+        C = np.cumsum(w).tolist()
+        S = C[-1]
+        if near:
+            continue
+        ref = []
+        for j in range(P):
+            tau = (j + _uniform(seed, j, i, 1)) * S / P
+            ref.append(next((k for k in range(P) if C[k] > tau), P - 1))
+        assert anc.tolist() == ref
+
+
+def test_multinomial_matches_order_statistics_of_exponential_spacings():
+    rng = np.random.default_rng(8)
+    for trial in range(100):
+        P = int(rng.integers(1, 40))
+        ell = rng.normal(0, 2, P)
+        seed, i = int(rng.integers(1, 2 ** 40)), int(rng.integers(1, 50))
+        anc, near = O.resample(ell, O.RESAMPLE_MULTINOMIAL, seed, i)
+        e = [-math.log(float(_uniform(seed, l, i, 2, open_zero=True))) for l in range(P + 1)]
+        G = [math.fsum(e[:j + 1]) for j in range(P + 1)]
+        M = ell.max()
+        w = [math.exp(x - M) for x in ell]
+        C = [math.fsum(w[:k + 1]) for k in range(P)]
+        targets = [G[j] / G[P] * C[-1] for j in range(P)]
+        gap = min(abs(t - c) for t in targets for c in C) / C[-1]
+        if near or gap < 1e-9:
+            continue
+        ref = [next((k for k in range(P) if C[k] > t), P - 1) for t in targets]
+        assert anc.tolist() == ref
+        assert np.all(np.diff(anc) >= 0)
+
+
+@pytest.mark.parametrize("kind", [O.RESAMPLE_STRATIFIED, O.RESAMPLE_MULTINOMIAL])
+def test_offspring_distribution(kind):
+    """Unbiased offspring counts for both; multinomial variance P w (1 - w);
+    stratified counts within one of P w and never more variable."""
+    P = 6
+    ell = np.log(np.array([0.02, 0.3, 0.05, 0.33, 0.1, 0.2]))
+    wbar = np.exp(ell) / np.exp(ell).sum()
+    n = 4000
+    counts = np.zeros((n, P))
+    for s in range(n):
+        anc, _ = O.resample(ell, kind, 1000 + s, 3)
+        counts[s] = np.bincount(anc, minlength=P)
+    assert np.all(counts.sum(axis=1) == P)
+    mean, var = counts.mean(axis=0), counts.var(axis=0)
+    se = np.sqrt(P * wbar * (1 - wbar) / n)
+    assert np.all(np.abs(mean - P * wbar) < 5 * se)
+    if kind == O.RESAMPLE_MULTINOMIAL:
+        assert np.all(np.abs(var / (P * wbar * (1 - wbar)) - 1) < 0.15)
+        # the smallest weight still draws: P(o >= 1) = 1 - (1 - w)^P
+        p1 = 1 - (1 - wbar[0]) ** P
+        assert abs(np.mean(counts[:, 0] >= 1) - p1) < 5 * math.sqrt(p1 * (1 - p1) / n)
+    else:
+        assert np.all(counts >= np.floor(P * wbar) - 1) and np.all(counts <= np.ceil(P * wbar) + 1)
+        assert np.all(var <= P * wbar * (1 - wbar) + 0.02)
+
+
+@pytest.mark.parametrize("kind", [O.RESAMPLE_STRATIFIED, O.RESAMPLE_MULTINOMIAL])
+def test_filter_with_other_resamplers_converges_to_kalman(kind):
+    import workloads as W
+    w = W.windkessel(P=1024, T=100)
+    m = O.model(w.kind, dt=w.dt, resampler=kind)
+    kf = O.kalman_windkessel(m, w.theta, w.y)
+    lls = np.array([O.pf_run(m, w.theta, w.y, s, w.P, w.T, want_x=False, want_anc=False,
+                             want_diag=False)["loglik"] for s in range(1, 25)])
+    se = math.sqrt(lls.var(ddof=1) / len(lls))
+    assert abs(lls.mean() - (kf - lls.var(ddof=1) / 2)) < 4 * se + 0.02

@@ -51,6 +51,7 @@ class Workload:
     flow_peak: float = 400.0
     flow_period: float = 1.0
     seed: int = 1
+    resampler: int = 0  # 0 systematic, 1 stratified, 2 multinomial
     y: np.ndarray = field(default=None, repr=False)
 
     @property
