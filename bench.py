@@ -35,7 +35,7 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 PROFILES = os.path.join(ROOT, "profiles")
-DESCRIPTOR_BYTES = 240  # per-filter descriptor the library uploads with every run
+DESCRIPTOR_BYTES = 256  # per-filter descriptor the library uploads with every run
 
 
 def kernel_source_hash():

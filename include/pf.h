@@ -60,6 +60,17 @@ typedef enum {
 
 typedef enum { PF_WINDKESSEL = 0, PF_LORENZ96 = 1 } pf_model_kind;
 typedef enum { PF_FP64 = 0, PF_MIXED = 1 } pf_precision;
+/* Resampling scheme (Sec. 3.3; Algorithm 2 writes the multinomial draw).  All
+ * three give sorted ancestors: target j sits at (j + u) S / P with one u per
+ * step (systematic), at (j + u_j) S / P with one u_j per target (stratified),
+ * or at the j-th order statistic of P uniforms, built from P + 1 exponential
+ * spacings (multinomial).  The multinomial scheme adds one scan of the
+ * spacings per step; the request server and pf_run_noalloc do not take it. */
+typedef enum {
+  PF_RESAMPLE_SYSTEMATIC = 0,
+  PF_RESAMPLE_STRATIFIED = 1,
+  PF_RESAMPLE_MULTINOMIAL = 2
+} pf_resampler;
 
 typedef struct {
   int32_t kind;          /* pf_model_kind                                       */
@@ -67,7 +78,7 @@ typedef struct {
   int32_t substeps;      /* integrator substeps per observation interval, >= 1  */
   int32_t obs_stride;    /* Lorenz '96: observe n % obs_stride == 0, >= 1        */
   int32_t prec;          /* pf_precision                                        */
-  int32_t reserved;      /* must be 0                                           */
+  int32_t resampler;     /* pf_resampler (0: systematic)                          */
   double ess_threshold;  /* >= 1: resample after every observation but the last;
                             in (0, 1): resample iff ESS < ess_threshold * P;
                             0: never resample                                  */

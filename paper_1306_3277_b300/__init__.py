@@ -34,7 +34,7 @@ class PFError(RuntimeError):
 class pf_model(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("N", ctypes.c_int32), ("substeps", ctypes.c_int32),
                 ("obs_stride", ctypes.c_int32), ("prec", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("ess_threshold", ctypes.c_double),
+                ("resampler", ctypes.c_int32), ("ess_threshold", ctypes.c_double),
                 ("flow_peak", ctypes.c_double), ("flow_period", ctypes.c_double)]
 
 
@@ -117,9 +117,13 @@ def _check(st, ok=(PF_OK,)):
     return st
 
 
+PF_RESAMPLE_SYSTEMATIC, PF_RESAMPLE_STRATIFIED, PF_RESAMPLE_MULTINOMIAL = range(3)
+
+
 def model(kind, N=1, substeps=1, obs_stride=1, prec=PF_FP64, ess_threshold=1.0, flow_peak=400.0,
-          flow_period=1.0):
-    return pf_model(kind, N, substeps, obs_stride, prec, 0, ess_threshold, flow_peak, flow_period)
+          flow_period=1.0, resampler=PF_RESAMPLE_SYSTEMATIC):
+    return pf_model(kind, N, substeps, obs_stride, prec, resampler, ess_threshold, flow_peak,
+                    flow_period)
 
 
 PF_PRIOR_FIXED, PF_PRIOR_UNIFORM, PF_PRIOR_GAUSSIAN, PF_PRIOR_GAMMA, PF_PRIOR_INV_GAMMA = range(5)
@@ -180,7 +184,7 @@ def pf_smc2_run(m, P, T, dt, y, ntheta, spec, theta_base, seed, stream=None):
 
 def model_from_workload(w):
     return model(w.kind, w.N, w.substeps, w.obs_stride, w.prec, w.ess_threshold, w.flow_peak,
-                 w.flow_period)
+                 w.flow_period, getattr(w, "resampler", PF_RESAMPLE_SYSTEMATIC))
 
 
 def pf_theta_size(kind):

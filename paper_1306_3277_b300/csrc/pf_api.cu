@@ -49,7 +49,8 @@ extern "C" int32_t pf_theta_size(int32_t kind) {
 
 pf_status pfb::check_shape(const pf_model* m, int64_t P, int32_t T, double dt, Shape* sh) {
   if (!m) return fail(PF_EINVAL, "model is NULL");
-  if (m->reserved != 0) return fail(PF_EINVAL, "pf_model.reserved must be 0");
+  if (m->resampler < PF_RESAMPLE_SYSTEMATIC || m->resampler > PF_RESAMPLE_MULTINOMIAL)
+    return fail(PF_EINVAL, "unknown resampler %d", m->resampler);
   if (!supported(m->kind, m->N, m->prec))
     return fail(PF_EINVAL, "unsupported model: kind %d, N %d, precision %d", m->kind, m->N,
                 m->prec);
@@ -92,6 +93,8 @@ static size_t bytes_for(const pf_model* m, const Shape& sh, int64_t P, int32_t T
   b += size_t(sh.ntiles) * sizeof(TilePart) + size_t(sh.ngroups) * sizeof(GroupPart);
   b += sizeof(Ctl);
   b += size_t(T) * size_t(sh.Ny) * 8;                     // observations (plan side)
+  if (m->resampler == PF_RESAMPLE_MULTINOMIAL)             // spacing sums, tile offsets
+    b += size_t(P) * 8 + (size_t(sh.ntiles) + 1) * 8;
   return b;
 }
 
@@ -107,7 +110,7 @@ extern "C" size_t pf_device_bytes(const pf_model* m, int64_t P, int32_t T, int32
 // ---------------------------------------------------------------------------
 static void free_filter_buffers(pf_filter* f) {
   void* ptrs[] = {f->x[0], f->x[1], f->ctil, f->ell, f->lam, f->anc, f->hist,
-                  f->flow, f->tp, f->gp, f->ctl, f->path, f->path_idx};
+                  f->flow, f->tp, f->gp, f->ctl, f->path, f->path_idx, f->mn_t, f->mn_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (f->h_res) cudaFreeHost(f->h_res);
@@ -147,6 +150,9 @@ extern "C" pf_status pf_create(const pf_model* m, int64_t P, int32_t T, double d
   ok = ok && alloc((void**)&f->tp, size_t(sh.ntiles) * sizeof(TilePart));
   ok = ok && alloc((void**)&f->gp, size_t(sh.ngroups) * sizeof(GroupPart));
   ok = ok && alloc((void**)&f->ctl, sizeof(Ctl));
+  if (m->resampler == PF_RESAMPLE_MULTINOMIAL)
+    ok = ok && alloc((void**)&f->mn_t, size_t(P) * 8) &&
+         alloc((void**)&f->mn_part, (size_t(sh.ntiles) + 1) * 8);
   ok = ok && cudaMallocHost((void**)&f->h_res, 64) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -178,6 +184,7 @@ extern "C" pf_status pf_create(const pf_model* m, int64_t P, int32_t T, double d
   d.ngroups = sh.ngroups;
   d.hist = 0;
   d.mode = sh.mode;
+  d.resampler = m->resampler;
   d.obs_mask = sh.obs_mask;
   d.dt = dt;
   d.thr = m->ess_threshold;
@@ -191,6 +198,8 @@ extern "C" pf_status pf_create(const pf_model* m, int64_t P, int32_t T, double d
   d.tp = f->tp;
   d.gp = f->gp;
   d.ctl = f->ctl;
+  d.mn_t = f->mn_t;
+  d.mn_part = f->mn_part;
   f->bytes = bytes_for(m, sh, P, T, 0);
   *out = f;
   return PF_OK;
@@ -257,6 +266,10 @@ static cudaError_t enqueue_steps(Plan* p, int first, int last, cudaStream_t st, 
       });
     }
     if (le == cudaSuccess) le = hook(i);
+    if (le == cudaSuccess && p->has_mn && p->cnt_all[i + 1] > 0)
+      le = timed(PROF_RESAMPLE, [&] {
+        return launch_mn_scan(p->d_fds, p->d_tmap, p->cnt_all[i + 1], p->nf, st);
+      });
     if (le == cudaSuccess && p->cnt_all[i + 1] > 0)
       le = timed(PROF_RESAMPLE,
                  [&] { return launch_resample(p->d_fds, p->d_tmap, p->cnt_all[i + 1], st); });
@@ -328,6 +341,7 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out) {
   }
   p->nf = nf;
   p->maxT = maxT;
+  for (pf_filter* f : fl) p->has_mn = p->has_mn || f->m.resampler == PF_RESAMPLE_MULTINOMIAL;
   p->ntiles_all = int(all_tiles.size());
   // per-step counts: tiles of filters with T >= i
   auto counts = [&](const std::vector<int>& Ts, std::vector<int>& cnt) {

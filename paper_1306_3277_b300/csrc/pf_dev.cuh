@@ -20,6 +20,7 @@ constexpr int64_t MAX_P = int64_t(1) << 24;  // GROUP * GROUP * TILE
 enum { KIND_WK = 0, KIND_L96 = 1 };
 enum { PREC_FP64 = 0, PREC_MIXED = 1 };
 enum { MODE_ALWAYS = 0, MODE_ADAPTIVE = 1, MODE_NEVER = 2 };
+enum { RS_SYSTEMATIC = 0, RS_STRATIFIED = 1, RS_MULTINOMIAL = 2 };
 enum { PURPOSE_INIT = 1, PURPOSE_PROP = 2, PURPOSE_RESAMPLE = 3, PURPOSE_PATH = 4 };
 enum { ST_OK = 0, ST_DEGENERATE = 4 };
 
@@ -68,6 +69,7 @@ struct alignas(16) Ctl {
 struct alignas(16) FilterDev {
   int32_t kind, N, s, stride, prec, Ny;
   int32_t P, T, ntiles, ngroups, hist, mode;
+  int32_t resampler;  // RS_*
   uint64_t obs_mask;  // Lorenz '96: bit n set iff component n is observed
   uint64_t seed;
   double dt, thr;
@@ -82,7 +84,10 @@ struct alignas(16) FilterDev {
   TilePart* tp;       // [ntiles]
   GroupPart* gp;      // [ngroups]
   Ctl* ctl;
+  double* mn_t;       // multinomial: in-tile inclusive sums of the spacings [P]
+  double* mn_part;    // multinomial: tile offsets [ntiles], then P / (sum of all P + 1)
 };
+static_assert(sizeof(FilterDev) == 256, "descriptor layout");
 
 // -------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two

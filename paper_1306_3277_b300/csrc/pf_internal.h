@@ -15,6 +15,8 @@ cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks,
 cudaError_t launch_flow(double* flow, int64_t n, double peak, double period, double dt,
                         cudaStream_t st);
 cudaError_t launch_results(const FilterDev* fds, int nf, double* out, cudaStream_t st);
+cudaError_t launch_mn_scan(const FilterDev* fds, const int2* tmap, int ntiles, int nf,
+                           cudaStream_t st);
 cudaError_t launch_path_pick(const FilterDev* fds, int ntiles, int32_t* pick, cudaStream_t st);
 cudaError_t launch_path_trace(const FilterDev* fds, int32_t* idx, cudaStream_t st);
 cudaError_t launch_path_copy(const void* x, int prec, int N, int P, const int32_t* idx, int i,

@@ -559,6 +559,33 @@ __device__ __forceinline__ int tile_targets_below(double scale_r, double prefix,
   return __double2int_ru(fma(scale_r, prefix, e0));
 }
 
+// Stratified count: targets j + u_j (u_j from Philox block (j, i, RESAMPLE, 1))
+// below the scaled cumulative weight e: every j < floor(e), plus j = floor(e)
+// when e - floor(e) > u_j (exact, since e - floor(e) is exact).
+__device__ __forceinline__ int strat_below(double e, uint64_t seed, int i, int P) {
+  if (!(e > 0.0)) return 0;
+  if (e >= double(P)) return P;
+  const int f = int(floor(e));
+  const uint4 w = rng_block(seed, uint32_t(f), uint32_t(i), PURPOSE_RESAMPLE, 1u);
+  return f + ((e - double(f)) > u53_closed_open(w.x, w.y) ? 1 : 0);
+}
+
+// Multinomial target j: the sum of spacings 0..j scaled by P / (sum of all P + 1).
+__device__ __forceinline__ double mn_target(const FilterDev& fd, int j, double scale) {
+  return (ldcg(&fd.mn_part[j >> 8]) + ldcg(&fd.mn_t[j])) * scale;
+}
+
+// Multinomial count: the number of targets below e, searched in [lo, hi].
+__device__ __forceinline__ int mn_below(const FilterDev& fd, double e, double scale, int lo,
+                                        int hi) {
+  while (lo < hi) {
+    const int mid = lo + (hi - lo) / 2;
+    if (mn_target(fd, mid, scale) < e) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // Systematic resampling of one tile.  Its particles k have cumulative weights
 // C_k = base + scale * prefix_k; the tile owns the targets [lo, hi) between
 // its base and the next tile's base (both counts computed from the same
@@ -590,16 +617,18 @@ __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__
   const double gG = fd.gp[g].G, gB = fd.gp[g].B, tbase = fd.tp[t].base, tg = fd.tp[t].g;
   // one thread reads the control block and shares it (see k_propagate)
   __shared__ int s_i, s_go, s_flag;
-  __shared__ double s_u, s_ratio, s_M, s_S;
+  __shared__ double s_u, s_ratio, s_M, s_S, s_mscale;
+  const int rs = fd.resampler;
   if (tid == 0) {
     const int i0 = ldcg(&ctl->rs_step);
     s_i = i0;
     s_go = ldcg(&ctl->status) == ST_OK && i0 >= 1 && i0 < fd.T && ldcg(&ctl->step) == i0 + 1;
     s_flag = ldcg(&ctl->rs_flag);
-    s_u = ldcg(&ctl->u);
+    s_u = rs == RS_SYSTEMATIC ? ldcg(&ctl->u) : 0.0;
     s_ratio = ldcg(&ctl->ratio);
     s_M = ldcg(&ctl->M);
     s_S = ldcg(&ctl->S);
+    s_mscale = rs == RS_MULTINOMIAL ? ldcg(&fd.mn_part[fd.ntiles]) : 0.0;
   }
   __syncthreads();
   if (!s_go) return;
@@ -614,9 +643,16 @@ __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__
   }
   const double u = s_u;
   const double ratio = s_ratio;
+  // the counts of targets below a scaled cumulative weight, per scheme
+  // (systematic: e = C (P/S) - u; the others: e = C (P/S))
+  auto below = [&](double e, int a, int b) -> int {
+    if (rs == RS_STRATIFIED) return strat_below(e, fd.seed, i, P);
+    if (rs == RS_MULTINOMIAL) return mn_below(fd, e, s_mscale, a, b);
+    return __double2int_ru(e);
+  };
   if (tid == 0) {
     const double base = fma(gG, tbase, gB);
-    range[0] = targets_below(base, ratio, u, P);
+    range[0] = rs == RS_SYSTEMATIC ? targets_below(base, ratio, u, P) : below(base * ratio, 0, P);
     tile_e0 = base * ratio - u;
     tile_scale_r = (gG * tg) * ratio;
     nlong = 0;
@@ -629,14 +665,15 @@ __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__
     } else {
       nb = s_S;
     }
-    range[1] = targets_below(nb, ratio, u, P);
+    range[1] = rs == RS_SYSTEMATIC ? targets_below(nb, ratio, u, P) : below(nb * ratio, 0, P);
   }
   __syncthreads();
   const int lo = range[0];
   const int hi = range[1];
   const int nvalid = min(TILE, P - j0);
   if (tid < nvalid) {
-    int n = tile_targets_below(tile_scale_r, ct, tile_e0);
+    int n = rs == RS_SYSTEMATIC ? tile_targets_below(tile_scale_r, ct, tile_e0)
+                                : below(fma(tile_scale_r, ct, tile_e0), lo, hi);
     n = min(max(n, lo), hi);
     nk[tid] = tid == nvalid - 1 ? hi : n;
   }
@@ -659,6 +696,70 @@ __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__
     const int b = nk[k];
     for (int jj = a + tid; jj < b; jj += TILE) aout[jj] = j0 + k;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Multinomial resampling: the spacings of the sorted uniforms
+// ---------------------------------------------------------------------------
+// After the propagate launch of step i (rs_step = i), for every filter that
+// resamples with the multinomial scheme: unit exponentials e_l = -log u_l
+// (u_l in (0, 1] from Philox block (l, i, RESAMPLE, 2)), l = 0..P; their
+// in-tile inclusive sums go to mn_t, the tile totals to mn_part.
+__device__ __forceinline__ bool mn_active(const FilterDev& fd, int* step) {
+  const Ctl* c = fd.ctl;
+  const int i0 = ldcg(&c->rs_step);
+  *step = i0;
+  return fd.resampler == RS_MULTINOMIAL && ldcg(&c->status) == ST_OK && i0 >= 1 && i0 < fd.T &&
+         ldcg(&c->step) == i0 + 1 && ldcg(&c->rs_flag) != 0;
+}
+
+__device__ __forceinline__ double mn_spacing(const FilterDev& fd, int l, int i) {
+  const uint4 w = rng_block(fd.seed, uint32_t(l), uint32_t(i), PURPOSE_RESAMPLE, 2u);
+  return -log_pos(u53_open_closed(w.x, w.y));
+}
+
+__global__ void __launch_bounds__(TILE) k_mn_tiles(const FilterDev* __restrict__ fds,
+                                                   const int2* __restrict__ tmap) {
+  __shared__ BlockScratch b;
+  __shared__ int s_go, s_i;
+  const int2 ft = tmap[blockIdx.x];
+  const FilterDev& fd = fds[ft.x];
+  if (fd.resampler != RS_MULTINOMIAL) return;
+  if (threadIdx.x == 0) s_go = mn_active(fd, &s_i);
+  __syncthreads();
+  if (!s_go) return;
+  const int l = ft.y * TILE + threadIdx.x;
+  const double e = l < fd.P ? mn_spacing(fd, l, s_i) : 0.0;
+  double tot;
+  const double incl = block_scan(e, b, &tot);
+  if (l < fd.P) fd.mn_t[l] = incl;
+  if (threadIdx.x == 0) fd.mn_part[ft.y] = tot;
+}
+
+// One block per filter: exclusive scan of the tile totals in place, then
+// mn_part[ntiles] = P / (all P + 1 spacings).
+__global__ void __launch_bounds__(TILE) k_mn_total(const FilterDev* __restrict__ fds, int nf) {
+  __shared__ BlockScratch b;
+  __shared__ int s_go, s_i;
+  const FilterDev& fd = fds[blockIdx.x];
+  if (fd.resampler != RS_MULTINOMIAL || fd.ctl == nullptr) return;
+  if (threadIdx.x == 0) s_go = mn_active(fd, &s_i);
+  __syncthreads();
+  if (!s_go) return;
+  const int nt = fd.ntiles;
+  const int chunk = (nt + TILE - 1) / TILE;
+  const int lo = min(nt, int(threadIdx.x) * chunk), hi = min(nt, lo + chunk);
+  double s = 0.0;
+  for (int q = lo; q < hi; ++q) s += fd.mn_part[q];
+  double tot;
+  const double incl = block_scan(s, b, &tot);
+  double run = incl - s;
+  for (int q = lo; q < hi; ++q) {
+    const double v = fd.mn_part[q];
+    fd.mn_part[q] = run;
+    run += v;
+  }
+  if (threadIdx.x == 0) fd.mn_part[nt] = double(fd.P) / (tot + mn_spacing(fd, fd.P, s_i));
 }
 
 // ---------------------------------------------------------------------------
@@ -834,6 +935,14 @@ cudaError_t launch_flow(double* flow, int64_t n, double peak, double period, dou
 cudaError_t launch_results(const FilterDev* fds, int nf, double* out, cudaStream_t st) {
   if (nf <= 0) return cudaSuccess;
   k_results<<<(nf + 127) / 128, 128, 0, st>>>(fds, nf, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mn_scan(const FilterDev* fds, const int2* tmap, int ntiles, int nf,
+                           cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  k_mn_tiles<<<ntiles, TILE, 0, st>>>(fds, tmap);
+  k_mn_total<<<nf, TILE, 0, st>>>(fds, nf);
   return cudaGetLastError();
 }
 

@@ -115,6 +115,8 @@ extern "C" pf_status pf_run_noalloc(const pf_model* m, int64_t P, int32_t T, dou
   Shape sh;
   pf_status st = check_shape(m, P, T, dt, &sh);
   if (st != PF_OK) return st;
+  if (m->resampler == PF_RESAMPLE_MULTINOMIAL)
+    return fail(PF_EINVAL, "pf_run_noalloc does not take the multinomial resampler");
   if (!theta || !y || !loglik) return fail(PF_EINVAL, "pf_run_noalloc: theta, y, loglik required");
   const size_t need = layout_bytes(m, sh, P);
   if (need > size_t(PF_NOALLOC_SCRATCH_BYTES))
@@ -157,6 +159,7 @@ extern "C" pf_status pf_run_noalloc(const pf_model* m, int64_t P, int32_t T, dou
   d.ngroups = sh.ngroups;
   d.hist = 0;
   d.mode = sh.mode;
+  d.resampler = m->resampler;
   d.obs_mask = sh.obs_mask;
   d.seed = seed;
   d.dt = dt;

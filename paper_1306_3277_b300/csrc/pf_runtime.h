@@ -91,6 +91,8 @@ struct pf_filter {
   double* lam = nullptr;
   int32_t* anc = nullptr;
   int32_t* hist = nullptr;
+  double* mn_t = nullptr;        // multinomial resampling: spacing sums [P]
+  double* mn_part = nullptr;     // multinomial resampling: tile offsets [ntiles + 1]
   double* path = nullptr;        // [T+1][N] sampled path (pf_sample_path)
   int32_t* path_idx = nullptr;   // [T+1] its particle indices
   double* flow = nullptr;
@@ -113,6 +115,7 @@ namespace pfb {
 struct Plan {
   std::vector<pf_filter*> filters;
   int nf = 0, maxT = 0, ntiles_all = 0;
+  bool has_mn = false;                      // some filter resamples multinomially
   std::vector<PlanClass> classes;
   std::vector<int> cnt_all;                 // [i]: tiles of filters with T >= i
   std::vector<std::vector<int>> cnt_cls;    // per class

@@ -136,6 +136,7 @@ bool alloc_request(pf_server* s, Request* r) {
   d.ntiles = sh.ntiles;
   d.ngroups = sh.ngroups;
   d.mode = sh.mode;
+  d.resampler = r->m.resampler;
   d.obs_mask = sh.obs_mask;
   d.dt = r->dt;
   d.thr = r->m.ess_threshold;
@@ -376,6 +377,8 @@ extern "C" pf_status pf_server_submit(pf_server* s, const pf_model* m, int64_t P
   Shape sh;
   pf_status st = check_shape(m, P, T, dt, &sh);
   if (st != PF_OK) return st;
+  if (m->resampler == PF_RESAMPLE_MULTINOMIAL)
+    return fail(PF_EINVAL, "the server does not take the multinomial resampler");
   const size_t need = pf_device_bytes(m, P, T, 0) + 256 * 16;
   if (need > s->budget || size_t(T) * sh.Ny * 8 > ARENA_HALF)
     return fail(PF_ENOMEM, "request needs %zu bytes, budget is %zu", need, s->budget);
