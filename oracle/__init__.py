@@ -80,6 +80,8 @@ class Model(ctypes.Structure):
         ("ess_threshold", ctypes.c_double),
         ("flow_peak", ctypes.c_double),
         ("flow_period", ctypes.c_double),
+        ("obs_every", ctypes.c_int32),
+        ("obs_count", ctypes.c_int32),
     ]
 
 
@@ -157,9 +159,9 @@ def _ptr(a, t):
 
 
 def model(kind, N=1, substeps=1, obs_stride=1, prec=FP64, dt=0.01, ess_threshold=1.0,
-          flow_peak=400.0, flow_period=1.0, resampler=0):
+          flow_peak=400.0, flow_period=1.0, resampler=0, obs_every=0, obs_count=0):
     return Model(kind, N, substeps, obs_stride, prec, resampler, dt, ess_threshold, flow_peak,
-                 flow_period)
+                 flow_period, obs_every, obs_count)
 
 
 def philox4x32_10(ctr, key):

@@ -397,6 +397,7 @@ double or_kalman_windkessel(const or_model *m, const double *th, const double *y
       mu = a * mu + dt * F[k] / C;
       V = a * a * V + q;
     }
+    if (m->obs_every > 1 && i % m->obs_every != 0) continue; /* no observation at t_i */
     nu = mu + Z * F[(int64_t)i * s];
     Sv = V + r;
     d = y[i - 1] - nu;
@@ -616,7 +617,7 @@ static double or_prop_weight64(const or_ctx *cx, uint32_t j, int32_t i, double *
       double z = or_normal64(cx->seed, j, (uint32_t)i, OR_PURPOSE_PROP, (uint32_t)n);
       x[n] = fma(sx, z, x[n]);
     }
-    for (n = 0; n < N; n += m->obs_stride) {
+    for (n = 0; n < N && n / m->obs_stride < cx->Ny; n += m->obs_stride) {
       double d = yi[n / m->obs_stride] - x[n];
       acc = fma(d, d, acc);
     }
@@ -656,7 +657,7 @@ static double or_prop_weight32(const or_ctx *cx, uint32_t j, int32_t i, float *x
       float z = or_normal32(cx->seed, j, (uint32_t)i, OR_PURPOSE_PROP, (uint32_t)n);
       x[n] = fmaf(sx, z, x[n]);
     }
-    for (n = 0; n < N; n += m->obs_stride) {
+    for (n = 0; n < N && n / m->obs_stride < cx->Ny; n += m->obs_stride) {
       double d = yi[n / m->obs_stride] - (double)x[n];
       acc = fma(d, d, acc);
     }
@@ -707,7 +708,10 @@ int32_t or_pf_run_sched(const or_model *m, const double *th, const double *y, ui
   const int32_t N = m->N, s = m->substeps;
   const int mixed = (m->prec == OR_MIXED);
   const int32_t stride = (m->kind == OR_LORENZ96) ? m->obs_stride : 1;
-  const int32_t Ny = (m->kind == OR_LORENZ96) ? (N + stride - 1) / stride : 1;
+  const int32_t Nys = (m->kind == OR_LORENZ96) ? (N + stride - 1) / stride : 1;
+  const int32_t Ny = (m->kind == OR_LORENZ96 && m->obs_count > 0 && m->obs_count < Nys)
+                         ? m->obs_count : Nys;
+  const int32_t every = m->obs_every > 1 ? m->obs_every : 1;
   const double r = (m->kind == OR_LORENZ96) ? th[2] : th[4];
   const double m0 = (m->kind == OR_LORENZ96) ? th[3] : th[5];
   const double s0 = (m->kind == OR_LORENZ96) ? th[4] : th[6];
@@ -728,6 +732,7 @@ int32_t or_pf_run_sched(const or_model *m, const double *th, const double *y, ui
   if (m->kind == OR_LORENZ96 && (N < 4 || N > 256 || stride <= 0)) return OR_EINVAL;
   if (m->resampler < OR_RESAMPLE_SYSTEMATIC || m->resampler > OR_RESAMPLE_MULTINOMIAL)
     return OR_EINVAL;
+  if (m->obs_every < 0 || m->obs_count < 0) return OR_EINVAL;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
@@ -778,6 +783,9 @@ int32_t or_pf_run_sched(const or_model *m, const double *th, const double *y, ui
     double M, S, Q, ess, incr, u = 0.0;
     int resample;
     int64_t near = 0;
+    /* a step without an observation only propagates: no weight, no
+     * likelihood term, no resampling, carried weights unchanged */
+    const int observed = (i % every) == 0;
     if (sched) cx.seed = sched[i];
     if (anc) {
       for (j = 0; j < P; ++j) anc[(int64_t)(i - 1) * P + j] = anc_identity ? (int32_t)j : acur[j];
@@ -801,6 +809,7 @@ int32_t or_pf_run_sched(const or_model *m, const double *th, const double *y, ui
           lw = or_prop_weight64(&cx, (uint32_t)j, i, xloc, xloc + N, yi);
           for (n = 0; n < N; ++n) xb[(int64_t)n * P + j] = xloc[n];
         }
+        if (!observed) lw = 0.0;
         e = lam_zero ? lw : lam[j] + lw;
         if (e != e) e = -INFINITY;
         ell[j] = e;
@@ -813,6 +822,14 @@ int32_t or_pf_run_sched(const or_model *m, const double *th, const double *y, ui
       for (j = 0; j < (int64_t)N * P; ++j) xr[j] = mixed ? (double)fa[j] : xa[j];
     }
     if (ellT && i == T) memcpy(ellT, ell, sizeof(double) * (size_t)P);
+    if (!observed) {
+      anc_identity = 1;
+      if (diag) {
+        double *dg = diag + (int64_t)(i - 1) * 8;
+        dg[0] = dg[1] = dg[2] = dg[3] = dg[4] = dg[5] = dg[6] = dg[7] = 0.0;
+      }
+      continue;
+    }
 
     or_lse(ell, P, &M, &S, &Q);
     if (!(M > -INFINITY) || !(S > 0.0) || M == INFINITY) {

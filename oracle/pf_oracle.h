@@ -44,6 +44,9 @@ typedef struct {
   double ess_threshold;  /* >= 1: resample every step; else resample iff ESS < thr * P */
   double flow_peak;      /* windkessel input F(t): peak of the half sine */
   double flow_period;    /* windkessel input F(t): period */
+  int32_t obs_every;     /* 0 or 1: every step observed; k: only steps i with i % k == 0 */
+  int32_t obs_count;     /* Lorenz '96: 0 = every strided component; else the first
+                            obs_count of them (sparse observations) */
 } or_model;
 
 /* --- random numbers ---------------------------------------------------- */

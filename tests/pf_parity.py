@@ -8,7 +8,8 @@ import oracle as O
 def oracle_model(w):
     return O.model(w.kind, N=w.N, substeps=w.substeps, obs_stride=w.obs_stride, prec=w.prec,
                    dt=w.dt, ess_threshold=w.ess_threshold, flow_peak=w.flow_peak,
-                   flow_period=w.flow_period, resampler=w.resampler)
+                   flow_period=w.flow_period, resampler=w.resampler, obs_every=w.obs_every,
+                   obs_count=w.obs_count)
 
 
 def run_oracle(w, seed, theta=None, nthreads=0):

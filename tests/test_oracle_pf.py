@@ -150,3 +150,67 @@ def test_seed_schedule_constant_is_plain_run_and_still_converges():
                                    w.P, w.T)["loglik"] for _ in range(32)])
     se = math.sqrt(lls.var(ddof=1) / 32)
     assert abs(lls.mean() - (kf - lls.var(ddof=1) / 2)) < 4 * se + 0.02
+
+
+# ---- sparse observations (Sec. 5: the first four components every other step) ----
+def _brute_force_sparse(theta, y, s, dt, every, flow_fn):
+    """log N(y_obs; mu, Sigma) of the Euler windkessel at the observed steps only."""
+    from scipy import stats
+    R, C, Z, q, r, m0, s0 = theta
+    a = 1.0 - dt / (R * C)
+    obs = [i for i in range(1, len(y) + 1) if i % every == 0]
+    K = [i * s for i in obs]
+    flow = flow_fn(max(K) + 1)
+    mu = np.array([a ** k * m0 + sum(a ** (k - 1 - m) * dt * flow[m] / C for m in range(k))
+                   + Z * flow[k] for k in K])
+    Sig = np.array([[a ** (ki + kj) * s0 ** 2 +
+                     q * sum(a ** (ki - 1 - m) * a ** (kj - 1 - m) for m in range(min(ki, kj)))
+                     + (r if ii == jj else 0.0) for jj, kj in enumerate(K)]
+                    for ii, ki in enumerate(K)])
+    return stats.multivariate_normal(mean=mu, cov=Sig).logpdf(np.array([y[i - 1] for i in obs]))
+
+
+@pytest.mark.parametrize("every", [2, 3])
+def test_sparse_kalman_against_joint_gaussian(every):
+    theta = (1.1, 1.4, 0.04, 0.3, 3.0, 85.0, 10.0)
+    m = O.model(O.WINDKESSEL, substeps=2, dt=0.01, obs_every=every)
+    y = np.array([92.0, 97.0, 101.5, 99.0, 95.5, 94.0, 96.5])
+    ref = _brute_force_sparse(theta, y, 2, 0.01, every,
+                              lambda n: O.flow_table(400.0, 1.0, 0.01, n))
+    assert O.kalman_windkessel(m, theta, y) == pytest.approx(ref, rel=1e-12, abs=1e-10)
+
+
+def test_sparse_windkessel_filter_exact_and_convergent():
+    w = W.windkessel(P=1024, T=100).with_(obs_every=3)
+    m = _om(w)
+    m.obs_every = 3
+    th0 = (1.0, 1.5, 0.03, 0.0, 4.0, 90.0, 0.0)
+    kf0 = O.kalman_windkessel(m, th0, w.y)
+    assert O.pf_run(m, th0, w.y, 5, 64, w.T)["loglik"] == pytest.approx(kf0, rel=1e-12)
+    kf = O.kalman_windkessel(m, w.theta, w.y)
+    lls = np.array([O.pf_run(m, w.theta, w.y, s, w.P, w.T, want_x=False, want_anc=False)["loglik"]
+                    for s in range(1, 25)])
+    se = math.sqrt(lls.var(ddof=1) / len(lls))
+    assert abs(lls.mean() - (kf - lls.var(ddof=1) / 2)) < 4 * se + 0.02
+    r = O.pf_run(m, w.theta, w.y, 1, 256, 30)
+    for i in range(1, 31):
+        if i % 3:
+            assert r["diag"][i - 1, 6] == 0.0 and r["diag"][i - 1, 4] == 0.0
+            if i < 30:
+                assert np.array_equal(r["anc"][i], np.arange(256))  # no resampling after it
+
+
+def test_sparse_lorenz96_deterministic_closed_form():
+    F, r = 8.0, 0.25
+    th = (F, 0.0, r, 1.3, 0.0)
+    w = W.lorenz96_sparse(P=16, T=20)
+    m = O.model(O.LORENZ96, N=8, substeps=w.substeps, dt=w.dt, obs_every=2, obs_count=4)
+    x = np.full(8, 1.3)
+    ll = 0.0
+    for i in range(1, w.T + 1):
+        x = O.l96_rk4(x, F, w.dt, w.substeps)
+        if i % 2 == 0:
+            d = w.y[i - 1] - x[:4]
+            ll += -0.5 * 4 * math.log(2 * math.pi * r) - 0.5 * float(np.sum(d * d)) / r
+    res = O.pf_run(m, th, w.y, 9, 16, w.T)
+    assert res["loglik"] == pytest.approx(ll, rel=1e-12)

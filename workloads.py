@@ -52,11 +52,16 @@ class Workload:
     flow_period: float = 1.0
     seed: int = 1
     resampler: int = 0  # 0 systematic, 1 stratified, 2 multinomial
+    obs_every: int = 0  # 0/1: every step observed; k: steps i with i % k == 0 only
+    obs_count: int = 0  # Lorenz '96: observe only the first obs_count strided components
     y: np.ndarray = field(default=None, repr=False)
 
     @property
     def Ny(self):
-        return 1 if self.kind == WINDKESSEL else (self.N + self.obs_stride - 1) // self.obs_stride
+        if self.kind == WINDKESSEL:
+            return 1
+        ny = (self.N + self.obs_stride - 1) // self.obs_stride
+        return min(ny, self.obs_count) if self.obs_count > 0 else ny
 
     def with_(self, **kw):
         return replace(self, **kw)
@@ -82,6 +87,16 @@ def lorenz96_large(P=1 << 20, T=500, prec=MIXED, ess_threshold=1.0, theta=L96_TH
     """Lorenz '96, N=40, RK4 dt=0.005 x 10 substeps, every 2nd component observed."""
     w = Workload("lorenz96_N40_P%d_T%d" % (P, T), LORENZ96, 40, 10, 2, 0.005, P, T, prec,
                  ess_threshold, tuple(theta), seed=seed)
+    w.y = simulate(w)
+    return w
+
+
+def lorenz96_sparse(P=1 << 14, T=60, prec=FP64, ess_threshold=1.0, theta=L96_THETA_8, seed=1):
+    """Lorenz '96, N=8 (step 0.05 = RK4 0.01 x 5) with sparse observations as in
+    the paper's Lorenz '96 example (Sec. 5): the first four components at every
+    other step.  Rows of y at unobserved steps are simulated but not used."""
+    w = Workload("lorenz96_sparse_P%d_T%d" % (P, T), LORENZ96, 8, 5, 1, 0.01, P, T, prec,
+                 ess_threshold, tuple(theta), seed=seed, obs_every=2, obs_count=4)
     w.y = simulate(w)
     return w
 
@@ -125,7 +140,7 @@ def simulate(w, data_seed=DATA_SEED, T=None):
             k4 = _l96_rhs(x + h * k3, F)
             x = x + h / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
         x = x + math.sqrt(q) * rng.standard_normal(w.N)
-        y[i] = x[::w.obs_stride] + math.sqrt(r) * rng.standard_normal(w.Ny)
+        y[i] = x[::w.obs_stride][:w.Ny] + math.sqrt(r) * rng.standard_normal(w.Ny)
     return y
 
 
