@@ -84,6 +84,11 @@ typedef struct {
                             0: never resample                                  */
   double flow_peak;      /* windkessel input: peak of the half-sine flow        */
   double flow_period;    /* windkessel input: period of the flow, > 0           */
+  int32_t obs_every;     /* 0 or 1: every step is observed; k > 1: only steps i
+                            with i % k == 0 (sparse observations: the other
+                            steps only propagate; their rows of y are unused) */
+  int32_t obs_count;     /* Lorenz '96: 0 = every strided component observed;
+                            else only the first obs_count of them (Ny)       */
 } pf_model;
 
 typedef struct pf_filter pf_filter;

@@ -35,7 +35,8 @@ class pf_model(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("N", ctypes.c_int32), ("substeps", ctypes.c_int32),
                 ("obs_stride", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("resampler", ctypes.c_int32), ("ess_threshold", ctypes.c_double),
-                ("flow_peak", ctypes.c_double), ("flow_period", ctypes.c_double)]
+                ("flow_peak", ctypes.c_double), ("flow_period", ctypes.c_double),
+                ("obs_every", ctypes.c_int32), ("obs_count", ctypes.c_int32)]
 
 
 _lib = None
@@ -121,9 +122,9 @@ PF_RESAMPLE_SYSTEMATIC, PF_RESAMPLE_STRATIFIED, PF_RESAMPLE_MULTINOMIAL = range(
 
 
 def model(kind, N=1, substeps=1, obs_stride=1, prec=PF_FP64, ess_threshold=1.0, flow_peak=400.0,
-          flow_period=1.0, resampler=PF_RESAMPLE_SYSTEMATIC):
+          flow_period=1.0, resampler=PF_RESAMPLE_SYSTEMATIC, obs_every=0, obs_count=0):
     return pf_model(kind, N, substeps, obs_stride, prec, resampler, ess_threshold, flow_peak,
-                    flow_period)
+                    flow_period, obs_every, obs_count)
 
 
 PF_PRIOR_FIXED, PF_PRIOR_UNIFORM, PF_PRIOR_GAUSSIAN, PF_PRIOR_GAMMA, PF_PRIOR_INV_GAMMA = range(5)
@@ -184,7 +185,8 @@ def pf_smc2_run(m, P, T, dt, y, ntheta, spec, theta_base, seed, stream=None):
 
 def model_from_workload(w):
     return model(w.kind, w.N, w.substeps, w.obs_stride, w.prec, w.ess_threshold, w.flow_peak,
-                 w.flow_period, getattr(w, "resampler", PF_RESAMPLE_SYSTEMATIC))
+                 w.flow_period, getattr(w, "resampler", PF_RESAMPLE_SYSTEMATIC),
+                 getattr(w, "obs_every", 0), getattr(w, "obs_count", 0))
 
 
 def pf_theta_size(kind):
@@ -226,7 +228,8 @@ class Filter:
         self.model = m
         self.P, self.T, self.dt = P, T, dt
         self.N = m.N
-        self.Ny = 1 if m.kind == PF_WINDKESSEL else (m.N + m.obs_stride - 1) // m.obs_stride
+        ny = 1 if m.kind == PF_WINDKESSEL else (m.N + m.obs_stride - 1) // m.obs_stride
+        self.Ny = min(ny, m.obs_count) if (m.kind != PF_WINDKESSEL and m.obs_count > 0) else ny
         self.state_dtype = np.float64 if m.prec == PF_FP64 else np.float32
 
     def run(self, theta, y, seed, want_particles=False, want_ancestors=False, stream=None):

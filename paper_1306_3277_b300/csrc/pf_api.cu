@@ -60,13 +60,16 @@ pf_status pfb::check_shape(const pf_model* m, int64_t P, int32_t T, double dt, S
   if (m->substeps < 1) return fail(PF_EINVAL, "substeps must be >= 1");
   if (!(m->ess_threshold >= 0.0) || !std::isfinite(m->ess_threshold))
     return fail(PF_EINVAL, "ess_threshold must be finite and >= 0");
+  if (m->obs_every < 0 || m->obs_count < 0)
+    return fail(PF_EINVAL, "obs_every and obs_count must be >= 0");
   int Ny = 1;
   uint64_t mask = 1;
   if (m->kind == PF_LORENZ96) {
     if (m->obs_stride < 1) return fail(PF_EINVAL, "obs_stride must be >= 1");
     Ny = (m->N + m->obs_stride - 1) / m->obs_stride;
+    if (m->obs_count > 0 && m->obs_count < Ny) Ny = m->obs_count;
     mask = 0;
-    for (int n = 0; n < m->N; n += m->obs_stride) mask |= (1ull << n);
+    for (int n = 0, k = 0; n < m->N && k < Ny; n += m->obs_stride, ++k) mask |= (1ull << n);
   } else {
     if (!(m->flow_period > 0.0) || !std::isfinite(m->flow_period) || !std::isfinite(m->flow_peak))
       return fail(PF_EINVAL, "flow_period must be finite and > 0, flow_peak finite");
@@ -185,6 +188,7 @@ extern "C" pf_status pf_create(const pf_model* m, int64_t P, int32_t T, double d
   d.hist = 0;
   d.mode = sh.mode;
   d.resampler = m->resampler;
+  d.obs_every = m->obs_every > 1 ? m->obs_every : 1;
   d.obs_mask = sh.obs_mask;
   d.dt = dt;
   d.thr = m->ess_threshold;

@@ -70,6 +70,7 @@ struct alignas(16) FilterDev {
   int32_t kind, N, s, stride, prec, Ny;
   int32_t P, T, ntiles, ngroups, hist, mode;
   int32_t resampler;  // RS_*
+  int32_t obs_every;  // >= 1: step i is observed iff i % obs_every == 0
   uint64_t obs_mask;  // Lorenz '96: bit n set iff component n is observed
   uint64_t seed;
   double dt, thr;

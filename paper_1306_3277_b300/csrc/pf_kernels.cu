@@ -372,6 +372,14 @@ __device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs) {
       c->ll = -INFINITY;
       c->rs_flag = 0;
       c->step = fd.T + 1;
+    } else if (!(fd.obs_every == 1 || i % fd.obs_every == 0)) {
+      // no observation at t_i: no likelihood term, no resampling, the
+      // carried weights stay as they are (M = 0 makes the carry an identity)
+      c->M = 0.0;
+      c->S = S;
+      c->rs_flag = 0;
+      if (i < fd.T) c->anc_identity = 1;
+      c->step = i + 1;
     } else {
       const double incr = ((M + log(S)) - c->L) + c->c_obs;
       c->ll = c->ll + incr;
@@ -505,10 +513,13 @@ __global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value))
   }
   __syncthreads();  // observation row staged
   double ell = -INFINITY;
+  const bool observed = fd.obs_every == 1 || i % fd.obs_every == 0;
   if (valid) {
-    double lw;
-    if constexpr (KIND == KIND_WK) lw = wk_weight<R>(fd, i, x[0], ys[0], cw);
-    else lw = l96_weight<N, R>(fd, x, ys, cw);
+    double lw = 0.0;  // a step without an observation carries the weights
+    if (observed) {
+      if constexpr (KIND == KIND_WK) lw = wk_weight<R>(fd, i, x[0], ys[0], cw);
+      else lw = l96_weight<N, R>(fd, x, ys, cw);
+    }
     double e = lam_zero ? lw : fd.lam[j] + lw;
     if (e != e) e = -INFINITY;
     ell = e;
@@ -635,8 +646,8 @@ __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__
   const int i = s_i;
   if (!s_flag) {
     const int j = j0 + tid;
-    if (j < P && fd.mode != MODE_ALWAYS) {
-      fd.lam[j] = fd.ell[j] - s_M;
+    if (j < P) {
+      if (fd.mode != MODE_ALWAYS) fd.lam[j] = fd.ell[j] - s_M;
       if (fd.hist) fd.anc[int64_t(i) * P + j] = j;
     }
     return;

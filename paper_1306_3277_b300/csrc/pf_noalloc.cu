@@ -160,6 +160,7 @@ extern "C" pf_status pf_run_noalloc(const pf_model* m, int64_t P, int32_t T, dou
   d.hist = 0;
   d.mode = sh.mode;
   d.resampler = m->resampler;
+  d.obs_every = m->obs_every > 1 ? m->obs_every : 1;
   d.obs_mask = sh.obs_mask;
   d.seed = seed;
   d.dt = dt;

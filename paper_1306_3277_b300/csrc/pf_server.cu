@@ -137,6 +137,7 @@ bool alloc_request(pf_server* s, Request* r) {
   d.ngroups = sh.ngroups;
   d.mode = sh.mode;
   d.resampler = r->m.resampler;
+  d.obs_every = r->m.obs_every > 1 ? r->m.obs_every : 1;
   d.obs_mask = sh.obs_mask;
   d.dt = r->dt;
   d.thr = r->m.ess_threshold;

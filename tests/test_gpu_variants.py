@@ -1,0 +1,76 @@
+"""GPU parity of the paper-exact model variants: sparse observations (steps
+without an observation, the first components only, as in the paper's
+Lorenz '96 example).  Ancestors and final particles bit-exact and
+log-likelihood within 1e-9 relative against the oracle, outside
+near-boundary targets; batched and sampled-path runs agree too."""
+import numpy as np
+import pytest
+
+import workloads as W
+from pf_parity import compare, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _resim(w):
+    w.y = W.simulate(w)
+    return w
+
+
+SPARSE = [
+    ("lorenz96 sparse N=8 P=2^14 T=60 FP64", lambda: W.lorenz96_sparse(), (1, 2)),
+    ("lorenz96 sparse N=8 P=2^14 T=60 mixed", lambda: W.lorenz96_sparse(prec=W.MIXED), (3,)),
+    ("lorenz96 sparse P=3000 T=40 ESS 0.5", lambda: W.lorenz96_sparse(P=3000, T=40,
+                                                                      ess_threshold=0.5), (4,)),
+    ("windkessel every 3rd step P=1000 T=60",
+     lambda: W.windkessel(P=1000, T=60).with_(obs_every=3), (5,)),
+    ("windkessel every 2nd step, never resample",
+     lambda: W.windkessel(P=300, T=30, ess_threshold=0.0).with_(obs_every=2), (6,)),
+    ("windkessel every 4th step multinomial",
+     lambda: W.windkessel(P=500, T=40).with_(obs_every=4, resampler=2), (7,)),
+    ("lorenz96 N=40 first 10 of the even components every 3rd step",
+     lambda: _resim(W.lorenz96_large(P=3000, T=21).with_(obs_count=10, obs_every=3)), (8,)),
+]
+
+
+@pytest.mark.parametrize("name,factory,seeds", SPARSE, ids=[c[0] for c in SPARSE])
+def test_sparse_parity(name, factory, seeds):
+    w = factory()
+    for seed in seeds:
+        o = run_oracle(w, seed)
+        g = run_gpu(w, seed)
+        rows, _ = compare(w, g, o)
+        assert rows >= 1
+        steps = np.arange(1, w.T + 1)
+        unobserved = steps % max(w.obs_every, 1) != 0
+        assert np.all(o["diag"][unobserved, 6] == 0.0)
+
+
+def test_sparse_batch_and_path():
+    import oracle as O
+    import paper_1306_3277_b300 as pf
+    from pf_parity import oracle_model
+    ws = [W.lorenz96_sparse(P=1000, T=30, seed=3), W.windkessel(P=700, T=33).with_(obs_every=3),
+          W.lorenz96_8(P=900, T=20)]
+    fs = [pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt) for w in ws]
+    try:
+        lls, sts = pf.pf_batch_run(fs, [w.theta for w in ws], [w.y for w in ws],
+                                   [w.seed for w in ws])
+        for k, (w, f) in enumerate(zip(ws, fs)):
+            st, ll, _, _ = f.run(w.theta, w.y, w.seed)
+            assert sts[k] == st and lls[k] == ll
+        w, f = ws[0], fs[0]
+        st, ll, path, idx = f.sample_path(w.theta, w.y, 5)
+        ost, oll, opath, oidx = O.sample_path(oracle_model(w), w.theta, w.y, 5, w.P, w.T)
+        assert st == ost == pf.PF_OK and abs(ll - oll) <= 1e-9 * abs(oll)
+        assert np.array_equal(idx, oidx) and np.array_equal(path, opath)
+    finally:
+        for f in fs:
+            f.destroy()
