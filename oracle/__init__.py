@@ -14,6 +14,7 @@ function                  follows                                   pinned by
 philox4x32_10             Salmon et al. SC'11 (Philox4x32-10)       published known-answer vectors
                                                                     (tests/golden/philox4x32_10_kat.txt)
 log / logf                atanh series of log (own)                libm log, <= 2 ulp; exact special values
+exp                       Cody-Waite reduction + Taylor (own)      libm exp, <= 2 ulp; special values
 sincos2pi / sincos2pif    quarter-turn reduction + Taylor (own)    libm sin/cos, exact quadrant points
 normal64 / normal32       Box-Muller                               moments, Kolmogorov-Smirnov vs scipy
 flow_table                Eq. (flow) read as a half sine           closed form with numpy.sin
@@ -54,6 +55,8 @@ from . import build as _build
 
 WINDKESSEL = 0
 LORENZ96 = 1
+WINDKESSEL_EXP = 2
+LORENZ96_SDE = 3
 FP64 = 0
 MIXED = 1
 PURPOSE_INIT = 1
@@ -122,6 +125,8 @@ def lib():
         L.or_lse.argtypes = [_dp, ctypes.c_int64, _dp, _dp, _dp]
         L.or_systematic.argtypes = [_dp, ctypes.c_int64, ctypes.c_double, _ip]
         L.or_systematic.restype = ctypes.c_int64
+        L.or_exp.argtypes = [ctypes.c_double]
+        L.or_exp.restype = ctypes.c_double
         L.or_resample.argtypes = [_dp, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
                                   ctypes.c_uint32, _ip]
         L.or_resample.restype = ctypes.c_int64
@@ -192,6 +197,10 @@ def resample_uniform(seed, i):
 
 def log(x):
     return lib().or_log(float(x))
+
+
+def exp(x):
+    return lib().or_exp(x)
 
 
 def logf(x):
@@ -376,7 +385,7 @@ def pmmh(m, y, P, T, lik, spec, theta0, niter, seed, nthreads=0):
 def smc2(m, y, P, T, lik, ntheta, spec, base, seed, nthreads=0):
     """SMC^2 (Algorithm 4): final theta-particles, their log-weights, the log
     evidence and its per-step increments, accepted moves and near flags."""
-    nth = 7 if m.kind == WINDKESSEL else 5
+    nth = 7 if m.kind in (WINDKESSEL, WINDKESSEL_EXP) else 5
     yy = np.ascontiguousarray(y, dtype=np.float64)
     b = np.ascontiguousarray(base, dtype=np.float64)
     sp = params(spec)

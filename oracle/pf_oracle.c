@@ -135,6 +135,40 @@ double or_log(double x) {
 }
 
 /* ======================================================================
+ * Own exponential (FP64), Cody and Waite's reduction: k = rint(x / ln2),
+ * r = x - k ln2 with ln2 in two parts (two fmas), |r| <= ln2 / 2; e^r by its
+ * Taylor series to r^14 (truncation below 2^-63 relative), then
+ * e^x = e^r 2^k.  +inf above 709.78, 0 below -745.14, NaN passes through.
+ * Used where the state depends on an exponential (the exact windkessel),
+ * so that both implementations compute it bit for bit alike.
+ * ==================================================================== */
+double or_exp(double x) {
+  double k, r, p;
+  if (x != x) return x;
+  if (x > 709.782712893384) return INFINITY;
+  if (x < -745.1332191019412) return 0.0;
+  k = rint(x * 0x1.71547652b82fep+0);
+  r = fma(-k, OR_LN2_HI, x);
+  r = fma(-k, OR_LN2_LO, r);
+  p = 1.0 / 87178291200.0;
+  p = fma(p, r, 1.0 / 6227020800.0);
+  p = fma(p, r, 1.0 / 479001600.0);
+  p = fma(p, r, 1.0 / 39916800.0);
+  p = fma(p, r, 1.0 / 3628800.0);
+  p = fma(p, r, 1.0 / 362880.0);
+  p = fma(p, r, 1.0 / 40320.0);
+  p = fma(p, r, 1.0 / 5040.0);
+  p = fma(p, r, 1.0 / 720.0);
+  p = fma(p, r, 1.0 / 120.0);
+  p = fma(p, r, 1.0 / 24.0);
+  p = fma(p, r, 1.0 / 6.0);
+  p = fma(p, r, 0.5);
+  p = fma(p, r, 1.0);
+  p = fma(p, r, 1.0);
+  return ldexp(p, (int)k);
+}
+
+/* ======================================================================
  * Own sin(2 pi u), cos(2 pi u) for u in [0, 1) (FP64).  Quarter-turn
  * reduction q = rint(4u), r = 4u - q in [-1/2, 1/2] (exact), x = r pi/2 with
  * pi/2 split in two doubles, then the Taylor series of sin to x^19 and of cos
@@ -374,6 +408,56 @@ void or_l96_rk4f(float *x, int32_t N, float F, float dt, int32_t nsteps) {
   free(buf);
 }
 
+/* The same RK4 step with a per-component forcing Fv[n] in place of F (the
+ * stochastic form: F plus the substep's Wiener increment over its length). */
+static void or_l96_rhs_v(const double *xs, double *k, int32_t N, const double *Fv) {
+  int32_t n;
+  for (n = 0; n < N; ++n) {
+    double xp1 = xs[(n + 1) % N];
+    double xm1 = xs[(n + N - 1) % N];
+    double xm2 = xs[(n + N - 2) % N];
+    k[n] = fma(xp1 - xm2, xm1, Fv[n] - xs[n]);
+  }
+}
+
+static void or_l96_rk4_step_v(double *x, int32_t N, const double *Fv, double dt, double *k,
+                              double *xs, double *acc) {
+  double h2 = 0.5 * dt, h3 = dt / 3.0, h6 = dt / 6.0;
+  int32_t n;
+  or_l96_rhs_v(x, k, N, Fv);
+  for (n = 0; n < N; ++n) { acc[n] = fma(h6, k[n], x[n]); xs[n] = fma(h2, k[n], x[n]); }
+  or_l96_rhs_v(xs, k, N, Fv);
+  for (n = 0; n < N; ++n) { acc[n] = fma(h3, k[n], acc[n]); xs[n] = fma(h2, k[n], x[n]); }
+  or_l96_rhs_v(xs, k, N, Fv);
+  for (n = 0; n < N; ++n) { acc[n] = fma(h3, k[n], acc[n]); xs[n] = fma(dt, k[n], x[n]); }
+  or_l96_rhs_v(xs, k, N, Fv);
+  for (n = 0; n < N; ++n) x[n] = fma(h6, k[n], acc[n]);
+}
+
+static void or_l96_rhs_vf(const float *xs, float *k, int32_t N, const float *Fv) {
+  int32_t n;
+  for (n = 0; n < N; ++n) {
+    float xp1 = xs[(n + 1) % N];
+    float xm1 = xs[(n + N - 1) % N];
+    float xm2 = xs[(n + N - 2) % N];
+    k[n] = fmaf(xp1 - xm2, xm1, Fv[n] - xs[n]);
+  }
+}
+
+static void or_l96_rk4_step_vf(float *x, int32_t N, const float *Fv, float dt, float *k,
+                               float *xs, float *acc) {
+  float h2 = 0.5f * dt, h3 = dt / 3.0f, h6 = dt / 6.0f;
+  int32_t n;
+  or_l96_rhs_vf(x, k, N, Fv);
+  for (n = 0; n < N; ++n) { acc[n] = fmaf(h6, k[n], x[n]); xs[n] = fmaf(h2, k[n], x[n]); }
+  or_l96_rhs_vf(xs, k, N, Fv);
+  for (n = 0; n < N; ++n) { acc[n] = fmaf(h3, k[n], acc[n]); xs[n] = fmaf(h2, k[n], x[n]); }
+  or_l96_rhs_vf(xs, k, N, Fv);
+  for (n = 0; n < N; ++n) { acc[n] = fmaf(h3, k[n], acc[n]); xs[n] = fmaf(dt, k[n], x[n]); }
+  or_l96_rhs_vf(xs, k, N, Fv);
+  for (n = 0; n < N; ++n) x[n] = fmaf(h6, k[n], acc[n]);
+}
+
 /* ======================================================================
  * Scalar Kalman filter (Algorithm 1 reduced to one dimension) for the
  * Euler windkessel: x_{k+1} = a x_k + b_k + N(0, q), a = 1 - dt/(RC),
@@ -386,7 +470,13 @@ double or_kalman_windkessel(const or_model *m, const double *th, const double *y
   const double dt = m->dt;
   const int64_t nflow = (int64_t)T * s + 1;
   double *F = (double *)malloc(sizeof(double) * (size_t)nflow);
-  double a = 1.0 - dt / (R * C);
+  /* Euler form: a = 1 - dt/(RC), input dt F/C, noise q; exact form (the
+   * paper's transition): a = exp(-dt/(RC)), input R(1-a) F, and the flow
+   * noise N(0, (dt sqrt(q))^2) scaled by R(1-a) */
+  const int exact = m->kind == OR_WINDKESSEL_EXP;
+  double a = exact ? exp(-dt / (R * C)) : 1.0 - dt / (R * C);
+  const double bin = exact ? R * (1.0 - a) : dt / C;
+  const double qv = exact ? bin * bin * dt * dt * q : q;
   double mu = m0, V = s0 * s0, ll = 0.0;
   int32_t i, mm;
   or_flow_table(m->flow_peak, m->flow_period, dt, nflow, F);
@@ -394,8 +484,8 @@ double or_kalman_windkessel(const or_model *m, const double *th, const double *y
     double nu, Sv, d, K;
     for (mm = 0; mm < s; ++mm) {
       int64_t k = (int64_t)(i - 1) * s + mm;
-      mu = a * mu + dt * F[k] / C;
-      V = a * a * V + q;
+      mu = exact ? a * mu + bin * F[k] : a * mu + dt * F[k] / C;
+      V = a * a * V + qv;
     }
     if (m->obs_every > 1 && i % m->obs_every != 0) continue; /* no observation at t_i */
     nu = mu + Z * F[(int64_t)i * s];
@@ -610,6 +700,39 @@ static double or_prop_weight64(const or_ctx *cx, uint32_t j, int32_t i, double *
     h = fma(Z, cx->flow[(int64_t)i * s], xv);
     d = yi[0] - h;
     acc = fma(d, d, acc);
+  } else if (m->kind == OR_WINDKESSEL_EXP) {
+    /* the paper's transition: x <- a x + R (1 - a) (F_k + xi), a = exp(-dt/(RC)),
+     * xi ~ N(0, (dt sqrt(sigma2))^2), normal number mm of stream (j, i, PROP) */
+    const double R = cx->th[0], C = cx->th[1], Z = cx->th[2];
+    const double a = or_exp(-(m->dt / (R * C)));
+    const double b = R * (1.0 - a);
+    const double sd = m->dt * sqrt(cx->th[3]);
+    double xv = x[0], h, d;
+    for (mm = 0; mm < s; ++mm) {
+      double Fk = cx->flow[(int64_t)(i - 1) * s + mm];
+      double z = or_normal64(cx->seed, j, (uint32_t)i, OR_PURPOSE_PROP, (uint32_t)mm);
+      xv = fma(a, xv, b * fma(sd, z, Fk));
+    }
+    x[0] = xv;
+    h = fma(Z, cx->flow[(int64_t)i * s], xv);
+    d = yi[0] - h;
+    acc = fma(d, d, acc);
+  } else if (m->kind == OR_LORENZ96_SDE) {
+    /* the paper's form: RK4 substep mm with forcing F + sqrt(sigma2) dW_n / dt,
+     * dW_n = sqrt(dt) z, z = normal number mm N + n of stream (j, i, PROP) */
+    const double F = cx->th[0], sw = sqrt(cx->th[1] / m->dt);
+    double Fv[256];
+    for (mm = 0; mm < s; ++mm) {
+      for (n = 0; n < N; ++n) {
+        double z = or_normal64(cx->seed, j, (uint32_t)i, OR_PURPOSE_PROP, (uint32_t)(mm * N + n));
+        Fv[n] = fma(sw, z, F);
+      }
+      or_l96_rk4_step_v(x, N, Fv, m->dt, tmp, tmp + N, tmp + 2 * N);
+    }
+    for (n = 0; n < N && n / m->obs_stride < cx->Ny; n += m->obs_stride) {
+      double d = yi[n / m->obs_stride] - x[n];
+      acc = fma(d, d, acc);
+    }
   } else {
     const double F = cx->th[0], sx = sqrt(cx->th[1]);
     for (mm = 0; mm < s; ++mm) or_l96_rk4_step(x, N, F, m->dt, tmp, tmp + N, tmp + 2 * N);
@@ -650,6 +773,37 @@ static double or_prop_weight32(const or_ctx *cx, uint32_t j, int32_t i, float *x
     h = fma(Z, cx->flow[(int64_t)i * s], (double)xv);
     d = yi[0] - h;
     acc = fma(d, d, acc);
+  } else if (m->kind == OR_WINDKESSEL_EXP) {
+    /* a, R (1 - a) and dt sqrt(sigma2) in FP64 (own exp), rounded to FP32 */
+    const double R = cx->th[0], C = cx->th[1], Z = cx->th[2];
+    const double a64 = or_exp(-(m->dt / (R * C)));
+    const float a = (float)a64, b = (float)(R * (1.0 - a64));
+    const float sd = (float)(m->dt * sqrt(cx->th[3]));
+    float xv = x[0];
+    double h, d;
+    for (mm = 0; mm < s; ++mm) {
+      float Fk = (float)cx->flow[(int64_t)(i - 1) * s + mm];
+      float z = or_normal32(cx->seed, j, (uint32_t)i, OR_PURPOSE_PROP, (uint32_t)mm);
+      xv = fmaf(a, xv, b * fmaf(sd, z, Fk));
+    }
+    x[0] = xv;
+    h = fma(Z, cx->flow[(int64_t)i * s], (double)xv);
+    d = yi[0] - h;
+    acc = fma(d, d, acc);
+  } else if (m->kind == OR_LORENZ96_SDE) {
+    const float F = (float)cx->th[0], sw = sqrtf((float)cx->th[1] / dtf);
+    float Fv[256];
+    for (mm = 0; mm < s; ++mm) {
+      for (n = 0; n < N; ++n) {
+        float z = or_normal32(cx->seed, j, (uint32_t)i, OR_PURPOSE_PROP, (uint32_t)(mm * N + n));
+        Fv[n] = fmaf(sw, z, F);
+      }
+      or_l96_rk4_step_vf(x, N, Fv, dtf, tmp, tmp + N, tmp + 2 * N);
+    }
+    for (n = 0; n < N && n / m->obs_stride < cx->Ny; n += m->obs_stride) {
+      double d = yi[n / m->obs_stride] - (double)x[n];
+      acc = fma(d, d, acc);
+    }
   } else {
     const float F = (float)cx->th[0], sx = sqrtf((float)cx->th[1]);
     for (mm = 0; mm < s; ++mm) or_l96_rk4_stepf(x, N, F, dtf, tmp, tmp + N, tmp + 2 * N);
@@ -707,14 +861,14 @@ int32_t or_pf_run_sched(const or_model *m, const double *th, const double *y, ui
                         double *xhist, double *ellT) {
   const int32_t N = m->N, s = m->substeps;
   const int mixed = (m->prec == OR_MIXED);
-  const int32_t stride = (m->kind == OR_LORENZ96) ? m->obs_stride : 1;
-  const int32_t Nys = (m->kind == OR_LORENZ96) ? (N + stride - 1) / stride : 1;
-  const int32_t Ny = (m->kind == OR_LORENZ96 && m->obs_count > 0 && m->obs_count < Nys)
+  const int32_t stride = OR_IS_L96(m->kind) ? m->obs_stride : 1;
+  const int32_t Nys = OR_IS_L96(m->kind) ? (N + stride - 1) / stride : 1;
+  const int32_t Ny = (OR_IS_L96(m->kind) && m->obs_count > 0 && m->obs_count < Nys)
                          ? m->obs_count : Nys;
   const int32_t every = m->obs_every > 1 ? m->obs_every : 1;
-  const double r = (m->kind == OR_LORENZ96) ? th[2] : th[4];
-  const double m0 = (m->kind == OR_LORENZ96) ? th[3] : th[5];
-  const double s0 = (m->kind == OR_LORENZ96) ? th[4] : th[6];
+  const double r = OR_IS_L96(m->kind) ? th[2] : th[4];
+  const double m0 = OR_IS_L96(m->kind) ? th[3] : th[5];
+  const double s0 = OR_IS_L96(m->kind) ? th[4] : th[6];
   const double c_obs = -0.5 * (double)Ny * log(2.0 * M_PI * r);
   double *flow = NULL;
   double *xa = NULL, *xb = NULL;   /* FP64 state, SoA [N][P] */
@@ -728,8 +882,9 @@ int32_t or_pf_run_sched(const or_model *m, const double *th, const double *y, ui
   or_ctx cx;
 
   if (P <= 0 || T <= 0 || N <= 0 || s <= 0) return OR_EINVAL;
-  if (m->kind == OR_WINDKESSEL && N != 1) return OR_EINVAL;
-  if (m->kind == OR_LORENZ96 && (N < 4 || N > 256 || stride <= 0)) return OR_EINVAL;
+  if (m->kind < OR_WINDKESSEL || m->kind > OR_LORENZ96_SDE) return OR_EINVAL;
+  if (OR_IS_WK(m->kind) && N != 1) return OR_EINVAL;
+  if (OR_IS_L96(m->kind) && (N < 4 || N > 256 || stride <= 0)) return OR_EINVAL;
   if (m->resampler < OR_RESAMPLE_SYSTEMATIC || m->resampler > OR_RESAMPLE_MULTINOMIAL)
     return OR_EINVAL;
   if (m->obs_every < 0 || m->obs_count < 0) return OR_EINVAL;
@@ -739,7 +894,7 @@ int32_t or_pf_run_sched(const or_model *m, const double *th, const double *y, ui
   (void)nthreads;
 #endif
 
-  if (m->kind == OR_WINDKESSEL) {
+  if (OR_IS_WK(m->kind)) {
     flow = (double *)malloc(sizeof(double) * (size_t)((int64_t)T * s + 1));
     or_flow_table(m->flow_peak, m->flow_period, m->dt, (int64_t)T * s + 1, flow);
   }

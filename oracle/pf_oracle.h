@@ -25,7 +25,13 @@
 extern "C" {
 #endif
 
-enum { OR_WINDKESSEL = 0, OR_LORENZ96 = 1 };
+/* Model kinds: the windkessel with Euler substeps and additive state noise,
+ * Lorenz '96 with additive noise once per observation, and the paper-exact
+ * forms of both: the windkessel's exponential decay with noise on the flow,
+ * and Lorenz '96 with a Wiener increment inside every RK4 substep. */
+enum { OR_WINDKESSEL = 0, OR_LORENZ96 = 1, OR_WINDKESSEL_EXP = 2, OR_LORENZ96_SDE = 3 };
+#define OR_IS_WK(kind) ((kind) == OR_WINDKESSEL || (kind) == OR_WINDKESSEL_EXP)
+#define OR_IS_L96(kind) ((kind) == OR_LORENZ96 || (kind) == OR_LORENZ96_SDE)
 enum { OR_FP64 = 0, OR_MIXED = 1 };
 enum { OR_OK = 0, OR_EINVAL = 1, OR_EDEGENERATE = 4 };
 enum { OR_RESAMPLE_SYSTEMATIC = 0, OR_RESAMPLE_STRATIFIED = 1, OR_RESAMPLE_MULTINOMIAL = 2 };
@@ -67,6 +73,7 @@ void or_fill_normals(uint64_t seed, int32_t prec, uint32_t i, uint32_t purpose, 
 
 /* --- project-written elementary functions ----------------------------- */
 double or_log(double x);
+double or_exp(double x);
 void or_sincos2pi(double u, double *s, double *c);
 float or_logf(float x);
 void or_sincos2pif(float u, float *s, float *c);

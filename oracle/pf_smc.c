@@ -24,7 +24,7 @@
 #define OR_MAX_THETA 8
 #define OR_TG_ATTEMPTS 64
 
-static int32_t or_theta_size(int32_t kind) { return kind == OR_WINDKESSEL ? 7 : 5; }
+static int32_t or_theta_size(int32_t kind) { return OR_IS_WK(kind) ? 7 : 5; }
 
 /* Standard normal CDF. */
 static double or_Phi(double x) { return 0.5 * erfc(-x * M_SQRT1_2); }
@@ -155,7 +155,7 @@ int32_t or_pmmh(const or_model *m, const double *y, int64_t P, int32_t T, int32_
   const int32_t nth = or_theta_size(m->kind);
   int32_t c, i;
   if (nchains < 1 || niter < 0 || P < 1 || T < 1) return OR_EINVAL;
-  if (lik == OR_LIK_KALMAN && m->kind != OR_WINDKESSEL) return OR_EINVAL;
+  if (lik == OR_LIK_KALMAN && !OR_IS_WK(m->kind)) return OR_EINVAL;
   for (c = 0; c < nchains; ++c) {
     double th[OR_MAX_THETA], thp[OR_MAX_THETA];
     double ll, lp;
@@ -306,7 +306,7 @@ int32_t or_smc2(const or_model *m, const double *y, int64_t P, int32_t T, int32_
   int32_t j, i, status = OR_OK;
   double logZ = 0.0;
   if (ntheta < 1 || P < 1 || T < 1) return OR_EINVAL;
-  if (lik == OR_LIK_KALMAN && m->kind != OR_WINDKESSEL) return OR_EINVAL;
+  if (lik == OR_LIK_KALMAN && !OR_IS_WK(m->kind)) return OR_EINVAL;
   th = (double *)malloc(sizeof(double) * (size_t)ntheta * OR_MAX_THETA);
   thn = (double *)malloc(sizeof(double) * (size_t)ntheta * OR_MAX_THETA);
   lp = (double *)malloc(sizeof(double) * (size_t)ntheta);

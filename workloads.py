@@ -27,6 +27,8 @@ DATA_SEED = 0x13063277
 
 WINDKESSEL = 0
 LORENZ96 = 1
+WINDKESSEL_EXP = 2  # the paper's exact windkessel transition
+LORENZ96_SDE = 3    # the paper's Lorenz '96 with the Wiener increment inside RK4
 FP64 = 0
 MIXED = 1
 
@@ -58,7 +60,7 @@ class Workload:
 
     @property
     def Ny(self):
-        if self.kind == WINDKESSEL:
+        if self.kind in (WINDKESSEL, WINDKESSEL_EXP):
             return 1
         ny = (self.N + self.obs_stride - 1) // self.obs_stride
         return min(ny, self.obs_count) if self.obs_count > 0 else ny
@@ -101,6 +103,32 @@ def lorenz96_sparse(P=1 << 14, T=60, prec=FP64, ess_threshold=1.0, theta=L96_THE
     return w
 
 
+WKX_THETA = (1.0, 1.5, 0.03, 25.0, 4.0, 90.0, 15.0)  # sigma2 = 25: the prior mean
+L96W_THETA_8 = (8.0, 0.25, 0.25, 0.0, 1.0)           # sigma2 = 0.25: the prior mean
+
+
+def windkessel_exact(P=1024, T=100, prec=FP64, ess_threshold=1.0, substeps=1, theta=WKX_THETA,
+                     seed=1):
+    """The paper's windkessel transition (Sec. 2.1.1, model listing): exponential
+    decay over each step h = dt with noise on the flow,
+    x <- exp(-h/(RC)) x + R (1 - exp(-h/(RC))) (F + xi), xi ~ N(0, (h sqrt(sigma2))^2)."""
+    w = Workload("windkessel_exact_P%d_T%d" % (P, T), WINDKESSEL_EXP, 1, substeps, 1, 0.01, P, T,
+                 prec, ess_threshold, tuple(theta), seed=seed)
+    w.y = simulate(w)
+    return w
+
+
+def lorenz96_sde(P=1 << 14, T=200, N=8, prec=FP64, ess_threshold=1.0, theta=L96W_THETA_8,
+                 substeps=1, dt=0.05, obs_stride=1, seed=1):
+    """The paper's Lorenz '96 transition (Sec. 2.1.2, model listing): one RK4 step
+    of h = 0.05 per observation whose right-hand side carries the Wiener increment
+    sqrt(sigma2) dW_n / h, dW_n ~ N(0, h), held over the step."""
+    w = Workload("lorenz96_sde_N%d_P%d_T%d" % (N, P, T), LORENZ96_SDE, N, substeps, obs_stride,
+                 dt, P, T, prec, ess_threshold, tuple(theta), seed=seed)
+    w.y = simulate(w)
+    return w
+
+
 def _flow(t, peak, period):
     ph = t / period
     fr = ph - np.floor(ph)
@@ -116,15 +144,20 @@ def simulate(w, data_seed=DATA_SEED, T=None):
     T = w.T if T is None else T
     rng = np.random.default_rng([data_seed, w.kind, w.N, w.substeps, w.obs_stride])
     th = w.theta
-    if w.kind == WINDKESSEL:
+    if w.kind in (WINDKESSEL, WINDKESSEL_EXP):
         R, C, Z, q, r, m0, s0 = th
+        a = math.exp(-w.dt / (R * C))
         x = m0 + s0 * rng.standard_normal()
         y = np.zeros((T, 1))
         for i in range(1, T + 1):
             for m in range(w.substeps):
                 k = (i - 1) * w.substeps + m
                 F = _flow(k * w.dt, w.flow_peak, w.flow_period)
-                x = x + w.dt * (F / C - x / (R * C)) + math.sqrt(q) * rng.standard_normal()
+                if w.kind == WINDKESSEL:
+                    x = x + w.dt * (F / C - x / (R * C)) + math.sqrt(q) * rng.standard_normal()
+                else:
+                    xi = w.dt * math.sqrt(q) * rng.standard_normal()
+                    x = a * x + R * (1.0 - a) * (F + xi)
             Fo = _flow(i * w.substeps * w.dt, w.flow_peak, w.flow_period)
             y[i - 1, 0] = x + Z * Fo + math.sqrt(r) * rng.standard_normal()
         return y
@@ -134,12 +167,16 @@ def simulate(w, data_seed=DATA_SEED, T=None):
     y = np.zeros((T, w.Ny))
     for i in range(T):
         for _ in range(w.substeps):
-            k1 = _l96_rhs(x, F)
-            k2 = _l96_rhs(x + 0.5 * h * k1, F)
-            k3 = _l96_rhs(x + 0.5 * h * k2, F)
-            k4 = _l96_rhs(x + h * k3, F)
+            Fs = F
+            if w.kind == LORENZ96_SDE:  # Wiener increment held over the substep
+                Fs = F + math.sqrt(q / h) * rng.standard_normal(w.N)
+            k1 = _l96_rhs(x, Fs)
+            k2 = _l96_rhs(x + 0.5 * h * k1, Fs)
+            k3 = _l96_rhs(x + 0.5 * h * k2, Fs)
+            k4 = _l96_rhs(x + h * k3, Fs)
             x = x + h / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
-        x = x + math.sqrt(q) * rng.standard_normal(w.N)
+        if w.kind == LORENZ96:
+            x = x + math.sqrt(q) * rng.standard_normal(w.N)
         y[i] = x[::w.obs_stride][:w.Ny] + math.sqrt(r) * rng.standard_normal(w.Ny)
     return y
 
