@@ -58,7 +58,23 @@ typedef enum {
   PF_EBUSY = 6         /* result not ready / no capacity right now           */
 } pf_status;
 
-typedef enum { PF_WINDKESSEL = 0, PF_LORENZ96 = 1 } pf_model_kind;
+/* Model kinds (Sec. 2.1).  theta layouts:
+ *   PF_WINDKESSEL, PF_WINDKESSEL_EXP: (R, C, Z, q, r, m0, s0)
+ *   PF_LORENZ96, PF_LORENZ96_SDE:     (F, q, r, m0, s0)
+ * r is the observation variance, (m0, s0) the initial mean and standard
+ * deviation.  PF_WINDKESSEL takes Euler substeps x += dt (F/C - x/(RC)) plus
+ * N(0, q) per substep; PF_WINDKESSEL_EXP is the paper's transition
+ * x <- a x + R (1 - a) (F + xi), a = exp(-dt/(RC)), xi ~ N(0, (dt sqrt(q))^2)
+ * (q the flow-noise variance sigma2).  PF_LORENZ96 adds N(0, q) to every
+ * component once per observation after the RK4 substeps; PF_LORENZ96_SDE is
+ * the paper's form, each RK4 substep of length dt carrying the forcing
+ * F + sqrt(q) dW_n / dt with dW_n ~ N(0, dt) held over the substep. */
+typedef enum {
+  PF_WINDKESSEL = 0,
+  PF_LORENZ96 = 1,
+  PF_WINDKESSEL_EXP = 2,
+  PF_LORENZ96_SDE = 3
+} pf_model_kind;
 typedef enum { PF_FP64 = 0, PF_MIXED = 1 } pf_precision;
 /* Resampling scheme (Sec. 3.3; Algorithm 2 writes the multinomial draw).  All
  * three give sorted ancestors: target j sits at (j + u) S / P with one u per

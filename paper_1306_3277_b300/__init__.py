@@ -17,7 +17,7 @@ import numpy as np
 from . import build as _build
 
 PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_EDEGENERATE, PF_ETIMEOUT, PF_EBUSY = range(7)
-PF_WINDKESSEL, PF_LORENZ96 = 0, 1
+PF_WINDKESSEL, PF_LORENZ96, PF_WINDKESSEL_EXP, PF_LORENZ96_SDE = 0, 1, 2, 3
 PF_FP64, PF_MIXED = 0, 1
 PF_FLAG_ASYNC = 1
 STATUS_NAMES = {0: "PF_OK", 1: "PF_EINVAL", 2: "PF_ENOMEM", 3: "PF_ECUDA", 4: "PF_EDEGENERATE",
@@ -228,8 +228,9 @@ class Filter:
         self.model = m
         self.P, self.T, self.dt = P, T, dt
         self.N = m.N
-        ny = 1 if m.kind == PF_WINDKESSEL else (m.N + m.obs_stride - 1) // m.obs_stride
-        self.Ny = min(ny, m.obs_count) if (m.kind != PF_WINDKESSEL and m.obs_count > 0) else ny
+        wk = m.kind in (PF_WINDKESSEL, PF_WINDKESSEL_EXP)
+        ny = 1 if wk else (m.N + m.obs_stride - 1) // m.obs_stride
+        self.Ny = min(ny, m.obs_count) if (not wk and m.obs_count > 0) else ny
         self.state_dtype = np.float64 if m.prec == PF_FP64 else np.float32
 
     def run(self, theta, y, seed, want_particles=False, want_ancestors=False, stream=None):

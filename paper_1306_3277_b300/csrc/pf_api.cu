@@ -44,7 +44,7 @@ extern "C" const char* pf_last_error(void) { return g_err.c_str(); }
 // shapes
 // ---------------------------------------------------------------------------
 extern "C" int32_t pf_theta_size(int32_t kind) {
-  return kind == PF_WINDKESSEL ? 7 : kind == PF_LORENZ96 ? 5 : 0;
+  return wk_kind(kind) ? 7 : l96_kind(kind) ? 5 : 0;
 }
 
 pf_status pfb::check_shape(const pf_model* m, int64_t P, int32_t T, double dt, Shape* sh) {
@@ -64,7 +64,7 @@ pf_status pfb::check_shape(const pf_model* m, int64_t P, int32_t T, double dt, S
     return fail(PF_EINVAL, "obs_every and obs_count must be >= 0");
   int Ny = 1;
   uint64_t mask = 1;
-  if (m->kind == PF_LORENZ96) {
+  if (l96_kind(m->kind)) {
     if (m->obs_stride < 1) return fail(PF_EINVAL, "obs_stride must be >= 1");
     Ny = (m->N + m->obs_stride - 1) / m->obs_stride;
     if (m->obs_count > 0 && m->obs_count < Ny) Ny = m->obs_count;
@@ -82,7 +82,7 @@ pf_status pfb::check_shape(const pf_model* m, int64_t P, int32_t T, double dt, S
   sh->mode = m->ess_threshold >= 1.0 ? MODE_ALWAYS : (m->ess_threshold == 0.0 ? MODE_NEVER
                                                                               : MODE_ADAPTIVE);
   sh->state_bytes = size_t(m->prec == PF_FP64 ? 8 : 4);
-  sh->nflow = m->kind == PF_WINDKESSEL ? int64_t(T) * m->substeps + 1 : 0;
+  sh->nflow = wk_kind(m->kind) ? int64_t(T) * m->substeps + 1 : 0;
   return PF_OK;
 }
 
@@ -178,7 +178,7 @@ extern "C" pf_status pf_create(const pf_model* m, int64_t P, int32_t T, double d
   d.kind = m->kind;
   d.N = m->N;
   d.s = m->substeps;
-  d.stride = m->kind == PF_LORENZ96 ? m->obs_stride : 1;
+  d.stride = l96_kind(m->kind) ? m->obs_stride : 1;
   d.prec = m->prec;
   d.Ny = sh.Ny;
   d.P = int32_t(P);

@@ -17,7 +17,9 @@ constexpr int GROUP = 256;       // tiles per group (two-level combine)
 constexpr int WARPS = TILE / 32;
 constexpr int64_t MAX_P = int64_t(1) << 24;  // GROUP * GROUP * TILE
 
-enum { KIND_WK = 0, KIND_L96 = 1 };
+enum { KIND_WK = 0, KIND_L96 = 1, KIND_WKX = 2, KIND_L96W = 3 };
+__host__ __device__ constexpr bool wk_kind(int k) { return k == KIND_WK || k == KIND_WKX; }
+__host__ __device__ constexpr bool l96_kind(int k) { return k == KIND_L96 || k == KIND_L96W; }
 enum { PREC_FP64 = 0, PREC_MIXED = 1 };
 enum { MODE_ALWAYS = 0, MODE_ADAPTIVE = 1, MODE_NEVER = 2 };
 enum { RS_SYSTEMATIC = 0, RS_STRATIFIED = 1, RS_MULTINOMIAL = 2 };
@@ -156,6 +158,34 @@ __device__ __forceinline__ double log_pos(double x) {
   const double lm = fma(__dmul_rn(two_f, f2), p, two_f);
   const double de = double(e);
   return fma(de, 0x1.62e42fefa39efp-1, fma(de, 0x1.abc9e3b39803fp-56, lm));
+}
+
+// Exponential, FP64 (Cody and Waite): k = rint(x / ln2), r = x - k ln2 with
+// ln2 in two parts, e^r by its Taylor series to r^14, e^x = e^r 2^k; used
+// where the state itself depends on an exponential.
+__device__ __forceinline__ double exp_own(double x) {
+  if (x != x) return x;
+  if (x > 709.782712893384) return INFINITY;
+  if (x < -745.1332191019412) return 0.0;
+  const double k = rint(__dmul_rn(x, 0x1.71547652b82fep+0));
+  double r = fma(-k, 0x1.62e42fefa39efp-1, x);
+  r = fma(-k, 0x1.abc9e3b39803fp-56, r);
+  double p = 1.0 / 87178291200.0;
+  p = fma(p, r, 1.0 / 6227020800.0);
+  p = fma(p, r, 1.0 / 479001600.0);
+  p = fma(p, r, 1.0 / 39916800.0);
+  p = fma(p, r, 1.0 / 3628800.0);
+  p = fma(p, r, 1.0 / 362880.0);
+  p = fma(p, r, 1.0 / 40320.0);
+  p = fma(p, r, 1.0 / 5040.0);
+  p = fma(p, r, 1.0 / 720.0);
+  p = fma(p, r, 1.0 / 120.0);
+  p = fma(p, r, 1.0 / 24.0);
+  p = fma(p, r, 1.0 / 6.0);
+  p = fma(p, r, 0.5);
+  p = fma(p, r, 1.0);
+  p = fma(p, r, 1.0);
+  return ldexp(p, int(k));
 }
 
 // sin(2 pi u), cos(2 pi u), FP64, u in [0,1): quarter turns q = rint(4u),

@@ -32,32 +32,39 @@ __device__ __forceinline__ float fmaR(float a, float b, float c) { return fmaf(a
 // One classic RK4 step of dt for dx_n/dt = (x_{n+1} - x_{n-2}) x_{n-1} - x_n + F
 // (cyclic), the right-hand side evaluated as fma(x_{n+1} - x_{n-2}, x_{n-1}, F - x_n)
 // and the update accumulated as x + h/6 k1 + h/3 k2 + h/3 k3 + h/6 k4.
-template <int N, typename R>
-__device__ __forceinline__ void l96_rk4_step(R (&x)[N], R F, R dt, R h2, R h3, R h6) {
+// force(n) is the forcing of component n: F, or F plus the substep's Wiener
+// increment over its length for the stochastic form.
+template <int N, typename R, typename Force>
+__device__ __forceinline__ void l96_rk4_step_f(R (&x)[N], Force force, R dt, R h2, R h3, R h6) {
   R acc[N], xa[N], xb[N];
 #pragma unroll
   for (int n = 0; n < N; ++n) {
-    const R k = fmaR(x[(n + 1) % N] - x[(n + N - 2) % N], x[(n + N - 1) % N], F - x[n]);
+    const R k = fmaR(x[(n + 1) % N] - x[(n + N - 2) % N], x[(n + N - 1) % N], force(n) - x[n]);
     acc[n] = fmaR(h6, k, x[n]);
     xa[n] = fmaR(h2, k, x[n]);
   }
 #pragma unroll
   for (int n = 0; n < N; ++n) {
-    const R k = fmaR(xa[(n + 1) % N] - xa[(n + N - 2) % N], xa[(n + N - 1) % N], F - xa[n]);
+    const R k = fmaR(xa[(n + 1) % N] - xa[(n + N - 2) % N], xa[(n + N - 1) % N], force(n) - xa[n]);
     acc[n] = fmaR(h3, k, acc[n]);
     xb[n] = fmaR(h2, k, x[n]);
   }
 #pragma unroll
   for (int n = 0; n < N; ++n) {
-    const R k = fmaR(xb[(n + 1) % N] - xb[(n + N - 2) % N], xb[(n + N - 1) % N], F - xb[n]);
+    const R k = fmaR(xb[(n + 1) % N] - xb[(n + N - 2) % N], xb[(n + N - 1) % N], force(n) - xb[n]);
     acc[n] = fmaR(h3, k, acc[n]);
     xa[n] = fmaR(dt, k, x[n]);
   }
 #pragma unroll
   for (int n = 0; n < N; ++n) {
-    const R k = fmaR(xa[(n + 1) % N] - xa[(n + N - 2) % N], xa[(n + N - 1) % N], F - xa[n]);
+    const R k = fmaR(xa[(n + 1) % N] - xa[(n + N - 2) % N], xa[(n + N - 1) % N], force(n) - xa[n]);
     x[n] = fmaR(h6, k, acc[n]);
   }
+}
+
+template <int N, typename R>
+__device__ __forceinline__ void l96_rk4_step(R (&x)[N], R F, R dt, R h2, R h3, R h6) {
+  l96_rk4_step_f<N, R>(x, [F](int) { return F; }, dt, h2, h3, h6);
 }
 
 // ---------------------------------------------------------------------------
@@ -103,55 +110,62 @@ __device__ __forceinline__ f32x2 l96_rhs2(const f32x2 (&Y)[H], int p, f32x2 FF) 
   return fma2(sub2(xp1, xm2), xm1, sub2(FF, Y[p]));
 }
 
-// The RK4 step of l96_rk4_step on the packed state (same operations per lane).
-template <int H>
-__device__ __forceinline__ void l96_rk4_step2(f32x2 (&X)[H], f32x2 FF, f32x2 dt, f32x2 h2,
-                                              f32x2 h3, f32x2 h6) {
+// The RK4 step of l96_rk4_step_f on the packed state (same operations per
+// lane); force(p) is the packed forcing of the pair p.
+template <int H, typename Force>
+__device__ __forceinline__ void l96_rk4_step2_f(f32x2 (&X)[H], Force force, f32x2 dt, f32x2 h2,
+                                                f32x2 h3, f32x2 h6) {
   f32x2 acc[H], A[H], B[H];
 #pragma unroll
   for (int p = 0; p < H; ++p) {
-    const f32x2 k = l96_rhs2<H>(X, p, FF);
+    const f32x2 k = l96_rhs2<H>(X, p, force(p));
     acc[p] = fma2(h6, k, X[p]);
     A[p] = fma2(h2, k, X[p]);
   }
 #pragma unroll
   for (int p = 0; p < H; ++p) {
-    const f32x2 k = l96_rhs2<H>(A, p, FF);
+    const f32x2 k = l96_rhs2<H>(A, p, force(p));
     acc[p] = fma2(h3, k, acc[p]);
     B[p] = fma2(h2, k, X[p]);
   }
 #pragma unroll
   for (int p = 0; p < H; ++p) {
-    const f32x2 k = l96_rhs2<H>(B, p, FF);
+    const f32x2 k = l96_rhs2<H>(B, p, force(p));
     acc[p] = fma2(h3, k, acc[p]);
     A[p] = fma2(dt, k, X[p]);
   }
 #pragma unroll
   for (int p = 0; p < H; ++p) {
-    const f32x2 k = l96_rhs2<H>(A, p, FF);
+    const f32x2 k = l96_rhs2<H>(A, p, force(p));
     X[p] = fma2(h6, k, acc[p]);
   }
+}
+
+template <int H>
+__device__ __forceinline__ void l96_rk4_step2(f32x2 (&X)[H], f32x2 FF, f32x2 dt, f32x2 h2,
+                                              f32x2 h3, f32x2 h6) {
+  l96_rk4_step2_f<H>(X, [FF](int) { return FF; }, dt, h2, h3, h6);
 }
 
 // Normals number 0..N-1 of the stream (j, i, purpose) into z (N a multiple of 4
 // for Lorenz '96; the windkessel uses its own loop).
 template <int N>
 __device__ __forceinline__ void normals(double (&z)[N], uint64_t seed, uint32_t j, uint32_t i,
-                                        uint32_t purpose) {
+                                        uint32_t purpose, uint32_t b0 = 0) {
 #pragma unroll
   for (int b = 0; b < (N + 1) / 2; ++b) {
     double z0, z1;
-    normal_pair64(rng_block(seed, j, i, purpose, b), &z0, &z1);
+    normal_pair64(rng_block(seed, j, i, purpose, b0 + b), &z0, &z1);
     z[2 * b] = z0;
     if (2 * b + 1 < N) z[2 * b + 1] = z1;
   }
 }
 template <int N>
 __device__ __forceinline__ void normals(float (&z)[N], uint64_t seed, uint32_t j, uint32_t i,
-                                        uint32_t purpose) {
+                                        uint32_t purpose, uint32_t b0 = 0) {
 #pragma unroll
   for (int b = 0; b < (N + 3) / 4; ++b) {
-    const uint4 w = rng_block(seed, j, i, purpose, b);
+    const uint4 w = rng_block(seed, j, i, purpose, b0 + b);
     float z0, z1, z2, z3;
     normal_pair32(w.x, w.y, &z0, &z1);
     normal_pair32(w.z, w.w, &z2, &z3);
@@ -178,6 +192,39 @@ __device__ __forceinline__ double to_double(float v) {
 template <typename R> __device__ __forceinline__ R from_double(double v);
 template <> __device__ __forceinline__ double from_double<double>(double v) { return v; }
 template <> __device__ __forceinline__ float from_double<float>(double v) { return __double2float_rn(v); }
+
+// The paper's windkessel transition: s steps x <- a x + b (F_k + sd z_mm),
+// a = exp(-dt/(RC)) (own exponential), b = R (1 - a), sd = dt sqrt(sigma2),
+// z_mm = normal number mm of stream (j, i, PROP); a, b, sd in FP64, rounded to
+// the state precision.
+template <typename R>
+__device__ __forceinline__ void wkx_propagate(const FilterDev& fd, uint32_t j, int i, R& xv) {
+  const int s = fd.s;
+  const double Rr = fd.theta[0], Cc = fd.theta[1];
+  const double a64 = exp_own(-(fd.dt / (Rr * Cc)));
+  const R a = from_double<R>(a64), b = from_double<R>(Rr * (1.0 - a64));
+  const R sd = from_double<R>(fd.dt * sqrt(fd.theta[3]));
+  const double* fl = fd.flow + int64_t(i - 1) * s;
+  if constexpr (sizeof(R) == 8) {
+    for (int mm = 0; mm < s; mm += 2) {
+      double z[2];
+      normal_pair64(rng_block(fd.seed, j, uint32_t(i), PURPOSE_PROP, uint32_t(mm >> 1)), &z[0], &z[1]);
+#pragma unroll
+      for (int e = 0; e < 2; ++e)
+        if (mm + e < s) xv = fmaR(a, xv, b * fmaR(sd, R(z[e]), R(fl[mm + e])));
+    }
+  } else {
+    for (int mm = 0; mm < s; mm += 4) {
+      const uint4 w = rng_block(fd.seed, j, uint32_t(i), PURPOSE_PROP, uint32_t(mm >> 2));
+      float z[4];
+      normal_pair32(w.x, w.y, &z[0], &z[1]);
+      normal_pair32(w.z, w.w, &z[2], &z[3]);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (mm + e < s) xv = fmaR(a, xv, b * fmaR(sd, z[e], from_double<R>(fl[mm + e])));
+    }
+  }
+}
 
 // Windkessel propagation: s Euler substeps x <- x + dt (F_k/C - x/(RC)) +
 // sqrt(q) z_mm (normal number mm of stream (j, i, PROP)).
@@ -265,6 +312,47 @@ __device__ __forceinline__ void l96_propagate(const FilterDev& fd, uint32_t j, i
     const R sx = sqrt(from_double<R>(fd.theta[1]));
 #pragma unroll
     for (int n = 0; n < N; ++n) x[n] = fmaR(sx, z[n], x[n]);
+  }
+}
+
+// The paper's Lorenz '96 transition: s RK4 substeps, substep mm with the
+// forcing F + sqrt(q/dt) z_{mm N + n} on component n (the Wiener increment
+// over the substep divided by its length), normal numbers mm N .. mm N + N-1
+// of stream (j, i, PROP); no noise after the substeps.
+template <int N, typename R>
+__device__ __forceinline__ void l96w_propagate(const FilterDev& fd, uint32_t j, int i,
+                                               R (&x)[N]) {
+  const R F = from_double<R>(fd.theta[0]);
+  const R dt = from_double<R>(fd.dt);
+  const R h2 = R(0.5) * dt, h3 = dt / R(3.0), h6 = dt / R(6.0);
+  const R sw = sqrt(from_double<R>(fd.theta[1]) / dt);
+  constexpr uint32_t per_block = sizeof(R) == 4 ? 4u : 2u;  // normals per Philox block
+  if constexpr (sizeof(R) == 4 && N % 2 == 0) {
+    constexpr int H = N / 2;
+    f32x2 X[H];
+#pragma unroll
+    for (int p = 0; p < H; ++p) X[p] = pk(x[p], x[p + H]);
+    const f32x2 FF = pk(F, F), dt2 = pk(dt, dt), h22 = pk(h2, h2), h32 = pk(h3, h3),
+                h62 = pk(h6, h6), sw2 = pk(sw, sw);
+    for (int mm = 0; mm < fd.s; ++mm) {
+      R z[N];
+      normals<N>(z, fd.seed, j, uint32_t(i), PURPOSE_PROP, uint32_t(mm) * (N / per_block));
+      f32x2 FV[H];
+#pragma unroll
+      for (int p = 0; p < H; ++p) FV[p] = fma2(sw2, pk(z[p], z[p + H]), FF);
+      l96_rk4_step2_f<H>(X, [&](int p) { return FV[p]; }, dt2, h22, h32, h62);
+    }
+#pragma unroll
+    for (int p = 0; p < H; ++p) upk(X[p], x[p], x[p + H]);
+  } else {
+    for (int mm = 0; mm < fd.s; ++mm) {
+      R z[N];
+      normals<N>(z, fd.seed, j, uint32_t(i), PURPOSE_PROP, uint32_t(mm) * (N / per_block));
+      R Fv[N];
+#pragma unroll
+      for (int n = 0; n < N; ++n) Fv[n] = fmaR(sw, z[n], F);
+      l96_rk4_step_f<N, R>(x, [&](int n) { return Fv[n]; }, dt, h2, h3, h6);
+    }
   }
 }
 
@@ -422,8 +510,8 @@ __global__ void __launch_bounds__(TILE) k_init(const FilterDev* __restrict__ fds
   const int t = ft.y;
   const int j = t * TILE + threadIdx.x;
   const int P = fd.P;
-  const double m0 = KIND == KIND_WK ? fd.theta[5] : fd.theta[3];
-  const double s0 = KIND == KIND_WK ? fd.theta[6] : fd.theta[4];
+  const double m0 = wk_kind(KIND) ? fd.theta[5] : fd.theta[3];
+  const double s0 = wk_kind(KIND) ? fd.theta[6] : fd.theta[4];
   if (j < P) {
     R z[N];
     normals<N>(z, fd.seed, uint32_t(j), 0u, PURPOSE_INIT);
@@ -436,7 +524,7 @@ __global__ void __launch_bounds__(TILE) k_init(const FilterDev* __restrict__ fds
   if (threadIdx.x == 0 && (t % GROUP) == 0) fd.gp[t / GROUP].ticket = 0u;
   if (threadIdx.x == 0 && t == 0) {
     Ctl* c = fd.ctl;
-    const double r = KIND == KIND_WK ? fd.theta[4] : fd.theta[2];
+    const double r = wk_kind(KIND) ? fd.theta[4] : fd.theta[2];
     c->step = 1;
     c->rs_step = 0;
     c->rs_flag = 0;
@@ -461,7 +549,7 @@ __global__ void __launch_bounds__(TILE) k_init(const FilterDev* __restrict__ fds
 // (every FP32 size, FP64 up to N = 12, the windkessel), else one.
 template <int KIND, int N, typename R>
 struct PropagateOccupancy {
-  static constexpr int value = (KIND == KIND_WK || sizeof(R) == 4 || N <= 12) ? 2 : 1;
+  static constexpr int value = (wk_kind(KIND) || sizeof(R) == 4 || N <= 12) ? 2 : 1;
 };
 
 template <int KIND, int N, typename R>
@@ -507,6 +595,8 @@ __global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value))
 #pragma unroll
     for (int n = 0; n < N; ++n) x[n] = xin[int64_t(n) * P + a];
     if constexpr (KIND == KIND_WK) wk_propagate<R>(fd, uint32_t(j), i, x[0]);
+    else if constexpr (KIND == KIND_WKX) wkx_propagate<R>(fd, uint32_t(j), i, x[0]);
+    else if constexpr (KIND == KIND_L96W) l96w_propagate<N, R>(fd, uint32_t(j), i, x);
     else l96_propagate<N, R>(fd, uint32_t(j), i, x);
 #pragma unroll
     for (int n = 0; n < N; ++n) xout[int64_t(n) * P + j] = x[n];
@@ -517,7 +607,7 @@ __global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value))
   if (valid) {
     double lw = 0.0;  // a step without an observation carries the weights
     if (observed) {
-      if constexpr (KIND == KIND_WK) lw = wk_weight<R>(fd, i, x[0], ys[0], cw);
+      if constexpr (wk_kind(KIND)) lw = wk_weight<R>(fd, i, x[0], ys[0], cw);
       else lw = l96_weight<N, R>(fd, x, ys, cw);
     }
     double e = lam_zero ? lw : fd.lam[j] + lw;
@@ -885,8 +975,8 @@ __global__ void k_results(const FilterDev* __restrict__ fds, int nf, double* __r
 
 bool supported(int kind, int N, int prec) {
   if (prec != PREC_FP64 && prec != PREC_MIXED) return false;
-  if (kind == KIND_WK) return N == 1;
-  if (kind != KIND_L96) return false;
+  if (wk_kind(kind)) return N == 1;
+  if (!l96_kind(kind)) return false;
 #define PF_CASE(n) if (N == n) return true;
   PF_L96_SIZES(PF_CASE)
 #undef PF_CASE
@@ -909,12 +999,26 @@ static cudaError_t dispatch(bool init, int kind, int N, int prec, const FilterDe
     return dp ? launch_pair<KIND_WK, 1, double>(init, fds, tmap, nblocks, st)
               : launch_pair<KIND_WK, 1, float>(init, fds, tmap, nblocks, st);
   }
+  if (kind == KIND_WKX) {
+    return dp ? launch_pair<KIND_WKX, 1, double>(init, fds, tmap, nblocks, st)
+              : launch_pair<KIND_WKX, 1, float>(init, fds, tmap, nblocks, st);
+  }
+  if (kind == KIND_L96) {
 #define PF_CASE(n)                                                                       \
   if (N == n)                                                                            \
     return dp ? launch_pair<KIND_L96, n, double>(init, fds, tmap, nblocks, st)           \
               : launch_pair<KIND_L96, n, float>(init, fds, tmap, nblocks, st);
-  PF_L96_SIZES(PF_CASE)
+    PF_L96_SIZES(PF_CASE)
 #undef PF_CASE
+  }
+  if (kind == KIND_L96W) {
+#define PF_CASE(n)                                                                       \
+  if (N == n)                                                                            \
+    return dp ? launch_pair<KIND_L96W, n, double>(init, fds, tmap, nblocks, st)          \
+              : launch_pair<KIND_L96W, n, float>(init, fds, tmap, nblocks, st);
+    PF_L96_SIZES(PF_CASE)
+#undef PF_CASE
+  }
   return cudaErrorInvalidValue;
 }
 

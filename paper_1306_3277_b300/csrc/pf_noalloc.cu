@@ -150,7 +150,7 @@ extern "C" pf_status pf_run_noalloc(const pf_model* m, int64_t P, int32_t T, dou
   d.kind = m->kind;
   d.N = m->N;
   d.s = m->substeps;
-  d.stride = m->kind == PF_LORENZ96 ? m->obs_stride : 1;
+  d.stride = l96_kind(m->kind) ? m->obs_stride : 1;
   d.prec = m->prec;
   d.Ny = sh.Ny;
   d.P = int32_t(P);

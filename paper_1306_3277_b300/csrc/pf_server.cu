@@ -128,7 +128,7 @@ bool alloc_request(pf_server* s, Request* r) {
   d.kind = r->m.kind;
   d.N = r->m.N;
   d.s = r->m.substeps;
-  d.stride = r->m.kind == PF_LORENZ96 ? r->m.obs_stride : 1;
+  d.stride = l96_kind(r->m.kind) ? r->m.obs_stride : 1;
   d.prec = r->m.prec;
   d.Ny = sh.Ny;
   d.P = int32_t(r->P);

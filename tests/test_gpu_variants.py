@@ -1,8 +1,10 @@
 """GPU parity of the paper-exact model variants: sparse observations (steps
 without an observation, the first components only, as in the paper's
-Lorenz '96 example).  Ancestors and final particles bit-exact and
-log-likelihood within 1e-9 relative against the oracle, outside
-near-boundary targets; batched and sampled-path runs agree too."""
+Lorenz '96 example), the exact windkessel transition (exponential decay,
+noise on the flow) and Lorenz '96 with the Wiener increment inside RK4.
+Ancestors and final particles bit-exact and log-likelihood within 1e-9
+relative against the oracle, outside near-boundary targets; batched,
+sampled-path and server runs agree too."""
 import numpy as np
 import pytest
 
@@ -74,3 +76,72 @@ def test_sparse_batch_and_path():
     finally:
         for f in fs:
             f.destroy()
+
+
+BIG = (1.0, 1.5, 0.03, 4.0e4, 4.0, 90.0, 15.0)  # flow noise large enough to matter
+L96W_40 = (8.0, 0.25, 1.0, 0.0, 1.0)
+
+EXACT = [
+    ("exact windkessel P=1024 T=100 FP64", lambda: W.windkessel_exact(), (1, 2)),
+    ("exact windkessel sigma2=4e4 P=1000 T=60 s=3 FP64",
+     lambda: W.windkessel_exact(P=1000, T=60, substeps=3, theta=BIG), (3,)),
+    ("exact windkessel sigma2=4e4 P=1000 T=60 s=3 mixed",
+     lambda: W.windkessel_exact(P=1000, T=60, substeps=3, theta=BIG, prec=W.MIXED), (4,)),
+    ("exact windkessel ESS 0.5 P=777 T=80",
+     lambda: W.windkessel_exact(P=777, T=80, ess_threshold=0.5, theta=BIG), (5,)),
+    ("sde lorenz96 N=8 P=2^14 T=100 FP64", lambda: W.lorenz96_sde(T=100), (6,)),
+    ("sde lorenz96 N=8 P=2^14 T=100 mixed", lambda: W.lorenz96_sde(T=100, prec=W.MIXED), (7,)),
+    ("sde lorenz96 N=8 s=5 dt=0.01 P=5000 T=40 mixed",
+     lambda: W.lorenz96_sde(P=5000, T=40, substeps=5, dt=0.01, prec=W.MIXED), (8,)),
+    ("sde lorenz96 N=40 s=10 dt=0.005 P=3000 T=10 mixed",
+     lambda: W.lorenz96_sde(P=3000, T=10, N=40, substeps=10, dt=0.005, obs_stride=2,
+                            prec=W.MIXED, theta=L96W_40), (9,)),
+    ("sde lorenz96 N=40 FP64 P=2^12+5 T=6",
+     lambda: W.lorenz96_sde(P=4101, T=6, N=40, substeps=10, dt=0.005, obs_stride=2,
+                            theta=L96W_40), (10,)),
+]
+
+
+@pytest.mark.parametrize("name,factory,seeds", EXACT, ids=[c[0] for c in EXACT])
+def test_exact_variant_parity(name, factory, seeds):
+    w = factory()
+    for seed in seeds:
+        o = run_oracle(w, seed)
+        g = run_gpu(w, seed)
+        rows, _ = compare(w, g, o)
+        assert rows >= 1
+
+
+def test_exact_variants_in_batch_and_server():
+    import time
+    import paper_1306_3277_b300 as pf
+    ws = [W.windkessel_exact(P=600, T=25, theta=BIG, seed=2),
+          W.lorenz96_sde(P=800, T=20, prec=W.MIXED, seed=3), W.windkessel(P=300, T=20),
+          W.lorenz96_8(P=500, T=15, prec=W.MIXED)]
+    fs = [pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt) for w in ws]
+    try:
+        lls, sts = pf.pf_batch_run(fs, [w.theta for w in ws], [w.y for w in ws],
+                                   [w.seed for w in ws])
+        ref = []
+        for k, (w, f) in enumerate(zip(ws, fs)):
+            st, ll, _, _ = f.run(w.theta, w.y, w.seed)
+            assert sts[k] == st and lls[k] == ll
+            ref.append(ll)
+    finally:
+        for f in fs:
+            f.destroy()
+    srv = pf.pf_server_create(1 << 30, 8)
+    try:
+        ts = [srv.submit(pf.model_from_workload(w), w.P, w.T, w.dt, w.theta, w.y, w.seed)
+              for w in ws]
+        got, deadline = {}, time.time() + 60
+        while len(got) < len(ts) and time.time() < deadline:
+            for t in ts:
+                if t not in got:
+                    r = srv.poll(t)
+                    if r is not None:
+                        got[t] = r
+            time.sleep(0.001)
+        assert [got[t][1] for t in ts] == ref
+    finally:
+        srv.destroy()
