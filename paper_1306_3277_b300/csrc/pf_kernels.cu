@@ -687,115 +687,133 @@ __device__ __forceinline__ int mn_below(const FilterDev& fd, double e, double sc
   return lo;
 }
 
-// Systematic resampling of one tile.  Its particles k have cumulative weights
+// Resampling of one tile.  Its particles k have cumulative weights
 // C_k = base + scale * prefix_k; the tile owns the targets [lo, hi) between
 // its base and the next tile's base (both counts computed from the same
 // values in the two tiles), and particle k takes the targets [n_{k-1}, n_k)
-// with n_k = targets_below(C_k) clamped to [lo, hi] (the last particle takes
-// the rest).  Each particle writes its own offspring range; ranges longer
-// than SHORT_RANGE are queued and written by the whole block, so a tile that
-// owns most of the targets still writes them with coalesced stores.  Only
-// the per-particle counts use FP64.
+// with n_k = the count of targets below C_k, clamped to [lo, hi] (the last
+// particle takes the rest).  Counts: systematic ceil(C (P/S) - u); stratified
+// and multinomial as strat_below / mn_below on C (P/S).  Only the counts use
+// FP64 (one fma, one conversion per particle).
+//
+// Two barriers per block: one after the control block is read (threads 0 and
+// 32 also derive the tile's range and scaled base there), one vote for very
+// long offspring ranges.  A particle's predecessor count comes from the
+// neighbouring lane (lane 0 recomputes it from the previous prefix); ranges
+// up to SHORT_RANGE are written by the particle's thread, up to BLOCK_RANGE by
+// its warp, longer ones by the whole block, so a tile that owns most of the
+// targets still writes them with coalesced stores.
 constexpr int SHORT_RANGE = 16;
+constexpr int BLOCK_RANGE = 2048;
 
 __global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__ fds,
                                                    const int2* __restrict__ tmap) {
-  __shared__ int nk[TILE];
-  __shared__ int range[2];
-  __shared__ int nlong;
-  __shared__ int longk[TILE];
-  __shared__ double tile_e0, tile_scale_r;
+  __shared__ int s_i, s_go, s_flag, s_lo, s_hi, nlong;
+  __shared__ double s_M, s_e0, s_scale_r, s_mscale;
+  __shared__ int3 longr[TILE];
   const int2 ft = tmap[blockIdx.x];
   const FilterDev& fd = fds[ft.x];
   const Ctl* ctl = fd.ctl;
   const int P = fd.P;
   const int t = ft.y;
   const int tid = threadIdx.x;
+  const int lane = tid & 31;
   const int j0 = t * TILE;
-  const int g = t / GROUP;
-  // the tile's inputs are independent of the control block: issue them first
-  const double ct = j0 + tid < P ? fd.ctil[j0 + tid] : 0.0;
-  const double gG = fd.gp[g].G, gB = fd.gp[g].B, tbase = fd.tp[t].base, tg = fd.tp[t].g;
-  // one thread reads the control block and shares it (see k_propagate)
-  __shared__ int s_i, s_go, s_flag;
-  __shared__ double s_u, s_ratio, s_M, s_S, s_mscale;
+  const int j = j0 + tid;
   const int rs = fd.resampler;
+  // every input that does not depend on the control block is issued first
+  const double ct = j < P ? fd.ctil[j] : 0.0;
+  const double ctp = (lane == 0 && tid > 0 && j <= P) ? fd.ctil[j - 1] : 0.0;
+  double base = 0.0, scale = 0.0;
+  bool last_tile = false;
   if (tid == 0) {
+    const int g = t / GROUP;
+    const double gG = fd.gp[g].G;
+    base = fma(gG, fd.tp[t].base, fd.gp[g].B);
+    scale = gG * fd.tp[t].g;
+    nlong = 0;
+  } else if (tid == 32) {
+    if (t + 1 < fd.ntiles) {
+      const int g1 = (t + 1) / GROUP;
+      base = fma(fd.gp[g1].G, fd.tp[t + 1].base, fd.gp[g1].B);
+    } else {
+      last_tile = true;
+    }
+  }
+  // threads 0 and 32 read the control block (every thread reading it would
+  // queue on one L2 line) and turn the tile's two bases into target counts
+  if (tid == 0 || tid == 32) {
     const int i0 = ldcg(&ctl->rs_step);
-    s_i = i0;
-    s_go = ldcg(&ctl->status) == ST_OK && i0 >= 1 && i0 < fd.T && ldcg(&ctl->step) == i0 + 1;
-    s_flag = ldcg(&ctl->rs_flag);
-    s_u = rs == RS_SYSTEMATIC ? ldcg(&ctl->u) : 0.0;
-    s_ratio = ldcg(&ctl->ratio);
-    s_M = ldcg(&ctl->M);
-    s_S = ldcg(&ctl->S);
-    s_mscale = rs == RS_MULTINOMIAL ? ldcg(&fd.mn_part[fd.ntiles]) : 0.0;
+    const int go = ldcg(&ctl->status) == ST_OK && i0 >= 1 && i0 < fd.T &&
+                   ldcg(&ctl->step) == i0 + 1;
+    const int flag = ldcg(&ctl->rs_flag);
+    const double u = rs == RS_SYSTEMATIC ? ldcg(&ctl->u) : 0.0;
+    const double ratio = ldcg(&ctl->ratio);
+    const double msc = rs == RS_MULTINOMIAL ? ldcg(&fd.mn_part[fd.ntiles]) : 0.0;
+    if (last_tile) base = ldcg(&ctl->S);
+    int n0 = 0;
+    if (go && flag) {
+      if (rs == RS_SYSTEMATIC) n0 = targets_below(base, ratio, u, P);
+      else if (rs == RS_STRATIFIED) n0 = strat_below(base * ratio, fd.seed, i0, P);
+      else n0 = mn_below(fd, base * ratio, msc, 0, P);
+    }
+    if (tid == 0) {
+      s_i = i0;
+      s_go = go;
+      s_flag = flag;
+      s_M = ldcg(&ctl->M);
+      s_mscale = msc;
+      s_e0 = base * ratio - u;
+      s_scale_r = scale * ratio;
+      s_lo = n0;
+    } else {
+      s_hi = n0;
+    }
   }
   __syncthreads();
   if (!s_go) return;
   const int i = s_i;
   if (!s_flag) {
-    const int j = j0 + tid;
     if (j < P) {
       if (fd.mode != MODE_ALWAYS) fd.lam[j] = fd.ell[j] - s_M;
       if (fd.hist) fd.anc[int64_t(i) * P + j] = j;
     }
     return;
   }
-  const double u = s_u;
-  const double ratio = s_ratio;
-  // the counts of targets below a scaled cumulative weight, per scheme
-  // (systematic: e = C (P/S) - u; the others: e = C (P/S))
-  auto below = [&](double e, int a, int b) -> int {
-    if (rs == RS_STRATIFIED) return strat_below(e, fd.seed, i, P);
-    if (rs == RS_MULTINOMIAL) return mn_below(fd, e, s_mscale, a, b);
-    return __double2int_ru(e);
-  };
-  if (tid == 0) {
-    const double base = fma(gG, tbase, gB);
-    range[0] = rs == RS_SYSTEMATIC ? targets_below(base, ratio, u, P) : below(base * ratio, 0, P);
-    tile_e0 = base * ratio - u;
-    tile_scale_r = (gG * tg) * ratio;
-    nlong = 0;
-  }
-  if (tid == 32) {
-    double nb;
-    if (t + 1 < fd.ntiles) {
-      const int g1 = (t + 1) / GROUP;
-      nb = fma(fd.gp[g1].G, fd.tp[t + 1].base, fd.gp[g1].B);
-    } else {
-      nb = s_S;
-    }
-    range[1] = rs == RS_SYSTEMATIC ? targets_below(nb, ratio, u, P) : below(nb * ratio, 0, P);
-  }
-  __syncthreads();
-  const int lo = range[0];
-  const int hi = range[1];
+  const int lo = s_lo, hi = s_hi;
+  const double e0 = s_e0, scale_r = s_scale_r;
   const int nvalid = min(TILE, P - j0);
-  if (tid < nvalid) {
-    int n = rs == RS_SYSTEMATIC ? tile_targets_below(tile_scale_r, ct, tile_e0)
-                                : below(fma(tile_scale_r, ct, tile_e0), lo, hi);
-    n = min(max(n, lo), hi);
-    nk[tid] = tid == nvalid - 1 ? hi : n;
-  }
-  __syncthreads();
+  auto count = [&](double c) -> int {
+    int n;
+    if (rs == RS_SYSTEMATIC) n = tile_targets_below(scale_r, c, e0);
+    else if (rs == RS_STRATIFIED) n = strat_below(fma(scale_r, c, e0), fd.seed, i, P);
+    else n = mn_below(fd, fma(scale_r, c, e0), s_mscale, lo, hi);
+    return min(max(n, lo), hi);
+  };
+  const bool valid = tid < nvalid;
+  const int n = (valid && tid != nvalid - 1) ? count(ct) : hi;
+  int prev = __shfl_up_sync(0xffffffffu, n, 1);
+  if (lane == 0) prev = tid == 0 ? lo : (valid ? count(ctp) : hi);
+  const int len = valid ? n - prev : 0;
   int32_t* aout = fd.anc + (fd.hist ? int64_t(i) * P : 0);
-  if (tid < nvalid) {
-    const int a = tid == 0 ? lo : nk[tid - 1];
-    const int b = nk[tid];
-    if (b - a <= SHORT_RANGE) {
-      for (int jj = a; jj < b; ++jj) aout[jj] = j0 + tid;
-    } else {
-      longk[atomicAdd(&nlong, 1)] = tid;
-    }
+  if (len > 0 && len <= SHORT_RANGE)
+    for (int jj = prev; jj < n; ++jj) aout[jj] = j;
+  unsigned wl = __ballot_sync(0xffffffffu, len > SHORT_RANGE && len <= BLOCK_RANGE);
+  while (wl) {
+    const int src = __ffs(wl) - 1;
+    wl &= wl - 1;
+    const int a = __shfl_sync(0xffffffffu, prev, src);
+    const int b = __shfl_sync(0xffffffffu, n, src);
+    const int who = j0 + (tid & ~31) + src;
+    for (int jj = a + lane; jj < b; jj += 32) aout[jj] = who;
   }
-  __syncthreads();
-  const int nl = nlong;
-  for (int q = 0; q < nl; ++q) {
-    const int k = longk[q];
-    const int a = k == 0 ? lo : nk[k - 1];
-    const int b = nk[k];
-    for (int jj = a + tid; jj < b; jj += TILE) aout[jj] = j0 + k;
+  if (len > BLOCK_RANGE) longr[atomicAdd(&nlong, 1)] = make_int3(prev, n, j);
+  if (__syncthreads_or(len > BLOCK_RANGE)) {
+    const int nl = nlong;
+    for (int q = 0; q < nl; ++q) {
+      const int3 r = longr[q];
+      for (int jj = r.x + tid; jj < r.y; jj += TILE) aout[jj] = r.z;
+    }
   }
 }
 
