@@ -656,8 +656,24 @@ __device__ __forceinline__ int targets_below(double b, double ratio, double u, i
 // with scale' = scale ratio and e0 = base ratio - u prepared once per tile
 // (one FP64 fma per particle; the conversion saturates, and the caller clamps
 // the count to the tile's own target range).
+__device__ __forceinline__ int ceil_count(double e) {
+  // ceil(e) read off the bits with integer operations (B300's FP64 unit, at
+  // 1/64 of the FP32 rate, would spend several cycles on the conversion):
+  // 0 for e <= 0, the exact ceiling for 0 < e < 2^30, a large count above
+  // (callers clamp the count to the tile's range).
+  const long long b = __double_as_longlong(e);
+  if (b <= 0) return 0;  // +0, negative values (and -NaN)
+  const int ex = int(b >> 52) - 1023;
+  if (ex < 0) return 1;  // 0 < e < 1
+  if (ex >= 30) return 0x7fffffff;
+  const long long m = (b & 0x000fffffffffffffLL) | 0x0010000000000000LL;
+  const int sh = 52 - ex;
+  const long long ip = m >> sh;
+  return int(ip) + ((m & ((1LL << sh) - 1)) != 0 ? 1 : 0);
+}
+
 __device__ __forceinline__ int tile_targets_below(double scale_r, double prefix, double e0) {
-  return __double2int_ru(fma(scale_r, prefix, e0));
+  return ceil_count(fma(scale_r, prefix, e0));
 }
 
 // Stratified count: targets j + u_j (u_j from Philox block (j, i, RESAMPLE, 1))
