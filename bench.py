@@ -386,6 +386,96 @@ def run_precision(args):
     return 0
 
 
+def run_variants(args):
+    """The Large shape (P = 2^20, N = 40, mixed) with each resampling scheme and
+    the paper's stochastic Lorenz '96, plus the exact windkessel: ms per whole
+    run (CUDA graph) and the per-step propagate / resample kernel times (one
+    profiled run, events around every launch)."""
+    import torch
+    import paper_1306_3277_b300 as pf
+    torch.cuda.set_device(0)
+    T = args.T or 100
+    large = W.lorenz96_large(T=T)
+    cases = [("systematic", large), ("stratified", large.with_(resampler=1)),
+             ("multinomial", large.with_(resampler=2)),
+             ("sde_lorenz96", W.lorenz96_sde(P=1 << 20, T=T, N=40, substeps=10, dt=0.005,
+                                             obs_stride=2, prec=W.MIXED,
+                                             theta=(8.0, 0.01, 1.0, 0.0, 1.0))),
+             ("sparse_every2_first10", W.lorenz96_large(T=T).with_(obs_every=2, obs_count=10)),
+             ("exact_windkessel_P1M", W.windkessel_exact(P=1 << 20, T=T, prec=W.MIXED))]
+    out = {}
+    for name, w in cases:
+        if name == "sparse_every2_first10":
+            w.y = W.simulate(w)
+        f = pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt)
+        for k in range(3):
+            st, ll, _, _ = f.run(w.theta, w.y, 10 + k)
+        t0 = time.perf_counter()
+        reps = 3
+        for k in range(reps):
+            f.run(w.theta, w.y, 20 + k)
+        ms = (time.perf_counter() - t0) / reps * 1e3
+        pf.pf_profile_enable(f, True)
+        f.run(w.theta, w.y, 30)
+        prof = pf.pf_profile_read(f)
+        pf.pf_profile_enable(f, False)
+        f.destroy()
+        pm, pn = prof["propagate"]
+        rm, rn = prof["resample"]
+        out[name] = {"P": w.P, "T": w.T, "ms_per_run": ms,
+                     "particle_steps_per_s": w.P * w.T / (ms * 1e-3),
+                     "propagate_ms_per_step": pm / max(pn, 1),
+                     "resample_ms_per_step": rm / max(w.T - 1, 1),
+                     "status": st, "loglik": ll}
+    print(json.dumps({"metric": "ms per whole run, per-step kernel times", "results": out}),
+          flush=True)
+    return 0
+
+
+def run_samplers(args):
+    """Throughput of the samplers built on the filter: marginal Metropolis-
+    Hastings (64 chains, each iteration one batched launch of all chains'
+    filters) and SMC^2 (Algorithm 4, its O(T^2) rejuvenation runs included)."""
+    import torch
+    import paper_1306_3277_b300 as pf
+    torch.cuda.set_device(0)
+    inf = float("inf")
+    out = {}
+    w = W.windkessel(P=1024, T=100)
+    spec = [(3, 1, 2.0, 0.9, 0.03, 0.0, inf), (0, 0), (3, 1, 2.0, 0.03, 0.002, 0.0, inf),
+            (4, 2, 2.0, 0.01, 2.0, 3.0), (0, 0), (0, 0), (0, 0)]
+    nc, niter = 64, 200
+    fs = [pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt) for _ in range(nc)]
+    th0 = np.tile(np.array(w.theta), (nc, 1))
+    pf.pf_pmmh_run(fs, w.y, spec, th0, 5, 1)  # plan and graph
+    t0 = time.perf_counter()
+    _, _, acc = pf.pf_pmmh_run(fs, w.y, spec, th0, niter, 2)
+    dt = time.perf_counter() - t0
+    for f in fs:
+        f.destroy()
+    out["pmmh_windkessel_P1024_T100_64chains"] = {
+        "iterations": niter, "chains": nc, "seconds": dt,
+        "chain_iterations_per_s": nc * (niter + 1) / dt,
+        "particle_steps_per_s": nc * (niter + 1) * w.P * w.T / dt,
+        "acceptance": float(acc.sum()) / (nc * niter)}
+    w = W.windkessel(P=256, T=50)
+    spec2 = [(0, 0), (0, 0), (3, 1, 2.0, 0.03, 0.005, 0.0, inf), (4, 2, 2.0, 0.01, 2.0, 3.0),
+             (0, 0), (0, 0), (0, 0)]
+    nt = 256
+    m = pf.model_from_workload(w)
+    pf.pf_smc2_run(m, w.P, 5, w.dt, w.y[:5], 8, spec2, w.theta, 1)  # warm the code path
+    t0 = time.perf_counter()
+    st, th, logw, lz, incr, acc2 = pf.pf_smc2_run(m, w.P, w.T, w.dt, w.y, nt, spec2, w.theta, 2)
+    dt = time.perf_counter() - t0
+    steps = sum(2 * i - 1 for i in range(1, w.T + 1))  # rejuvenation runs + continuations
+    out["smc2_windkessel_P256_T50_256theta"] = {
+        "seconds": dt, "log_evidence": lz, "theta_particles": nt,
+        "particle_steps_per_s": nt * steps * w.P / dt,
+        "acceptance": float(acc2.sum()) / (nt * w.T)}
+    print(json.dumps({"metric": "sampler throughput", "results": out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__,
                                  formatter_class=argparse.RawTextHelpFormatter)
@@ -395,7 +485,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="large",
                     choices=["large", "l96_8", "l96_8_fp64", "windkessel", "serving",
-                             "precision"])
+                             "precision", "variants", "samplers"])
     ap.add_argument("--rates", default="250,500,1000,1500,2000", help="serving: offered rates")
     ap.add_argument("--duration", type=float, default=4.0, help="serving: seconds of arrivals")
     ap.add_argument("--drain", type=float, default=20.0, help="serving: extra seconds to finish")
@@ -416,6 +506,10 @@ def main():
         return run_serving(args)
     if args.config == "precision":
         return run_precision(args)
+    if args.config == "variants":
+        return run_variants(args)
+    if args.config == "samplers":
+        return run_samplers(args)
     args.warmup = max(args.warmup, 3)
 
     import torch

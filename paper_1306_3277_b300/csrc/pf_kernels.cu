@@ -722,8 +722,8 @@ __device__ __forceinline__ int mn_below(const FilterDev& fd, double e, double sc
 constexpr int SHORT_RANGE = 16;
 constexpr int BLOCK_RANGE = 2048;
 
-__global__ void __launch_bounds__(TILE) k_resample(const FilterDev* __restrict__ fds,
-                                                   const int2* __restrict__ tmap) {
+__global__ void __launch_bounds__(TILE, 8) k_resample(const FilterDev* __restrict__ fds,
+                                                      const int2* __restrict__ tmap) {
   __shared__ int s_i, s_go, s_flag, s_lo, s_hi, nlong;
   __shared__ double s_M, s_e0, s_scale_r, s_mscale;
   __shared__ int3 longr[TILE];
