@@ -573,9 +573,10 @@ static int64_t or_systematic_from_w(const double *w, int64_t P, double u, int32_
  *                (j, i, RESAMPLE, 1), words 1:0; E_k > j + u_j is evaluated
  *                as E_k - j > u_j, which is exact (E_k - j is exact whenever
  *                the comparison is not decided by sign or magnitude).
- *   multinomial: P + 1 unit exponentials e_l = -log u_l (own log; u_l in
- *                (0, 1] from block (l, i, RESAMPLE, 2), words 1:0), partial
- *                sums G_m = e_0 + .. + e_m (compensated); target_j =
+ *   multinomial: P + 1 unit exponentials e_l = -log u_l in FP32 (own logf;
+ *                u_l = ((w0 >> 8) + 1) 2^-24 in (0, 1], w0 word 0 of block
+ *                (l, i, RESAMPLE, 2)), partial sums G_m = e_0 + .. + e_m in
+ *                FP64 (compensated); target_j =
  *                G_j (P / G_P).  (G_0, .., G_{P-1}) / G_P are the order
  *                statistics of P independent uniforms, so the offspring
  *                counts are Multinomial(P, w / S).
@@ -599,7 +600,8 @@ static int64_t or_resample_other(const double *w, int64_t P, int32_t kind, uint6
     G = (double *)malloc(sizeof(double) * (size_t)P);
     for (j = 0; j <= P; ++j) {
       or_block(seed, (uint32_t)j, i, OR_PURPOSE_RESAMPLE, 2u, wd);
-      or_neumaier_add(&gs, &gc, -or_log(or_u53_open_zero(wd[0], wd[1])));
+      /* FP32 spacing: -logf of the 24-bit uniform ((w0 >> 8) + 1) 2^-24, exact in FP64 */
+      or_neumaier_add(&gs, &gc, (double)-or_logf((float)((wd[0] >> 8) + 1u) * 0x1.0p-24f));
       if (j < P) G[j] = gs + gc;
     }
     tscale = (double)P / (gs + gc);

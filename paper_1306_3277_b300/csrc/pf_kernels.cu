@@ -679,25 +679,43 @@ __device__ __forceinline__ int tile_targets_below(double scale_r, double prefix,
 // Stratified count: targets j + u_j (u_j from Philox block (j, i, RESAMPLE, 1))
 // below the scaled cumulative weight e: every j < floor(e), plus j = floor(e)
 // when e - floor(e) > u_j (exact, since e - floor(e) is exact).
+// Both parts are read off the bits with integer operations, so the test
+// frac(e) > u_j (u_j = v 2^-53, v the 53-bit integer of the uniform) is exact:
+// for e >= 1, floor(e) is the 53-bit mantissa m shifted right by 52 - ex and
+// frac(e) 2^53 the remaining bits shifted left by ex + 1; for e < 1,
+// e 2^53 = m 2^(ex+1) is compared through its integer part and whether
+// anything was shifted out.
 __device__ __forceinline__ int strat_below(double e, uint64_t seed, int i, int P) {
-  if (!(e > 0.0)) return 0;
+  const long long b = __double_as_longlong(e);
+  if (b <= 0) return 0;  // e <= 0
   if (e >= double(P)) return P;
-  const int f = int(floor(e));
+  const int ex = int(b >> 52) - 1023;
+  const unsigned long long m = (b & 0x000fffffffffffffLL) | 0x0010000000000000LL;
+  unsigned long long q;  // integer part of frac(e) 2^53
+  bool rem = false;      // frac(e) 2^53 is not an integer
+  int f = 0;
+  if (ex >= 0) {
+    const int sh = 52 - ex;
+    f = int(m >> sh);
+    q = (m & ((1ull << sh) - 1ull)) << (ex + 1);
+  } else {
+    const int k = -(ex + 1);
+    q = k < 53 ? m >> k : 0ull;
+    rem = k < 53 ? (m & ((1ull << k) - 1ull)) != 0ull : true;
+  }
   const uint4 w = rng_block(seed, uint32_t(f), uint32_t(i), PURPOSE_RESAMPLE, 1u);
-  return f + ((e - double(f)) > u53_closed_open(w.x, w.y) ? 1 : 0);
+  const unsigned long long v = ((static_cast<unsigned long long>(w.y) << 32) | w.x) >> 11;
+  return f + ((q > v || (q == v && rem)) ? 1 : 0);
 }
 
-// Multinomial target j: the sum of spacings 0..j scaled by P / (sum of all P + 1).
-__device__ __forceinline__ double mn_target(const FilterDev& fd, int j, double scale) {
-  return (ldcg(&fd.mn_part[j >> 8]) + ldcg(&fd.mn_t[j])) * scale;
-}
-
-// Multinomial count: the number of targets below e, searched in [lo, hi].
+// Multinomial count: the number of targets (mn_t, scaled and sorted) below e,
+// searched in [lo, hi].
 __device__ __forceinline__ int mn_below(const FilterDev& fd, double e, double scale, int lo,
                                         int hi) {
+  (void)scale;
   while (lo < hi) {
     const int mid = lo + (hi - lo) / 2;
-    if (mn_target(fd, mid, scale) < e) lo = mid + 1;
+    if (ldcg(&fd.mn_t[mid]) < e) lo = mid + 1;
     else hi = mid;
   }
   return lo;
@@ -848,9 +866,12 @@ __device__ __forceinline__ bool mn_active(const FilterDev& fd, int* step) {
          ldcg(&c->step) == i0 + 1 && ldcg(&c->rs_flag) != 0;
 }
 
+// Spacing l: -log u in FP32 (own logf; u = ((w0 >> 8) + 1) 2^-24 in (0, 1],
+// w0 word 0 of block (l, i, RESAMPLE, 2)), exact in FP64 for the sums.
 __device__ __forceinline__ double mn_spacing(const FilterDev& fd, int l, int i) {
   const uint4 w = rng_block(fd.seed, uint32_t(l), uint32_t(i), PURPOSE_RESAMPLE, 2u);
-  return -log_pos(u53_open_closed(w.x, w.y));
+  const float u = __fmul_rn(float((w.x >> 8) + 1u), 0x1.0p-24f);
+  return to_double(-log_posf(u));
 }
 
 __global__ void __launch_bounds__(TILE) k_mn_tiles(const FilterDev* __restrict__ fds,
@@ -895,6 +916,21 @@ __global__ void __launch_bounds__(TILE) k_mn_total(const FilterDev* __restrict__
     run += v;
   }
   if (threadIdx.x == 0) fd.mn_part[nt] = double(fd.P) / (tot + mn_spacing(fd, fd.P, s_i));
+}
+
+// Scaled targets in place: mn_t[l] = (tile offset + in-tile sum) P / total.
+__global__ void __launch_bounds__(TILE) k_mn_targets(const FilterDev* __restrict__ fds,
+                                                     const int2* __restrict__ tmap) {
+  __shared__ int s_go, s_i;
+  const int2 ft = tmap[blockIdx.x];
+  const FilterDev& fd = fds[ft.x];
+  if (fd.resampler != RS_MULTINOMIAL) return;
+  if (threadIdx.x == 0) s_go = mn_active(fd, &s_i);
+  __syncthreads();
+  if (!s_go) return;
+  const int l = ft.y * TILE + threadIdx.x;
+  if (l < fd.P)
+    fd.mn_t[l] = (ldcg(&fd.mn_part[ft.y]) + fd.mn_t[l]) * ldcg(&fd.mn_part[fd.ntiles]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1092,6 +1128,7 @@ cudaError_t launch_mn_scan(const FilterDev* fds, const int2* tmap, int ntiles, i
   if (ntiles <= 0) return cudaSuccess;
   k_mn_tiles<<<ntiles, TILE, 0, st>>>(fds, tmap);
   k_mn_total<<<nf, TILE, 0, st>>>(fds, nf);
+  k_mn_targets<<<ntiles, TILE, 0, st>>>(fds, tmap);
   return cudaGetLastError();
 }
 

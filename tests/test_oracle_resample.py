@@ -119,6 +119,13 @@ def _uniform(seed, j, i, blk, open_zero=False):
     return Fraction(v + (1 if open_zero else 0), 1 << 53)
 
 
+def _uniform24(seed, j, i, blk):
+    """((w0 >> 8) + 1) 2^-24 of Philox block (j, i, RESAMPLE << 16 | blk, 0)."""
+    w = O.philox4x32_10([j, i, (O.PURPOSE_RESAMPLE << 16) | blk, 0],
+                        [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF])
+    return ((int(w[0]) >> 8) + 1) / float(1 << 24)
+
+
 def test_stratified_matches_exact_rational():
     rng = np.random.default_rng(7)
     for trial in range(150):
@@ -146,14 +153,14 @@ def test_multinomial_matches_order_statistics_of_exponential_spacings():
         ell = rng.normal(0, 2, P)
         seed, i = int(rng.integers(1, 2 ** 40)), int(rng.integers(1, 50))
         anc, near = O.resample(ell, O.RESAMPLE_MULTINOMIAL, seed, i)
-        e = [-math.log(float(_uniform(seed, l, i, 2, open_zero=True))) for l in range(P + 1)]
+        e = [-math.log(_uniform24(seed, l, i, 2)) for l in range(P + 1)]
         G = [math.fsum(e[:j + 1]) for j in range(P + 1)]
         M = ell.max()
         w = [math.exp(x - M) for x in ell]
         C = [math.fsum(w[:k + 1]) for k in range(P)]
         targets = [G[j] / G[P] * C[-1] for j in range(P)]
         gap = min(abs(t - c) for t in targets for c in C) / C[-1]
-        if near or gap < 1e-9:
+        if near or gap < 1e-5:  # the oracle's spacings use its FP32 logf (<= 2 ulp)
             continue
         ref = [next((k for k in range(P) if C[k] > t), P - 1) for t in targets]
         assert anc.tolist() == ref
