@@ -61,6 +61,36 @@ def test_parity_large_config_full_particle_count():
     compare(w, g, o)
 
 
+def test_parity_maximum_particle_count():
+    """P = 2^24, the largest filter the library takes.  At this size about
+    2e-12 P^2 targets per step fall within the near-boundary window, so the
+    comparison is per target: the likelihood up to the first resampling step
+    within 1e-9, at most the oracle's near count of ancestor differences in
+    the first resampling (each one particle off), sorted valid ancestors, and
+    bit-exact states wherever the ancestors agree."""
+    import paper_1306_3277_b300 as pf
+    w = W.windkessel(P=1 << 24, T=2)
+    o = run_oracle(w, 7)
+    near1 = int(o["diag"][0, 7])
+    f = pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt)
+    try:
+        st, ll1, _ = f.run_range(w.theta, w.y[:1], 7, 0, 1)
+        assert st == pf.PF_OK and abs(ll1 - o["diag"][0, 6]) <= 1e-9 * abs(o["diag"][0, 6])
+        st, ll, x, anc = f.run(w.theta, w.y, 7, want_particles=True, want_ancestors=True)
+    finally:
+        f.destroy()
+    assert st == pf.PF_OK
+    assert np.array_equal(anc[0], np.arange(w.P))
+    d = np.nonzero(anc[1] != o["anc"][1])[0]
+    assert len(d) <= near1, (len(d), near1)
+    assert np.all(np.abs(anc[1][d].astype(np.int64) - o["anc"][1][d]) <= 1)
+    assert np.all(np.diff(anc[1]) >= 0) and anc[1].min() >= 0 and anc[1].max() < w.P
+    same = anc[1] == o["anc"][1]
+    assert np.array_equal(x[0][same], o["x"][0][same])
+    with pytest.raises(pf.PFError):
+        pf.pf_create(pf.model_from_workload(w), (1 << 24) + 1, 2, w.dt)
+
+
 @pytest.mark.parametrize("P,T", [(1, 1), (1, 5), (2, 3), (255, 2), (256, 2), (257, 2)])
 def test_edge_sizes(P, T):
     w = W.windkessel(P=P, T=T)
