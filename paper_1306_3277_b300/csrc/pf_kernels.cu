@@ -710,9 +710,7 @@ __device__ __forceinline__ int strat_below(double e, uint64_t seed, int i, int P
 
 // Multinomial count: the number of targets (mn_t, scaled and sorted) below e,
 // searched in [lo, hi].
-__device__ __forceinline__ int mn_below(const FilterDev& fd, double e, double scale, int lo,
-                                        int hi) {
-  (void)scale;
+__device__ __forceinline__ int mn_below(const FilterDev& fd, double e, int lo, int hi) {
   while (lo < hi) {
     const int mid = lo + (hi - lo) / 2;
     if (ldcg(&fd.mn_t[mid]) < e) lo = mid + 1;
@@ -728,7 +726,7 @@ __device__ __forceinline__ int mn_below(const FilterDev& fd, double e, double sc
 // with n_k = the count of targets below C_k, clamped to [lo, hi] (the last
 // particle takes the rest).  Counts: systematic ceil(C (P/S) - u); stratified
 // and multinomial as strat_below / mn_below on C (P/S).  Only the counts use
-// FP64 (one fma, one conversion per particle).
+// FP64 (one fma per particle; ceilings and floors are taken on the bits).
 //
 // Two barriers per block: one after the control block is read (threads 0 and
 // 32 also derive the tile's range and scaled base there), one vote for very
@@ -743,7 +741,7 @@ constexpr int BLOCK_RANGE = 2048;
 __global__ void __launch_bounds__(TILE, 8) k_resample(const FilterDev* __restrict__ fds,
                                                       const int2* __restrict__ tmap) {
   __shared__ int s_i, s_go, s_flag, s_lo, s_hi, nlong;
-  __shared__ double s_M, s_e0, s_scale_r, s_mscale;
+  __shared__ double s_M, s_e0, s_scale_r;
   __shared__ int3 longr[TILE];
   const int2 ft = tmap[blockIdx.x];
   const FilterDev& fd = fds[ft.x];
@@ -783,20 +781,18 @@ __global__ void __launch_bounds__(TILE, 8) k_resample(const FilterDev* __restric
     const int flag = ldcg(&ctl->rs_flag);
     const double u = rs == RS_SYSTEMATIC ? ldcg(&ctl->u) : 0.0;
     const double ratio = ldcg(&ctl->ratio);
-    const double msc = rs == RS_MULTINOMIAL ? ldcg(&fd.mn_part[fd.ntiles]) : 0.0;
     if (last_tile) base = ldcg(&ctl->S);
     int n0 = 0;
     if (go && flag) {
       if (rs == RS_SYSTEMATIC) n0 = targets_below(base, ratio, u, P);
       else if (rs == RS_STRATIFIED) n0 = strat_below(base * ratio, fd.seed, i0, P);
-      else n0 = mn_below(fd, base * ratio, msc, 0, P);
+      else n0 = mn_below(fd, base * ratio, 0, P);
     }
     if (tid == 0) {
       s_i = i0;
       s_go = go;
       s_flag = flag;
       s_M = ldcg(&ctl->M);
-      s_mscale = msc;
       s_e0 = base * ratio - u;
       s_scale_r = scale * ratio;
       s_lo = n0;
@@ -821,7 +817,7 @@ __global__ void __launch_bounds__(TILE, 8) k_resample(const FilterDev* __restric
     int n;
     if (rs == RS_SYSTEMATIC) n = tile_targets_below(scale_r, c, e0);
     else if (rs == RS_STRATIFIED) n = strat_below(fma(scale_r, c, e0), fd.seed, i, P);
-    else n = mn_below(fd, fma(scale_r, c, e0), s_mscale, lo, hi);
+    else n = mn_below(fd, fma(scale_r, c, e0), lo, hi);
     return min(max(n, lo), hi);
   };
   const bool valid = tid < nvalid;
