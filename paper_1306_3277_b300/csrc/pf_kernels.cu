@@ -16,6 +16,7 @@
 // Any number of filters share a launch: the tile map lists (filter, tile)
 // pairs, and every reduction is per tile / group / filter in a fixed order,
 // so a filter's result does not depend on what else is in the launch.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -737,112 +738,124 @@ __device__ __forceinline__ int mn_below(const FilterDev& fd, double e, int lo, i
 // targets still writes them with coalesced stores.
 constexpr int SHORT_RANGE = 16;
 constexpr int BLOCK_RANGE = 2048;
+constexpr int RESAMPLE_BLOCKS_PER_SM = 8;
 
-__global__ void __launch_bounds__(TILE, 8) k_resample(const FilterDev* __restrict__ fds,
-                                                      const int2* __restrict__ tmap) {
-  __shared__ int s_i, s_go, s_flag, s_lo, s_hi, nlong;
+// Grid-stride over the tiles of the tile map: a block takes tiles q, q + G,
+// ... (G = the grid size, a multiple of the SM count), so the control block
+// is read once per block and filter rather than once per tile.
+__global__ void __launch_bounds__(TILE, RESAMPLE_BLOCKS_PER_SM)
+    k_resample(const FilterDev* __restrict__ fds, const int2* __restrict__ tmap, int ntiles) {
+  __shared__ int s_i, s_go, s_flag, s_lo, s_hi;
+  __shared__ int nlong[2];
   __shared__ double s_M, s_e0, s_scale_r;
-  __shared__ int3 longr[TILE];
-  const int2 ft = tmap[blockIdx.x];
-  const FilterDev& fd = fds[ft.x];
-  const Ctl* ctl = fd.ctl;
-  const int P = fd.P;
-  const int t = ft.y;
+  __shared__ int3 longr[2][TILE];
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  const int j0 = t * TILE;
-  const int j = j0 + tid;
-  const int rs = fd.resampler;
-  // every input that does not depend on the control block is issued first
-  const double ct = j < P ? fd.ctil[j] : 0.0;
-  const double ctp = (lane == 0 && tid > 0 && j <= P) ? fd.ctil[j - 1] : 0.0;
-  double base = 0.0, scale = 0.0;
-  bool last_tile = false;
-  if (tid == 0) {
-    const int g = t / GROUP;
-    const double gG = fd.gp[g].G;
-    base = fma(gG, fd.tp[t].base, fd.gp[g].B);
-    scale = gG * fd.tp[t].g;
-    nlong = 0;
-  } else if (tid == 32) {
-    if (t + 1 < fd.ntiles) {
-      const int g1 = (t + 1) / GROUP;
-      base = fma(fd.gp[g1].G, fd.tp[t + 1].base, fd.gp[g1].B);
-    } else {
-      last_tile = true;
+  // threads 0 and 32 keep the control block of the last filter they saw
+  int c_filter = -1, c_i = 0, c_go = 0, c_flag = 0;
+  double c_u = 0.0, c_ratio = 0.0, c_S = 0.0, c_M = 0.0;
+  for (int q = blockIdx.x, it = 0; q < ntiles; q += gridDim.x, ++it) {
+    const int buf = it & 1;
+    const int2 ft = tmap[q];
+    const FilterDev& fd = fds[ft.x];
+    const int P = fd.P;
+    const int t = ft.y;
+    const int j0 = t * TILE;
+    const int j = j0 + tid;
+    const int rs = fd.resampler;
+    // every input that does not depend on the control block is issued first
+    const double ct = j < P ? fd.ctil[j] : 0.0;
+    const double ctp = (lane == 0 && tid > 0 && j <= P) ? fd.ctil[j - 1] : 0.0;
+    if (tid == 0) nlong[buf] = 0;  // last used two tiles ago, behind two barriers
+    if (tid == 0 || tid == 32) {
+      double base = 0.0, scale = 0.0;
+      bool last_tile = false;
+      if (tid == 0) {
+        const int g = t / GROUP;
+        const double gG = fd.gp[g].G;
+        base = fma(gG, fd.tp[t].base, fd.gp[g].B);
+        scale = gG * fd.tp[t].g;
+      } else if (t + 1 < fd.ntiles) {
+        const int g1 = (t + 1) / GROUP;
+        base = fma(fd.gp[g1].G, fd.tp[t + 1].base, fd.gp[g1].B);
+      } else {
+        last_tile = true;
+      }
+      if (ft.x != c_filter) {
+        const Ctl* ctl = fd.ctl;
+        c_filter = ft.x;
+        c_i = ldcg(&ctl->rs_step);
+        c_go = ldcg(&ctl->status) == ST_OK && c_i >= 1 && c_i < fd.T &&
+               ldcg(&ctl->step) == c_i + 1;
+        c_flag = ldcg(&ctl->rs_flag);
+        c_u = rs == RS_SYSTEMATIC ? ldcg(&ctl->u) : 0.0;
+        c_ratio = ldcg(&ctl->ratio);
+        c_S = ldcg(&ctl->S);
+        c_M = ldcg(&ctl->M);
+      }
+      if (last_tile) base = c_S;
+      int n0 = 0;
+      if (c_go && c_flag) {
+        if (rs == RS_SYSTEMATIC) n0 = targets_below(base, c_ratio, c_u, P);
+        else if (rs == RS_STRATIFIED) n0 = strat_below(base * c_ratio, fd.seed, c_i, P);
+        else n0 = mn_below(fd, base * c_ratio, 0, P);
+      }
+      if (tid == 0) {
+        s_i = c_i;
+        s_go = c_go;
+        s_flag = c_flag;
+        s_M = c_M;
+        s_e0 = base * c_ratio - c_u;
+        s_scale_r = scale * c_ratio;
+        s_lo = n0;
+      } else {
+        s_hi = n0;
+      }
     }
-  }
-  // threads 0 and 32 read the control block (every thread reading it would
-  // queue on one L2 line) and turn the tile's two bases into target counts
-  if (tid == 0 || tid == 32) {
-    const int i0 = ldcg(&ctl->rs_step);
-    const int go = ldcg(&ctl->status) == ST_OK && i0 >= 1 && i0 < fd.T &&
-                   ldcg(&ctl->step) == i0 + 1;
-    const int flag = ldcg(&ctl->rs_flag);
-    const double u = rs == RS_SYSTEMATIC ? ldcg(&ctl->u) : 0.0;
-    const double ratio = ldcg(&ctl->ratio);
-    if (last_tile) base = ldcg(&ctl->S);
-    int n0 = 0;
-    if (go && flag) {
-      if (rs == RS_SYSTEMATIC) n0 = targets_below(base, ratio, u, P);
-      else if (rs == RS_STRATIFIED) n0 = strat_below(base * ratio, fd.seed, i0, P);
-      else n0 = mn_below(fd, base * ratio, 0, P);
+    __syncthreads();
+    const int go = s_go, flag = s_flag, i = s_i;
+    if (!go || !flag) {
+      if (go && j < P) {  // no resampling at this step: carry the weights
+        if (fd.mode != MODE_ALWAYS) fd.lam[j] = fd.ell[j] - s_M;
+        if (fd.hist) fd.anc[int64_t(i) * P + j] = j;
+      }
+      __syncthreads();  // the shared values are rewritten for the next tile
+      continue;
     }
-    if (tid == 0) {
-      s_i = i0;
-      s_go = go;
-      s_flag = flag;
-      s_M = ldcg(&ctl->M);
-      s_e0 = base * ratio - u;
-      s_scale_r = scale * ratio;
-      s_lo = n0;
-    } else {
-      s_hi = n0;
+    const int lo = s_lo, hi = s_hi;
+    const double e0 = s_e0, scale_r = s_scale_r;
+    const int nvalid = min(TILE, P - j0);
+    auto count = [&](double c) -> int {
+      int n;
+      if (rs == RS_SYSTEMATIC) n = tile_targets_below(scale_r, c, e0);
+      else if (rs == RS_STRATIFIED) n = strat_below(fma(scale_r, c, e0), fd.seed, i, P);
+      else n = mn_below(fd, fma(scale_r, c, e0), lo, hi);
+      return min(max(n, lo), hi);
+    };
+    const bool valid = tid < nvalid;
+    const int n = (valid && tid != nvalid - 1) ? count(ct) : hi;
+    int prev = __shfl_up_sync(0xffffffffu, n, 1);
+    if (lane == 0) prev = tid == 0 ? lo : (valid ? count(ctp) : hi);
+    const int len = valid ? n - prev : 0;
+    int32_t* aout = fd.anc + (fd.hist ? int64_t(i) * P : 0);
+    if (len > 0 && len <= SHORT_RANGE)
+      for (int jj = prev; jj < n; ++jj) aout[jj] = j;
+    unsigned wl = __ballot_sync(0xffffffffu, len > SHORT_RANGE && len <= BLOCK_RANGE);
+    while (wl) {
+      const int src = __ffs(wl) - 1;
+      wl &= wl - 1;
+      const int a = __shfl_sync(0xffffffffu, prev, src);
+      const int b = __shfl_sync(0xffffffffu, n, src);
+      const int who = j0 + (tid & ~31) + src;
+      for (int jj = a + lane; jj < b; jj += 32) aout[jj] = who;
     }
-  }
-  __syncthreads();
-  if (!s_go) return;
-  const int i = s_i;
-  if (!s_flag) {
-    if (j < P) {
-      if (fd.mode != MODE_ALWAYS) fd.lam[j] = fd.ell[j] - s_M;
-      if (fd.hist) fd.anc[int64_t(i) * P + j] = j;
-    }
-    return;
-  }
-  const int lo = s_lo, hi = s_hi;
-  const double e0 = s_e0, scale_r = s_scale_r;
-  const int nvalid = min(TILE, P - j0);
-  auto count = [&](double c) -> int {
-    int n;
-    if (rs == RS_SYSTEMATIC) n = tile_targets_below(scale_r, c, e0);
-    else if (rs == RS_STRATIFIED) n = strat_below(fma(scale_r, c, e0), fd.seed, i, P);
-    else n = mn_below(fd, fma(scale_r, c, e0), lo, hi);
-    return min(max(n, lo), hi);
-  };
-  const bool valid = tid < nvalid;
-  const int n = (valid && tid != nvalid - 1) ? count(ct) : hi;
-  int prev = __shfl_up_sync(0xffffffffu, n, 1);
-  if (lane == 0) prev = tid == 0 ? lo : (valid ? count(ctp) : hi);
-  const int len = valid ? n - prev : 0;
-  int32_t* aout = fd.anc + (fd.hist ? int64_t(i) * P : 0);
-  if (len > 0 && len <= SHORT_RANGE)
-    for (int jj = prev; jj < n; ++jj) aout[jj] = j;
-  unsigned wl = __ballot_sync(0xffffffffu, len > SHORT_RANGE && len <= BLOCK_RANGE);
-  while (wl) {
-    const int src = __ffs(wl) - 1;
-    wl &= wl - 1;
-    const int a = __shfl_sync(0xffffffffu, prev, src);
-    const int b = __shfl_sync(0xffffffffu, n, src);
-    const int who = j0 + (tid & ~31) + src;
-    for (int jj = a + lane; jj < b; jj += 32) aout[jj] = who;
-  }
-  if (len > BLOCK_RANGE) longr[atomicAdd(&nlong, 1)] = make_int3(prev, n, j);
-  if (__syncthreads_or(len > BLOCK_RANGE)) {
-    const int nl = nlong;
-    for (int q = 0; q < nl; ++q) {
-      const int3 r = longr[q];
-      for (int jj = r.x + tid; jj < r.y; jj += TILE) aout[jj] = r.z;
+    if (len > BLOCK_RANGE) longr[buf][atomicAdd(&nlong[buf], 1)] = make_int3(prev, n, j);
+    if (__syncthreads_or(len > BLOCK_RANGE)) {
+      const int nl = nlong[buf];
+      for (int r = 0; r < nl; ++r) {
+        const int3 rg = longr[buf][r];
+        for (int jj = rg.x + tid; jj < rg.y; jj += TILE) aout[jj] = rg.z;
+      }
     }
   }
 }
@@ -1101,7 +1114,15 @@ cudaError_t launch_propagate(int kind, int N, int prec, const FilterDev* fds, co
 cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks,
                             cudaStream_t st) {
   if (nblocks <= 0) return cudaSuccess;
-  k_resample<<<nblocks, TILE, 0, st>>>(fds, tmap);
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 148;
+  }
+  const int grid = std::min(nblocks, sms * RESAMPLE_BLOCKS_PER_SM);
+  k_resample<<<grid, TILE, 0, st>>>(fds, tmap, nblocks);
   return cudaGetLastError();
 }
 
