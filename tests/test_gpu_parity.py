@@ -61,6 +61,44 @@ def test_parity_large_config_full_particle_count():
     compare(w, g, o)
 
 
+def test_large_config_full_size_properties():
+    """The whole Large run (P = 2^20, T = 500) in the launch configuration the
+    benchmark times, checked by properties that hold at any size: the CUDA-graph
+    run, the profiled run (one launch at a time) and a run split into intervals
+    give the same bits; every ancestor row is sorted and in range; the
+    log-likelihood is finite and its first step agrees with the oracle."""
+    import torch
+    import paper_1306_3277_b300 as pf
+    w = W.lorenz96_large()
+    f = pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt)
+    dev = torch.device("cuda", 0)
+    th = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+    y = torch.tensor(w.y, dtype=torch.float64, device=dev)
+    ll = torch.zeros(1, dtype=torch.float64, device=dev)
+    x = torch.zeros((w.N, w.P), dtype=torch.float32, device=dev)
+    anc = torch.zeros((w.T, w.P), dtype=torch.int32, device=dev)
+    try:
+        pf.pf_run(f, th, y, 77, ll, x, anc)
+        ll_graph, x_graph = float(ll.item()), x.clone()
+        pf.pf_profile_enable(f, True)
+        pf.pf_run(f, th, y, 77, ll, x, None)
+        pf.pf_profile_enable(f, False)
+        assert float(ll.item()) == ll_graph and torch.equal(x, x_graph)
+        for r, s_ in ((0, 1), (1, 250), (250, 500)):
+            st, l_r, _ = f.run_range(w.theta if r == 0 else None, w.y[r:s_], 77, r, s_)
+            if r == 0:
+                ll_step1 = l_r
+        assert l_r == ll_graph
+    finally:
+        f.destroy()
+    assert np.isfinite(ll_graph)
+    assert bool((anc[1:, 1:] >= anc[1:, :-1]).all()) and int(anc.min()) >= 0
+    assert int(anc.max()) < w.P
+    assert torch.equal(anc[0], torch.arange(w.P, dtype=torch.int32, device=dev))
+    o1 = run_oracle(w.with_(T=1, y=w.y[:1].copy()), 77)
+    assert abs(ll_step1 - o1["loglik"]) <= 1e-9 * abs(o1["loglik"])
+
+
 def test_parity_maximum_particle_count():
     """P = 2^24, the largest filter the library takes.  At this size about
     2e-12 P^2 targets per step fall within the near-boundary window, so the
