@@ -38,11 +38,30 @@ PROFILES = os.path.join(ROOT, "profiles")
 DESCRIPTOR_BYTES = 256  # per-filter descriptor the library uploads with every run
 
 
-def kernel_source_hash():
+def _code_only(text):
+    """Source text without // comments, trailing blanks and empty lines, so the
+    hash below changes with the code of the kernels and not with their comments."""
+    out = []
+    for line in text.splitlines():
+        k = line.find("//")
+        if k >= 0:
+            line = line[:k]
+        line = line.rstrip()
+        if line:
+            out.append(line)
+    return "\n".join(out)
+
+
+def kernel_source_hash(read=None):
+    """Hash of the code of pf_kernels.cu and pf_dev.cuh (comments ignored)."""
     h = hashlib.sha256()
     for fn in ("pf_kernels.cu", "pf_dev.cuh"):
-        with open(os.path.join(ROOT, "paper_1306_3277_b300", "csrc", fn), "rb") as f:
-            h.update(f.read())
+        if read is None:
+            with open(os.path.join(ROOT, "paper_1306_3277_b300", "csrc", fn)) as f:
+                text = f.read()
+        else:
+            text = read(fn)
+        h.update(_code_only(text).encode())
     return h.hexdigest()[:16]
 
 

@@ -1,7 +1,8 @@
 // pf_dev.cuh -- device-side building blocks of the B300 bootstrap particle
 // filter (arXiv 1306.3277, Algorithm 2): descriptors, Philox4x32-10,
-// project-written log / sincos(2 pi u) for Box-Muller, and the canonical
-// block reductions and scans that fix the summation order of every run.
+// project-written log / sincos(2 pi u) for Box-Muller and exp for the exact
+// windkessel, and the canonical block reductions and scans that fix the
+// summation order of every run.
 //
 // The whole library is compiled with -fmad=false: a fused multiply-add
 // happens only where the code calls fma()/fmaf(); every other operation is

@@ -2,17 +2,21 @@
 // (arXiv 1306.3277, Algorithm 2) and their host-side launchers.
 //
 // One step i of one filter is two launches over its tiles of TILE particles:
-//   k_propagate  gather x(t_{i-1}) at the ancestors, propagate to t_i
-//                (windkessel Euler substeps or Lorenz '96 RK4 substeps plus
-//                noise), weight with y(t_i) in FP64, then per tile the max,
-//                the inclusive prefix of exp(ell - M_tile) and its total.  The
-//                last tile of each group of GROUP tiles combines the group;
-//                the last group combines the filter: max, scaled sums,
-//                likelihood increment, ESS test, resampling uniform.
+//   k_propagate  gather x(t_{i-1}) at the ancestors, propagate to t_i (the
+//                windkessel's Euler or exact transition, Lorenz '96 RK4
+//                substeps with additive or in-step Wiener noise), weight with
+//                y(t_i) in FP64 (skipped at a step without an observation),
+//                then per tile the max, the inclusive prefix of
+//                exp(ell - M_tile) and its total.  The last tile of each
+//                group of GROUP tiles combines the group; the last group
+//                combines the filter: max, scaled sums, likelihood increment,
+//                ESS test, resampling uniform.
 //   k_resample   per tile: cumulative weights C_k = base + scale * prefix,
-//                each particle's count of systematic targets below C_k, and
-//                each particle's offspring range written out (long ranges
-//                by the whole block).
+//                each particle's count of targets below C_k (systematic,
+//                stratified or multinomial), and each particle's offspring
+//                range written out by its thread, its warp or its block.
+// The multinomial scheme adds three small kernels between the two (its
+// sorted targets); the path sample adds a pick, a trace and a copy kernel.
 // Any number of filters share a launch: the tile map lists (filter, tile)
 // pairs, and every reduction is per tile / group / filter in a fixed order,
 // so a filter's result does not depend on what else is in the launch.
