@@ -186,9 +186,9 @@ def cpu_oracle_rate(w, P_sample, T_sample, nthreads=0):
 
 
 def oracle_sample(w):
-    """Sample sizes for the oracle: about 10-30 s of CPU work."""
+    """Sample sizes for the oracle: about 10 s of CPU work on 16 cores."""
     if w.kind == W.LORENZ96 and w.N >= 40:
-        return min(w.P, 1 << 18), min(w.T, 2)
+        return min(w.P, 1 << 18), min(w.T, 40)
     if w.kind == W.LORENZ96:
         return min(w.P, 1 << 14), min(w.T, 100)
     return min(w.P, 1 << 14), min(w.T, 100)
@@ -650,6 +650,7 @@ def main():
         cpu = None
         if not args.no_cpu_baseline:
             P_s, T_s = oracle_sample(w)
+            cpu_oracle_rate(w, max(P_s // 16, 1), 1)  # warm-up: library, threads, pages
             rate, secs = cpu_oracle_rate(w, P_s, T_s)
             cpu = {"value": rate, "unit": "particle-steps/s", "cores": cores(), "kind": "oracle",
                    "sample": "P=%d T=%d of the same workload, OpenMP over particles, %.1f s wall"
