@@ -421,6 +421,7 @@ def run_variants(args):
                                              obs_stride=2, prec=W.MIXED,
                                              theta=(8.0, 0.01, 1.0, 0.0, 1.0))),
              ("sparse_every2_first10", W.lorenz96_large(T=T).with_(obs_every=2, obs_count=10)),
+             ("one_rk4_substep", large.with_(substeps=1)),
              ("exact_windkessel_P1M", W.windkessel_exact(P=1 << 20, T=T, prec=W.MIXED))]
     out = {}
     for name, w in cases:
@@ -446,6 +447,15 @@ def run_variants(args):
                      "propagate_ms_per_step": pm / max(pn, 1),
                      "resample_ms_per_step": rm / max(w.T - 1, 1),
                      "status": st, "loglik": ll}
+        if name == "one_rk4_substep":
+            # the step's algorithmic bytes (gather, write, weights, ancestors) over
+            # its propagate + resample time, against the measured copy bandwidth
+            step_bytes = (propagate_bytes_per_particle(w) + RESAMPLE_BYTES_PER_PARTICLE) * w.P
+            step_s = (pm / max(pn, 1) + rm / max(w.T - 1, 1)) * 1e-3
+            hbm = measured_peaks()[0]["hbm_gbs"]
+            out[name]["step_bytes"] = step_bytes
+            out[name]["step_hbm_gbs"] = step_bytes / step_s / 1e9
+            out[name]["step_hbm_frac"] = step_bytes / step_s / 1e9 / hbm
     print(json.dumps({"metric": "ms per whole run, per-step kernel times", "results": out}),
           flush=True)
     return 0
