@@ -350,8 +350,9 @@ pf_status pf_profile_enable(pf_filter* f, int32_t on);
 pf_status pf_profile_read(pf_filter* f, double* ms, int64_t* launches);
 
 /* Measured dense fused-multiply-add throughput of the current GPU, in flop/s
- * (2 per FMA): prec PF_FP64 or PF_MIXED (FP32).  Runs a few ~40 ms kernels;
- * *ms receives the duration of the best one. */
+ * (2 per FMA): prec PF_FP64, PF_MIXED (FP32) or 2 (FP32 pairs through the
+ * packed f32x2 instruction, 4 flop per instruction).  Runs a few ~40 ms
+ * kernels; *ms receives the duration of the best one. */
 pf_status pf_measure_fma_peak(int32_t prec, double* flops_per_s, double* ms);
 
 #ifdef __cplusplus
