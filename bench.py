@@ -296,10 +296,21 @@ def secondary(pf, torch, dev):
     tp = time.perf_counter() - t0
     maxrel = max(abs(a - b) / abs(b) for a, b in zip(lls_b, lls_p))
     psteps = sum(w.P * w.T for w in ws)
+    # the autotuned split: small filters run whole, one block each
+    chosen = pf.pf_batch_autotune(fs, ths, ys, seeds)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        lls_a, _ = pf.pf_batch_run(fs, ths, ys, seeds)
+    ta = (time.perf_counter() - t0) / reps
+    maxrel_a = max(abs(a - b) / abs(b) for a, b in zip(lls_a, lls_p))
     out["batched_256"] = {"filters": len(ws), "batched_evals_per_s": len(ws) / tb,
                           "plain_evals_per_s": len(ws) / tp, "speedup": tp / tb,
                           "batched_particle_steps_per_s": psteps / tb,
-                          "max_rel_loglik_diff_vs_plain": maxrel}
+                          "max_rel_loglik_diff_vs_plain": maxrel,
+                          "autotuned_one_block_max_particles": chosen,
+                          "autotuned_evals_per_s": len(ws) / ta,
+                          "autotuned_speedup_vs_plain": tp / ta,
+                          "autotuned_max_rel_loglik_diff_vs_plain": maxrel_a}
     for f in fs:
         f.destroy()
     return out

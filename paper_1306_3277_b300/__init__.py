@@ -77,6 +77,12 @@ def lib():
                                   ctypes.c_double, _vp, ctypes.c_int32, ctypes.POINTER(pf_param),
                                   _vp, ctypes.c_uint64, _vp, _vp, _vp, _vp, _vp, _vp]
         L.pf_smc2_run.restype = ctypes.c_int
+        L.pf_batch_configure.argtypes = [ctypes.c_int32, ctypes.POINTER(_vp), ctypes.c_int64]
+        L.pf_batch_configure.restype = ctypes.c_int
+        L.pf_batch_autotune.argtypes = [ctypes.c_int32, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                        ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_uint64),
+                                        ctypes.POINTER(ctypes.c_int64)]
+        L.pf_batch_autotune.restype = ctypes.c_int
         L.pf_run_range.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32,
                                    _vp, _vp, _vp]
         L.pf_sample_path.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp, _vp]
@@ -345,6 +351,30 @@ def pf_measure_fma_peak(prec):
     ms = ctypes.c_double()
     _check(lib().pf_measure_fma_peak(prec, ctypes.byref(f), ctypes.byref(ms)))
     return f.value
+
+
+def pf_batch_configure(filters, cta_max_particles):
+    """Send the filters of this list with at most cta_max_particles particles
+    to the one-block path (0: none); results do not change."""
+    nf = len(filters)
+    hs = (_vp * nf)(*[f.h for f in filters])
+    _check(lib().pf_batch_configure(nf, hs, int(cta_max_particles)))
+
+
+def pf_batch_autotune(filters, thetas, ys, seeds):
+    """Time the candidate splits on these inputs, keep the fastest, return it."""
+    nf = len(filters)
+    hs = (_vp * nf)(*[f.h for f in filters])
+    th = [np.ascontiguousarray(t, dtype=np.float64) if not hasattr(t, "data_ptr") else t
+          for t in thetas]
+    yy = [np.ascontiguousarray(v, dtype=np.float64) if not hasattr(v, "data_ptr") else v
+          for v in ys]
+    tp = (_vp * nf)(*[_ptr(t) for t in th])
+    yp = (_vp * nf)(*[_ptr(v) for v in yy])
+    sd = (ctypes.c_uint64 * nf)(*[int(x) for x in seeds])
+    chosen = ctypes.c_int64()
+    _check(lib().pf_batch_autotune(nf, hs, tp, yp, sd, ctypes.byref(chosen)))
+    return chosen.value
 
 
 def pf_batch_run(filters, thetas, ys, seeds, stream=None):

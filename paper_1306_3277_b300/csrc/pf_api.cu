@@ -2,6 +2,7 @@
 // creation, launch plans (descriptor tables, tile maps and one captured CUDA
 // graph per plan), single and batched runs.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -214,12 +215,15 @@ extern "C" pf_status pf_create(const pf_model* m, int64_t P, int32_t T, double d
 // ---------------------------------------------------------------------------
 static std::mutex g_plan_mu;
 static std::map<std::vector<pf_filter*>, Plan*> g_plans;  // cached batch plans
+// per filter list: the largest particle count sent to the one-block path
+static std::map<std::vector<pf_filter*>, int64_t> g_cta_choice;
 
 static void destroy_plan(Plan* p) {
   if (!p) return;
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->st) cudaStreamSynchronize(p->st);
-  void* dptrs[] = {p->d_fds, p->d_tmap, p->d_ycat, p->d_res};
+  if (p->st2) cudaStreamSynchronize(p->st2);
+  void* dptrs[] = {p->d_fds, p->d_tmap, p->d_ycat, p->d_res, p->d_cta};
   for (void* q : dptrs)
     if (q) cudaFree(q);
   void* hptrs[] = {p->h_fds, p->h_ycat, p->h_res};
@@ -227,6 +231,9 @@ static void destroy_plan(Plan* p) {
     if (q) cudaFreeHost(q);
   if (p->ev_staged) cudaEventDestroy(p->ev_staged);
   if (p->ev_done) cudaEventDestroy(p->ev_done);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->st2) cudaStreamDestroy(p->st2);
   if (p->st) cudaStreamDestroy(p->st);
   delete p;
 }
@@ -242,7 +249,7 @@ static cudaError_t no_hook(int) { return cudaSuccess; }
 
 template <typename Hook>
 static cudaError_t enqueue_steps(Plan* p, int first, int last, cudaStream_t st, Profiler* prof,
-                                 Hook&& hook, bool init) {
+                                 Hook&& hook, bool init, bool results = true) {
   cudaError_t le = cudaSuccess;
   auto timed = [&](int kind, auto&& launch) {
     if (prof) prof->begin(kind, st);
@@ -278,25 +285,60 @@ static cudaError_t enqueue_steps(Plan* p, int first, int last, cudaStream_t st, 
       le = timed(PROF_RESAMPLE,
                  [&] { return launch_resample(p->d_fds, p->d_tmap, p->cnt_all[i + 1], st); });
   }
-  if (le == cudaSuccess)
+  if (le == cudaSuccess && results)
     le = timed(PROF_RESULTS, [&] { return launch_results(p->d_fds, p->nf, p->d_res, st); });
   return le;
 }
 
-// The launch sequence of one whole run of a plan.
+// The launch sequence of one whole run of a plan.  The one-block filters run
+// on a side branch (their own stream, forked and joined with events, so a
+// captured graph holds two parallel branches) next to the tiled steps of the
+// others; with a profiler everything runs on st, one launch after the other.
 static cudaError_t enqueue_run(Plan* p, cudaStream_t st, Profiler* prof) {
-  return enqueue_steps(p, 1, p->maxT, st, prof, no_hook, true);
+  if (p->cta_total == 0) return enqueue_steps(p, 1, p->maxT, st, prof, no_hook, true);
+  cudaStream_t side = prof ? st : p->st2;
+  cudaError_t le = cudaSuccess;
+  if (!prof) {
+    le = cudaEventRecord(p->ev_fork, st);
+    if (le == cudaSuccess) le = cudaStreamWaitEvent(side, p->ev_fork, 0);
+  }
+  for (size_t c = 0; c < p->cta_classes.size() && le == cudaSuccess; ++c) {
+    const PlanClass& pc = p->cta_classes[c];
+    if (prof) prof->begin(PROF_PROPAGATE, st);
+    le = launch_filter_cta(pc.kind, pc.N, pc.prec, p->d_fds, p->d_cta + pc.offset, pc.ntiles,
+                           side);
+    if (prof) prof->end(st);
+  }
+  if (le == cudaSuccess && !prof) le = cudaEventRecord(p->ev_join, side);
+  if (le == cudaSuccess) le = enqueue_steps(p, 1, p->maxT, st, prof, no_hook, true, false);
+  if (le == cudaSuccess && !prof) le = cudaStreamWaitEvent(st, p->ev_join, 0);
+  if (le == cudaSuccess) {
+    if (prof) prof->begin(PROF_RESULTS, st);
+    le = launch_results(p->d_fds, p->nf, p->d_res, st);
+    if (prof) prof->end(st);
+  }
+  return le;
 }
 
 cudaError_t pfb::enqueue_plan_steps(Plan* p, int first, int last, bool init, cudaStream_t st) {
+  if (p->cta_total > 0) return cudaErrorNotSupported;  // one-block filters run whole runs only
   return enqueue_steps(p, first, last, st, nullptr, no_hook, init);
 }
 
 // Tile maps sorted by T descending so that the filters still running at step
 // i own a prefix of every map.
-pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out) {
+// A filter runs on the one-block path when the plan allows it for its
+// particle count, its tiles fit one group and its resampling is not
+// multinomial (the spacing scan is a separate set of launches).
+static bool cta_eligible(const pf_filter* f, int64_t cta_max_p) {
+  return cta_max_p > 0 && f->P <= cta_max_p && f->sh.ntiles <= GROUP &&
+         f->m.resampler != PF_RESAMPLE_MULTINOMIAL;
+}
+
+pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out, int64_t cta_max_p) {
   Plan* p = new Plan();
   p->filters = fl;
+  p->cta_max_p = cta_max_p;
   const int nf = int(fl.size());
   std::vector<int> order(nf);
   for (int k = 0; k < nf; ++k) order[k] = k;
@@ -314,8 +356,26 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out) {
     p->yoff[k] = ytot;
     ytot += size_t(fl[k]->T) * size_t(fl[k]->sh.Ny);
   }
+  // the one-block filters, per class, the most expensive first (a block
+  // takes a filter as the hardware hands out blocks in order)
+  std::map<std::tuple<int, int, int>, std::vector<int>> cta_lists;
+  for (int k = 0; k < nf; ++k)
+    if (cta_eligible(fl[k], cta_max_p))
+      cta_lists[std::make_tuple(fl[k]->m.kind, fl[k]->m.N, fl[k]->m.prec)].push_back(k);
+  std::vector<int> cta_all;
+  for (auto& kv : cta_lists) {
+    std::vector<int>& v = kv.second;
+    std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
+      return double(fl[a]->P) * fl[a]->T > double(fl[b]->P) * fl[b]->T;
+    });
+    p->cta_classes.push_back({std::get<0>(kv.first), std::get<1>(kv.first),
+                              std::get<2>(kv.first), int(cta_all.size()), int(v.size())});
+    cta_all.insert(cta_all.end(), v.begin(), v.end());
+  }
+  p->cta_total = int(cta_all.size());
   for (int k : order) {
     pf_filter* f = fl[k];
+    if (cta_eligible(f, cta_max_p)) continue;
     auto key = std::make_tuple(f->m.kind, f->m.N, f->m.prec);
     auto it = cls_index.find(key);
     int c;
@@ -365,12 +425,21 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_fds, sizeof(FilterDev) * nf);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_fds, sizeof(FilterDev) * nf);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_tmap, sizeof(int2) * tm.size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_tmap, sizeof(int2) * std::max<size_t>(tm.size(), 1));
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_ycat, sizeof(double) * std::max<size_t>(ytot, 1));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_ycat, sizeof(double) * std::max<size_t>(ytot, 1));
   if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_res, sizeof(double) * 3 * nf);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_res, sizeof(double) * 3 * nf);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && p->cta_total > 0) {
+    e = cudaStreamCreateWithFlags(&p->st2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->d_cta, sizeof(int) * cta_all.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->d_cta, cta_all.data(), sizeof(int) * cta_all.size(),
+                          cudaMemcpyHostToDevice, p->st);
+  }
+  if (e == cudaSuccess && !tm.empty())
     e = cudaMemcpyAsync(p->d_tmap, tm.data(), sizeof(int2) * tm.size(), cudaMemcpyHostToDevice,
                         p->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
@@ -493,7 +562,7 @@ extern "C" pf_status pf_run(pf_filter* f, const double* theta, const double* y, 
   }
   if (!f->plan) {
     std::vector<pf_filter*> one{f};
-    pf_status ps = build_plan(one, &f->plan);
+    pf_status ps = build_plan(one, &f->plan, 0);
     if (ps != PF_OK) return ps;
   }
   Plan* p = f->plan;
@@ -539,7 +608,7 @@ static pf_status ensure_history(pf_filter* f) {
 static pf_status ensure_plan(pf_filter* f) {
   if (f->plan) return PF_OK;
   std::vector<pf_filter*> one{f};
-  return build_plan(one, &f->plan);
+  return build_plan(one, &f->plan, 0);
 }
 
 extern "C" pf_status pf_run_range(pf_filter* f, const double* theta, const double* y,
@@ -667,6 +736,12 @@ extern "C" pf_status pf_destroy(pf_filter* f) {
         ++it;
       }
     }
+    for (auto it = g_cta_choice.begin(); it != g_cta_choice.end();) {
+      if (std::find(it->first.begin(), it->first.end(), f) != it->first.end())
+        it = g_cta_choice.erase(it);
+      else
+        ++it;
+    }
   }
   destroy_plan(f->plan);
   free_filter_buffers(f);
@@ -681,6 +756,7 @@ extern "C" pf_status pf_destroy(pf_filter* f) {
 // The cached launch plan of a filter list (built on first use; at most eight
 // are kept, the oldest evicted).  The filters must be distinct.
 pf_status pfb::batch_plan(const std::vector<pf_filter*>& key, Plan** out) {
+  int64_t cta_max_p = 0;
   {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto it = g_plans.find(key);
@@ -688,9 +764,11 @@ pf_status pfb::batch_plan(const std::vector<pf_filter*>& key, Plan** out) {
       *out = it->second;
       return PF_OK;
     }
+    auto c = g_cta_choice.find(key);
+    if (c != g_cta_choice.end()) cta_max_p = c->second;
   }
   Plan* p = nullptr;
-  pf_status ps = build_plan(key, &p);
+  pf_status ps = build_plan(key, &p, cta_max_p);
   if (ps != PF_OK) return ps;
   std::lock_guard<std::mutex> lk(g_plan_mu);
   if (g_plans.size() >= 8) {
@@ -729,6 +807,63 @@ extern "C" pf_status pf_batch_run(int32_t nfilt, pf_filter* const* f, const doub
     per_filter_status[k] = int(p->h_res[3 * k + 1]) == ST_OK ? PF_OK : PF_EDEGENERATE;
   }
   return PF_OK;
+}
+
+static pf_status batch_key(int32_t nfilt, pf_filter* const* f, std::vector<pf_filter*>* key) {
+  if (nfilt < 1 || !f) return fail(PF_EINVAL, "empty filter list");
+  key->assign(f, f + nfilt);
+  for (int k = 0; k < nfilt; ++k)
+    if (!(*key)[k]) return fail(PF_EINVAL, "filter %d is NULL", k);
+  std::vector<pf_filter*> sorted(*key);
+  std::sort(sorted.begin(), sorted.end());
+  if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+    return fail(PF_EINVAL, "a filter appears twice in the batch");
+  return PF_OK;
+}
+
+extern "C" pf_status pf_batch_configure(int32_t nfilt, pf_filter* const* f,
+                                        int64_t cta_max_particles) {
+  std::vector<pf_filter*> key;
+  pf_status ps = batch_key(nfilt, f, &key);
+  if (ps != PF_OK) return ps;
+  if (cta_max_particles < 0) return fail(PF_EINVAL, "cta_max_particles must be >= 0");
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  g_cta_choice[key] = cta_max_particles;
+  auto it = g_plans.find(key);
+  if (it != g_plans.end() && it->second->cta_max_p != cta_max_particles) {
+    destroy_plan(it->second);  // rebuilt with the new split on its next use
+    g_plans.erase(it);
+  }
+  return PF_OK;
+}
+
+extern "C" pf_status pf_batch_autotune(int32_t nfilt, pf_filter* const* f,
+                                       const double* const* theta, const double* const* y,
+                                       const uint64_t* seeds, int64_t* chosen) {
+  static const int64_t candidates[] = {0, 256, 1024, 4096, 16384, 65536};
+  std::vector<double> ll(nfilt > 0 ? nfilt : 1);
+  std::vector<int32_t> st(nfilt > 0 ? nfilt : 1);
+  double best_ms = 0.0;
+  int64_t best = 0;
+  for (int64_t c : candidates) {
+    pf_status ps = pf_batch_configure(nfilt, f, c);
+    if (ps != PF_OK) return ps;
+    double ms = 0.0;
+    for (int rep = 0; rep < 3; ++rep) {  // plan and graph, then two timed runs
+      const auto t0 = std::chrono::steady_clock::now();
+      ps = pf_batch_run(nfilt, f, theta, y, seeds, ll.data(), st.data(), nullptr);
+      if (ps != PF_OK) return ps;
+      const auto t1 = std::chrono::steady_clock::now();
+      if (rep > 0) ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
+    }
+    if (c == candidates[0] || ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  pf_status ps = pf_batch_configure(nfilt, f, best);
+  if (ps == PF_OK && chosen) *chosen = best;
+  return ps;
 }
 
 // ---------------------------------------------------------------------------

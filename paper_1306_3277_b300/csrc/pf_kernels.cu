@@ -507,12 +507,10 @@ __device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs) {
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
+// Initial draw of tile t of a filter (Algorithm 2, initialise lines): x_n^j(t_0)
+// = m0 + s0 z_n; tile 0 also resets the control block.
 template <int KIND, int N, typename R>
-__global__ void __launch_bounds__(TILE) k_init(const FilterDev* __restrict__ fds,
-                                               const int2* __restrict__ tmap) {
-  const int2 ft = tmap[blockIdx.x];
-  const FilterDev& fd = fds[ft.x];
-  const int t = ft.y;
+__device__ __forceinline__ void init_tile(const FilterDev& fd, int t) {
   const int j = t * TILE + threadIdx.x;
   const int P = fd.P;
   const double m0 = wk_kind(KIND) ? fd.theta[5] : fd.theta[3];
@@ -549,6 +547,13 @@ __global__ void __launch_bounds__(TILE) k_init(const FilterDev* __restrict__ fds
   }
 }
 
+template <int KIND, int N, typename R>
+__global__ void __launch_bounds__(TILE) k_init(const FilterDev* __restrict__ fds,
+                                               const int2* __restrict__ tmap) {
+  const int2 ft = tmap[blockIdx.x];
+  init_tile<KIND, N, R>(fds[ft.x], ft.y);
+}
+
 // Blocks per SM the propagate kernel is compiled for: two wherever the state
 // fits in 128 registers per thread without spilling more than a few words
 // (every FP32 size, FP64 up to N = 12, the windkessel), else one.
@@ -557,39 +562,19 @@ struct PropagateOccupancy {
   static constexpr int value = (wk_kind(KIND) || sizeof(R) == 4 || N <= 12) ? 2 : 1;
 };
 
+// Step i of tile t (Algorithm 2, propagate and weight lines): gather the
+// ancestors' states, propagate, store, weight with y(t_i) in FP64 (skipped at a
+// step without an observation), then the tile partials: max, inclusive prefix
+// of exp(ell - M_t) (ctil) and its total; thread 0 writes them to tp[t].
+// a_spec is the ancestor row's entry when there is no history (loaded early).
 template <int KIND, int N, typename R>
-__global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value)) k_propagate(const FilterDev* __restrict__ fds,
-                                                    const int2* __restrict__ tmap) {
-  __shared__ CombineScratch cs;
-  __shared__ double ys[64];
-  const int2 ft = tmap[blockIdx.x];
-  const FilterDev& fd = fds[ft.x];
-  Ctl* ctl = fd.ctl;
+__device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i, int anc_identity,
+                                               int lam_zero, double cw, int a_spec, double* ys,
+                                               CombineScratch& cs) {
   const int P = fd.P;
-  const int t = ft.y;
   const int tid = threadIdx.x;
   const int j = t * TILE + tid;
   const bool valid = j < P;
-  // issued before the control block is read (without a history the ancestor
-  // row does not depend on the step), so the two loads overlap
-  const int a_spec = (valid && !fd.hist) ? fd.anc[j] : j;
-  // one thread reads the control block (written by the previous launch) and
-  // shares it: every thread reading it would queue on one L2 line
-  __shared__ int s_step, s_ok, s_anc_identity, s_lam_zero;
-  __shared__ double s_cw;
-  if (tid == 0) {
-    s_step = ldcg(&ctl->step);
-    s_ok = ldcg(&ctl->status) == ST_OK;
-    s_anc_identity = ldcg(&ctl->anc_identity);
-    s_lam_zero = ldcg(&ctl->lam_zero);
-    s_cw = ldcg(&ctl->cw);
-  }
-  __syncthreads();
-  const int i = s_step;
-  if (i > fd.T || !s_ok) return;
-  const int anc_identity = s_anc_identity;
-  const int lam_zero = s_lam_zero;
-  const double cw = s_cw;
   if (tid < fd.Ny) ys[tid] = fd.y[int64_t(i - 1) * fd.Ny + tid];  // read after the barrier below
 
   R x[N];
@@ -634,6 +619,41 @@ __global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value))
     tp.M = Mt;
     tp.S = St;
     tp.Q = Qt;
+  }
+}
+
+template <int KIND, int N, typename R>
+__global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value)) k_propagate(const FilterDev* __restrict__ fds,
+                                                    const int2* __restrict__ tmap) {
+  __shared__ CombineScratch cs;
+  __shared__ double ys[64];
+  const int2 ft = tmap[blockIdx.x];
+  const FilterDev& fd = fds[ft.x];
+  Ctl* ctl = fd.ctl;
+  const int P = fd.P;
+  const int t = ft.y;
+  const int tid = threadIdx.x;
+  const int j = t * TILE + tid;
+  const bool valid = j < P;
+  // issued before the control block is read (without a history the ancestor
+  // row does not depend on the step), so the two loads overlap
+  const int a_spec = (valid && !fd.hist) ? fd.anc[j] : j;
+  // one thread reads the control block (written by the previous launch) and
+  // shares it: every thread reading it would queue on one L2 line
+  __shared__ int s_step, s_ok, s_anc_identity, s_lam_zero;
+  __shared__ double s_cw;
+  if (tid == 0) {
+    s_step = ldcg(&ctl->step);
+    s_ok = ldcg(&ctl->status) == ST_OK;
+    s_anc_identity = ldcg(&ctl->anc_identity);
+    s_lam_zero = ldcg(&ctl->lam_zero);
+    s_cw = ldcg(&ctl->cw);
+  }
+  __syncthreads();
+  const int i = s_step;
+  if (i > fd.T || !s_ok) return;
+  propagate_tile<KIND, N, R>(fd, t, i, s_anc_identity, s_lam_zero, s_cw, a_spec, ys, cs);
+  if (tid == 0) {
     __threadfence();
     const int g = t / GROUP;
     const int ntg = min(GROUP, fd.ntiles - g * GROUP);
@@ -744,6 +764,90 @@ constexpr int SHORT_RANGE = 16;
 constexpr int BLOCK_RANGE = 2048;
 constexpr int RESAMPLE_BLOCKS_PER_SM = 8;
 
+// Tile t's cumulative weights are C_k = base + scale * prefix_k: which = 0
+// gives this tile's base and scale, which = 1 the next tile's base (S after the
+// last tile), from the group and tile partials of the filter combine.
+__device__ __forceinline__ void tile_base(const FilterDev& fd, int t, int which, double S,
+                                          double* base, double* scale) {
+  if (which == 0) {
+    const int g = t / GROUP;
+    const double gG = fd.gp[g].G;
+    *base = fma(gG, fd.tp[t].base, fd.gp[g].B);
+    *scale = gG * fd.tp[t].g;
+  } else if (t + 1 < fd.ntiles) {
+    const int g1 = (t + 1) / GROUP;
+    *base = fma(fd.gp[g1].G, fd.tp[t + 1].base, fd.gp[g1].B);
+  } else {
+    *base = S;
+  }
+}
+
+// The count of targets below a tile end, per scheme.
+__device__ __forceinline__ int range_count(const FilterDev& fd, int rs, double base, double ratio,
+                                           double u, int i) {
+  if (rs == RS_SYSTEMATIC) return targets_below(base, ratio, u, fd.P);
+  if (rs == RS_STRATIFIED) return strat_below(base * ratio, fd.seed, i, fd.P);
+  return mn_below(fd, base * ratio, 0, fd.P);
+}
+
+// The particles of tile t take their targets [n_{k-1}, n_k): counts from the
+// scaled cumulative weights (ct = this particle's in-tile prefix, ctp = the
+// previous particle's, read by lane 0 only), written by the particle's thread,
+// its warp or the block.  Every thread of the block calls it (one barrier).
+__device__ __forceinline__ void resample_particles(const FilterDev& fd, int t, int i, int rs,
+                                                   int lo, int hi, double e0, double scale_r,
+                                                   double ct, double ctp, int* nlong,
+                                                   int3* longr) {
+  const int P = fd.P;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int j0 = t * TILE;
+  const int j = j0 + tid;
+  const int nvalid = min(TILE, P - j0);
+  auto count = [&](double c) -> int {
+    int n;
+    if (rs == RS_SYSTEMATIC) n = tile_targets_below(scale_r, c, e0);
+    else if (rs == RS_STRATIFIED) n = strat_below(fma(scale_r, c, e0), fd.seed, i, P);
+    else n = mn_below(fd, fma(scale_r, c, e0), lo, hi);
+    return min(max(n, lo), hi);
+  };
+  const bool valid = tid < nvalid;
+  const int n = (valid && tid != nvalid - 1) ? count(ct) : hi;
+  int prev = __shfl_up_sync(0xffffffffu, n, 1);
+  if (lane == 0) prev = tid == 0 ? lo : (valid ? count(ctp) : hi);
+  const int len = valid ? n - prev : 0;
+  int32_t* aout = fd.anc + (fd.hist ? int64_t(i) * P : 0);
+  if (len > 0 && len <= SHORT_RANGE)
+    for (int jj = prev; jj < n; ++jj) aout[jj] = j;
+  unsigned wl = __ballot_sync(0xffffffffu, len > SHORT_RANGE && len <= BLOCK_RANGE);
+  while (wl) {
+    const int src = __ffs(wl) - 1;
+    wl &= wl - 1;
+    const int a = __shfl_sync(0xffffffffu, prev, src);
+    const int b = __shfl_sync(0xffffffffu, n, src);
+    const int who = j0 + (tid & ~31) + src;
+    for (int jj = a + lane; jj < b; jj += 32) aout[jj] = who;
+  }
+  if (len > BLOCK_RANGE) longr[atomicAdd(nlong, 1)] = make_int3(prev, n, j);
+  if (__syncthreads_or(len > BLOCK_RANGE)) {
+    const int nl = *nlong;
+    for (int r = 0; r < nl; ++r) {
+      const int3 rg = longr[r];
+      for (int jj = rg.x + tid; jj < rg.y; jj += TILE) aout[jj] = rg.z;
+    }
+  }
+}
+
+// No resampling after step i: carry the log-weights (lam = ell - M) and, with
+// a history, write the identity ancestor row.
+__device__ __forceinline__ void carry_tile(const FilterDev& fd, int t, int i, double M) {
+  const int j = t * TILE + threadIdx.x;
+  if (j < fd.P) {
+    if (fd.mode != MODE_ALWAYS) fd.lam[j] = fd.ell[j] - M;
+    if (fd.hist) fd.anc[int64_t(i) * fd.P + j] = j;
+  }
+}
+
 // Grid-stride over the tiles of the tile map: a block takes tiles q, q + G,
 // ... (G = the grid size, a multiple of the SM count), so the control block
 // is read once per block and filter rather than once per tile.
@@ -764,27 +868,13 @@ __global__ void __launch_bounds__(TILE, RESAMPLE_BLOCKS_PER_SM)
     const FilterDev& fd = fds[ft.x];
     const int P = fd.P;
     const int t = ft.y;
-    const int j0 = t * TILE;
-    const int j = j0 + tid;
+    const int j = t * TILE + tid;
     const int rs = fd.resampler;
     // every input that does not depend on the control block is issued first
     const double ct = j < P ? fd.ctil[j] : 0.0;
     const double ctp = (lane == 0 && tid > 0 && j <= P) ? fd.ctil[j - 1] : 0.0;
     if (tid == 0) nlong[buf] = 0;  // last used two tiles ago, behind two barriers
     if (tid == 0 || tid == 32) {
-      double base = 0.0, scale = 0.0;
-      bool last_tile = false;
-      if (tid == 0) {
-        const int g = t / GROUP;
-        const double gG = fd.gp[g].G;
-        base = fma(gG, fd.tp[t].base, fd.gp[g].B);
-        scale = gG * fd.tp[t].g;
-      } else if (t + 1 < fd.ntiles) {
-        const int g1 = (t + 1) / GROUP;
-        base = fma(fd.gp[g1].G, fd.tp[t + 1].base, fd.gp[g1].B);
-      } else {
-        last_tile = true;
-      }
       if (ft.x != c_filter) {
         const Ctl* ctl = fd.ctl;
         c_filter = ft.x;
@@ -797,13 +887,9 @@ __global__ void __launch_bounds__(TILE, RESAMPLE_BLOCKS_PER_SM)
         c_S = ldcg(&ctl->S);
         c_M = ldcg(&ctl->M);
       }
-      if (last_tile) base = c_S;
-      int n0 = 0;
-      if (c_go && c_flag) {
-        if (rs == RS_SYSTEMATIC) n0 = targets_below(base, c_ratio, c_u, P);
-        else if (rs == RS_STRATIFIED) n0 = strat_below(base * c_ratio, fd.seed, c_i, P);
-        else n0 = mn_below(fd, base * c_ratio, 0, P);
-      }
+      double base = 0.0, scale = 0.0;
+      tile_base(fd, t, tid == 0 ? 0 : 1, c_S, &base, &scale);
+      const int n0 = (c_go && c_flag) ? range_count(fd, rs, base, c_ratio, c_u, c_i) : 0;
       if (tid == 0) {
         s_i = c_i;
         s_go = c_go;
@@ -817,50 +903,98 @@ __global__ void __launch_bounds__(TILE, RESAMPLE_BLOCKS_PER_SM)
       }
     }
     __syncthreads();
-    const int go = s_go, flag = s_flag, i = s_i;
-    if (!go || !flag) {
-      if (go && j < P) {  // no resampling at this step: carry the weights
-        if (fd.mode != MODE_ALWAYS) fd.lam[j] = fd.ell[j] - s_M;
-        if (fd.hist) fd.anc[int64_t(i) * P + j] = j;
-      }
+    if (!s_go || !s_flag) {
+      if (s_go) carry_tile(fd, t, s_i, s_M);
       __syncthreads();  // the shared values are rewritten for the next tile
       continue;
     }
-    const int lo = s_lo, hi = s_hi;
-    const double e0 = s_e0, scale_r = s_scale_r;
-    const int nvalid = min(TILE, P - j0);
-    auto count = [&](double c) -> int {
-      int n;
-      if (rs == RS_SYSTEMATIC) n = tile_targets_below(scale_r, c, e0);
-      else if (rs == RS_STRATIFIED) n = strat_below(fma(scale_r, c, e0), fd.seed, i, P);
-      else n = mn_below(fd, fma(scale_r, c, e0), lo, hi);
-      return min(max(n, lo), hi);
-    };
-    const bool valid = tid < nvalid;
-    const int n = (valid && tid != nvalid - 1) ? count(ct) : hi;
-    int prev = __shfl_up_sync(0xffffffffu, n, 1);
-    if (lane == 0) prev = tid == 0 ? lo : (valid ? count(ctp) : hi);
-    const int len = valid ? n - prev : 0;
-    int32_t* aout = fd.anc + (fd.hist ? int64_t(i) * P : 0);
-    if (len > 0 && len <= SHORT_RANGE)
-      for (int jj = prev; jj < n; ++jj) aout[jj] = j;
-    unsigned wl = __ballot_sync(0xffffffffu, len > SHORT_RANGE && len <= BLOCK_RANGE);
-    while (wl) {
-      const int src = __ffs(wl) - 1;
-      wl &= wl - 1;
-      const int a = __shfl_sync(0xffffffffu, prev, src);
-      const int b = __shfl_sync(0xffffffffu, n, src);
-      const int who = j0 + (tid & ~31) + src;
-      for (int jj = a + lane; jj < b; jj += 32) aout[jj] = who;
+    resample_particles(fd, t, s_i, rs, s_lo, s_hi, s_e0, s_scale_r, ct, ctp, &nlong[buf],
+                       longr[buf]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One filter per block: the batched form's persistent path for small filters
+// ---------------------------------------------------------------------------
+// Block b runs filter list[b] from its initial draw through all its steps:
+// per step its tiles are propagated one after the other (propagate_tile), its
+// single group and the filter are combined (combine_group, combine_filter),
+// and its tiles are resampled (resample_particles) or carried (carry_tile).
+// These are the tiled kernels' own functions in the tiled kernels' order, so
+// every result is bit-identical to the tiled path's; what disappears is the
+// two launches and two grid-wide hand-offs per step.  The plan sends here the
+// filters with at most GROUP tiles whose resampling is not multinomial.
+template <int KIND, int N, typename R>
+__global__ void __launch_bounds__(TILE) k_filter_cta(const FilterDev* __restrict__ fds,
+                                                     const int* __restrict__ list) {
+  __shared__ CombineScratch cs;
+  __shared__ double ys[64];
+  __shared__ int s_step, s_ok, s_anc_identity, s_lam_zero, s_go, s_flag, s_lo, s_hi, nlong;
+  __shared__ double s_cw, s_M, s_u, s_ratio, s_S, s_e0, s_scale_r;
+  __shared__ int3 longr[TILE];
+  const FilterDev& fd = fds[list[blockIdx.x]];
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int P = fd.P, nt = fd.ntiles, T = fd.T, rs = fd.resampler;
+  for (int t = 0; t < nt; ++t) init_tile<KIND, N, R>(fd, t);
+  __syncthreads();
+  for (int i = 1; i <= T; ++i) {
+    if (tid == 0) {
+      const Ctl* ctl = fd.ctl;
+      s_step = ldcg(&ctl->step);
+      s_ok = ldcg(&ctl->status) == ST_OK;
+      s_anc_identity = ldcg(&ctl->anc_identity);
+      s_lam_zero = ldcg(&ctl->lam_zero);
+      s_cw = ldcg(&ctl->cw);
     }
-    if (len > BLOCK_RANGE) longr[buf][atomicAdd(&nlong[buf], 1)] = make_int3(prev, n, j);
-    if (__syncthreads_or(len > BLOCK_RANGE)) {
-      const int nl = nlong[buf];
-      for (int r = 0; r < nl; ++r) {
-        const int3 rg = longr[buf][r];
-        for (int jj = rg.x + tid; jj < rg.y; jj += TILE) aout[jj] = rg.z;
+    __syncthreads();
+    if (!s_ok || s_step != i) break;  // a degenerate step ended the run
+    for (int t = 0; t < nt; ++t) {
+      const int j = t * TILE + tid;
+      const int a_spec = (j < P && !fd.hist) ? fd.anc[j] : j;
+      propagate_tile<KIND, N, R>(fd, t, i, s_anc_identity, s_lam_zero, s_cw, a_spec, ys, cs);
+      __syncthreads();  // the scratch is reused by the next tile
+    }
+    if (combine_group(fd, 0, cs)) combine_filter(fd, i, cs);
+    __syncthreads();
+    if (tid == 0) {
+      const Ctl* ctl = fd.ctl;
+      const int i0 = ldcg(&ctl->rs_step);
+      s_go = ldcg(&ctl->status) == ST_OK && i0 == i && i < T && ldcg(&ctl->step) == i + 1;
+      s_flag = ldcg(&ctl->rs_flag);
+      s_M = ldcg(&ctl->M);
+      s_u = rs == RS_SYSTEMATIC ? ldcg(&ctl->u) : 0.0;
+      s_ratio = ldcg(&ctl->ratio);
+      s_S = ldcg(&ctl->S);
+    }
+    __syncthreads();
+    if (!s_go) continue;  // the last step, or a degenerate one
+    for (int t = 0; t < nt; ++t) {
+      if (!s_flag) {
+        carry_tile(fd, t, i, s_M);
+        continue;
       }
+      const int j = t * TILE + tid;
+      const double ct = j < P ? fd.ctil[j] : 0.0;
+      const double ctp = (lane == 0 && tid > 0 && j <= P) ? fd.ctil[j - 1] : 0.0;
+      if (tid == 0) nlong = 0;  // the previous tile's readers passed the barrier below
+      if (tid == 0 || tid == 32) {
+        double base = 0.0, scale = 0.0;
+        tile_base(fd, t, tid == 0 ? 0 : 1, s_S, &base, &scale);
+        const int n0 = range_count(fd, rs, base, s_ratio, s_u, i);
+        if (tid == 0) {
+          s_e0 = base * s_ratio - s_u;
+          s_scale_r = scale * s_ratio;
+          s_lo = n0;
+        } else {
+          s_hi = n0;
+        }
+      }
+      __syncthreads();
+      resample_particles(fd, t, i, rs, s_lo, s_hi, s_e0, s_scale_r, ct, ctp, &nlong, longr);
+      __syncthreads();  // the shared values are rewritten for the next tile
     }
+    __syncthreads();
   }
 }
 
@@ -1066,16 +1200,19 @@ bool supported(int kind, int N, int prec) {
   return false;
 }
 
+enum { LAUNCH_INIT = 0, LAUNCH_PROPAGATE = 1, LAUNCH_CTA = 2 };
+
 template <int KIND, int N, typename R>
-static cudaError_t launch_pair(bool init, const FilterDev* fds, const int2* tmap, int nblocks,
+static cudaError_t launch_pair(int what, const FilterDev* fds, const int2* tmap, int nblocks,
                                cudaStream_t st) {
   if (nblocks <= 0) return cudaSuccess;
-  if (init) k_init<KIND, N, R><<<nblocks, TILE, 0, st>>>(fds, tmap);
-  else k_propagate<KIND, N, R><<<nblocks, TILE, 0, st>>>(fds, tmap);
+  if (what == LAUNCH_INIT) k_init<KIND, N, R><<<nblocks, TILE, 0, st>>>(fds, tmap);
+  else if (what == LAUNCH_PROPAGATE) k_propagate<KIND, N, R><<<nblocks, TILE, 0, st>>>(fds, tmap);
+  else k_filter_cta<KIND, N, R><<<nblocks, TILE, 0, st>>>(fds, reinterpret_cast<const int*>(tmap));
   return cudaGetLastError();
 }
 
-static cudaError_t dispatch(bool init, int kind, int N, int prec, const FilterDev* fds,
+static cudaError_t dispatch(int init, int kind, int N, int prec, const FilterDev* fds,
                             const int2* tmap, int nblocks, cudaStream_t st) {
   const bool dp = prec == PREC_FP64;
   if (kind == KIND_WK) {
@@ -1107,12 +1244,18 @@ static cudaError_t dispatch(bool init, int kind, int N, int prec, const FilterDe
 
 cudaError_t launch_init(int kind, int N, int prec, const FilterDev* fds, const int2* tmap,
                         int nblocks, cudaStream_t st) {
-  return dispatch(true, kind, N, prec, fds, tmap, nblocks, st);
+  return dispatch(LAUNCH_INIT, kind, N, prec, fds, tmap, nblocks, st);
 }
 
 cudaError_t launch_propagate(int kind, int N, int prec, const FilterDev* fds, const int2* tmap,
                              int nblocks, cudaStream_t st) {
-  return dispatch(false, kind, N, prec, fds, tmap, nblocks, st);
+  return dispatch(LAUNCH_PROPAGATE, kind, N, prec, fds, tmap, nblocks, st);
+}
+
+cudaError_t launch_filter_cta(int kind, int N, int prec, const FilterDev* fds, const int* list,
+                              int nfilters, cudaStream_t st) {
+  return dispatch(LAUNCH_CTA, kind, N, prec, fds, reinterpret_cast<const int2*>(list), nfilters,
+                  st);
 }
 
 cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks,

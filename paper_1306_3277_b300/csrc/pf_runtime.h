@@ -130,11 +130,19 @@ struct Plan {
   cudaStream_t st = nullptr;
   cudaEvent_t ev_staged = nullptr, ev_done = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // one-block path: filters with at most cta_max_p particles (0: none) run
+  // whole, one block each, on a side branch of the graph
+  int64_t cta_max_p = 0;
+  int cta_total = 0;
+  std::vector<PlanClass> cta_classes;       // offset / ntiles = first / count in d_cta
+  int* d_cta = nullptr;                     // filter indices, per class
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 pf_status fail(pf_status st, const char* fmt, ...);
 pf_status check_shape(const pf_model* m, int64_t P, int32_t T, double dt, Shape* sh);
-pf_status build_plan(const std::vector<pf_filter*>& fl, Plan** out);
+pf_status build_plan(const std::vector<pf_filter*>& fl, Plan** out, int64_t cta_max_p);
 pf_status stage_plan(Plan* p, const double* const* theta, const double* const* y,
                      const uint64_t* seeds, const int32_t* hist_on, cudaStream_t st);
 pf_status run_plan(Plan* p, const double* const* theta, const double* const* y,
