@@ -201,18 +201,20 @@ pf_status pf_batch_run(int32_t nfilt, pf_filter* const* f, const double* const* 
                        int32_t* per_filter_status, void* cuda_stream);
 
 /* The batched form's split of a filter list between its two paths: filters
- * with at most cta_max_particles particles (and at most 2^16, not resampled
- * multinomially) run whole, one thread block each, on a side branch of the
- * plan's CUDA graph -- no per-step launches or grid-wide hand-offs -- while the
- * others take the tiled per-step launches.  Both paths compute every filter
- * with the same functions in the same order, so results are bit-identical
- * whatever the split.  0 (the default) sends every filter to the tiled path.
- * Applies to pf_batch_run and pf_pmmh_run on this exact filter list. */
+ * with at most cta_max_particles particles (and at most 2048, not resampled
+ * multinomially) run whole, each on one thread-block cluster (one CTA per
+ * tile of 256 particles, cluster barriers between the phases of a step), on a
+ * side branch of the plan's CUDA graph -- no per-step launches or grid-wide
+ * hand-offs -- while the others take the tiled per-step launches.  Both paths
+ * compute every filter with the same functions in the same order, so results
+ * are bit-identical whatever the split.  0 (the default) sends every filter
+ * to the tiled path.  Applies to pf_batch_run and pf_pmmh_run on this exact
+ * filter list. */
 pf_status pf_batch_configure(int32_t nfilt, pf_filter* const* f, int64_t cta_max_particles);
 
 /* Autotuner of that split: runs the batch (inputs as for pf_batch_run) with
- * each candidate bound (0, 2^8, 2^10, 2^12, 2^14, 2^16 particles), keeps the
- * fastest for the filter list and returns it in *chosen (may be NULL). */
+ * each candidate bound (0, 256, 512, 1024, 2048 particles), keeps the fastest
+ * for the filter list and returns it in *chosen (may be NULL). */
 pf_status pf_batch_autotune(int32_t nfilt, pf_filter* const* f, const double* const* theta,
                             const double* const* y, const uint64_t* seeds, int64_t* chosen);
 

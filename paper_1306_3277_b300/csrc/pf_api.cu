@@ -290,8 +290,8 @@ static cudaError_t enqueue_steps(Plan* p, int first, int last, cudaStream_t st, 
   return le;
 }
 
-// The launch sequence of one whole run of a plan.  The one-block filters run
-// on a side branch (their own stream, forked and joined with events, so a
+// The launch sequence of one whole run of a plan.  The cluster filters run on
+// a side branch (their own stream, forked and joined with events, so a
 // captured graph holds two parallel branches) next to the tiled steps of the
 // others; with a profiler everything runs on st, one launch after the other.
 static cudaError_t enqueue_run(Plan* p, cudaStream_t st, Profiler* prof) {
@@ -305,8 +305,8 @@ static cudaError_t enqueue_run(Plan* p, cudaStream_t st, Profiler* prof) {
   for (size_t c = 0; c < p->cta_classes.size() && le == cudaSuccess; ++c) {
     const PlanClass& pc = p->cta_classes[c];
     if (prof) prof->begin(PROF_PROPAGATE, st);
-    le = launch_filter_cta(pc.kind, pc.N, pc.prec, p->d_fds, p->d_cta + pc.offset, pc.ntiles,
-                           side);
+    le = launch_filter_cluster(pc.kind, pc.N, pc.prec, p->d_fds, p->d_cta + pc.offset,
+                               pc.ntiles, p->cta_cluster[c], side);
     if (prof) prof->end(st);
   }
   if (le == cudaSuccess && !prof) le = cudaEventRecord(p->ev_join, side);
@@ -321,17 +321,18 @@ static cudaError_t enqueue_run(Plan* p, cudaStream_t st, Profiler* prof) {
 }
 
 cudaError_t pfb::enqueue_plan_steps(Plan* p, int first, int last, bool init, cudaStream_t st) {
-  if (p->cta_total > 0) return cudaErrorNotSupported;  // one-block filters run whole runs only
+  if (p->cta_total > 0) return cudaErrorNotSupported;  // cluster filters run whole runs only
   return enqueue_steps(p, first, last, st, nullptr, no_hook, init);
 }
 
 // Tile maps sorted by T descending so that the filters still running at step
 // i own a prefix of every map.
-// A filter runs on the one-block path when the plan allows it for its
-// particle count, its tiles fit one group and its resampling is not
-// multinomial (the spacing scan is a separate set of launches).
+// A filter runs whole on a thread-block cluster when the plan allows it for
+// its particle count, its tiles fit one cluster (one CTA per tile) and its
+// resampling is not multinomial (the spacing scan is a separate set of
+// launches).
 static bool cta_eligible(const pf_filter* f, int64_t cta_max_p) {
-  return cta_max_p > 0 && f->P <= cta_max_p && f->sh.ntiles <= GROUP &&
+  return cta_max_p > 0 && f->P <= cta_max_p && f->sh.ntiles <= MAX_CLUSTER_TILES &&
          f->m.resampler != PF_RESAMPLE_MULTINOMIAL;
 }
 
@@ -356,20 +357,20 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out, int64_t
     p->yoff[k] = ytot;
     ytot += size_t(fl[k]->T) * size_t(fl[k]->sh.Ny);
   }
-  // the one-block filters, per class, the most expensive first (a block
-  // takes a filter as the hardware hands out blocks in order)
-  std::map<std::tuple<int, int, int>, std::vector<int>> cta_lists;
+  // the cluster filters, per class and cluster size (= their tile count), the
+  // longest runs first (clusters start in the order the hardware hands them out)
+  std::map<std::tuple<int, int, int, int>, std::vector<int>> cta_lists;
   for (int k = 0; k < nf; ++k)
     if (cta_eligible(fl[k], cta_max_p))
-      cta_lists[std::make_tuple(fl[k]->m.kind, fl[k]->m.N, fl[k]->m.prec)].push_back(k);
+      cta_lists[std::make_tuple(fl[k]->m.kind, fl[k]->m.N, fl[k]->m.prec, fl[k]->sh.ntiles)]
+          .push_back(k);
   std::vector<int> cta_all;
   for (auto& kv : cta_lists) {
     std::vector<int>& v = kv.second;
-    std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
-      return double(fl[a]->P) * fl[a]->T > double(fl[b]->P) * fl[b]->T;
-    });
+    std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return fl[a]->T > fl[b]->T; });
     p->cta_classes.push_back({std::get<0>(kv.first), std::get<1>(kv.first),
                               std::get<2>(kv.first), int(cta_all.size()), int(v.size())});
+    p->cta_cluster.push_back(std::get<3>(kv.first));
     cta_all.insert(cta_all.end(), v.begin(), v.end());
   }
   p->cta_total = int(cta_all.size());
@@ -840,7 +841,7 @@ extern "C" pf_status pf_batch_configure(int32_t nfilt, pf_filter* const* f,
 extern "C" pf_status pf_batch_autotune(int32_t nfilt, pf_filter* const* f,
                                        const double* const* theta, const double* const* y,
                                        const uint64_t* seeds, int64_t* chosen) {
-  static const int64_t candidates[] = {0, 256, 1024, 4096, 16384, 65536};
+  static const int64_t candidates[] = {0, 256, 512, 1024, 2048};
   std::vector<double> ll(nfilt > 0 ? nfilt : 1);
   std::vector<int32_t> st(nfilt > 0 ? nfilt : 1);
   double best_ms = 0.0;

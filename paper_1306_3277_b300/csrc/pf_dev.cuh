@@ -17,6 +17,7 @@ constexpr int TILE = 256;        // particles per tile == threads per block
 constexpr int GROUP = 256;       // tiles per group (two-level combine)
 constexpr int WARPS = TILE / 32;
 constexpr int64_t MAX_P = int64_t(1) << 24;  // GROUP * GROUP * TILE
+constexpr int MAX_CLUSTER_TILES = 8;          // the portable thread-block cluster size
 
 enum { KIND_WK = 0, KIND_L96 = 1, KIND_WKX = 2, KIND_L96W = 3 };
 __host__ __device__ constexpr bool wk_kind(int k) { return k == KIND_WK || k == KIND_WKX; }

@@ -12,9 +12,12 @@ cudaError_t launch_init(int kind, int N, int prec, const FilterDev* fds, const i
 cudaError_t launch_propagate(int kind, int N, int prec, const FilterDev* fds, const int2* tmap,
                              int nblocks, cudaStream_t st);
 cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks, cudaStream_t st);
-// one block per listed filter runs its whole run (initial draw and all steps)
-cudaError_t launch_filter_cta(int kind, int N, int prec, const FilterDev* fds, const int* list,
-                              int nfilters, cudaStream_t st);
+// one thread-block cluster of cluster_size CTAs per listed filter runs its
+// whole run (initial draw and all steps); the filters have at most
+// cluster_size tiles
+cudaError_t launch_filter_cluster(int kind, int N, int prec, const FilterDev* fds,
+                                  const int* list, int nfilters, int cluster_size,
+                                  cudaStream_t st);
 cudaError_t launch_flow(double* flow, int64_t n, double peak, double period, double dt,
                         cudaStream_t st);
 cudaError_t launch_results(const FilterDev* fds, int nf, double* out, cudaStream_t st);

@@ -914,30 +914,43 @@ __global__ void __launch_bounds__(TILE, RESAMPLE_BLOCKS_PER_SM)
 }
 
 // ---------------------------------------------------------------------------
-// One filter per block: the batched form's persistent path for small filters
+// One thread-block cluster per small filter: the batched form's persistent path
 // ---------------------------------------------------------------------------
-// Block b runs filter list[b] from its initial draw through all its steps:
-// per step its tiles are propagated one after the other (propagate_tile), its
-// single group and the filter are combined (combine_group, combine_filter),
-// and its tiles are resampled (resample_particles) or carried (carry_tile).
-// These are the tiled kernels' own functions in the tiled kernels' order, so
-// every result is bit-identical to the tiled path's; what disappears is the
-// two launches and two grid-wide hand-offs per step.  The plan sends here the
-// filters with at most GROUP tiles whose resampling is not multinomial.
+// All the CTAs of a cluster wait here, with release / acquire semantics at
+// cluster scope (every CTA of a cluster arrives the same number of times).
+__device__ __forceinline__ void cluster_sync() {
+  __threadfence();
+  asm volatile("barrier.cluster.arrive.release.aligned;\n"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Filter list[blockIdx.x / CS] runs whole on a cluster of CS CTAs, CTA r
+// owning tile r (CTAs past the filter's tiles only take part in the
+// barriers): its initial draw, then per step its tiles propagated in parallel
+// (propagate_tile), CTA 0 combining the group and the filter (combine_group,
+// combine_filter), and its tiles resampled in parallel (resample_particles) or
+// carried (carry_tile), with a cluster barrier between the phases.  These are
+// the tiled kernels' own functions in their order, so every result is
+// bit-identical to the tiled path's; the two launches and the last-block
+// hand-offs of every step disappear.  Every CTA of a cluster reads the same
+// control block after the same barrier, so all take the same branches and
+// reach the same barriers.
 template <int KIND, int N, typename R>
-__global__ void __launch_bounds__(TILE) k_filter_cta(const FilterDev* __restrict__ fds,
-                                                     const int* __restrict__ list) {
+__global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __restrict__ fds,
+                                                         const int* __restrict__ list, int cs_size) {
   __shared__ CombineScratch cs;
   __shared__ double ys[64];
   __shared__ int s_step, s_ok, s_anc_identity, s_lam_zero, s_go, s_flag, s_lo, s_hi, nlong;
   __shared__ double s_cw, s_M, s_u, s_ratio, s_S, s_e0, s_scale_r;
   __shared__ int3 longr[TILE];
-  const FilterDev& fd = fds[list[blockIdx.x]];
+  const FilterDev& fd = fds[list[blockIdx.x / cs_size]];
+  const int t = blockIdx.x % cs_size;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  const int P = fd.P, nt = fd.ntiles, T = fd.T, rs = fd.resampler;
-  for (int t = 0; t < nt; ++t) init_tile<KIND, N, R>(fd, t);
-  __syncthreads();
+  const int P = fd.P, T = fd.T, rs = fd.resampler;
+  const bool mine = t < fd.ntiles;
+  if (mine) init_tile<KIND, N, R>(fd, t);
+  cluster_sync();
   for (int i = 1; i <= T; ++i) {
     if (tid == 0) {
       const Ctl* ctl = fd.ctl;
@@ -948,15 +961,17 @@ __global__ void __launch_bounds__(TILE) k_filter_cta(const FilterDev* __restrict
       s_cw = ldcg(&ctl->cw);
     }
     __syncthreads();
-    if (!s_ok || s_step != i) break;  // a degenerate step ended the run
-    for (int t = 0; t < nt; ++t) {
+    if (!s_ok || s_step != i) break;  // a degenerate step ended the run (same in every CTA)
+    if (mine) {
       const int j = t * TILE + tid;
       const int a_spec = (j < P && !fd.hist) ? fd.anc[j] : j;
       propagate_tile<KIND, N, R>(fd, t, i, s_anc_identity, s_lam_zero, s_cw, a_spec, ys, cs);
-      __syncthreads();  // the scratch is reused by the next tile
     }
-    if (combine_group(fd, 0, cs)) combine_filter(fd, i, cs);
-    __syncthreads();
+    cluster_sync();  // the tile partials of every CTA
+    if (t == 0) {
+      if (combine_group(fd, 0, cs)) combine_filter(fd, i, cs);
+    }
+    cluster_sync();  // the group partials and the step's decisions
     if (tid == 0) {
       const Ctl* ctl = fd.ctl;
       const int i0 = ldcg(&ctl->rs_step);
@@ -966,35 +981,33 @@ __global__ void __launch_bounds__(TILE) k_filter_cta(const FilterDev* __restrict
       s_u = rs == RS_SYSTEMATIC ? ldcg(&ctl->u) : 0.0;
       s_ratio = ldcg(&ctl->ratio);
       s_S = ldcg(&ctl->S);
+      nlong = 0;
     }
     __syncthreads();
-    if (!s_go) continue;  // the last step, or a degenerate one
-    for (int t = 0; t < nt; ++t) {
+    if (s_go && mine) {
       if (!s_flag) {
         carry_tile(fd, t, i, s_M);
-        continue;
-      }
-      const int j = t * TILE + tid;
-      const double ct = j < P ? fd.ctil[j] : 0.0;
-      const double ctp = (lane == 0 && tid > 0 && j <= P) ? fd.ctil[j - 1] : 0.0;
-      if (tid == 0) nlong = 0;  // the previous tile's readers passed the barrier below
-      if (tid == 0 || tid == 32) {
-        double base = 0.0, scale = 0.0;
-        tile_base(fd, t, tid == 0 ? 0 : 1, s_S, &base, &scale);
-        const int n0 = range_count(fd, rs, base, s_ratio, s_u, i);
-        if (tid == 0) {
-          s_e0 = base * s_ratio - s_u;
-          s_scale_r = scale * s_ratio;
-          s_lo = n0;
-        } else {
-          s_hi = n0;
+      } else {
+        const int j = t * TILE + tid;
+        const double ct = j < P ? fd.ctil[j] : 0.0;
+        const double ctp = (lane == 0 && tid > 0 && j <= P) ? fd.ctil[j - 1] : 0.0;
+        if (tid == 0 || tid == 32) {
+          double base = 0.0, scale = 0.0;
+          tile_base(fd, t, tid == 0 ? 0 : 1, s_S, &base, &scale);
+          const int n0 = range_count(fd, rs, base, s_ratio, s_u, i);
+          if (tid == 0) {
+            s_e0 = base * s_ratio - s_u;
+            s_scale_r = scale * s_ratio;
+            s_lo = n0;
+          } else {
+            s_hi = n0;
+          }
         }
+        __syncthreads();
+        resample_particles(fd, t, i, rs, s_lo, s_hi, s_e0, s_scale_r, ct, ctp, &nlong, longr);
       }
-      __syncthreads();
-      resample_particles(fd, t, i, rs, s_lo, s_hi, s_e0, s_scale_r, ct, ctp, &nlong, longr);
-      __syncthreads();  // the shared values are rewritten for the next tile
     }
-    __syncthreads();
+    cluster_sync();  // the ancestors and carried weights of the next step
   }
 }
 
@@ -1206,9 +1219,29 @@ template <int KIND, int N, typename R>
 static cudaError_t launch_pair(int what, const FilterDev* fds, const int2* tmap, int nblocks,
                                cudaStream_t st) {
   if (nblocks <= 0) return cudaSuccess;
-  if (what == LAUNCH_INIT) k_init<KIND, N, R><<<nblocks, TILE, 0, st>>>(fds, tmap);
-  else if (what == LAUNCH_PROPAGATE) k_propagate<KIND, N, R><<<nblocks, TILE, 0, st>>>(fds, tmap);
-  else k_filter_cta<KIND, N, R><<<nblocks, TILE, 0, st>>>(fds, reinterpret_cast<const int*>(tmap));
+  if (what == LAUNCH_INIT) {
+    k_init<KIND, N, R><<<nblocks, TILE, 0, st>>>(fds, tmap);
+  } else if (what == LAUNCH_PROPAGATE) {
+    k_propagate<KIND, N, R><<<nblocks, TILE, 0, st>>>(fds, tmap);
+  } else {
+    // nblocks = filters x cluster size, what - LAUNCH_CTA = the cluster size
+    const int cs_size = what - LAUNCH_CTA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(nblocks));
+    cfg.blockDim = dim3(TILE);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = unsigned(cs_size);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_filter_cluster<KIND, N, R>, fds,
+                                             reinterpret_cast<const int*>(tmap), cs_size);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 
@@ -1252,10 +1285,12 @@ cudaError_t launch_propagate(int kind, int N, int prec, const FilterDev* fds, co
   return dispatch(LAUNCH_PROPAGATE, kind, N, prec, fds, tmap, nblocks, st);
 }
 
-cudaError_t launch_filter_cta(int kind, int N, int prec, const FilterDev* fds, const int* list,
-                              int nfilters, cudaStream_t st) {
-  return dispatch(LAUNCH_CTA, kind, N, prec, fds, reinterpret_cast<const int2*>(list), nfilters,
-                  st);
+cudaError_t launch_filter_cluster(int kind, int N, int prec, const FilterDev* fds,
+                                  const int* list, int nfilters, int cluster_size,
+                                  cudaStream_t st) {
+  if (cluster_size < 1 || cluster_size > MAX_CLUSTER_TILES) return cudaErrorInvalidValue;
+  return dispatch(LAUNCH_CTA + cluster_size, kind, N, prec, fds,
+                  reinterpret_cast<const int2*>(list), nfilters * cluster_size, st);
 }
 
 cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks,

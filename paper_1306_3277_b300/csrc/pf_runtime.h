@@ -130,11 +130,13 @@ struct Plan {
   cudaStream_t st = nullptr;
   cudaEvent_t ev_staged = nullptr, ev_done = nullptr;
   cudaGraphExec_t exec = nullptr;
-  // one-block path: filters with at most cta_max_p particles (0: none) run
-  // whole, one block each, on a side branch of the graph
+  // cluster path: filters with at most cta_max_p particles (0: none) and at
+  // most MAX_CLUSTER_TILES tiles run whole, one thread-block cluster each, on
+  // a side branch of the graph
   int64_t cta_max_p = 0;
   int cta_total = 0;
   std::vector<PlanClass> cta_classes;       // offset / ntiles = first / count in d_cta
+  std::vector<int> cta_cluster;             // cluster size (= tiles) of each of those
   int* d_cta = nullptr;                     // filter indices, per class
   cudaStream_t st2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
