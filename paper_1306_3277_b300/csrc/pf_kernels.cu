@@ -202,13 +202,23 @@ template <> __device__ __forceinline__ float from_double<float>(double v) { retu
 // a = exp(-dt/(RC)) (own exponential), b = R (1 - a), sd = dt sqrt(sigma2),
 // z_mm = normal number mm of stream (j, i, PROP); a, b, sd in FP64, rounded to
 // the state precision.
+// The filter's constants (a, b, sd) of the exact windkessel transition, computed
+// by one thread per block: an FP64 exponential, a division and a square root
+// that every particle shares.
 template <typename R>
-__device__ __forceinline__ void wkx_propagate(const FilterDev& fd, uint32_t j, int i, R& xv) {
-  const int s = fd.s;
+__device__ __forceinline__ void wkx_constants(const FilterDev& fd, R (&c)[3]) {
   const double Rr = fd.theta[0], Cc = fd.theta[1];
   const double a64 = exp_own(-(fd.dt / (Rr * Cc)));
-  const R a = from_double<R>(a64), b = from_double<R>(Rr * (1.0 - a64));
-  const R sd = from_double<R>(fd.dt * sqrt(fd.theta[3]));
+  c[0] = from_double<R>(a64);
+  c[1] = from_double<R>(Rr * (1.0 - a64));
+  c[2] = from_double<R>(fd.dt * sqrt(fd.theta[3]));
+}
+
+template <typename R>
+__device__ __forceinline__ void wkx_propagate(const FilterDev& fd, uint32_t j, int i, R& xv,
+                                              const R (&c)[3]) {
+  const int s = fd.s;
+  const R a = c[0], b = c[1], sd = c[2];
   const double* fl = fd.flow + int64_t(i - 1) * s;
   if constexpr (sizeof(R) == 8) {
     for (int mm = 0; mm < s; mm += 2) {
@@ -577,6 +587,11 @@ __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i
   const bool valid = j < P;
   if (tid < fd.Ny) ys[tid] = fd.y[int64_t(i - 1) * fd.Ny + tid];  // read after the barrier below
 
+  __shared__ R kc[3];  // per-filter constants of the exact windkessel
+  if constexpr (KIND == KIND_WKX) {
+    if (tid == 0) wkx_constants<R>(fd, kc);
+    __syncthreads();
+  }
   R x[N];
   if (valid) {
     const int a = anc_identity ? j : (fd.hist ? fd.anc[int64_t(i - 1) * P + j] : a_spec);
@@ -585,7 +600,7 @@ __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i
 #pragma unroll
     for (int n = 0; n < N; ++n) x[n] = xin[int64_t(n) * P + a];
     if constexpr (KIND == KIND_WK) wk_propagate<R>(fd, uint32_t(j), i, x[0]);
-    else if constexpr (KIND == KIND_WKX) wkx_propagate<R>(fd, uint32_t(j), i, x[0]);
+    else if constexpr (KIND == KIND_WKX) wkx_propagate<R>(fd, uint32_t(j), i, x[0], kc);
     else if constexpr (KIND == KIND_L96W) l96w_propagate<N, R>(fd, uint32_t(j), i, x);
     else l96_propagate<N, R>(fd, uint32_t(j), i, x);
 #pragma unroll
