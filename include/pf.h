@@ -373,6 +373,18 @@ pf_status pf_profile_read(pf_filter* f, double* ms, int64_t* launches);
  * kernels; *ms receives the duration of the best one. */
 pf_status pf_measure_fma_peak(int32_t prec, double* flops_per_s, double* ms);
 
+/* The exponential that the propagate kernels apply to the log-weights relative
+ * to their tile maximum (Algorithm 2, weight and normalisation lines:
+ * w = exp(ell - M), d = ell - M <= 0), evaluated on the device for n given
+ * arguments: w[i] = e^{d[i]}.  A diagnostic that lets a test compare the
+ * kernels' exponential (a table-driven method on the FP32 unit with two FP64
+ * operations, relative error about 2^-52 for -700 < d <= 0) with a correctly
+ * rounded one.  d and w are HOST arrays of n doubles owned by the caller
+ * (they may not overlap); n = 0 does nothing.  Synchronous, on the current
+ * device; allocates 16 n bytes of device memory for the call.  PF_EINVAL for
+ * n < 0, n > 2^28 or a NULL array with n > 0; PF_ECUDA on a CUDA error. */
+pf_status pf_weight_exp(const double* d, double* w, int64_t n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,6 +69,7 @@ def lib():
                                       ctypes.POINTER(ctypes.c_int64)]
         L.pf_measure_fma_peak.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]
+        L.pf_weight_exp.argtypes = [_vp, _vp, ctypes.c_int64]
         L.pf_pmmh_run.argtypes = [ctypes.c_int32, ctypes.POINTER(_vp), _vp,
                                   ctypes.POINTER(pf_param), _vp, ctypes.c_int32,
                                   ctypes.c_uint64, _vp, _vp, _vp, _vp]
@@ -88,7 +89,7 @@ def lib():
         L.pf_sample_path.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp, _vp]
         for name in ("pf_run", "pf_wait", "pf_destroy", "pf_create", "pf_batch_run",
                      "pf_profile_enable", "pf_profile_read", "pf_measure_fma_peak",
-                     "pf_run_range", "pf_sample_path"):
+                     "pf_run_range", "pf_sample_path", "pf_weight_exp"):
             getattr(L, name).restype = ctypes.c_int
         L.pf_run_noalloc.argtypes = [ctypes.POINTER(pf_model), ctypes.c_int64, ctypes.c_int32,
                                      ctypes.c_double, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp,
@@ -353,9 +354,18 @@ def pf_measure_fma_peak(prec):
     return f.value
 
 
+def pf_weight_exp(d):
+    """e^d evaluated on the GPU by the propagate kernels' weight exponential
+    (diagnostic; d: float64 array, returns a new float64 array)."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    w = np.empty_like(d)
+    _check(lib().pf_weight_exp(d.ctypes.data, w.ctypes.data, d.size))
+    return w
+
+
 def pf_batch_configure(filters, cta_max_particles):
     """Send the filters of this list with at most cta_max_particles particles
-    to the one-block path (0: none); results do not change."""
+    to the thread-block cluster path (0: none); results do not change."""
     nf = len(filters)
     hs = (_vp * nf)(*[f.h for f in filters])
     _check(lib().pf_batch_configure(nf, hs, int(cta_max_particles)))

@@ -215,7 +215,7 @@ extern "C" pf_status pf_create(const pf_model* m, int64_t P, int32_t T, double d
 // ---------------------------------------------------------------------------
 static std::mutex g_plan_mu;
 static std::map<std::vector<pf_filter*>, Plan*> g_plans;  // cached batch plans
-// per filter list: the largest particle count sent to the one-block path
+// per filter list: the largest particle count sent to the cluster path
 static std::map<std::vector<pf_filter*>, int64_t> g_cta_choice;
 
 static void destroy_plan(Plan* p) {

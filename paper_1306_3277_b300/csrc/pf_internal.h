@@ -6,6 +6,9 @@
 
 namespace pfb {
 
+// The propagate kernels' weight exponential on n device values (diagnostic).
+cudaError_t launch_weight_exp(const double* d, double* w, int64_t n, cudaStream_t st);
+
 bool supported(int kind, int N, int prec);
 cudaError_t launch_init(int kind, int N, int prec, const FilterDev* fds, const int2* tmap,
                         int nblocks, cudaStream_t st);

@@ -198,6 +198,82 @@ template <typename R> __device__ __forceinline__ R from_double(double v);
 template <> __device__ __forceinline__ double from_double<double>(double v) { return v; }
 template <> __device__ __forceinline__ float from_double<float>(double v) { return __double2float_rn(v); }
 
+// ---------------------------------------------------------------------------
+// Weight exponential w = e^d, d = ell - M <= 0, at FP64 accuracy with two
+// FP64 operations.  B300's FP64 unit runs at 1/64 of the FP32 rate and the
+// library exponential spends about a dozen FP64 instructions per call, which
+// made it a fifth of the small-state propagate kernels; here the work runs on
+// the FP32 and integer units instead.  Method: Tang's table-driven
+// exponential (ACM TOMS 15(2), 1989), d = (256 m + j) ln2/256 + r with
+// |r| <= ln2/512, e^d = 2^m 2^(j/256) e^r, evaluated with double-float
+// (unevaluated sums of two floats; Dekker 1971, Knuth's two-sum):
+//  * d splits exactly into three floats (24 + 24 + 5 significant bits);
+//  * k = rint(d 256/ln2) in FP32; r = d - k ln2/256 with ln2/256 in three
+//    floats (the first product is exact inside the fma), carried as a
+//    double-float;
+//  * q = e^r - 1 = r + r^2/2 + (r^3/6 + r^4/24 + r^5/120), the square as a
+//    double-float, the cubic tail in FP32;
+//  * in FP64: Q = qh + ql, W = T_j (1 + Q) by one fma (T_j = 2^(j/256)
+//    rounded to the nearest double), and 2^m goes into W's exponent bits.
+// Relative error about 2^-52 (tests compare it with the correctly rounded
+// value).  Outside -700 < d <= 0 it takes the library exponential (d > 0,
+// d in (-745.2, -700]) or returns 0 (d <= -745.2, including -inf).
+// ---------------------------------------------------------------------------
+#include "pf_exp2_table.h"
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+__device__ __forceinline__ float pow2f(int e) {  // 2^e for -126 <= e <= 127
+  return __uint_as_float(unsigned(e + 127) << 23);
+}
+
+__device__ __forceinline__ double exp_weight(double d) {
+  const unsigned long long ub = static_cast<unsigned long long>(__double_as_longlong(d));
+  if (ub == 0ull) return 1.0;                          // +0
+  if (ub < 0x8000000000000000ull) return exp(d);       // d > 0, +inf, +NaN
+  if (ub > 0xfff0000000000000ull) return d;            // -NaN
+  if (ub >= 0xc08749999999999aull) return 0.0;         // d <= -745.2, -inf
+  if (ub >= 0xc085e00000000000ull) return exp(d);      // -745.2 < d <= -700
+  const int ex = int((ub >> 52) & 0x7ffu) - 1023;
+  if (ex < -60) return 1.0;                            // |d| < 2^-60 (and -0)
+  // d = -(mh 2^(ex-23) + mm 2^(ex-47) + ml 2^(ex-52)), each part exact in FP32
+  const unsigned long long m = (ub & 0x000fffffffffffffull) | 0x0010000000000000ull;
+  const unsigned mh = unsigned(m >> 29), mm = unsigned(m >> 5) & 0xffffffu, ml = unsigned(m) & 31u;
+  const float dh = __uint_as_float(0x80000000u | (unsigned(ex + 127) << 23) | (mh & 0x7fffffu));
+  const float dm = -__fmul_rn(__uint2float_rn(mm), pow2f(ex - 47));
+  const float dl = -__fmul_rn(__uint2float_rn(ml), pow2f(ex - 52));
+  // range reduction: |k| < 2^18, r1 = dh - k C1 exact
+  const float kf = rintf(__fmul_rn(dh, 0x1.715476p+8f));  // 256 / ln2
+  const int k = int(kf);
+  constexpr float C1 = 0x1.62e43p-9f, C2 = -0x1.05c61p-37f, C3 = -0x1.950d88p-62f;
+  const float r1 = __fmaf_rn(-kf, C1, dh);
+  const float p2 = __fmul_rn(kf, C2);
+  const float e2 = __fmaf_rn(kf, C2, -p2);  // kf C2 = p2 + e2 exactly
+  const float p3 = __fmul_rn(kf, C3);
+  float a, ae, b, be, rh, rl;
+  two_sum(r1, dm, a, ae);
+  two_sum(a, -p2, b, be);
+  const float low = __fsub_rn(__fsub_rn(__fadd_rn(__fadd_rn(ae, be), dl), e2), p3);
+  two_sum(b, low, rh, rl);  // r = rh + rl
+  // q = e^r - 1
+  const float sh = __fmul_rn(rh, rh);
+  const float sl = __fadd_rn(__fmaf_rn(rh, rh, -sh), __fmul_rn(__fmul_rn(2.0f, rh), rl));
+  const float poly = __fmaf_rn(__fmaf_rn(rh, 0x1.111112p-7f, 0x1.555556p-5f), rh, 0x1.555556p-3f);
+  const float tail = __fmul_rn(__fmul_rn(sh, rh), poly);
+  float u, ue, qh, ql;
+  two_sum(rh, __fmul_rn(0.5f, sh), u, ue);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(ue, __fmul_rn(0.5f, sl)), rl), tail);
+  two_sum(u, lo, qh, ql);
+  const double Q = __dadd_rn(to_double(qh), to_double(ql));
+  const double T = __ldg(&k_exp2_256[k & 255]);
+  const double W = __fma_rn(T, Q, T);  // in [0.998, 2): 2^(k >> 8) W stays a normal number
+  return __longlong_as_double(__double_as_longlong(W) + (static_cast<long long>(k >> 8) << 52));
+}
+
 // The paper's windkessel transition: s steps x <- a x + b (F_k + sd z_mm),
 // a = exp(-dt/(RC)) (own exponential), b = R (1 - a), sd = dt sqrt(sigma2),
 // z_mm = normal number mm of stream (j, i, PROP); a, b, sd in FP64, rounded to
@@ -567,9 +643,16 @@ __global__ void __launch_bounds__(TILE) k_init(const FilterDev* __restrict__ fds
 // Blocks per SM the propagate kernel is compiled for: two wherever the state
 // fits in 128 registers per thread without spilling more than a few words
 // (every FP32 size, FP64 up to N = 12, the windkessel), else one.
+// Blocks per SM the propagate kernel is compiled for (registers per thread =
+// 65536 / (256 x blocks)).  The small states are FP64-latency-bound, so more
+// resident warps pay: windkessel 4 (64 registers), Lorenz '96 in FP32 up to
+// N = 12 3 (85); the N = 40 FP32 state needs its 128 registers (2 blocks).
 template <int KIND, int N, typename R>
 struct PropagateOccupancy {
-  static constexpr int value = (wk_kind(KIND) || sizeof(R) == 4 || N <= 12) ? 2 : 1;
+  static constexpr int value = wk_kind(KIND)                    ? 4
+                               : (sizeof(R) == 4 && N <= 12)     ? 3
+                               : (sizeof(R) == 4 || N <= 12)     ? 2
+                                                                 : 1;
 };
 
 // Step i of tile t (Algorithm 2, propagate and weight lines): gather the
@@ -623,7 +706,7 @@ __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i
 
   // tile partials: max, inclusive prefix of exp(ell - M_t), total
   const double Mt = block_max(ell, cs.b);
-  const double w = (Mt == -INFINITY) ? 0.0 : exp(ell - Mt);
+  const double w = (Mt == -INFINITY) ? 0.0 : exp_weight(ell - Mt);
   double St;
   const double c = block_scan(w, cs.b, &St);
   if (j < P) fd.ctil[j] = c;
@@ -1288,6 +1371,20 @@ static cudaError_t dispatch(int init, int kind, int N, int prec, const FilterDev
 #undef PF_CASE
   }
   return cudaErrorInvalidValue;
+}
+
+// The weight exponential on n given arguments (diagnostic entry point).
+__global__ void k_weight_exp(const double* __restrict__ d, double* __restrict__ w, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    w[i] = exp_weight(d[i]);
+}
+
+cudaError_t launch_weight_exp(const double* d, double* w, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t nb = (n + TILE - 1) / TILE;
+  k_weight_exp<<<unsigned(nb < 4096 ? nb : 4096), TILE, 0, st>>>(d, w, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_init(int kind, int N, int prec, const FilterDev* fds, const int2* tmap,

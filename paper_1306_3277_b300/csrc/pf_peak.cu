@@ -1,12 +1,14 @@
-// pf_peak.cu -- measured fused multiply-add throughput of this GPU, FP32 and
-// FP64.  A diagnostic for the roofline denominators of the filter's kernels
-// (the filter is FP32 and FP64 ALU work, not a tensor contraction); it has no
-// counterpart in the paper.
+// pf_peak.cu -- diagnostics: the measured fused multiply-add throughput of this
+// GPU, FP32 and FP64 (the roofline denominators of the filter's kernels, which
+// are FP32 and FP64 ALU work, not a tensor contraction), and the propagate
+// kernels' weight exponential on given arguments.  Neither has a counterpart
+// in the paper.
 #include <algorithm>
 #include <type_traits>
 #include <cuda_runtime.h>
 
 #include "pf.h"
+#include "pf_internal.h"
 #include "pf_runtime.h"
 
 namespace {
@@ -136,4 +138,21 @@ extern "C" pf_status pf_measure_fma_peak(int32_t prec, double* flops_per_s, doub
   if (prec == PF_MIXED) return measure<float>(flops_per_s, ms);
   if (prec == 2) return measure<Packed>(flops_per_s, ms);
   return pfb::fail(PF_EINVAL, "prec must be PF_FP64, PF_MIXED or 2 (packed FP32 pairs)");
+}
+
+extern "C" pf_status pf_weight_exp(const double* d, double* w, int64_t n) {
+  if (n < 0) return pfb::fail(PF_EINVAL, "n = %lld < 0", static_cast<long long>(n));
+  if (n == 0) return PF_OK;
+  if (!d || !w) return pfb::fail(PF_EINVAL, "d or w is NULL");
+  if (n > (int64_t(1) << 28)) return pfb::fail(PF_EINVAL, "n = %lld > 2^28", static_cast<long long>(n));
+  double* buf = nullptr;
+  const size_t bytes = size_t(n) * sizeof(double);
+  cudaError_t e = cudaMalloc(&buf, 2 * bytes);
+  if (e != cudaSuccess) return pfb::fail(PF_ECUDA, "cudaMalloc: %s", cudaGetErrorString(e));
+  e = cudaMemcpy(buf, d, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = pfb::launch_weight_exp(buf, buf + n, n, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(w, buf + n, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) return pfb::fail(PF_ECUDA, "weight exponential: %s", cudaGetErrorString(e));
+  return PF_OK;
 }
