@@ -851,9 +851,9 @@ __device__ __forceinline__ int mn_below(const FilterDev& fd, double e, int lo, i
 // and multinomial as strat_below / mn_below on C (P/S).  Only the counts use
 // FP64 (one fma per particle; ceilings and floors are taken on the bits).
 //
-// Two barriers per block: one after the control block is read (threads 0 and
-// 32 also derive the tile's range and scaled base there), one vote for very
-// long offspring ranges.  A particle's predecessor count comes from the
+// Barriers: one per chunk of tiles after their ranges and scaled bases are
+// prepared, one vote per resampled tile for very long offspring ranges, one at
+// the end of the chunk.  A particle's predecessor count comes from the
 // neighbouring lane (lane 0 recomputes it from the previous prefix); ranges
 // up to SHORT_RANGE are written by the particle's thread, up to BLOCK_RANGE by
 // its warp, longer ones by the whole block, so a tile that owns most of the
@@ -888,10 +888,20 @@ __device__ __forceinline__ int range_count(const FilterDev& fd, int rs, double b
   return mn_below(fd, base * ratio, 0, fd.P);
 }
 
+// The offspring ranges longer than BLOCK_RANGE of one tile, written by the
+// whole block with coalesced stores.
+__device__ __forceinline__ void write_long_ranges(int32_t* aout, int nl, const int3* longr) {
+  for (int r = 0; r < nl; ++r) {
+    const int3 rg = longr[r];
+    for (int jj = rg.x + int(threadIdx.x); jj < rg.y; jj += TILE) aout[jj] = rg.z;
+  }
+}
+
 // The particles of tile t take their targets [n_{k-1}, n_k): counts from the
 // scaled cumulative weights (ct = this particle's in-tile prefix, ctp = the
 // previous particle's, read by lane 0 only), written by the particle's thread,
-// its warp or the block.  Every thread of the block calls it (one barrier).
+// its warp or the block.  Every thread of the block calls it (one barrier:
+// the vote for ranges longer than BLOCK_RANGE).
 __device__ __forceinline__ void resample_particles(const FilterDev& fd, int t, int i, int rs,
                                                    int lo, int hi, double e0, double scale_r,
                                                    double ct, double ctp, int* nlong,
@@ -927,13 +937,7 @@ __device__ __forceinline__ void resample_particles(const FilterDev& fd, int t, i
     for (int jj = a + lane; jj < b; jj += 32) aout[jj] = who;
   }
   if (len > BLOCK_RANGE) longr[atomicAdd(nlong, 1)] = make_int3(prev, n, j);
-  if (__syncthreads_or(len > BLOCK_RANGE)) {
-    const int nl = *nlong;
-    for (int r = 0; r < nl; ++r) {
-      const int3 rg = longr[r];
-      for (int jj = rg.x + tid; jj < rg.y; jj += TILE) aout[jj] = rg.z;
-    }
-  }
+  if (__syncthreads_or(len > BLOCK_RANGE)) write_long_ranges(aout, *nlong, longr);
 }
 
 // No resampling after step i: carry the log-weights (lam = ell - M) and, with
@@ -946,68 +950,89 @@ __device__ __forceinline__ void carry_tile(const FilterDev& fd, int t, int i, do
   }
 }
 
-// Grid-stride over the tiles of the tile map: a block takes tiles q, q + G,
-// ... (G = the grid size, a multiple of the SM count), so the control block
-// is read once per block and filter rather than once per tile.
+// A block takes the tiles q, q + G, q + 2G, ... of the tile map (G = the grid
+// size, a multiple of the SM count) in chunks of up to RS_CHUNK tiles.  For a
+// chunk, every thread first issues the loads of its particle's in-tile prefix
+// in each tile, and lanes 2m and 2m + 1 of warp 0 read tile m's control block
+// and compute the counts at its two ends (tile_base, range_count), so the
+// dependent loads and FP64 operations of all the chunk's tiles overlap; then
+// the tiles are resampled (or carried) one after the other.  The previous
+// particle's prefix of a warp's lane 0 is the previous warp's last value,
+// passed through shared memory.
+constexpr int RS_CHUNK = 4;
+
 __global__ void __launch_bounds__(TILE, RESAMPLE_BLOCKS_PER_SM)
     k_resample(const FilterDev* __restrict__ fds, const int2* __restrict__ tmap, int ntiles) {
-  __shared__ int s_i, s_go, s_flag, s_lo, s_hi;
-  __shared__ int nlong[2];
-  __shared__ double s_M, s_e0, s_scale_r;
+  __shared__ int2 s_ft[RS_CHUNK];
+  __shared__ int s_i[RS_CHUNK], s_go[RS_CHUNK], s_flag[RS_CHUNK], s_lo[RS_CHUNK], s_hi[RS_CHUNK];
+  __shared__ int nlong[RS_CHUNK];
+  __shared__ double s_M[RS_CHUNK], s_e0[RS_CHUNK], s_sr[RS_CHUNK];
+  __shared__ double s_last[RS_CHUNK][WARPS];
   __shared__ int3 longr[2][TILE];
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  // threads 0 and 32 keep the control block of the last filter they saw
-  int c_filter = -1, c_i = 0, c_go = 0, c_flag = 0;
-  double c_u = 0.0, c_ratio = 0.0, c_S = 0.0, c_M = 0.0;
-  for (int q = blockIdx.x, it = 0; q < ntiles; q += gridDim.x, ++it) {
-    const int buf = it & 1;
-    const int2 ft = tmap[q];
-    const FilterDev& fd = fds[ft.x];
-    const int P = fd.P;
-    const int t = ft.y;
-    const int j = t * TILE + tid;
-    const int rs = fd.resampler;
-    // every input that does not depend on the control block is issued first
-    const double ct = j < P ? fd.ctil[j] : 0.0;
-    const double ctp = (lane == 0 && tid > 0 && j <= P) ? fd.ctil[j - 1] : 0.0;
-    if (tid == 0) nlong[buf] = 0;  // last used two tiles ago, behind two barriers
-    if (tid == 0 || tid == 32) {
-      if (ft.x != c_filter) {
-        const Ctl* ctl = fd.ctl;
-        c_filter = ft.x;
-        c_i = ldcg(&ctl->rs_step);
-        c_go = ldcg(&ctl->status) == ST_OK && c_i >= 1 && c_i < fd.T &&
-               ldcg(&ctl->step) == c_i + 1;
-        c_flag = ldcg(&ctl->rs_flag);
-        c_u = rs == RS_SYSTEMATIC ? ldcg(&ctl->u) : 0.0;
-        c_ratio = ldcg(&ctl->ratio);
-        c_S = ldcg(&ctl->S);
-        c_M = ldcg(&ctl->M);
+  const int w = tid >> 5;
+  const int G = gridDim.x;
+  int it = 0;  // resampled tiles so far: its parity picks the long-range list
+  for (int q0 = blockIdx.x; q0 < ntiles; q0 += RS_CHUNK * G) {
+    const int nq = min(RS_CHUNK, (ntiles - q0 + G - 1) / G);  // q0 + m G < ntiles for m < nq
+    double ct[RS_CHUNK];
+#pragma unroll
+    for (int m = 0; m < RS_CHUNK; ++m) {
+      ct[m] = 0.0;
+      if (m < nq) {
+        const int2 ft = tmap[q0 + m * G];
+        const FilterDev& fd = fds[ft.x];
+        const int j = ft.y * TILE + tid;
+        if (j < fd.P) ct[m] = fd.ctil[j];
+        if (lane == 31) s_last[m][w] = ct[m];
       }
+    }
+    if (tid < RS_CHUNK) nlong[tid] = 0;
+    if (tid < 2 * nq) {
+      const int m = tid >> 1, which = tid & 1;
+      const int2 ft = tmap[q0 + m * G];
+      const FilterDev& fd = fds[ft.x];
+      const Ctl* ctl = fd.ctl;
+      const int rs = fd.resampler;
+      const int i = ldcg(&ctl->rs_step);
+      const int go = ldcg(&ctl->status) == ST_OK && i >= 1 && i < fd.T && ldcg(&ctl->step) == i + 1;
+      const int flag = ldcg(&ctl->rs_flag);
+      const double u = rs == RS_SYSTEMATIC ? ldcg(&ctl->u) : 0.0;
+      const double ratio = ldcg(&ctl->ratio);
       double base = 0.0, scale = 0.0;
-      tile_base(fd, t, tid == 0 ? 0 : 1, c_S, &base, &scale);
-      const int n0 = (c_go && c_flag) ? range_count(fd, rs, base, c_ratio, c_u, c_i) : 0;
-      if (tid == 0) {
-        s_i = c_i;
-        s_go = c_go;
-        s_flag = c_flag;
-        s_M = c_M;
-        s_e0 = base * c_ratio - c_u;
-        s_scale_r = scale * c_ratio;
-        s_lo = n0;
+      tile_base(fd, ft.y, which, ldcg(&ctl->S), &base, &scale);
+      const int n0 = (go && flag) ? range_count(fd, rs, base, ratio, u, i) : 0;
+      if (which == 0) {
+        s_ft[m] = ft;
+        s_i[m] = i;
+        s_go[m] = go;
+        s_flag[m] = flag;
+        s_M[m] = ldcg(&ctl->M);
+        s_e0[m] = base * ratio - u;
+        s_sr[m] = scale * ratio;
+        s_lo[m] = n0;
       } else {
-        s_hi = n0;
+        s_hi[m] = n0;
       }
     }
     __syncthreads();
-    if (!s_go || !s_flag) {
-      if (s_go) carry_tile(fd, t, s_i, s_M);
-      __syncthreads();  // the shared values are rewritten for the next tile
-      continue;
+#pragma unroll
+    for (int m = 0; m < RS_CHUNK; ++m) {
+      if (m < nq) {
+        const int2 ft = s_ft[m];
+        const FilterDev& fd = fds[ft.x];
+        if (s_go[m] && s_flag[m]) {  // uniform over the block
+          const double ctp = (lane == 0 && w > 0) ? s_last[m][w - 1] : 0.0;
+          resample_particles(fd, ft.y, s_i[m], fd.resampler, s_lo[m], s_hi[m], s_e0[m], s_sr[m],
+                             ct[m], ctp, &nlong[m], longr[it & 1]);
+          ++it;
+        } else if (s_go[m]) {
+          carry_tile(fd, ft.y, s_i[m], s_M[m]);
+        }
+      }
     }
-    resample_particles(fd, t, s_i, rs, s_lo, s_hi, s_e0, s_scale_r, ct, ctp, &nlong[buf],
-                       longr[buf]);
+    __syncthreads();  // the chunk's shared values are rewritten by the next chunk
   }
 }
 
