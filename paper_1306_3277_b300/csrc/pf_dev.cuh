@@ -376,6 +376,33 @@ __device__ __forceinline__ double block_scan(double v, BlockScratch& sm, double*
   return w == 0 ? v : __dadd_rn(sm.wpre[w], v);
 }
 
+// Warp-level forms of the three canonical reductions for inputs held by the
+// lanes of one warp, the other warps' inputs being the neutral element (0 for
+// sums and scans, -inf for the max): block_max, block_sum and block_scan then
+// reduce the seven other warp totals to the neutral element, and x + 0 = x, so
+// these give the same bits with no block barrier.
+__device__ __forceinline__ double warp_max(double v) {
+  long long k = dkey(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) k = max(k, __shfl_xor_sync(0xffffffffu, k, o));
+  return dunkey(k);
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_scan(double v, double* total) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v = __dadd_rn(n, v);
+  }
+  *total = __shfl_sync(0xffffffffu, v, 31);
+  return v;
+}
+
 // L2-coherent loads for data written by other blocks of the same launch.
 template <typename T>
 __device__ __forceinline__ T ldcg(const T* p) {

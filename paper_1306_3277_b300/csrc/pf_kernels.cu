@@ -478,37 +478,64 @@ struct CombineScratch {
 // Combine the tile partials of group g: group max, tile scales g_t =
 // exp(M_t - M_g), inclusive scan of S_t g_t (tile bases = exclusive prefix),
 // group sum = scan total.  Returns true in every thread of the block that
-// finished the filter's last group.
+// finished the filter's last group.  With WARP, a group of at most 32 tiles is
+// combined by warp 0 alone, and the only group of a filter skips the group
+// ticket (it is the last by construction); both give the same bits as the
+// block path.
+template <bool WARP>
 __device__ bool combine_group(const FilterDev& fd, int g, CombineScratch& cs) {
   const int tid = threadIdx.x;
   const int t0 = g * GROUP;
   const int ntg = min(GROUP, fd.ntiles - t0);
-  double Mt = -INFINITY, St = 0.0, Qt = 0.0;
-  if (tid < ntg) {
-    Mt = ldcg(&fd.tp[t0 + tid].M);
-    St = ldcg(&fd.tp[t0 + tid].S);
-    Qt = ldcg(&fd.tp[t0 + tid].Q);
+  double Mg = -INFINITY, Sg = 0.0, Qg = 0.0;  // thread 0's values are stored
+  if (WARP && ntg <= 32) {
+    // warp 0 alone (warp_max / warp_scan / warp_sum: the same bits)
+    if (tid < 32) {
+      double Mt = -INFINITY, St = 0.0, Qt = 0.0;
+      if (tid < ntg) {
+        Mt = ldcg(&fd.tp[t0 + tid].M);
+        St = ldcg(&fd.tp[t0 + tid].S);
+        Qt = ldcg(&fd.tp[t0 + tid].Q);
+      }
+      Mg = warp_max(Mt);
+      const double gt = (Mt == -INFINITY) ? 0.0 : exp(Mt - Mg);
+      const double incl = warp_scan(St * gt, &Sg);
+      if (fd.mode == MODE_ADAPTIVE) Qg = warp_sum(Qt * (gt * gt));
+      const double before = __shfl_up_sync(0xffffffffu, incl, 1);
+      if (tid < ntg) {
+        fd.tp[t0 + tid].g = gt;
+        fd.tp[t0 + tid].base = tid == 0 ? 0.0 : before;
+      }
+    }
+  } else {
+    double Mt = -INFINITY, St = 0.0, Qt = 0.0;
+    if (tid < ntg) {
+      Mt = ldcg(&fd.tp[t0 + tid].M);
+      St = ldcg(&fd.tp[t0 + tid].S);
+      Qt = ldcg(&fd.tp[t0 + tid].Q);
+    }
+    Mg = block_max(Mt, cs.b);
+    const double gt = (Mt == -INFINITY) ? 0.0 : exp(Mt - Mg);
+    const double incl = block_scan(St * gt, cs.b, &Sg);
+    cs.incl[tid] = incl;
+    if (fd.mode == MODE_ADAPTIVE) Qg = block_sum(Qt * (gt * gt), cs.b);
+    __syncthreads();
+    if (tid < ntg) {
+      fd.tp[t0 + tid].g = gt;
+      fd.tp[t0 + tid].base = tid == 0 ? 0.0 : cs.incl[tid - 1];
+    }
   }
-  const double Mg = block_max(Mt, cs.b);
-  const double gt = (Mt == -INFINITY) ? 0.0 : exp(Mt - Mg);
-  const double Wt = St * gt;
-  double Sg;
-  const double incl = block_scan(Wt, cs.b, &Sg);
-  cs.incl[tid] = incl;
-  double Qg = 0.0;
-  if (fd.mode == MODE_ADAPTIVE) Qg = block_sum(Qt * (gt * gt), cs.b);
-  __syncthreads();
-  if (tid < ntg) {
-    fd.tp[t0 + tid].g = gt;
-    fd.tp[t0 + tid].base = tid == 0 ? 0.0 : cs.incl[tid - 1];
-  }
-  __syncthreads();
   if (tid == 0) {
     GroupPart& gp = fd.gp[g];
     gp.M = Mg;
     gp.S = Sg;
     gp.Q = Qg;
     gp.ticket = 0u;
+  }
+  // the only group of a filter is its last: no ticket, and the filter
+  // combine's warp 0 reads this group's partials back in thread 0
+  if (WARP && fd.ngroups == 1) return true;
+  if (tid == 0) {
     __threadfence();
     const unsigned old = atomicAdd(&fd.ctl->gticket, 1u);
     cs.last = (old == unsigned(fd.ngroups - 1));
@@ -519,28 +546,48 @@ __device__ bool combine_group(const FilterDev& fd, int g, CombineScratch& cs) {
   return last;
 }
 
-// Combine the groups of the filter and take the step's decisions.
+// Combine the groups of the filter and take the step's decisions (with WARP,
+// by warp 0 alone for at most 32 groups: the same bits).
+template <bool WARP>
 __device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs) {
   const int tid = threadIdx.x;
   const int ng = fd.ngroups;
-  double Mg = -INFINITY, Sg = 0.0, Qg = 0.0;
-  if (tid < ng) {
-    Mg = ldcg(&fd.gp[tid].M);
-    Sg = ldcg(&fd.gp[tid].S);
-    Qg = ldcg(&fd.gp[tid].Q);
-  }
-  const double M = block_max(Mg, cs.b);
-  const double G = (Mg == -INFINITY) ? 0.0 : exp(Mg - M);
-  const double W = Sg * G;
-  double S;
-  const double incl = block_scan(W, cs.b, &S);
-  cs.incl[tid] = incl;
-  double Q = 0.0;
-  if (fd.mode == MODE_ADAPTIVE) Q = block_sum(Qg * (G * G), cs.b);
-  __syncthreads();
-  if (tid < ng) {
-    fd.gp[tid].G = G;
-    fd.gp[tid].B = tid == 0 ? 0.0 : cs.incl[tid - 1];
+  double M, S, Q = 0.0;
+  if (WARP && ng <= 32) {
+    // warp 0 alone (the same bits as the block reductions)
+    if (tid >= 32) return;
+    double Mg = -INFINITY, Sg = 0.0, Qg = 0.0;
+    if (tid < ng) {
+      Mg = ldcg(&fd.gp[tid].M);
+      Sg = ldcg(&fd.gp[tid].S);
+      Qg = ldcg(&fd.gp[tid].Q);
+    }
+    M = warp_max(Mg);
+    const double G = (Mg == -INFINITY) ? 0.0 : exp(Mg - M);
+    const double incl = warp_scan(Sg * G, &S);
+    if (fd.mode == MODE_ADAPTIVE) Q = warp_sum(Qg * (G * G));
+    const double before = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (tid < ng) {
+      fd.gp[tid].G = G;
+      fd.gp[tid].B = tid == 0 ? 0.0 : before;
+    }
+  } else {
+    double Mg = -INFINITY, Sg = 0.0, Qg = 0.0;
+    if (tid < ng) {
+      Mg = ldcg(&fd.gp[tid].M);
+      Sg = ldcg(&fd.gp[tid].S);
+      Qg = ldcg(&fd.gp[tid].Q);
+    }
+    M = block_max(Mg, cs.b);
+    const double G = (Mg == -INFINITY) ? 0.0 : exp(Mg - M);
+    const double incl = block_scan(Sg * G, cs.b, &S);
+    cs.incl[tid] = incl;
+    if (fd.mode == MODE_ADAPTIVE) Q = block_sum(Qg * (G * G), cs.b);
+    __syncthreads();
+    if (tid < ng) {
+      fd.gp[tid].G = G;
+      fd.gp[tid].B = tid == 0 ? 0.0 : cs.incl[tid - 1];
+    }
   }
   if (tid == 0) {
     Ctl* c = fd.ctl;
@@ -761,7 +808,10 @@ __global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value))
   __syncthreads();
   if (!cs.last) return;
   __threadfence();
-  if (combine_group(fd, t / GROUP, cs)) combine_filter(fd, i, cs);
+  // the large states keep the block reductions only: the extra code of the
+  // warp paths measurably slows their register-bound main loop (same bits)
+  constexpr bool WARP = !(l96_kind(KIND) && N >= 16);
+  if (combine_group<WARP>(fd, t / GROUP, cs)) combine_filter<WARP>(fd, i, cs);
 }
 
 // Number of systematic targets j in [0, P) below cumulative weight b: target
@@ -1092,7 +1142,7 @@ __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __rest
     }
     cluster_sync();  // the tile partials of every CTA
     if (t == 0) {
-      if (combine_group(fd, 0, cs)) combine_filter(fd, i, cs);
+      if (combine_group<true>(fd, 0, cs)) combine_filter<true>(fd, i, cs);
     }
     cluster_sync();  // the group partials and the step's decisions
     if (tid == 0) {
