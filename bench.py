@@ -296,7 +296,7 @@ def secondary(pf, torch, dev):
     tp = time.perf_counter() - t0
     maxrel = max(abs(a - b) / abs(b) for a, b in zip(lls_b, lls_p))
     psteps = sum(w.P * w.T for w in ws)
-    # the autotuned split: small filters run whole, one block each
+    # the autotuned split: small filters run whole, one thread-block cluster each
     chosen = pf.pf_batch_autotune(fs, ths, ys, seeds)
     t0 = time.perf_counter()
     for _ in range(reps):
@@ -307,12 +307,25 @@ def secondary(pf, torch, dev):
                           "plain_evals_per_s": len(ws) / tp, "speedup": tp / tb,
                           "batched_particle_steps_per_s": psteps / tb,
                           "max_rel_loglik_diff_vs_plain": maxrel,
-                          "autotuned_one_block_max_particles": chosen,
+                          "autotuned_cluster_max_particles": chosen,
                           "autotuned_evals_per_s": len(ws) / ta,
                           "autotuned_speedup_vs_plain": tp / ta,
                           "autotuned_max_rel_loglik_diff_vs_plain": maxrel_a}
     for f in fs:
         f.destroy()
+    # one small filter alone: the tiled launches against one cluster per filter
+    w = W.windkessel(P=1024, T=100, prec=W.MIXED)
+    f = pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt)
+    small = {}
+    for name, cta in (("tiled", 0), ("cluster", 4096)):
+        pf.pf_batch_configure([f], cta)
+        pf.pf_batch_run([f], [w.theta], [w.y], [w.seed])
+        t0 = time.perf_counter()
+        for _ in range(20):
+            pf.pf_batch_run([f], [w.theta], [w.y], [w.seed])
+        small[name + "_ms_per_run"] = (time.perf_counter() - t0) / 20 * 1e3
+    f.destroy()
+    out["small_filter_" + w.name] = small
     return out
 
 
