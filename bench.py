@@ -168,6 +168,8 @@ def make_workload(args):
         return W.lorenz96_8(P=args.P or (1 << 14), T=args.T or 200, prec=W.MIXED)
     if args.config == "l96_8_fp64":
         return W.lorenz96_8(P=args.P or (1 << 14), T=args.T or 200, prec=W.FP64)
+    if args.config == "windkessel_mixed":
+        return W.windkessel(P=args.P or 1024, T=args.T or 100, prec=W.MIXED)
     return W.windkessel(P=args.P or 1024, T=args.T or 100)
 
 
@@ -541,7 +543,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="large",
-                    choices=["large", "l96_8", "l96_8_fp64", "windkessel", "serving",
+                    choices=["large", "l96_8", "l96_8_fp64", "windkessel", "windkessel_mixed",
+                             "serving",
                              "precision", "variants", "samplers"])
     ap.add_argument("--rates", default="250,500,1000,1500,2000", help="serving: offered rates")
     ap.add_argument("--duration", type=float, default=4.0, help="serving: seconds of arrivals")
