@@ -472,6 +472,7 @@ __device__ __forceinline__ double l96_weight(const FilterDev& fd, const R (&x)[N
 struct CombineScratch {
   BlockScratch b;
   double incl[TILE];
+  double gM, gS, gQ;  // thread 0's group partials, for a one-group filter's combine
   int last;
 };
 
@@ -498,7 +499,8 @@ __device__ bool combine_group(const FilterDev& fd, int g, CombineScratch& cs) {
         Qt = ldcg(&fd.tp[t0 + tid].Q);
       }
       Mg = warp_max(Mt);
-      const double gt = (Mt == -INFINITY) ? 0.0 : exp(Mt - Mg);
+      // exp(0) = 1 exactly: the maximal tile (and a one-tile group) skips the call
+      const double gt = (Mt == -INFINITY) ? 0.0 : (Mt == Mg ? 1.0 : exp(Mt - Mg));
       const double incl = warp_scan(St * gt, &Sg);
       if (fd.mode == MODE_ADAPTIVE) Qg = warp_sum(Qt * (gt * gt));
       const double before = __shfl_up_sync(0xffffffffu, incl, 1);
@@ -531,6 +533,9 @@ __device__ bool combine_group(const FilterDev& fd, int g, CombineScratch& cs) {
     gp.S = Sg;
     gp.Q = Qg;
     gp.ticket = 0u;
+    cs.gM = Mg;
+    cs.gS = Sg;
+    cs.gQ = Qg;
   }
   // the only group of a filter is its last: no ticket, and the filter
   // combine's warp 0 reads this group's partials back in thread 0
@@ -553,7 +558,17 @@ __device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs) {
   const int tid = threadIdx.x;
   const int ng = fd.ngroups;
   double M, S, Q = 0.0;
-  if (WARP && ng <= 32) {
+  if (WARP && ng == 1) {
+    // one group: M = M_g, G = exp(0) = 1, S = S_g, Q = Q_g, B = 0 -- what the
+    // reductions below give, without reading the partials back
+    if (tid != 0) return;
+    M = cs.gM;
+    const double G = (M == -INFINITY) ? 0.0 : 1.0;
+    S = cs.gS * G;
+    if (fd.mode == MODE_ADAPTIVE) Q = cs.gQ * (G * G);
+    fd.gp[0].G = G;
+    fd.gp[0].B = 0.0;
+  } else if (WARP && ng <= 32) {
     // warp 0 alone (the same bits as the block reductions)
     if (tid >= 32) return;
     double Mg = -INFINITY, Sg = 0.0, Qg = 0.0;
