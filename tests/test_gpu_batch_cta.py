@@ -88,7 +88,7 @@ def test_autotuner_choice_keeps_results_and_pmmh():
     finally:
         for f in fs:
             f.destroy()
-    # PMMH chains over one windkessel shape: tiled and one-block splits agree
+    # PMMH chains over one windkessel shape: tiled and cluster splits agree
     w = W.windkessel(P=512, T=40)
     spec = [(3, 1, 2.0, 0.9, 0.03, 0.0, math.inf), (0, 0), (3, 1, 2.0, 0.03, 0.002, 0.0, math.inf),
             (4, 2, 2.0, 0.01, 2.0, 3.0), (0, 0), (0, 0), (0, 0)]
