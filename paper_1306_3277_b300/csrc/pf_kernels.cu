@@ -916,13 +916,14 @@ __device__ __forceinline__ int mn_below(const FilterDev& fd, double e, int lo, i
 // and multinomial as strat_below / mn_below on C (P/S).  Only the counts use
 // FP64 (one fma per particle; ceilings and floors are taken on the bits).
 //
-// Barriers: one per chunk of tiles after their ranges and scaled bases are
-// prepared, one vote per resampled tile for very long offspring ranges, one at
-// the end of the chunk.  A particle's predecessor count comes from the
-// neighbouring lane (lane 0 recomputes it from the previous prefix); ranges
-// up to SHORT_RANGE are written by the particle's thread, up to BLOCK_RANGE by
-// its warp, longer ones by the whole block, so a tile that owns most of the
-// targets still writes them with coalesced stores.
+// Barriers: two per chunk of tiles (after their ranges and scaled bases are
+// prepared, after the counts), one vote per resampled tile for very long
+// offspring ranges, one at the end of the chunk.  A particle's predecessor
+// count comes from the neighbouring lane (lane 0's from the previous warp in
+// k_resample; the cluster path's lane 0 recomputes it from the previous
+// prefix); ranges up to SHORT_RANGE are written by the particle's thread, up
+// to BLOCK_RANGE by its warp, longer ones by the whole block, so a tile that
+// owns most of the targets still writes them with coalesced stores.
 constexpr int SHORT_RANGE = 16;
 constexpr int BLOCK_RANGE = 2048;
 constexpr int RESAMPLE_BLOCKS_PER_SM = 8;
@@ -962,34 +963,28 @@ __device__ __forceinline__ void write_long_ranges(int32_t* aout, int nl, const i
   }
 }
 
-// The particles of tile t take their targets [n_{k-1}, n_k): counts from the
-// scaled cumulative weights (ct = this particle's in-tile prefix, ctp = the
-// previous particle's, read by lane 0 only), written by the particle's thread,
-// its warp or the block.  Every thread of the block calls it (one barrier:
-// the vote for ranges longer than BLOCK_RANGE).
-__device__ __forceinline__ void resample_particles(const FilterDev& fd, int t, int i, int rs,
-                                                   int lo, int hi, double e0, double scale_r,
-                                                   double ct, double ctp, int* nlong,
-                                                   int3* longr) {
-  const int P = fd.P;
+// The count of targets below a particle's scaled cumulative weight (in-tile
+// prefix c), by scheme, clamped to its tile's target range [lo, hi].
+__device__ __forceinline__ int particle_count(const FilterDev& fd, int i, int rs, int lo, int hi,
+                                              double e0, double scale_r, double c) {
+  int n;
+  if (rs == RS_SYSTEMATIC) n = tile_targets_below(scale_r, c, e0);
+  else if (rs == RS_STRATIFIED) n = strat_below(fma(scale_r, c, e0), fd.seed, i, fd.P);
+  else n = mn_below(fd, fma(scale_r, c, e0), lo, hi);
+  return min(max(n, lo), hi);
+}
+
+// Particle j of tile t takes the targets [prev, n) as ancestor: written by its
+// thread, its warp or, for ranges longer than BLOCK_RANGE after a block vote,
+// the whole block.  Every thread of the block calls it (one barrier).
+__device__ __forceinline__ void write_offspring(const FilterDev& fd, int t, int i, int prev, int n,
+                                               bool valid, int* nlong, int3* longr) {
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int j0 = t * TILE;
   const int j = j0 + tid;
-  const int nvalid = min(TILE, P - j0);
-  auto count = [&](double c) -> int {
-    int n;
-    if (rs == RS_SYSTEMATIC) n = tile_targets_below(scale_r, c, e0);
-    else if (rs == RS_STRATIFIED) n = strat_below(fma(scale_r, c, e0), fd.seed, i, P);
-    else n = mn_below(fd, fma(scale_r, c, e0), lo, hi);
-    return min(max(n, lo), hi);
-  };
-  const bool valid = tid < nvalid;
-  const int n = (valid && tid != nvalid - 1) ? count(ct) : hi;
-  int prev = __shfl_up_sync(0xffffffffu, n, 1);
-  if (lane == 0) prev = tid == 0 ? lo : (valid ? count(ctp) : hi);
   const int len = valid ? n - prev : 0;
-  int32_t* aout = fd.anc + (fd.hist ? int64_t(i) * P : 0);
+  int32_t* aout = fd.anc + (fd.hist ? int64_t(i) * fd.P : 0);
   if (len > 0 && len <= SHORT_RANGE)
     for (int jj = prev; jj < n; ++jj) aout[jj] = j;
   unsigned wl = __ballot_sync(0xffffffffu, len > SHORT_RANGE && len <= BLOCK_RANGE);
@@ -1003,6 +998,24 @@ __device__ __forceinline__ void resample_particles(const FilterDev& fd, int t, i
   }
   if (len > BLOCK_RANGE) longr[atomicAdd(nlong, 1)] = make_int3(prev, n, j);
   if (__syncthreads_or(len > BLOCK_RANGE)) write_long_ranges(aout, *nlong, longr);
+}
+
+// The particles of tile t take their targets [n_{k-1}, n_k): counts from the
+// scaled cumulative weights (ct = this particle's in-tile prefix, ctp = the
+// previous particle's, read by lane 0 only, whose count it recomputes).
+__device__ __forceinline__ void resample_particles(const FilterDev& fd, int t, int i, int rs,
+                                                   int lo, int hi, double e0, double scale_r,
+                                                   double ct, double ctp, int* nlong,
+                                                   int3* longr) {
+  const int tid = threadIdx.x;
+  const int nvalid = min(TILE, fd.P - t * TILE);
+  const bool valid = tid < nvalid;
+  const int n = (valid && tid != nvalid - 1) ? particle_count(fd, i, rs, lo, hi, e0, scale_r, ct)
+                                              : hi;
+  int prev = __shfl_up_sync(0xffffffffu, n, 1);
+  if ((tid & 31) == 0)
+    prev = tid == 0 ? lo : (valid ? particle_count(fd, i, rs, lo, hi, e0, scale_r, ctp) : hi);
+  write_offspring(fd, t, i, prev, n, valid, nlong, longr);
 }
 
 // No resampling after step i: carry the log-weights (lam = ell - M) and, with
@@ -1021,9 +1034,10 @@ __device__ __forceinline__ void carry_tile(const FilterDev& fd, int t, int i, do
 // in each tile, and lanes 2m and 2m + 1 of warp 0 read tile m's control block
 // and compute the counts at its two ends (tile_base, range_count), so the
 // dependent loads and FP64 operations of all the chunk's tiles overlap; then
-// the tiles are resampled (or carried) one after the other.  The previous
-// particle's prefix of a warp's lane 0 is the previous warp's last value,
-// passed through shared memory.
+// every particle's count in every tile of the chunk is taken, and each warp's
+// last count passes through shared memory to the next warp's lane 0 (its
+// predecessor), so no lane recomputes a count; then the tiles' offspring are
+// written (or the tiles carried) one after the other.
 constexpr int RS_CHUNK = 4;
 
 __global__ void __launch_bounds__(TILE, RESAMPLE_BLOCKS_PER_SM)
@@ -1032,7 +1046,7 @@ __global__ void __launch_bounds__(TILE, RESAMPLE_BLOCKS_PER_SM)
   __shared__ int s_i[RS_CHUNK], s_go[RS_CHUNK], s_flag[RS_CHUNK], s_lo[RS_CHUNK], s_hi[RS_CHUNK];
   __shared__ int nlong[RS_CHUNK];
   __shared__ double s_M[RS_CHUNK], s_e0[RS_CHUNK], s_sr[RS_CHUNK];
-  __shared__ double s_last[RS_CHUNK][WARPS];
+  __shared__ int s_nlast[RS_CHUNK][WARPS];
   __shared__ int3 longr[2][TILE];
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -1050,7 +1064,6 @@ __global__ void __launch_bounds__(TILE, RESAMPLE_BLOCKS_PER_SM)
         const FilterDev& fd = fds[ft.x];
         const int j = ft.y * TILE + tid;
         if (j < fd.P) ct[m] = fd.ctil[j];
-        if (lane == 31) s_last[m][w] = ct[m];
       }
     }
     if (tid < RS_CHUNK) nlong[tid] = 0;
@@ -1082,15 +1095,34 @@ __global__ void __launch_bounds__(TILE, RESAMPLE_BLOCKS_PER_SM)
       }
     }
     __syncthreads();
+    // every particle's count in every tile of the chunk; each warp's last one
+    // goes through shared memory to the next warp's lane 0
+    int nn[RS_CHUNK];
+#pragma unroll
+    for (int m = 0; m < RS_CHUNK; ++m) {
+      nn[m] = 0;
+      if (m < nq && s_go[m] && s_flag[m]) {
+        const int2 ft = s_ft[m];
+        const FilterDev& fd = fds[ft.x];
+        const int nvalid = min(TILE, fd.P - ft.y * TILE);
+        nn[m] = (tid < nvalid && tid != nvalid - 1)
+                    ? particle_count(fd, s_i[m], fd.resampler, s_lo[m], s_hi[m], s_e0[m], s_sr[m],
+                                     ct[m])
+                    : s_hi[m];
+        if (lane == 31) s_nlast[m][w] = nn[m];
+      }
+    }
+    __syncthreads();
 #pragma unroll
     for (int m = 0; m < RS_CHUNK; ++m) {
       if (m < nq) {
         const int2 ft = s_ft[m];
         const FilterDev& fd = fds[ft.x];
         if (s_go[m] && s_flag[m]) {  // uniform over the block
-          const double ctp = (lane == 0 && w > 0) ? s_last[m][w - 1] : 0.0;
-          resample_particles(fd, ft.y, s_i[m], fd.resampler, s_lo[m], s_hi[m], s_e0[m], s_sr[m],
-                             ct[m], ctp, &nlong[m], longr[it & 1]);
+          int prev = __shfl_up_sync(0xffffffffu, nn[m], 1);
+          if (lane == 0) prev = w == 0 ? s_lo[m] : s_nlast[m][w - 1];
+          const bool valid = tid < min(TILE, fd.P - ft.y * TILE);
+          write_offspring(fd, ft.y, s_i[m], prev, nn[m], valid, &nlong[m], longr[it & 1]);
           ++it;
         } else if (s_go[m]) {
           carry_tile(fd, ft.y, s_i[m], s_M[m]);
