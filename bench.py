@@ -305,6 +305,16 @@ def secondary(pf, torch, dev):
         lls_a, _ = pf.pf_batch_run(fs, ths, ys, seeds)
     ta = (time.perf_counter() - t0) / reps
     maxrel_a = max(abs(a - b) / abs(b) for a, b in zip(lls_a, lls_p))
+    # the batch at each candidate cluster bound (what the autotuner compares)
+    sweep = {}
+    for bound in (0, 256, 512, 1024, 2048):
+        pf.pf_batch_configure(fs, bound)
+        pf.pf_batch_run(fs, ths, ys, seeds)  # plan + graph build
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            pf.pf_batch_run(fs, ths, ys, seeds)
+        sweep[str(bound)] = (time.perf_counter() - t0) / reps * 1e3
+    pf.pf_batch_configure(fs, chosen)
     out["batched_256"] = {"filters": len(ws), "batched_evals_per_s": len(ws) / tb,
                           "plain_evals_per_s": len(ws) / tp, "speedup": tp / tb,
                           "batched_particle_steps_per_s": psteps / tb,
@@ -312,22 +322,24 @@ def secondary(pf, torch, dev):
                           "autotuned_cluster_max_particles": chosen,
                           "autotuned_evals_per_s": len(ws) / ta,
                           "autotuned_speedup_vs_plain": tp / ta,
-                          "autotuned_max_rel_loglik_diff_vs_plain": maxrel_a}
+                          "autotuned_max_rel_loglik_diff_vs_plain": maxrel_a,
+                          "batch_ms_by_cluster_bound": sweep}
     for f in fs:
         f.destroy()
     # one small filter alone: the tiled launches against one cluster per filter
-    w = W.windkessel(P=1024, T=100, prec=W.MIXED)
-    f = pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt)
-    small = {}
-    for name, cta in (("tiled", 0), ("cluster", 4096)):
-        pf.pf_batch_configure([f], cta)
-        pf.pf_batch_run([f], [w.theta], [w.y], [w.seed])
-        t0 = time.perf_counter()
-        for _ in range(20):
+    for w in (W.windkessel(P=1024, T=100, prec=W.MIXED),
+              W.lorenz96_8(P=1024, T=200, prec=W.MIXED)):
+        f = pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt)
+        small = {}
+        for name, cta in (("tiled", 0), ("cluster", 4096)):
+            pf.pf_batch_configure([f], cta)
             pf.pf_batch_run([f], [w.theta], [w.y], [w.seed])
-        small[name + "_ms_per_run"] = (time.perf_counter() - t0) / 20 * 1e3
-    f.destroy()
-    out["small_filter_" + w.name] = small
+            t0 = time.perf_counter()
+            for _ in range(20):
+                pf.pf_batch_run([f], [w.theta], [w.y], [w.seed])
+            small[name + "_ms_per_run"] = (time.perf_counter() - t0) / 20 * 1e3
+        f.destroy()
+        out["small_filter_" + w.name] = small
     return out
 
 
