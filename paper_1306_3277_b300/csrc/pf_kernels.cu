@@ -782,11 +782,20 @@ __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i
   }
 }
 
+// The step kernels are launched with programmatic stream serialization: the
+// next one in the stream may be launched while this one drains, and waits
+// here, before its first read, until the previous grid has completed and its
+// writes are visible (a hardware wait; a no-op without the launch attribute).
+__device__ __forceinline__ void wait_prior_grid() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 template <int KIND, int N, typename R>
 __global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value)) k_propagate(const FilterDev* __restrict__ fds,
                                                     const int2* __restrict__ tmap) {
   __shared__ CombineScratch cs;
   __shared__ double ys[64];
+  wait_prior_grid();
   const int2 ft = tmap[blockIdx.x];
   const FilterDev& fd = fds[ft.x];
   Ctl* ctl = fd.ctl;
@@ -1052,6 +1061,7 @@ __global__ void __launch_bounds__(TILE, RESAMPLE_BLOCKS_PER_SM)
   const int lane = tid & 31;
   const int w = tid >> 5;
   const int G = gridDim.x;
+  wait_prior_grid();
   int it = 0;  // resampled tiles so far: its parity picks the long-range list
   for (int q0 = blockIdx.x; q0 < ntiles; q0 += RS_CHUNK * G) {
     const int nq = min(RS_CHUNK, (ntiles - q0 + G - 1) / G);  // q0 + m G < ntiles for m < nq
@@ -1435,6 +1445,23 @@ bool supported(int kind, int N, int prec) {
 
 enum { LAUNCH_INIT = 0, LAUNCH_PROPAGATE = 1, LAUNCH_CTA = 2 };
 
+// Launch with programmatic stream serialization (see wait_prior_grid): the
+// launch of a step kernel overlaps the drain of the one before it.
+template <typename... Params, typename... Args>
+static cudaError_t launch_chained(void (*kernel)(Params...), unsigned grid, cudaStream_t st,
+                                  Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(TILE);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <int KIND, int N, typename R>
 static cudaError_t launch_pair(int what, const FilterDev* fds, const int2* tmap, int nblocks,
                                cudaStream_t st) {
@@ -1442,7 +1469,9 @@ static cudaError_t launch_pair(int what, const FilterDev* fds, const int2* tmap,
   if (what == LAUNCH_INIT) {
     k_init<KIND, N, R><<<nblocks, TILE, 0, st>>>(fds, tmap);
   } else if (what == LAUNCH_PROPAGATE) {
-    k_propagate<KIND, N, R><<<nblocks, TILE, 0, st>>>(fds, tmap);
+    const cudaError_t e =
+        launch_chained(k_propagate<KIND, N, R>, unsigned(nblocks), st, fds, tmap);
+    if (e != cudaSuccess) return e;
   } else {
     // nblocks = filters x cluster size, what - LAUNCH_CTA = the cluster size
     const int cs_size = what - LAUNCH_CTA;
@@ -1538,7 +1567,8 @@ cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks,
       sms = 148;
   }
   const int grid = std::min(nblocks, sms * RESAMPLE_BLOCKS_PER_SM);
-  k_resample<<<grid, TILE, 0, st>>>(fds, tmap, nblocks);
+  const cudaError_t e = launch_chained(k_resample, unsigned(grid), st, fds, tmap, nblocks);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
