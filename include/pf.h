@@ -200,8 +200,9 @@ pf_status pf_batch_run(int32_t nfilt, pf_filter* const* f, const double* const* 
                        const double* const* y, const uint64_t* seeds, double* logliks,
                        int32_t* per_filter_status, void* cuda_stream);
 
-/* The batched form's split of a filter list between its two paths: filters
- * with at most cta_max_particles particles (and at most 2048, not resampled
+/* The batched form's split of a filter list between its two paths (a batched
+ * run of Algorithm 2 per filter either way): filters with at most
+ * cta_max_particles particles (and at most 2048, not resampled
  * multinomially) run whole, each on one thread-block cluster (one CTA per
  * tile of 256 particles, cluster barriers between the phases of a step), on a
  * side branch of the plan's CUDA graph -- no per-step launches or grid-wide
@@ -209,12 +210,19 @@ pf_status pf_batch_run(int32_t nfilt, pf_filter* const* f, const double* const* 
  * compute every filter with the same functions in the same order, so results
  * are bit-identical whatever the split.  0 (the default) sends every filter
  * to the tiled path.  Applies to pf_batch_run and pf_pmmh_run on this exact
- * filter list. */
+ * filter list (f: nfilt filters of the caller, the list's order matters); a
+ * cached plan for the list is rebuilt on its next use.  Host-only, no device
+ * work.  PF_EINVAL for nfilt <= 0, a NULL list or filter, a filter listed
+ * twice, or cta_max_particles < 0. */
 pf_status pf_batch_configure(int32_t nfilt, pf_filter* const* f, int64_t cta_max_particles);
 
-/* Autotuner of that split: runs the batch (inputs as for pf_batch_run) with
- * each candidate bound (0, 256, 512, 1024, 2048 particles), keeps the fastest
- * for the filter list and returns it in *chosen (may be NULL). */
+/* Autotuner of that split: runs the batch (inputs as for pf_batch_run, on the
+ * default stream, synchronously) with each candidate bound (0, 256, 512, 1024,
+ * 2048 particles), one untimed and two timed runs each on the host clock,
+ * keeps the fastest for the filter list (as pf_batch_configure would) and
+ * returns it in *chosen (may be NULL).  The filters' results are those of
+ * their last run, identical for every bound.  Errors: those of
+ * pf_batch_configure and pf_batch_run, returned as soon as one occurs. */
 pf_status pf_batch_autotune(int32_t nfilt, pf_filter* const* f, const double* const* theta,
                             const double* const* y, const uint64_t* seeds, int64_t* chosen);
 
