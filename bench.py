@@ -502,7 +502,8 @@ def run_variants(args):
 def run_samplers(args):
     """Throughput of the samplers built on the filter: marginal Metropolis-
     Hastings (64 chains, each iteration one batched launch of all chains'
-    filters) and SMC^2 (Algorithm 4, its O(T^2) rejuvenation runs included)."""
+    filters, split between the tiled and cluster paths by the autotuner) and
+    SMC^2 (Algorithm 4, its O(T^2) rejuvenation runs included)."""
     import torch
     import paper_1306_3277_b300 as pf
     torch.cuda.set_device(0)
@@ -514,17 +515,26 @@ def run_samplers(args):
     nc, niter = 64, 200
     fs = [pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt) for _ in range(nc)]
     th0 = np.tile(np.array(w.theta), (nc, 1))
+    # the chains' filters form one batch: the autotuner picks its tiled / cluster split
+    chosen = pf.pf_batch_autotune(fs, [w.theta] * nc, [w.y] * nc, list(range(1, nc + 1)))
     pf.pf_pmmh_run(fs, w.y, spec, th0, 5, 1)  # plan and graph
     t0 = time.perf_counter()
     _, _, acc = pf.pf_pmmh_run(fs, w.y, spec, th0, niter, 2)
     dt = time.perf_counter() - t0
+    pf.pf_batch_configure(fs, 0)  # the same chains on the tiled path alone
+    pf.pf_pmmh_run(fs, w.y, spec, th0, 5, 1)
+    t0 = time.perf_counter()
+    pf.pf_pmmh_run(fs, w.y, spec, th0, niter, 2)
+    dt_tiled = time.perf_counter() - t0
     for f in fs:
         f.destroy()
     out["pmmh_windkessel_P1024_T100_64chains"] = {
         "iterations": niter, "chains": nc, "seconds": dt,
         "chain_iterations_per_s": nc * (niter + 1) / dt,
         "particle_steps_per_s": nc * (niter + 1) * w.P * w.T / dt,
-        "acceptance": float(acc.sum()) / (nc * niter)}
+        "acceptance": float(acc.sum()) / (nc * niter),
+        "autotuned_cluster_max_particles": chosen,
+        "tiled_only_chain_iterations_per_s": nc * (niter + 1) / dt_tiled}
     w = W.windkessel(P=256, T=50)
     spec2 = [(0, 0), (0, 0), (3, 1, 2.0, 0.03, 0.005, 0.0, inf), (4, 2, 2.0, 0.01, 2.0, 3.0),
              (0, 0), (0, 0), (0, 0)]
