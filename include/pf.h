@@ -393,6 +393,15 @@ pf_status pf_measure_fma_peak(int32_t prec, double* flops_per_s, double* ms);
  * n < 0, n > 2^28 or a NULL array with n > 0; PF_ECUDA on a CUDA error. */
 pf_status pf_weight_exp(const double* d, double* w, int64_t n);
 
+/* Host-side fault injection for tests: the k-th next device allocation made
+ * for a filter (pf_create) or for a request the server admits fails as if
+ * the device were out of memory -- once; k = 0 disarms.  pf_create then
+ * returns PF_ENOMEM having freed what it had allocated, and the request is
+ * finished with PF_ENOMEM (pf_server_poll) while the server goes on.  The
+ * countdown is process-wide and shared by all threads.  PF_EINVAL for
+ * k < 0. */
+pf_status pf_debug_fail_allocation(int32_t k);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,6 +70,7 @@ def lib():
         L.pf_measure_fma_peak.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]
         L.pf_weight_exp.argtypes = [_vp, _vp, ctypes.c_int64]
+        L.pf_debug_fail_allocation.argtypes = [ctypes.c_int32]
         L.pf_pmmh_run.argtypes = [ctypes.c_int32, ctypes.POINTER(_vp), _vp,
                                   ctypes.POINTER(pf_param), _vp, ctypes.c_int32,
                                   ctypes.c_uint64, _vp, _vp, _vp, _vp]
@@ -89,7 +90,8 @@ def lib():
         L.pf_sample_path.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp, _vp]
         for name in ("pf_run", "pf_wait", "pf_destroy", "pf_create", "pf_batch_run",
                      "pf_profile_enable", "pf_profile_read", "pf_measure_fma_peak",
-                     "pf_run_range", "pf_sample_path", "pf_weight_exp"):
+                     "pf_run_range", "pf_sample_path", "pf_weight_exp",
+                     "pf_debug_fail_allocation"):
             getattr(L, name).restype = ctypes.c_int
         L.pf_run_noalloc.argtypes = [ctypes.POINTER(pf_model), ctypes.c_int64, ctypes.c_int32,
                                      ctypes.c_double, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp,
@@ -352,6 +354,12 @@ def pf_measure_fma_peak(prec):
     ms = ctypes.c_double()
     _check(lib().pf_measure_fma_peak(prec, ctypes.byref(f), ctypes.byref(ms)))
     return f.value
+
+
+def pf_debug_fail_allocation(k):
+    """Fault injection: the k-th next device allocation of a filter or a served
+    request fails as if the device were out of memory (once); 0 disarms."""
+    _check(lib().pf_debug_fail_allocation(k))
 
 
 def pf_weight_exp(d):

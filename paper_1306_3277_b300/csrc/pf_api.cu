@@ -2,6 +2,7 @@
 // creation, launch plans (descriptor tables, tile maps and one captured CUDA
 // graph per plan), single and batched runs.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -34,6 +35,26 @@ pf_status pfb::fail(pf_status st, const char* fmt, ...) {
 }
 
 extern "C" const char* pf_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// host-side fault injection: the k-th next device allocation of a filter or a
+// served request fails as if the device were out of memory
+// ---------------------------------------------------------------------------
+static std::atomic<int> g_fail_alloc_countdown{0};
+
+bool pfb::injected_alloc_failure() {
+  int k = g_fail_alloc_countdown.load();
+  while (k > 0) {
+    if (g_fail_alloc_countdown.compare_exchange_weak(k, k - 1)) return k == 1;
+  }
+  return false;
+}
+
+extern "C" pf_status pf_debug_fail_allocation(int32_t k) {
+  if (k < 0) return fail(PF_EINVAL, "k = %d < 0", k);
+  g_fail_alloc_countdown.store(k);
+  return PF_OK;
+}
 
 #define CK(call)                                                                          \
   do {                                                                                    \
@@ -141,6 +162,7 @@ extern "C" pf_status pf_create(const pf_model* m, int64_t P, int32_t T, double d
   cudaGetDevice(&f->device);
   auto alloc = [&](void** p, size_t n) -> bool {
     if (n == 0) return true;
+    if (injected_alloc_failure()) return false;
     return cudaMalloc(p, n) == cudaSuccess;
   };
   bool ok = cudaStreamCreateWithFlags(&f->own, cudaStreamNonBlocking) == cudaSuccess;

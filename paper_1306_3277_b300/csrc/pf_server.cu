@@ -98,6 +98,7 @@ bool alloc_request(pf_server* s, Request* r) {
   auto get = [&](size_t n) -> void* {
     if (n == 0) return nullptr;
     void* p = nullptr;
+    if (injected_alloc_failure()) return nullptr;
     if (cudaMallocFromPoolAsync(&p, n, s->pool, s->st) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
