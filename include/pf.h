@@ -402,6 +402,20 @@ pf_status pf_weight_exp(const double* d, double* w, int64_t n);
  * k < 0. */
 pf_status pf_debug_fail_allocation(int32_t k);
 
+/* Invariant counters of a checked build of this library (compiled with
+ * PF_CHECKED=1: libpf_b300_checked.so), the sanitizer substitute: the kernels
+ * count, instead of assuming, violations of the path's invariants.
+ *   counts[0]  ancestors read outside [0, P) (replaced by the particle's own
+ *              index, so every access stays in bounds)
+ *   counts[1]  particles whose propagated state is not finite
+ *   counts[2]  in-tile cumulative weights that are negative, NaN or decrease
+ *   counts[3]  offspring ranges that end before they start or leave [0, P]
+ * counts: host array of 4, owned by the caller, receives the counts since the
+ * last call (then zeroed); *checked (may be NULL) receives 1 in a checked
+ * build, 0 otherwise (whose counts are always 0).  Synchronous on the current
+ * device.  PF_EINVAL for NULL counts; PF_ECUDA on a CUDA error. */
+pf_status pf_debug_check_counts(uint64_t* counts, int32_t* checked);
+
 #ifdef __cplusplus
 }
 #endif

@@ -44,10 +44,11 @@ _vp = ctypes.c_void_p
 
 
 def lib():
-    """Load (building if stale) libpf_b300.so."""
+    """Load (building if stale) libpf_b300.so, or its checked build
+    libpf_b300_checked.so when PF_B300_CHECKED=1 is in the environment."""
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = _build.build(checked=os.environ.get("PF_B300_CHECKED") == "1")
         L = ctypes.CDLL(path)
         L.pf_theta_size.argtypes = [ctypes.c_int32]
         L.pf_theta_size.restype = ctypes.c_int32
@@ -71,6 +72,8 @@ def lib():
                                           ctypes.POINTER(ctypes.c_double)]
         L.pf_weight_exp.argtypes = [_vp, _vp, ctypes.c_int64]
         L.pf_debug_fail_allocation.argtypes = [ctypes.c_int32]
+        L.pf_debug_check_counts.argtypes = [ctypes.POINTER(ctypes.c_uint64),
+                                            ctypes.POINTER(ctypes.c_int32)]
         L.pf_pmmh_run.argtypes = [ctypes.c_int32, ctypes.POINTER(_vp), _vp,
                                   ctypes.POINTER(pf_param), _vp, ctypes.c_int32,
                                   ctypes.c_uint64, _vp, _vp, _vp, _vp]
@@ -91,7 +94,7 @@ def lib():
         for name in ("pf_run", "pf_wait", "pf_destroy", "pf_create", "pf_batch_run",
                      "pf_profile_enable", "pf_profile_read", "pf_measure_fma_peak",
                      "pf_run_range", "pf_sample_path", "pf_weight_exp",
-                     "pf_debug_fail_allocation"):
+                     "pf_debug_fail_allocation", "pf_debug_check_counts"):
             getattr(L, name).restype = ctypes.c_int
         L.pf_run_noalloc.argtypes = [ctypes.POINTER(pf_model), ctypes.c_int64, ctypes.c_int32,
                                      ctypes.c_double, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp,
@@ -360,6 +363,17 @@ def pf_debug_fail_allocation(k):
     """Fault injection: the k-th next device allocation of a filter or a served
     request fails as if the device were out of memory (once); 0 disarms."""
     _check(lib().pf_debug_fail_allocation(k))
+
+
+def pf_debug_check_counts():
+    """(checked build?, {invariant: violations since the last call}) -- the
+    counters of a PF_CHECKED=1 library (PF_B300_CHECKED=1); zeros otherwise."""
+    c = (ctypes.c_uint64 * 4)()
+    chk = ctypes.c_int32()
+    _check(lib().pf_debug_check_counts(c, ctypes.byref(chk)))
+    names = ("ancestor_out_of_range", "state_not_finite", "prefix_not_monotone",
+             "offspring_range_invalid")
+    return bool(chk.value), {n: int(v) for n, v in zip(names, c)}
 
 
 def pf_weight_exp(d):

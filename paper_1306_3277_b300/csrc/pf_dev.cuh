@@ -19,6 +19,17 @@ constexpr int WARPS = TILE / 32;
 constexpr int64_t MAX_P = int64_t(1) << 24;  // GROUP * GROUP * TILE
 constexpr int MAX_CLUSTER_TILES = 8;          // the portable thread-block cluster size
 
+// Checked builds (-DPF_CHECKED=1, libpf_b300_checked.so) count violations of
+// the path's invariants on the device instead of assuming them: an ancestor
+// outside [0, P) (then replaced by the particle's own index, so every access
+// stays in bounds), a non-finite propagated state, a decreasing in-tile
+// cumulative weight, an offspring range that ends before it starts or leaves
+// [0, P].  Nothing traps; pf_debug_check_counts reads the counts.
+#ifndef PF_CHECKED
+#define PF_CHECKED 0
+#endif
+enum { CHK_ANCESTOR = 0, CHK_STATE = 1, CHK_PREFIX = 2, CHK_RANGE = 3, CHK_KINDS = 4 };
+
 enum { KIND_WK = 0, KIND_L96 = 1, KIND_WKX = 2, KIND_L96W = 3 };
 __host__ __device__ constexpr bool wk_kind(int k) { return k == KIND_WK || k == KIND_WKX; }
 __host__ __device__ constexpr bool l96_kind(int k) { return k == KIND_L96 || k == KIND_L96W; }

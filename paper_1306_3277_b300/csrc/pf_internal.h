@@ -6,6 +6,9 @@
 
 namespace pfb {
 
+// The invariant-violation counters of a checked build (CHK_KINDS of them),
+// copied to out and zeroed (diagnostic).
+cudaError_t read_checks(unsigned long long* out);
 // The propagate kernels' weight exponential on n device values (diagnostic).
 cudaError_t launch_weight_exp(const double* d, double* w, int64_t n, cudaStream_t st);
 

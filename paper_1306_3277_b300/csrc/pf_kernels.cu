@@ -198,6 +198,10 @@ template <typename R> __device__ __forceinline__ R from_double(double v);
 template <> __device__ __forceinline__ double from_double<double>(double v) { return v; }
 template <> __device__ __forceinline__ float from_double<float>(double v) { return __double2float_rn(v); }
 
+// Invariant-violation counters of a checked build (see PF_CHECKED).
+__device__ unsigned long long g_checks[CHK_KINDS];
+__device__ __forceinline__ void check_failed(int kind) { atomicAdd(&g_checks[kind], 1ull); }
+
 // ---------------------------------------------------------------------------
 // Weight exponential w = e^d, d = ell - M <= 0, at FP64 accuracy with two
 // FP64 operations.  B300's FP64 unit runs at 1/64 of the FP32 rate and the
@@ -739,7 +743,13 @@ __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i
   }
   R x[N];
   if (valid) {
-    const int a = anc_identity ? j : (fd.hist ? fd.anc[int64_t(i - 1) * P + j] : a_spec);
+    int a = anc_identity ? j : (fd.hist ? fd.anc[int64_t(i - 1) * P + j] : a_spec);
+    if constexpr (PF_CHECKED) {
+      if (a < 0 || a >= P) {
+        check_failed(CHK_ANCESTOR);
+        a = j;
+      }
+    }
     const R* xin = static_cast<const R*>(fd.x[(i - 1) & 1]);
     R* xout = static_cast<R*>(fd.x[i & 1]);
 #pragma unroll
@@ -748,6 +758,12 @@ __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i
     else if constexpr (KIND == KIND_WKX) wkx_propagate<R>(fd, uint32_t(j), i, x[0], kc);
     else if constexpr (KIND == KIND_L96W) l96w_propagate<N, R>(fd, uint32_t(j), i, x);
     else l96_propagate<N, R>(fd, uint32_t(j), i, x);
+    if constexpr (PF_CHECKED) {
+      bool bad = false;
+#pragma unroll
+      for (int n = 0; n < N; ++n) bad |= !isfinite(x[n]);
+      if (bad) check_failed(CHK_STATE);
+    }
 #pragma unroll
     for (int n = 0; n < N; ++n) xout[int64_t(n) * P + j] = x[n];
   }
@@ -771,6 +787,14 @@ __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i
   const double w = (Mt == -INFINITY) ? 0.0 : exp_weight(ell - Mt);
   double St;
   const double c = block_scan(w, cs.b, &St);
+  if constexpr (PF_CHECKED) {
+    // neighbouring prefixes come from different addition trees, so they may
+    // differ by rounding (at most about ten ulp: five levels of sums of
+    // non-negative terms each); a larger decrease is a violation
+    const double before = __shfl_up_sync(0xffffffffu, c, 1);
+    if (j < P && (!(c >= 0.0) || ((tid & 31) > 0 && c < before * (1.0 - 0x1p-49))))
+      check_failed(CHK_PREFIX);
+  }
   if (j < P) fd.ctil[j] = c;
   double Qt = 0.0;
   if (fd.mode == MODE_ADAPTIVE) Qt = block_sum(w * w, cs.b);
@@ -992,6 +1016,7 @@ __device__ __forceinline__ void write_offspring(const FilterDev& fd, int t, int 
   const int lane = tid & 31;
   const int j0 = t * TILE;
   const int j = j0 + tid;
+  if (PF_CHECKED && valid && (n < prev || prev < 0 || n > fd.P)) check_failed(CHK_RANGE);
   const int len = valid ? n - prev : 0;
   int32_t* aout = fd.anc + (fd.hist ? int64_t(i) * fd.P : 0);
   if (len > 0 && len <= SHORT_RANGE)
@@ -1009,21 +1034,44 @@ __device__ __forceinline__ void write_offspring(const FilterDev& fd, int t, int 
   if (__syncthreads_or(len > BLOCK_RANGE)) write_long_ranges(aout, *nlong, longr);
 }
 
+// The running maximum of a count over the lanes of a warp.  The canonical
+// in-tile scans are monotone only up to rounding (neighbouring prefixes come
+// from different addition trees), so a count could in principle dip below
+// its predecessor's when a target falls inside that ulp; taking the running
+// maximum makes the offspring ranges disjoint and ordered by construction
+// (and changes nothing otherwise).
+__device__ __forceinline__ int warp_running_max(int n) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, n, o);
+    if (lane >= o) n = max(n, v);
+  }
+  return n;
+}
+
 // The particles of tile t take their targets [n_{k-1}, n_k): counts from the
-// scaled cumulative weights (ct = this particle's in-tile prefix, ctp = the
-// previous particle's, read by lane 0 only, whose count it recomputes).
+// scaled cumulative weights (ct = this particle's in-tile prefix), made
+// monotone over the tile (warp_running_max, then each warp's last count
+// through shared memory); nlast: WARPS ints of shared scratch.
 __device__ __forceinline__ void resample_particles(const FilterDev& fd, int t, int i, int rs,
                                                    int lo, int hi, double e0, double scale_r,
-                                                   double ct, double ctp, int* nlong,
+                                                   double ct, int* nlast, int* nlong,
                                                    int3* longr) {
   const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int w = tid >> 5;
   const int nvalid = min(TILE, fd.P - t * TILE);
   const bool valid = tid < nvalid;
-  const int n = (valid && tid != nvalid - 1) ? particle_count(fd, i, rs, lo, hi, e0, scale_r, ct)
-                                              : hi;
+  int n = (valid && tid != nvalid - 1) ? particle_count(fd, i, rs, lo, hi, e0, scale_r, ct) : hi;
+  n = warp_running_max(n);
+  if (lane == 31) nlast[w] = n;
+  __syncthreads();
+  int run = lo;
+  for (int q = 0; q < w; ++q) run = max(run, nlast[q]);
+  n = max(n, run);
   int prev = __shfl_up_sync(0xffffffffu, n, 1);
-  if ((tid & 31) == 0)
-    prev = tid == 0 ? lo : (valid ? particle_count(fd, i, rs, lo, hi, e0, scale_r, ctp) : hi);
+  if (lane == 0) prev = run;
   write_offspring(fd, t, i, prev, n, valid, nlong, longr);
 }
 
@@ -1119,6 +1167,7 @@ __global__ void __launch_bounds__(TILE, RESAMPLE_BLOCKS_PER_SM)
                     ? particle_count(fd, s_i[m], fd.resampler, s_lo[m], s_hi[m], s_e0[m], s_sr[m],
                                      ct[m])
                     : s_hi[m];
+        nn[m] = warp_running_max(nn[m]);
         if (lane == 31) s_nlast[m][w] = nn[m];
       }
     }
@@ -1129,8 +1178,12 @@ __global__ void __launch_bounds__(TILE, RESAMPLE_BLOCKS_PER_SM)
         const int2 ft = s_ft[m];
         const FilterDev& fd = fds[ft.x];
         if (s_go[m] && s_flag[m]) {  // uniform over the block
+          // the counts of the warps before this one bound this warp's below
+          int run = s_lo[m];
+          for (int q = 0; q < w; ++q) run = max(run, s_nlast[m][q]);
+          nn[m] = max(nn[m], run);
           int prev = __shfl_up_sync(0xffffffffu, nn[m], 1);
-          if (lane == 0) prev = w == 0 ? s_lo[m] : s_nlast[m][w - 1];
+          if (lane == 0) prev = run;
           const bool valid = tid < min(TILE, fd.P - ft.y * TILE);
           write_offspring(fd, ft.y, s_i[m], prev, nn[m], valid, &nlong[m], longr[it & 1]);
           ++it;
@@ -1171,12 +1224,12 @@ __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __rest
   __shared__ CombineScratch cs;
   __shared__ double ys[64];
   __shared__ int s_step, s_ok, s_anc_identity, s_lam_zero, s_go, s_flag, s_lo, s_hi, nlong;
+  __shared__ int s_nlast[WARPS];
   __shared__ double s_cw, s_M, s_u, s_ratio, s_S, s_e0, s_scale_r;
   __shared__ int3 longr[TILE];
   const FilterDev& fd = fds[list[blockIdx.x / cs_size]];
   const int t = blockIdx.x % cs_size;
   const int tid = threadIdx.x;
-  const int lane = tid & 31;
   const int P = fd.P, T = fd.T, rs = fd.resampler;
   const bool mine = t < fd.ntiles;
   if (mine) init_tile<KIND, N, R>(fd, t);
@@ -1220,7 +1273,6 @@ __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __rest
       } else {
         const int j = t * TILE + tid;
         const double ct = j < P ? fd.ctil[j] : 0.0;
-        const double ctp = (lane == 0 && tid > 0 && j <= P) ? fd.ctil[j - 1] : 0.0;
         if (tid == 0 || tid == 32) {
           double base = 0.0, scale = 0.0;
           tile_base(fd, t, tid == 0 ? 0 : 1, s_S, &base, &scale);
@@ -1234,7 +1286,7 @@ __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __rest
           }
         }
         __syncthreads();
-        resample_particles(fd, t, i, rs, s_lo, s_hi, s_e0, s_scale_r, ct, ctp, &nlong, longr);
+        resample_particles(fd, t, i, rs, s_lo, s_hi, s_e0, s_scale_r, ct, s_nlast, &nlong, longr);
       }
     }
     cluster_sync();  // the ancestors and carried weights of the next step
@@ -1522,6 +1574,14 @@ static cudaError_t dispatch(int init, int kind, int N, int prec, const FilterDev
 #undef PF_CASE
   }
   return cudaErrorInvalidValue;
+}
+
+// The checked build's counters, then zeroed.
+cudaError_t read_checks(unsigned long long* out) {
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_checks, sizeof(g_checks));
+  if (e != cudaSuccess) return e;
+  const unsigned long long zero[CHK_KINDS] = {};
+  return cudaMemcpyToSymbol(g_checks, zero, sizeof(zero));
 }
 
 // The weight exponential on n given arguments (diagnostic entry point).

@@ -1,8 +1,8 @@
 // pf_peak.cu -- diagnostics: the measured fused multiply-add throughput of this
 // GPU, FP32 and FP64 (the roofline denominators of the filter's kernels, which
-// are FP32 and FP64 ALU work, not a tensor contraction), and the propagate
-// kernels' weight exponential on given arguments.  Neither has a counterpart
-// in the paper.
+// are FP32 and FP64 ALU work, not a tensor contraction), the propagate
+// kernels' weight exponential on given arguments, and the invariant counters
+// of a checked build.  None has a counterpart in the paper.
 #include <algorithm>
 #include <type_traits>
 #include <cuda_runtime.h>
@@ -154,5 +154,15 @@ extern "C" pf_status pf_weight_exp(const double* d, double* w, int64_t n) {
   if (e == cudaSuccess) e = cudaMemcpy(w, buf + n, bytes, cudaMemcpyDeviceToHost);
   cudaFree(buf);
   if (e != cudaSuccess) return pfb::fail(PF_ECUDA, "weight exponential: %s", cudaGetErrorString(e));
+  return PF_OK;
+}
+
+extern "C" pf_status pf_debug_check_counts(uint64_t* counts, int32_t* checked) {
+  if (!counts) return pfb::fail(PF_EINVAL, "counts is NULL");
+  unsigned long long c[pfb::CHK_KINDS];
+  const cudaError_t e = pfb::read_checks(c);
+  if (e != cudaSuccess) return pfb::fail(PF_ECUDA, "check counters: %s", cudaGetErrorString(e));
+  for (int k = 0; k < pfb::CHK_KINDS; ++k) counts[k] = c[k];
+  if (checked) *checked = PF_CHECKED;
   return PF_OK;
 }
