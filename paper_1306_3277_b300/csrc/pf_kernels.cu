@@ -1042,6 +1042,9 @@ __device__ __forceinline__ void write_offspring(const FilterDev& fd, int t, int 
 // (and changes nothing otherwise).
 __device__ __forceinline__ int warp_running_max(int n) {
   const int lane = threadIdx.x & 31;
+  // nearly always the counts are monotone already: one shuffle and a vote
+  const int up = __shfl_up_sync(0xffffffffu, n, 1);
+  if (!__any_sync(0xffffffffu, lane > 0 && n < up)) return n;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int v = __shfl_up_sync(0xffffffffu, n, o);
