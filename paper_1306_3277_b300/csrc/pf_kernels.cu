@@ -1,13 +1,15 @@
 // pf_kernels.cu -- sm_103a kernels of the bootstrap particle filter
 // (arXiv 1306.3277, Algorithm 2) and their host-side launchers.
 //
-// One step i of one filter is two launches over its tiles of TILE particles:
+// One step i of one filter is two launches over its tiles of TILE particles,
+// chained by programmatic dependent launch:
 //   k_propagate  gather x(t_{i-1}) at the ancestors, propagate to t_i (the
 //                windkessel's Euler or exact transition, Lorenz '96 RK4
 //                substeps with additive or in-step Wiener noise), weight with
 //                y(t_i) in FP64 (skipped at a step without an observation),
 //                then per tile the max, the inclusive prefix of
-//                exp(ell - M_tile) and its total.  The last tile of each
+//                exp(ell - M_tile) (exp_weight: double-float on the FP32
+//                unit) and its total.  The last tile of each
 //                group of GROUP tiles combines the group; the last group
 //                combines the filter: max, scaled sums, likelihood increment,
 //                ESS test, resampling uniform.
@@ -17,6 +19,8 @@
 //                range written out by its thread, its warp or its block.
 // The multinomial scheme adds three small kernels between the two (its
 // sorted targets); the path sample adds a pick, a trace and a copy kernel.
+// Small filters of a batch may instead run whole, each on one thread-block
+// cluster (k_filter_cluster), through the same per-tile functions.
 // Any number of filters share a launch: the tile map lists (filter, tile)
 // pairs, and every reduction is per tile / group / filter in a fixed order,
 // so a filter's result does not depend on what else is in the launch.
@@ -952,9 +956,9 @@ __device__ __forceinline__ int mn_below(const FilterDev& fd, double e, int lo, i
 // Barriers: two per chunk of tiles (after their ranges and scaled bases are
 // prepared, after the counts), one vote per resampled tile for very long
 // offspring ranges, one at the end of the chunk.  A particle's predecessor
-// count comes from the neighbouring lane (lane 0's from the previous warp in
-// k_resample; the cluster path's lane 0 recomputes it from the previous
-// prefix); ranges up to SHORT_RANGE are written by the particle's thread, up
+// count comes from the neighbouring lane (lane 0's from the running maximum
+// of the earlier warps' last counts, through shared memory); ranges up to
+// SHORT_RANGE are written by the particle's thread, up
 // to BLOCK_RANGE by its warp, longer ones by the whole block, so a tile that
 // owns most of the targets still writes them with coalesced stores.
 constexpr int SHORT_RANGE = 16;
