@@ -90,6 +90,15 @@ struct pf_server {
   cudaEvent_t ev[2] = {nullptr, nullptr};
   bool ev_live[2] = {false, false};
   std::vector<Request*> launched[2];  // requests in slots as of each in-flight iteration
+  // the descriptor table and tile map on the device stay valid while no slot
+  // is filled or freed and no new filter needs its initial draw
+  bool map_dirty = true;
+  struct Seg {
+    int kind, N, prec;
+    size_t off, n;
+  };
+  std::vector<Seg> run_seg;  // the running filters' tile-map segments, by model class
+  size_t n_run = 0;
 };
 
 namespace {
@@ -183,6 +192,7 @@ void retire(pf_server* s, int parity) {
       s->used -= r->bytes;
       s->slots[k] = nullptr;
       r->slot = -1;
+      s->map_dirty = true;
       finish(s, r);
     }
   }
@@ -245,69 +255,73 @@ void scheduler(pf_server* s) {
       aoff += (r->y.size() * 8 + 255) & ~size_t(255);
       r->fresh = true;
     }
-    // descriptors and tile map of this iteration:
-    // [running tiles by class | new tiles by class]
-    FilterDev* hf = s->h_fds[parity];
-    std::map<std::tuple<int, int, int>, std::vector<int2>> run_cls, new_cls;
-    for (int k = 0; k < s->max_slots; ++k) {
-      Request* r = s->slots[k];
-      if (!r) {
-        memset(&hf[k], 0, sizeof(FilterDev));
+    if (!admitted.empty()) s->map_dirty = true;
+    std::vector<pf_server::Seg> new_seg;
+    if (s->map_dirty) {
+      // descriptors and tile map of this iteration:
+      // [running tiles by class | new tiles by class]
+      FilterDev* hf = s->h_fds[parity];
+      std::map<std::tuple<int, int, int>, std::vector<int2>> run_cls, new_cls;
+      for (int k = 0; k < s->max_slots; ++k) {
+        Request* r = s->slots[k];
+        if (!r) {
+          memset(&hf[k], 0, sizeof(FilterDev));
+          continue;
+        }
+        hf[k] = r->desc;
+        auto key = std::make_tuple(r->m.kind, r->m.N, r->m.prec);
+        for (int t = 0; t < r->sh.ntiles; ++t) {
+          run_cls[key].push_back(make_int2(k, t));
+          if (r->fresh) new_cls[key].push_back(make_int2(k, t));
+        }
+      }
+      size_t ntm = 0;
+      for (auto& kv : run_cls) ntm += kv.second.size();
+      for (auto& kv : new_cls) ntm += kv.second.size();
+      if (ntm == 0) {  // nothing running: drain the other parity and wait for work
+        retire(s, parity ^ 1);
         continue;
       }
-      hf[k] = r->desc;
-      auto key = std::make_tuple(r->m.kind, r->m.N, r->m.prec);
-      for (int t = 0; t < r->sh.ntiles; ++t) {
-        run_cls[key].push_back(make_int2(k, t));
-        if (r->fresh) new_cls[key].push_back(make_int2(k, t));
+      if (ntm > s->tmap_cap) {  // grow the staging copies and the device map (rare)
+        cudaStreamSynchronize(s->st);
+        for (int q = 0; q < 2; ++q) {
+          if (s->h_tmap[q]) cudaFreeHost(s->h_tmap[q]);
+          s->h_tmap[q] = nullptr;
+          cudaMallocHost((void**)&s->h_tmap[q], sizeof(int2) * ntm * 2);
+        }
+        if (s->d_tmap) cudaFree(s->d_tmap);
+        s->d_tmap = nullptr;
+        cudaMalloc((void**)&s->d_tmap, sizeof(int2) * ntm * 2);
+        s->tmap_cap = ntm * 2;
       }
-    }
-    size_t ntm = 0;
-    for (auto& kv : run_cls) ntm += kv.second.size();
-    for (auto& kv : new_cls) ntm += kv.second.size();
-    if (ntm == 0) {  // nothing running: drain the other parity and wait for work
-      retire(s, parity ^ 1);
-      continue;
-    }
-    if (ntm > s->tmap_cap) {  // grow the staging copies and the device map (rare)
-      cudaStreamSynchronize(s->st);
-      for (int q = 0; q < 2; ++q) {
-        if (s->h_tmap[q]) cudaFreeHost(s->h_tmap[q]);
-        s->h_tmap[q] = nullptr;
-        cudaMallocHost((void**)&s->h_tmap[q], sizeof(int2) * ntm * 2);
+      int2* tm = s->h_tmap[parity];
+      s->run_seg.clear();
+      size_t off = 0;
+      for (auto& kv : run_cls) {
+        memcpy(tm + off, kv.second.data(), kv.second.size() * sizeof(int2));
+        s->run_seg.push_back({std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                              off, kv.second.size()});
+        off += kv.second.size();
       }
-      if (s->d_tmap) cudaFree(s->d_tmap);
-      s->d_tmap = nullptr;
-      cudaMalloc((void**)&s->d_tmap, sizeof(int2) * ntm * 2);
-      s->tmap_cap = ntm * 2;
+      s->n_run = off;
+      for (auto& kv : new_cls) {
+        memcpy(tm + off, kv.second.data(), kv.second.size() * sizeof(int2));
+        new_seg.push_back({std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                           off, kv.second.size()});
+        off += kv.second.size();
+      }
+      cudaMemcpyAsync(s->d_fds, hf, sizeof(FilterDev) * s->max_slots, cudaMemcpyHostToDevice,
+                      s->st);
+      cudaMemcpyAsync(s->d_tmap, tm, sizeof(int2) * off, cudaMemcpyHostToDevice, s->st);
+      // the next iteration keeps this map unless the new filters (whose init
+      // tiles are in it) or a slot change make it stale
+      s->map_dirty = !new_seg.empty();
     }
-    int2* tm = s->h_tmap[parity];
-    struct Seg {
-      int kind, N, prec;
-      size_t off, n;
-    };
-    std::vector<Seg> run_seg, new_seg;
-    size_t off = 0;
-    for (auto& kv : run_cls) {
-      memcpy(tm + off, kv.second.data(), kv.second.size() * sizeof(int2));
-      run_seg.push_back({std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), off,
-                         kv.second.size()});
-      off += kv.second.size();
-    }
-    const size_t n_run = off;
-    for (auto& kv : new_cls) {
-      memcpy(tm + off, kv.second.data(), kv.second.size() * sizeof(int2));
-      new_seg.push_back({std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), off,
-                         kv.second.size()});
-      off += kv.second.size();
-    }
-    cudaMemcpyAsync(s->d_fds, hf, sizeof(FilterDev) * s->max_slots, cudaMemcpyHostToDevice, s->st);
-    cudaMemcpyAsync(s->d_tmap, tm, sizeof(int2) * off, cudaMemcpyHostToDevice, s->st);
-    for (const Seg& g : new_seg)
+    for (const pf_server::Seg& g : new_seg)
       launch_init(g.kind, g.N, g.prec, s->d_fds, s->d_tmap + g.off, int(g.n), s->st);
-    for (const Seg& g : run_seg)
+    for (const pf_server::Seg& g : s->run_seg)
       launch_propagate(g.kind, g.N, g.prec, s->d_fds, s->d_tmap + g.off, int(g.n), s->st);
-    launch_resample(s->d_fds, s->d_tmap, int(n_run), s->st);
+    launch_resample(s->d_fds, s->d_tmap, int(s->n_run), s->st);
     double* dres = s->d_res + size_t(parity) * 3 * s->max_slots;
     launch_results(s->d_fds, s->max_slots, dres, s->st);
     cudaMemcpyAsync(s->h_res[parity], dres, sizeof(double) * 3 * s->max_slots,
