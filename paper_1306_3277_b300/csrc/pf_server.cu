@@ -9,7 +9,10 @@
 //      stream-ordered memory pool, their y from a pinned staging arena;
 //   3. launches, over the tiles of every admitted filter, the init kernel for
 //      the new ones, then one propagate launch per model class and one
-//      resample launch, so every running filter advances one observation.
+//      resample launch, so every running filter advances one observation;
+//      the descriptor table and tile map are uploaded only when a slot
+//      changed, and results are copied back only by iterations that launch
+//      some filter's last observation or every RESULTS_EVERY-th one.
 // The same kernels and per-filter reduction order as pf_run are used, so a
 // request's log-likelihood is bit-identical to pf_run of the same request.
 #include <chrono>
@@ -51,6 +54,7 @@ struct Request {
   // while running
   int slot = -1;
   bool fresh = false;
+  int32_t launched_steps = 0;  // observations launched so far
   std::vector<void*> bufs;
   FilterDev desc{};
   // result
@@ -99,7 +103,14 @@ struct pf_server {
   };
   std::vector<Seg> run_seg;  // the running filters' tile-map segments, by model class
   size_t n_run = 0;
+  int64_t iter = 0;
 };
+
+// Results are fetched (the results kernel and a copy back) only by iterations
+// that launch some filter's last observation, and by every RESULTS_EVERY-th
+// iteration, which finds the filters that degenerated early (their kernels
+// are no-ops until then).
+constexpr int RESULTS_EVERY = 32;
 
 namespace {
 
@@ -322,15 +333,21 @@ void scheduler(pf_server* s) {
     for (const pf_server::Seg& g : s->run_seg)
       launch_propagate(g.kind, g.N, g.prec, s->d_fds, s->d_tmap + g.off, int(g.n), s->st);
     launch_resample(s->d_fds, s->d_tmap, int(s->n_run), s->st);
-    double* dres = s->d_res + size_t(parity) * 3 * s->max_slots;
-    launch_results(s->d_fds, s->max_slots, dres, s->st);
-    cudaMemcpyAsync(s->h_res[parity], dres, sizeof(double) * 3 * s->max_slots,
-                    cudaMemcpyDeviceToHost, s->st);
-    cudaEventRecord(s->ev[parity], s->st);
+    bool fetch = s->iter % RESULTS_EVERY == 0;
+    for (Request* r : s->slots)
+      if (r && ++r->launched_steps >= r->T) fetch = true;
+    if (fetch) {
+      double* dres = s->d_res + size_t(parity) * 3 * s->max_slots;
+      launch_results(s->d_fds, s->max_slots, dres, s->st);
+      cudaMemcpyAsync(s->h_res[parity], dres, sizeof(double) * 3 * s->max_slots,
+                      cudaMemcpyDeviceToHost, s->st);
+    }
+    cudaEventRecord(s->ev[parity], s->st);  // also guards this parity's staging buffers
     s->ev_live[parity] = true;
+    s->iter += 1;
     for (Request* r : s->slots)
       if (r) {
-        s->launched[parity].push_back(r);
+        if (fetch) s->launched[parity].push_back(r);  // retire() reads their results
         r->fresh = false;
       }
     {
