@@ -26,6 +26,8 @@
  * Precision: PF_FP64 computes everything in FP64.  PF_MIXED keeps the state,
  * the integrator and the process noise in FP32 and the observation
  * log-weights, log-sum-exp, cumulative-weight scan and likelihood in FP64.
+ * In both, the weight exponential exp(ell - M) is evaluated on the FP32 unit
+ * in double-float arithmetic to about 2^-52 relative (pf_weight_exp).
  *
  * Random numbers: Philox4x32-10 keyed by the 64-bit seed, counter
  * (particle, step, purpose << 16 | block, 0), Box-Muller normals.  A run is a
@@ -54,7 +56,7 @@ typedef enum {
   PF_ENOMEM = 2,       /* device allocation failed / over the memory budget  */
   PF_ECUDA = 3,        /* a CUDA runtime call failed                         */
   PF_EDEGENERATE = 4,  /* every particle weight was zero or not a number     */
-  PF_ETIMEOUT = 5,     /* a bounded wait ran out                             */
+  PF_ETIMEOUT = 5,     /* a bounded wait ran out (reserved: no kernel waits) */
   PF_EBUSY = 6         /* result not ready / no capacity right now           */
 } pf_status;
 
