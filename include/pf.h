@@ -411,6 +411,7 @@ pf_status pf_debug_fail_allocation(int32_t k);
  *              index, so every access stays in bounds)
  *   counts[1]  particles whose propagated state is not finite
  *   counts[2]  in-tile cumulative weights that are negative, NaN or decrease
+ *              by more than 2^-49 relative (a scan's rounding stays below it)
  *   counts[3]  offspring ranges that end before they start or leave [0, P]
  * counts: host array of 4, owned by the caller, receives the counts since the
  * last call (then zeroed); *checked (may be NULL) receives 1 in a checked
