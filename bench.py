@@ -225,6 +225,7 @@ def run_reference(args):
         return 0
     w = make_workload(args)
     P_s, T_s = oracle_sample(w)
+    P_s = max(P_s // 4, 1)  # a quarter of the baseline sample per step: K steps stay short
     for _ in range(args.warmup):
         cpu_oracle_rate(w, max(P_s // 16, 1), 1)
     secs = []
