@@ -500,6 +500,46 @@ def run_variants(args):
     return 0
 
 
+def run_batched(args):
+    """The batched form on its own: 256 uneven filters (Lorenz '96 N=8 and
+    windkessel, P 2^8..2^14, T 50..500, mixed precision) as one plan, the
+    small ones on thread-block clusters up to --cluster-bound particles (0: all
+    tiled).  K timed batch runs after W warm-ups; unless --no-secondary, the
+    same filters one pf_run at a time for comparison."""
+    import torch
+    import paper_1306_3277_b300 as pf
+    torch.cuda.set_device(0)
+    ws = W.batched()
+    fs = [pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt) for w in ws]
+    ths, ys, seeds = [w.theta for w in ws], [w.y for w in ws], [w.seed for w in ws]
+    pf.pf_batch_configure(fs, args.cluster_bound)
+    for _ in range(max(args.warmup, 1)):  # the first run builds the plan and its graph
+        pf.pf_batch_run(fs, ths, ys, seeds)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        lls, sts = pf.pf_batch_run(fs, ths, ys, seeds)
+    tb = (time.perf_counter() - t0) / args.steps
+    psteps = sum(w.P * w.T for w in ws)
+    line = {"metric": "batched evaluations/s", "value": len(ws) / tb, "unit": "evals/s",
+            "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_batch": tb * 1e3,
+            "particle_steps_per_s": psteps / tb, "filters": len(ws),
+            "cluster_bound": args.cluster_bound,
+            "degenerate": int(sum(1 for st in sts if int(st) != 0))}
+    if not args.no_secondary:
+        for f, w in zip(fs, ws):  # the single-filter plans
+            f.run(w.theta, w.y, w.seed)
+        t0 = time.perf_counter()
+        lp = [f.run(w.theta, w.y, w.seed)[1] for f, w in zip(fs, ws)]
+        tp = time.perf_counter() - t0
+        line["plain_evals_per_s"] = len(ws) / tp
+        line["speedup"] = tp / tb
+        line["max_rel_loglik_diff_vs_plain"] = max(abs(a - b) / abs(b) for a, b in zip(lls, lp))
+    for f in fs:
+        f.destroy()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_samplers(args):
     """Throughput of the samplers built on the filter: marginal Metropolis-
     Hastings (64 chains, each iteration one batched launch of all chains'
@@ -567,8 +607,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="large",
                     choices=["large", "l96_8", "l96_8_fp64", "windkessel", "windkessel_mixed",
-                             "serving",
+                             "serving", "batched",
                              "precision", "variants", "samplers"])
+    ap.add_argument("--cluster-bound", type=int, default=0,
+                    help="batched: largest filter (particles) run on one thread-block cluster")
     ap.add_argument("--rates", default="250,500,1000,1500,2000", help="serving: offered rates")
     ap.add_argument("--duration", type=float, default=4.0, help="serving: seconds of arrivals")
     ap.add_argument("--drain", type=float, default=20.0, help="serving: extra seconds to finish")
@@ -593,6 +635,8 @@ def main():
         return run_variants(args)
     if args.config == "samplers":
         return run_samplers(args)
+    if args.config == "batched":
+        return run_batched(args)
     args.warmup = max(args.warmup, 3)
 
     import torch
