@@ -891,7 +891,9 @@ int32_t or_pf_run_sched(const or_model *m, const double *th, const double *y, ui
     return OR_EINVAL;
   if (m->obs_every < 0 || m->obs_count < 0) return OR_EINVAL;
 #ifdef _OPENMP
-  if (nthreads > 0) omp_set_num_threads(nthreads);
+  /* 0 means every core this process may run on; set either way, so that an
+     earlier call's count does not carry over */
+  omp_set_num_threads(nthreads > 0 ? nthreads : omp_get_num_procs());
 #else
   (void)nthreads;
 #endif
