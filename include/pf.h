@@ -319,13 +319,16 @@ pf_status pf_smc2_run(const pf_model* m, int64_t P, int32_t T, double dt, const 
 typedef struct pf_server pf_server;
 pf_status pf_server_create(size_t device_mem_budget, int32_t max_slots, pf_server** out);
 /* Queue a request; theta and y are copied.  PF_ENOMEM if the request alone
- * exceeds the budget, PF_EINVAL on bad arguments. */
+ * exceeds the budget, PF_EINVAL on bad arguments, PF_ECUDA once a CUDA error
+ * has stopped the server. */
 pf_status pf_server_submit(pf_server* s, const pf_model* m, int64_t P, int32_t T, double dt,
                            const double* theta, const double* y, uint64_t seed,
                            uint64_t* ticket);
 /* PF_EBUSY while the request is queued or running; otherwise its final status,
- * with loglik and latency (seconds from submit to completion) filled in.  A
- * finished ticket can be polled once. */
+ * with loglik and latency (seconds from submit to completion) filled in:
+ * PF_OK, PF_EDEGENERATE, PF_ENOMEM (its buffers could not be allocated), or
+ * PF_ECUDA (a CUDA error stopped the server; it then refuses new requests).
+ * A finished ticket can be polled once. */
 pf_status pf_server_poll(pf_server* s, uint64_t ticket, double* loglik, double* latency_s);
 /* Counters: queued, running, completed requests and scheduler iterations. */
 pf_status pf_server_stats(pf_server* s, int64_t* queued, int64_t* running, int64_t* completed,
@@ -403,6 +406,14 @@ pf_status pf_weight_exp(const double* d, double* w, int64_t n);
  * countdown is process-wide and shared by all threads.  PF_EINVAL for
  * k < 0. */
 pf_status pf_debug_fail_allocation(int32_t k);
+
+/* Host-side fault injection for tests: the k-th next wait of a server's
+ * scheduler for one of its iterations (any server of the process) reports a
+ * CUDA error, as a failed kernel would -- once; k = 0 disarms.  That server
+ * then ends its running and queued requests with PF_ECUDA (pf_server_poll)
+ * and refuses new ones (pf_server_submit returns PF_ECUDA); pf_server_destroy
+ * still releases it.  The GPU itself is not touched.  PF_EINVAL for k < 0. */
+pf_status pf_debug_fail_server_wait(int32_t k);
 
 /* Invariant counters of a checked build of this library (compiled with
  * PF_CHECKED=1: libpf_b300_checked.so), the sanitizer substitute: the kernels

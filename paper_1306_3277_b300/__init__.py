@@ -72,6 +72,7 @@ def lib():
                                           ctypes.POINTER(ctypes.c_double)]
         L.pf_weight_exp.argtypes = [_vp, _vp, ctypes.c_int64]
         L.pf_debug_fail_allocation.argtypes = [ctypes.c_int32]
+        L.pf_debug_fail_server_wait.argtypes = [ctypes.c_int32]
         L.pf_debug_check_counts.argtypes = [ctypes.POINTER(ctypes.c_uint64),
                                             ctypes.POINTER(ctypes.c_int32)]
         L.pf_pmmh_run.argtypes = [ctypes.c_int32, ctypes.POINTER(_vp), _vp,
@@ -94,7 +95,8 @@ def lib():
         for name in ("pf_run", "pf_wait", "pf_destroy", "pf_create", "pf_batch_run",
                      "pf_profile_enable", "pf_profile_read", "pf_measure_fma_peak",
                      "pf_run_range", "pf_sample_path", "pf_weight_exp",
-                     "pf_debug_fail_allocation", "pf_debug_check_counts"):
+                     "pf_debug_fail_allocation", "pf_debug_fail_server_wait",
+                     "pf_debug_check_counts"):
             getattr(L, name).restype = ctypes.c_int
         L.pf_run_noalloc.argtypes = [ctypes.POINTER(pf_model), ctypes.c_int64, ctypes.c_int32,
                                      ctypes.c_double, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp,
@@ -363,6 +365,13 @@ def pf_debug_fail_allocation(k):
     """Fault injection: the k-th next device allocation of a filter or a served
     request fails as if the device were out of memory (once); 0 disarms."""
     _check(lib().pf_debug_fail_allocation(k))
+
+
+def pf_debug_fail_server_wait(k):
+    """Fault injection: the k-th next wait of a server's scheduler reports a
+    CUDA error (once; 0 disarms); that server ends its requests with PF_ECUDA
+    and refuses new ones."""
+    _check(lib().pf_debug_fail_server_wait(k))
 
 
 def pf_debug_check_counts():

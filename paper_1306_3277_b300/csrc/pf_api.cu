@@ -56,6 +56,24 @@ extern "C" pf_status pf_debug_fail_allocation(int32_t k) {
   return PF_OK;
 }
 
+// ... and the k-th next wait of a server's scheduler for one of its iterations
+// reports a CUDA error, as a failed kernel would
+static std::atomic<int> g_fail_wait_countdown{0};
+
+bool pfb::injected_wait_failure() {
+  int k = g_fail_wait_countdown.load();
+  while (k > 0) {
+    if (g_fail_wait_countdown.compare_exchange_weak(k, k - 1)) return k == 1;
+  }
+  return false;
+}
+
+extern "C" pf_status pf_debug_fail_server_wait(int32_t k) {
+  if (k < 0) return fail(PF_EINVAL, "k = %d < 0", k);
+  g_fail_wait_countdown.store(k);
+  return PF_OK;
+}
+
 #define CK(call)                                                                          \
   do {                                                                                    \
     cudaError_t e_ = (call);                                                              \

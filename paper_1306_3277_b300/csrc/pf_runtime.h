@@ -146,6 +146,9 @@ pf_status fail(pf_status st, const char* fmt, ...);
 // Host-side fault injection (pf_debug_fail_allocation): true for the one
 // device allocation of a filter or a served request chosen to fail.
 bool injected_alloc_failure();
+// ... (pf_debug_fail_server_wait): true for the one wait of a server's
+// scheduler chosen to report a CUDA error.
+bool injected_wait_failure();
 pf_status check_shape(const pf_model* m, int64_t P, int32_t T, double dt, Shape* sh);
 pf_status build_plan(const std::vector<pf_filter*>& fl, Plan** out, int64_t cta_max_p);
 pf_status stage_plan(Plan* p, const double* const* theta, const double* const* y,

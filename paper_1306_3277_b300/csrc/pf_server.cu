@@ -77,6 +77,7 @@ struct pf_server {
   uint64_t next_ticket = 1;
   int64_t n_running = 0, n_completed = 0, n_iter = 0;
   bool stop = false;
+  bool broken = false;  // a CUDA error ended the scheduler's work: requests fail with PF_ECUDA
   std::thread thr;
   // scheduler-owned
   cudaStream_t st = nullptr;
@@ -185,11 +186,54 @@ void finish(pf_server* s, Request* r) {
   s->n_running -= 1;
 }
 
+// End every request in a slot with status st (their buffers freed, stream-
+// ordered), and forget the in-flight iterations' result lists.
+void fail_running(pf_server* s, pf_status st) {
+  for (int q = 0; q < 2; ++q) s->launched[q].clear();
+  for (int k = 0; k < s->max_slots; ++k) {
+    Request* r = s->slots[k];
+    if (!r) continue;
+    free_request_buffers(s, r);
+    s->used -= r->bytes;
+    s->slots[k] = nullptr;
+    r->slot = -1;
+    r->status = st;
+    r->ll = 0.0;
+    finish(s, r);
+  }
+  s->map_dirty = true;
+}
+
+// A CUDA error is sticky for the context: end the running and the queued
+// requests with PF_ECUDA and take no more work (pf_server_submit refuses).
+void break_server(pf_server* s) {
+  cudaGetLastError();
+  fail_running(s, PF_ECUDA);
+  for (int q = 0; q < 2; ++q) s->ev_live[q] = false;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->broken = true;
+  const double t = now_s();
+  for (Request* r : s->queue) {
+    r->status = PF_ECUDA;
+    r->ll = 0.0;
+    r->t_done = t;
+    s->finished[r->ticket] = r;
+    s->n_completed += 1;
+  }
+  s->queue.clear();
+}
+
 // Wait for the iteration that used this parity, then retire the filters it
-// reported finished (degenerate, or past their last observation).
-void retire(pf_server* s, int parity) {
-  if (!s->ev_live[parity]) return;
-  cudaEventSynchronize(s->ev[parity]);
+// reported finished (degenerate, or past their last observation).  False if
+// the wait reported a CUDA error (the server is then broken).
+bool retire(pf_server* s, int parity) {
+  if (!s->ev_live[parity]) return true;
+  cudaError_t e = cudaEventSynchronize(s->ev[parity]);
+  if (e == cudaSuccess && injected_wait_failure()) e = cudaErrorLaunchFailure;
+  if (e != cudaSuccess) {
+    break_server(s);
+    return false;
+  }
   s->ev_live[parity] = false;
   const double* res = s->h_res[parity];
   for (Request* r : s->launched[parity]) {
@@ -208,6 +252,37 @@ void retire(pf_server* s, int parity) {
     }
   }
   s->launched[parity].clear();
+  return true;
+}
+
+// Room for ntm tile-map entries (twice that, to grow rarely) in both pinned
+// staging copies and on the device; after the stream has drained.  On a
+// failed allocation nothing is left allocated and false is returned.
+bool grow_tile_map(pf_server* s, size_t ntm) {
+  cudaStreamSynchronize(s->st);
+  for (int q = 0; q < 2; ++q) {
+    if (s->h_tmap[q]) cudaFreeHost(s->h_tmap[q]);
+    s->h_tmap[q] = nullptr;
+  }
+  if (s->d_tmap) cudaFree(s->d_tmap);
+  s->d_tmap = nullptr;
+  s->tmap_cap = 0;
+  bool ok = true;
+  for (int q = 0; q < 2; ++q)
+    ok = ok && cudaMallocHost((void**)&s->h_tmap[q], sizeof(int2) * ntm * 2) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&s->d_tmap, sizeof(int2) * ntm * 2) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    for (int q = 0; q < 2; ++q) {
+      if (s->h_tmap[q]) cudaFreeHost(s->h_tmap[q]);
+      s->h_tmap[q] = nullptr;
+    }
+    if (s->d_tmap) cudaFree(s->d_tmap);
+    s->d_tmap = nullptr;
+    return false;
+  }
+  s->tmap_cap = ntm * 2;
+  return true;
 }
 
 void scheduler(pf_server* s) {
@@ -215,14 +290,14 @@ void scheduler(pf_server* s) {
   int parity = 0;
   for (;;) {
     // the pinned buffers of this parity were last used two iterations ago
-    retire(s, parity);
+    if (!retire(s, parity)) continue;
     size_t arena_used = 0;
     std::vector<Request*> admitted;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       bool any_running = false;
       for (Request* r : s->slots) any_running = any_running || r;
-      if (!any_running && s->queue.empty() && !s->ev_live[0] && !s->ev_live[1]) {
+      if (s->broken || (!any_running && s->queue.empty() && !s->ev_live[0] && !s->ev_live[1])) {
         if (s->stop) break;
         s->cv.wait_for(lk, std::chrono::milliseconds(2));
         continue;
@@ -293,17 +368,11 @@ void scheduler(pf_server* s) {
         retire(s, parity ^ 1);
         continue;
       }
-      if (ntm > s->tmap_cap) {  // grow the staging copies and the device map (rare)
-        cudaStreamSynchronize(s->st);
-        for (int q = 0; q < 2; ++q) {
-          if (s->h_tmap[q]) cudaFreeHost(s->h_tmap[q]);
-          s->h_tmap[q] = nullptr;
-          cudaMallocHost((void**)&s->h_tmap[q], sizeof(int2) * ntm * 2);
-        }
-        if (s->d_tmap) cudaFree(s->d_tmap);
-        s->d_tmap = nullptr;
-        cudaMalloc((void**)&s->d_tmap, sizeof(int2) * ntm * 2);
-        s->tmap_cap = ntm * 2;
+      if (ntm > s->tmap_cap && !grow_tile_map(s, ntm)) {
+        // no room for the map: the stream has drained, so retire what the
+        // other parity's iteration finished and end the rest with PF_ENOMEM
+        if (retire(s, parity ^ 1)) fail_running(s, PF_ENOMEM);
+        continue;
       }
       int2* tm = s->h_tmap[parity];
       s->run_seg.clear();
@@ -343,6 +412,10 @@ void scheduler(pf_server* s) {
                       cudaMemcpyDeviceToHost, s->st);
     }
     cudaEventRecord(s->ev[parity], s->st);  // also guards this parity's staging buffers
+    if (cudaGetLastError() != cudaSuccess) {  // a launch or copy of this iteration failed
+      break_server(s);
+      continue;
+    }
     s->ev_live[parity] = true;
     s->iter += 1;
     for (Request* r : s->slots)
@@ -407,6 +480,10 @@ extern "C" pf_status pf_server_submit(pf_server* s, const pf_model* m, int64_t P
                                       double dt, const double* theta, const double* y,
                                       uint64_t seed, uint64_t* ticket) {
   if (!s || !theta || !y || !ticket) return fail(PF_EINVAL, "pf_server_submit: NULL argument");
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->broken) return fail(PF_ECUDA, "the server stopped after a CUDA error");
+  }
   Shape sh;
   pf_status st = check_shape(m, P, T, dt, &sh);
   if (st != PF_OK) return st;

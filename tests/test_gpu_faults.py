@@ -3,7 +3,10 @@ allocation of a filter or of a served request is made to fail through
 pf_debug_fail_allocation. pf_create must return PF_ENOMEM at every one of its
 allocations without leaking the others, a served request must finish with
 PF_ENOMEM while the server goes on, and filters created afterwards give the
-same bits as before."""
+same bits as before.  A server whose scheduler sees a CUDA error (reported by
+pf_debug_fail_server_wait in place of the real wait's result) must end every
+running and queued request with PF_ECUDA, refuse new ones and still shut
+down."""
 import time
 
 import pytest
@@ -91,4 +94,36 @@ def test_fault_injection_rejects_negative_k():
     import paper_1306_3277_b300 as pf
     with pytest.raises(pf.PFError) as e:
         pf.pf_debug_fail_allocation(-1)
+    assert e.value.status == pf.PF_EINVAL
+
+
+def test_server_ends_its_requests_after_a_cuda_error():
+    import paper_1306_3277_b300 as pf
+    w = W.windkessel(P=512, T=400, prec=W.MIXED)
+    m = pf.model_from_workload(w)
+    srv = pf.pf_server_create(1 << 30, 2)
+    try:
+        pf.pf_debug_fail_server_wait(1)  # the scheduler's first wait for an iteration
+        tickets = [srv.submit(m, w.P, w.T, w.dt, w.theta, w.y, k) for k in range(3)]
+        # two requests run (two slots), the third waits in the queue: all three end
+        assert [_wait(srv, t)[0] for t in tickets] == [pf.PF_ECUDA] * 3
+        with pytest.raises(pf.PFError) as e:
+            srv.submit(m, w.P, w.T, w.dt, w.theta, w.y, 9)
+        assert e.value.status == pf.PF_ECUDA
+        st = srv.stats()
+        assert st["running"] == 0 and st["queued"] == 0 and st["completed"] == 3
+    finally:
+        pf.pf_debug_fail_server_wait(0)
+        srv.destroy()
+    # the GPU was never at fault: a new server serves the same request exactly
+    f = pf.pf_create(m, w.P, w.T, w.dt)
+    ref = f.run(w.theta, w.y, 5)[:2]
+    f.destroy()
+    srv = pf.pf_server_create(1 << 30, 2)
+    try:
+        assert _wait(srv, srv.submit(m, w.P, w.T, w.dt, w.theta, w.y, 5)) == ref
+    finally:
+        srv.destroy()
+    with pytest.raises(pf.PFError) as e:
+        pf.pf_debug_fail_server_wait(-1)
     assert e.value.status == pf.PF_EINVAL
