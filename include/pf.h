@@ -328,7 +328,8 @@ pf_status pf_server_submit(pf_server* s, const pf_model* m, int64_t P, int32_t T
  * with loglik and latency (seconds from submit to completion) filled in:
  * PF_OK, PF_EDEGENERATE, PF_ENOMEM (its buffers could not be allocated), or
  * PF_ECUDA (a CUDA error stopped the server; it then refuses new requests).
- * A finished ticket can be polled once. */
+ * A finished ticket can be collected once: polling it again, or polling a
+ * ticket this server never issued, gives PF_EINVAL. */
 pf_status pf_server_poll(pf_server* s, uint64_t ticket, double* loglik, double* latency_s);
 /* Counters: queued, running, completed requests and scheduler iterations. */
 pf_status pf_server_stats(pf_server* s, int64_t* queued, int64_t* running, int64_t* completed,

@@ -24,6 +24,7 @@
 #include <thread>
 #include <tuple>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "pf.h"
@@ -74,6 +75,7 @@ struct pf_server {
   std::condition_variable cv;
   std::deque<Request*> queue;
   std::unordered_map<uint64_t, Request*> finished;
+  std::unordered_set<uint64_t> pending;  // tickets queued or running
   uint64_t next_ticket = 1;
   int64_t n_running = 0, n_completed = 0, n_iter = 0;
   bool stop = false;
@@ -182,6 +184,7 @@ void finish(pf_server* s, Request* r) {
   r->t_done = now_s();
   std::lock_guard<std::mutex> lk(s->mu);
   s->finished[r->ticket] = r;
+  s->pending.erase(r->ticket);
   s->n_completed += 1;
   s->n_running -= 1;
 }
@@ -218,6 +221,7 @@ void break_server(pf_server* s) {
     r->ll = 0.0;
     r->t_done = t;
     s->finished[r->ticket] = r;
+    s->pending.erase(r->ticket);
     s->n_completed += 1;
   }
   s->queue.clear();
@@ -506,6 +510,7 @@ extern "C" pf_status pf_server_submit(pf_server* s, const pf_model* m, int64_t P
   {
     std::lock_guard<std::mutex> lk(s->mu);
     r->ticket = s->next_ticket++;
+    s->pending.insert(r->ticket);
     s->queue.push_back(r);
   }
   s->cv.notify_one();
@@ -521,9 +526,9 @@ extern "C" pf_status pf_server_poll(pf_server* s, uint64_t ticket, double* logli
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->finished.find(ticket);
     if (it == s->finished.end()) {
-      if (ticket == 0 || ticket >= s->next_ticket)
-        return fail(PF_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
-      return PF_EBUSY;
+      if (s->pending.count(ticket)) return PF_EBUSY;
+      return fail(PF_EINVAL, "ticket %llu is unknown or was already collected",
+                  (unsigned long long)ticket);
     }
     r = it->second;
     s->finished.erase(it);

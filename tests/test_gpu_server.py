@@ -98,3 +98,22 @@ def test_server_rejects_oversized_and_bad_requests():
     with pytest.raises(pf.PFError):
         srv.poll(12345)
     srv.destroy()
+
+
+def test_server_ticket_is_collected_once():
+    import paper_1306_3277_b300 as pf
+    w = W.windkessel(P=256, T=20)
+    srv = pf.pf_server_create(1 << 30, 2)
+    try:
+        t = srv.submit(pf.model_from_workload(w), w.P, w.T, w.dt, w.theta, w.y, 3)
+        deadline = time.time() + 60
+        r = None
+        while r is None and time.time() < deadline:
+            r = srv.poll(t)  # None (PF_EBUSY) while queued or running
+            time.sleep(0.001)
+        assert r is not None and r[0] == pf.PF_OK
+        with pytest.raises(pf.PFError) as e:
+            srv.poll(t)
+        assert e.value.status == pf.PF_EINVAL
+    finally:
+        srv.destroy()
