@@ -185,6 +185,9 @@ pf_status pf_sample_path(pf_filter* f, const double* theta, const double* y, uin
  * status (PF_OK or PF_EDEGENERATE). */
 pf_status pf_wait(pf_filter* f);
 
+/* Wait for the filter's own pending work (an asynchronous run; other work on
+ * the device is not waited for), then free its device buffers and every
+ * cached batch plan that lists it.  f = NULL does nothing.  Always PF_OK. */
 pf_status pf_destroy(pf_filter* f);
 
 /* Message describing the last error on this host thread ("" if none). */

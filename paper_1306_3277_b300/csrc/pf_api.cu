@@ -766,7 +766,11 @@ extern "C" pf_status pf_wait(pf_filter* f) {
 
 extern "C" pf_status pf_destroy(pf_filter* f) {
   if (!f) return PF_OK;
-  cudaDeviceSynchronize();
+  // the filter's own work only: an asynchronous run ends with its plan's
+  // ev_done, set-up work runs on f->own, and destroy_plan drains the streams
+  // of every plan the filter is part of (the batched forms are synchronous)
+  if (f->plan && f->plan->ev_done) cudaEventSynchronize(f->plan->ev_done);
+  if (f->own) cudaStreamSynchronize(f->own);
   {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     for (auto it = g_plans.begin(); it != g_plans.end();) {
