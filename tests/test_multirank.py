@@ -62,3 +62,18 @@ def test_single_rank_helpers():
     import bench
     assert bench.max_over_ranks(1.25) == 1.25
     assert bench.whole_job_rate(10, 1, 2.0) == 5.0
+
+
+def test_report_helpers_describe_the_workload_they_measure():
+    """The JSON line's traffic figure belongs to the captured particle count only,
+    and its L2 note tells a streamed state from an L2-resident one."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    big, small = W.lorenz96_large(), W.windkessel()
+    for tag in ("k_propagate<L96,40,f32>", "k_resample"):
+        assert bench.read_traffic(tag, small.P) is None
+        t = bench.read_traffic(tag, big.P)
+        assert t is None or t > 0  # None once the kernels change after the capture
+    assert bench.l2_note(big).startswith("inputs larger than L2")
+    assert bench.l2_note(small).startswith("L2-resident")
