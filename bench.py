@@ -375,15 +375,26 @@ def run_serving(args):
         pending = {}
         lat, done_ll = [], 0
         psteps_done = 0
+        rejected, max_queued, queued_at_end, last_stat = 0, 0, None, -1.0
         t0 = time.perf_counter()
         k = 0
         while k < len(reqs) or pending:
             now = time.perf_counter() - t0
             while k < len(reqs) and reqs[k][0] <= now:
                 w = reqs[k][1]
-                t = srv.submit(pf.model_from_workload(w), w.P, w.T, w.dt, w.theta, w.y, w.seed)
-                pending[t] = w
+                try:
+                    t = srv.submit(pf.model_from_workload(w), w.P, w.T, w.dt, w.theta, w.y,
+                                   w.seed)
+                    pending[t] = w
+                except pf.PFError:
+                    rejected += 1
                 k += 1
+            if now - last_stat >= 0.01:  # queue length, sampled every 10 ms
+                queued = srv.stats()["queued"]
+                max_queued = max(max_queued, queued)
+                if queued_at_end is None and k == len(reqs):
+                    queued_at_end = queued
+                last_stat = now
             for t in list(pending):
                 r = srv.poll(t)
                 if r is not None:
@@ -399,8 +410,10 @@ def run_serving(args):
         srv.destroy()
         lat.sort()
         q = (lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None)
-        sweep.append({"offered_per_s": rate, "submitted": k, "completed": len(lat),
-                      "unfinished": len(pending), "goodput_per_s": len(lat) / elapsed,
+        sweep.append({"offered_per_s": rate, "submitted": k, "rejected": rejected,
+                      "completed": len(lat), "unfinished": len(pending),
+                      "max_queued": max_queued, "queued_when_arrivals_end": queued_at_end,
+                      "goodput_per_s": len(lat) / elapsed,
                       "particle_steps_per_s": psteps_done / elapsed,
                       "p50_s": q(0.5), "p99_s": q(0.99), "elapsed_s": elapsed,
                       "iterations": st["iterations"]})
