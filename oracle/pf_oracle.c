@@ -24,11 +24,10 @@
  *  - no resampling after the final observation;
  *  - the constant -Ny/2 log(2 pi r) of the Gaussian observation density is
  *    added to each likelihood increment, not to the particle log-weights;
- *  - the particle log-weight is the residual sum of squares (fma-accumulated
- *    over the observed components in index order) times the per-run
- *    constant cw = -0.5 / r;
- *  - systematic targets (j + u) S / P are compared with the cumulative
- *    weights in the scaled form C_k (P / S) - u > j.
+ *  - the particle log-weight is -(1/2) rss / r, rss the residual sum of
+ *    squares (fma-accumulated over the observed components in index order);
+ *  - systematic target j sits at (j + u) S / P and takes the first particle
+ *    whose cumulative weight C_k exceeds it (Sec. 3.3).
  */
 #include "pf_oracle.h"
 
@@ -529,35 +528,32 @@ void or_lse(const double *ell, int64_t P, double *Mo, double *So, double *Qo) {
 /* ======================================================================
  * Systematic resampling (Sec. 3.3): cumulative weights C_k (compensated
  * inclusive prefix of w = exp(ell - M)), total S = C_{P-1}, one uniform u.
- * Target j (j = 0..P-1) sits at (j + u) S / P and takes the first particle
- * whose cumulative weight exceeds it; the comparison is evaluated in the
- * scaled form E_k = C_k (P / S) - u > j (ratio P / S and E_k each rounded
- * once), so a_j = min{k : E_k > j}, clamped to P-1.  Ancestors come out
- * sorted; particle k has offspring j in [ceil E_{k-1}, ceil E_k).
+ * Target j (j = 0..P-1) sits at tau_j = (j + u) S / P and takes the first
+ * particle whose cumulative weight exceeds it: a_j = min{k : C_k > tau_j},
+ * clamped to P-1.  Ancestors come out sorted.  A target within 1e-12 S of
+ * C_k or C_{k-1} counts as near (another rounding of the same comparison
+ * may decide it the other way).
  * ==================================================================== */
 static int64_t or_systematic_from_w(const double *w, int64_t P, double u, int32_t *anc,
                                     double *Cbuf) {
-  double sum = 0.0, comp = 0.0, S, ratio;
+  double sum = 0.0, comp = 0.0, S;
   int64_t j, k, near = 0;
   for (k = 0; k < P; ++k) {
     or_neumaier_add(&sum, &comp, w[k]);
     Cbuf[k] = sum + comp;
   }
   S = Cbuf[P - 1];
-  ratio = (double)P / S;
-  for (k = 0; k < P; ++k) Cbuf[k] = Cbuf[k] * ratio - u; /* E_k */
   for (j = 0; j < P; ++j) {
-    const double tj = (double)j;
-    int64_t lo = 0, hi = P; /* first k in [lo, hi) with E_k > j */
+    const double tau = ((double)j + u) * S / (double)P;
+    int64_t lo = 0, hi = P; /* first k in [lo, hi) with C_k > tau */
     while (lo < hi) {
       int64_t mid = lo + (hi - lo) / 2;
-      if (Cbuf[mid] > tj) hi = mid;
+      if (Cbuf[mid] > tau) hi = mid;
       else lo = mid + 1;
     }
     k = lo < P ? lo : P - 1;
     anc[j] = (int32_t)k;
-    if (fabs(tj - Cbuf[k]) <= 1e-12 * (double)P ||
-        (k > 0 && fabs(tj - Cbuf[k - 1]) <= 1e-12 * (double)P))
+    if (fabs(tau - Cbuf[k]) <= 1e-12 * S || (k > 0 && fabs(tau - Cbuf[k - 1]) <= 1e-12 * S))
       ++near;
   }
   return near;
@@ -565,26 +561,22 @@ static int64_t or_systematic_from_w(const double *w, int64_t P, double u, int32_
 
 /* ======================================================================
  * Stratified and multinomial resampling (Sec. 3.3; Algorithm 2 draws the
- * ancestors from a multinomial).  Both compare targets against the scaled
- * cumulative weights E_k = C_k (P / S) (C_k compensated, ratio rounded once)
- * and give a_j = min{k : E_k > target_j}, clamped to P-1; targets increase
- * with j, so ancestors come out sorted.
- *   stratified:  target_j = j + u_j, u_j in [0, 1) from Philox block
- *                (j, i, RESAMPLE, 1), words 1:0; E_k > j + u_j is evaluated
- *                as E_k - j > u_j, which is exact (E_k - j is exact whenever
- *                the comparison is not decided by sign or magnitude).
- *   multinomial: P + 1 unit exponentials e_l = -log u_l in FP32 (own logf;
- *                u_l = ((w0 >> 8) + 1) 2^-24 in (0, 1], w0 word 0 of block
- *                (l, i, RESAMPLE, 2)), partial sums G_m = e_0 + .. + e_m in
- *                FP64 (compensated); target_j =
- *                G_j (P / G_P).  (G_0, .., G_{P-1}) / G_P are the order
- *                statistics of P independent uniforms, so the offspring
- *                counts are Multinomial(P, w / S).
- * A target within 1e-12 P of E_k or E_{k-1} counts as near.
+ * ancestors from a multinomial).  Both compare targets tau_j with the
+ * cumulative weights C_k (compensated) and give a_j = min{k : C_k > tau_j},
+ * clamped to P-1; targets increase with j, so ancestors come out sorted.
+ *   stratified:  tau_j = (j + u_j) S / P, u_j in [0, 1) from Philox block
+ *                (j, i, RESAMPLE, 1), words 1:0.
+ *   multinomial: P + 1 unit exponentials e_l = -log v_l (own log), v_l in
+ *                (0, 1] the 53-bit uniform of words 1:0 of block
+ *                (l, i, RESAMPLE, 2); partial sums G_m = e_0 + .. + e_m
+ *                (compensated); tau_j = (G_j / G_P) S.  (G_0, .., G_{P-1}) /
+ *                G_P are the order statistics of P independent uniforms, so
+ *                the offspring counts are Multinomial(P, w / S).
+ * A target within 1e-12 S of C_k or C_{k-1} counts as near.
  * ==================================================================== */
 static int64_t or_resample_other(const double *w, int64_t P, int32_t kind, uint64_t seed,
                                  uint32_t i, int32_t *anc, double *Cbuf) {
-  double sum = 0.0, comp = 0.0, S, ratio, tscale = 0.0;
+  double sum = 0.0, comp = 0.0, S, GP = 1.0;
   double *G = NULL;
   int64_t j, k, near = 0;
   for (k = 0; k < P; ++k) {
@@ -592,45 +584,35 @@ static int64_t or_resample_other(const double *w, int64_t P, int32_t kind, uint6
     Cbuf[k] = sum + comp;
   }
   S = Cbuf[P - 1];
-  ratio = (double)P / S;
-  for (k = 0; k < P; ++k) Cbuf[k] = Cbuf[k] * ratio; /* E_k */
   if (kind == OR_RESAMPLE_MULTINOMIAL) {
     double gs = 0.0, gc = 0.0;
     uint32_t wd[4];
     G = (double *)malloc(sizeof(double) * (size_t)P);
     for (j = 0; j <= P; ++j) {
       or_block(seed, (uint32_t)j, i, OR_PURPOSE_RESAMPLE, 2u, wd);
-      /* FP32 spacing: -logf of the 24-bit uniform ((w0 >> 8) + 1) 2^-24, exact in FP64 */
-      or_neumaier_add(&gs, &gc, (double)-or_logf((float)((wd[0] >> 8) + 1u) * 0x1.0p-24f));
+      or_neumaier_add(&gs, &gc, -or_log(or_u53_open_zero(wd[0], wd[1])));
       if (j < P) G[j] = gs + gc;
     }
-    tscale = (double)P / (gs + gc);
+    GP = gs + gc;
   }
   for (j = 0; j < P; ++j) {
-    double uj = 0.0, tj;
+    double tau;
     int64_t lo = 0, hi = P;
     if (kind == OR_RESAMPLE_STRATIFIED) {
       uint32_t wd[4];
       or_block(seed, (uint32_t)j, i, OR_PURPOSE_RESAMPLE, 1u, wd);
-      uj = or_u53_half_open(wd[0], wd[1]);
-      tj = (double)j + uj; /* for the near test only */
-      while (lo < hi) {
-        int64_t mid = lo + (hi - lo) / 2;
-        if (Cbuf[mid] - (double)j > uj) hi = mid;
-        else lo = mid + 1;
-      }
+      tau = ((double)j + or_u53_half_open(wd[0], wd[1])) * S / (double)P;
     } else {
-      tj = G[j] * tscale;
-      while (lo < hi) {
-        int64_t mid = lo + (hi - lo) / 2;
-        if (Cbuf[mid] > tj) hi = mid;
-        else lo = mid + 1;
-      }
+      tau = (G[j] / GP) * S;
+    }
+    while (lo < hi) {
+      int64_t mid = lo + (hi - lo) / 2;
+      if (Cbuf[mid] > tau) hi = mid;
+      else lo = mid + 1;
     }
     k = lo < P ? lo : P - 1;
     anc[j] = (int32_t)k;
-    if (fabs(tj - Cbuf[k]) <= 1e-12 * (double)P ||
-        (k > 0 && fabs(tj - Cbuf[k - 1]) <= 1e-12 * (double)P))
+    if (fabs(tau - Cbuf[k]) <= 1e-12 * S || (k > 0 && fabs(tau - Cbuf[k - 1]) <= 1e-12 * S))
       ++near;
   }
   free(G);
@@ -678,7 +660,6 @@ typedef struct {
   uint64_t seed;
   int32_t Ny;
   double r;
-  double cw; /* -0.5 / r: scale of the residual sum of squares */
 } or_ctx;
 
 /* FP64 path. */
@@ -747,7 +728,7 @@ static double or_prop_weight64(const or_ctx *cx, uint32_t j, int32_t i, double *
       acc = fma(d, d, acc);
     }
   }
-  return acc * cx->cw;
+  return -0.5 * acc / cx->r;
 }
 
 /* Mixed path: FP32 state, RK4/Euler and noise; FP64 residuals and weight. */
@@ -818,7 +799,7 @@ static double or_prop_weight32(const or_ctx *cx, uint32_t j, int32_t i, float *x
       acc = fma(d, d, acc);
     }
   }
-  return acc * cx->cw;
+  return -0.5 * acc / cx->r;
 }
 
 /* ======================================================================
@@ -917,7 +898,6 @@ int32_t or_pf_run_sched(const or_model *m, const double *th, const double *y, ui
 
   if (sched) seed = sched[0];
   cx.m = m; cx.th = th; cx.flow = flow; cx.seed = seed; cx.Ny = Ny; cx.r = r;
-  cx.cw = -0.5 / r;
 
   /* initialisation (Algorithm 2, init lines) */
 #pragma omp parallel for schedule(static)
@@ -1040,9 +1020,9 @@ int32_t or_pf_run_sched(const or_model *m, const double *th, const double *y, ui
 
 /* ======================================================================
  * Single state path (the last lines of Algorithm 2): draw one particle j
- * from the final weights, j = min{k : C_k (P / S) > v P} with v the path
- * uniform of the run (block (0, T + 1, PATH, 0), 53 bits) and C_k the
- * compensated prefix of exp(ell_T - M); then follow the ancestors back:
+ * from the final weights, j = min{k : C_k > v S} with v the path uniform of
+ * the run (block (0, T + 1, PATH, 0), 53 bits), C_k the compensated prefix
+ * of exp(ell_T - M) and S = C_{P-1}; then follow the ancestors back:
  * b_T = j, b_{i-1} = a(t_i)[b_i], and return x(t_i) of particle b_i.
  * path [T+1][N], idx [T+1].  Returns the filter's status.
  * ==================================================================== */
@@ -1057,7 +1037,7 @@ int32_t or_sample_path(const or_model *m, const double *th, const double *y, uin
   int32_t status = or_pf_run_ex(m, th, y, seed, P, T, nthreads, loglik, NULL, anc, NULL, xhist,
                                 ellT);
   if (status == OR_OK) {
-    double M = -INFINITY, sum = 0.0, comp = 0.0, ratio, v, vp;
+    double M = -INFINITY, sum = 0.0, comp = 0.0, v, vS;
     int64_t k, j, lo, hi;
     int32_t i, n;
     uint32_t w[4];
@@ -1067,15 +1047,14 @@ int32_t or_sample_path(const or_model *m, const double *th, const double *y, uin
       or_neumaier_add(&sum, &comp, exp(ellT[k] - M));
       C[k] = sum + comp;
     }
-    ratio = (double)P / C[P - 1];
     or_block(seed, 0u, (uint32_t)(T + 1), OR_PURPOSE_PATH, 0u, w);
     v = or_u53_half_open(w[0], w[1]);
-    vp = v * (double)P;
+    vS = v * C[P - 1];
     lo = 0;
     hi = P;
     while (lo < hi) {
       int64_t mid = lo + (hi - lo) / 2;
-      if (C[mid] * ratio > vp) hi = mid;
+      if (C[mid] > vS) hi = mid;
       else lo = mid + 1;
     }
     j = lo < P ? lo : P - 1;

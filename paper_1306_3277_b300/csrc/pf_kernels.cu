@@ -1304,8 +1304,8 @@ __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __rest
 // Multinomial resampling: the spacings of the sorted uniforms
 // ---------------------------------------------------------------------------
 // After the propagate launch of step i (rs_step = i), for every filter that
-// resamples with the multinomial scheme: unit exponentials e_l = -log u_l
-// (u_l in (0, 1] from Philox block (l, i, RESAMPLE, 2)), l = 0..P; their
+// resamples with the multinomial scheme: unit exponentials e_l = -log v_l
+// (v_l in (0, 1] from Philox block (l, i, RESAMPLE, 2)), l = 0..P; their
 // in-tile inclusive sums go to mn_t, the tile totals to mn_part.
 __device__ __forceinline__ bool mn_active(const FilterDev& fd, int* step) {
   const Ctl* c = fd.ctl;
@@ -1315,12 +1315,11 @@ __device__ __forceinline__ bool mn_active(const FilterDev& fd, int* step) {
          ldcg(&c->step) == i0 + 1 && ldcg(&c->rs_flag) != 0;
 }
 
-// Spacing l: -log u in FP32 (own logf; u = ((w0 >> 8) + 1) 2^-24 in (0, 1],
-// w0 word 0 of block (l, i, RESAMPLE, 2)), exact in FP64 for the sums.
+// Spacing l: -log v in FP64 (own log), v in (0, 1] the 53-bit uniform of
+// words 1:0 of block (l, i, RESAMPLE, 2).
 __device__ __forceinline__ double mn_spacing(const FilterDev& fd, int l, int i) {
   const uint4 w = rng_block(fd.seed, uint32_t(l), uint32_t(i), PURPOSE_RESAMPLE, 2u);
-  const float u = __fmul_rn(float((w.x >> 8) + 1u), 0x1.0p-24f);
-  return to_double(-log_posf(u));
+  return -log_pos(u53_open_closed(w.x, w.y));
 }
 
 __global__ void __launch_bounds__(TILE) k_mn_tiles(const FilterDev* __restrict__ fds,

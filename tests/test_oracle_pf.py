@@ -214,3 +214,133 @@ def test_sparse_lorenz96_deterministic_closed_form():
             ll += -0.5 * 4 * math.log(2 * math.pi * r) - 0.5 * float(np.sum(d * d)) / r
     res = O.pf_run(m, th, w.y, 9, 16, w.T)
     assert res["loglik"] == pytest.approx(ll, rel=1e-12)
+
+
+# ---- the mixed-precision Lorenz '96 branch (FP32 state, RK4 and noise; FP64
+# ---- residuals and weights): Sec. 2.1.2's model and observation, Algorithm 2's
+# ---- propagate and weight lines, pinned without the oracle's own integrator
+def _rk4_l96(x, F, dt, n):
+    """Classic RK4 of dx_n/dt = (x_{n+1} - x_{n-2}) x_{n-1} - x_n + F, numpy,
+    in the dtype of x (float64, or float32 with every operation rounded)."""
+    t = x.dtype.type
+    F, dt = t(F), t(dt)
+
+    def f(v):
+        return (np.roll(v, -1) - np.roll(v, 2)) * np.roll(v, 1) - v + F
+
+    for _ in range(n):
+        k1 = f(x)
+        k2 = f(x + t(0.5) * dt * k1)
+        k3 = f(x + t(0.5) * dt * k2)
+        k4 = f(x + dt * k3)
+        x = x + dt / t(6) * (k1 + t(2) * k2 + t(2) * k3 + k4)
+    return x
+
+
+def _normal32_math(seed, j, i, n, purpose=O.PURPOSE_PROP):
+    """Normal number n of stream (j, i, purpose) in the FP32 layout (two
+    Box-Muller pairs per Philox block from 24-bit uniforms), evaluated with
+    math.log / math.cos / math.sin in double precision from the raw words."""
+    w = O.philox4x32_10([j, i, (purpose << 16) | (n // 4), 0],
+                        [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF])
+    pair = (n // 2) % 2
+    wa, wb = int(w[2 * pair]), int(w[2 * pair + 1])
+    u1 = ((wa >> 8) + 1) * 2.0 ** -24
+    u2 = (wb >> 8) * 2.0 ** -24
+    rho = math.sqrt(-2.0 * math.log(u1))
+    return rho * (math.sin(2 * math.pi * u2) if n % 2 else math.cos(2 * math.pi * u2))
+
+
+L96_MIXED_SHAPES = [
+    # name, workload, observed components
+    ("N=8, all components", lambda **kw: W.lorenz96_8(prec=W.MIXED, **kw), slice(0, 8)),
+    ("N=40, every 2nd component", lambda **kw: W.lorenz96_large(prec=W.MIXED, **kw),
+     slice(0, 40, 2)),
+]
+
+
+@pytest.mark.parametrize("name,factory,obs", L96_MIXED_SHAPES, ids=[s[0] for s in L96_MIXED_SHAPES])
+def test_mixed_lorenz96_deterministic_closed_form(name, factory, obs):
+    """q = 0, one particle: x(t_0) = m0 + s0 z (z_n the normal number n of stream
+    (0, 0, INIT), recomputed from the raw Philox words; a random start, since
+    a uniform one stays uniform under Lorenz '96 and would hide a misplaced
+    component), then the deterministic FP32 RK4 trajectory, so the mixed
+    filter's log-likelihood is the closed form sum_i sum_{n observed}
+    log N(y_in; x_n(t_i), r).  The FP32 trajectory differs from the FP64 one
+    by rounding only; its distance delta_i at each t_i is measured here on an
+    independent float32 integration (unfused numpy), and the likelihood
+    tolerance is the first-order bound sum_i sum_n (|y_in - x_n| + delta)
+    delta / r with a tenfold margin on delta."""
+    w = factory(P=1, T=12)
+    F, r, m0, s0 = w.theta[0], w.theta[2], 1.25, 1.0
+    th = (F, 0.0, r, m0, s0)
+    seed = 0x5EED0
+    z0 = np.array([_normal32_math(seed, 0, 0, n, O.PURPOSE_INIT) for n in range(w.N)])
+    x64 = m0 + s0 * z0
+    x32 = x64.astype(np.float32)
+    ll, tol = 0.0, 0.0
+    ny = len(range(w.N)[obs])
+    for i in range(w.T):
+        x64 = _rk4_l96(x64, F, w.dt, w.substeps)
+        x32 = _rk4_l96(x32, F, w.dt, w.substeps)
+        delta = 10.0 * float(np.max(np.abs(x32.astype(np.float64) - x64))) + 1e-5
+        d = w.y[i] - x64[obs]
+        ll += -0.5 * ny * math.log(2 * math.pi * r) - 0.5 * float(np.sum(d * d)) / r
+        tol += float(np.sum((np.abs(d) + delta) * delta)) / r
+    assert tol < 0.05  # the bound is informative: far below the effect of any slip
+    res = O.pf_run(_om(w), th, w.y, seed, 1, w.T)
+    assert res["status"] == O.OK
+    assert abs(res["loglik"] - ll) <= tol, (res["loglik"], ll, tol)
+    assert np.allclose(res["x"][:, 0], x64, rtol=0, atol=1e-3)
+
+
+@pytest.mark.parametrize("name,factory,obs", L96_MIXED_SHAPES, ids=[s[0] for s in L96_MIXED_SHAPES])
+def test_mixed_lorenz96_noise_placement_closed_form(name, factory, obs):
+    """One particle, s0 = 0, q > 0: x(t_i) = RK4(x(t_{i-1})) + sqrt(q) z with z_n
+    the normal number n of stream (j = 0, i, PROP), recomputed here from the
+    raw Philox words with math.log / math.cos / math.sin (FP32 block layout);
+    the filter's log-likelihood is then the closed form of Sec. 2.1.2's
+    observation density at those states (one particle: weight = density).
+    Tolerance: the FP32 normals agree with the double-precision ones to 2e-6
+    and the FP32 RK4 with the FP64 one to the measured delta (as above), so
+    the states agree to delta + 2e-6 sqrt(q); a wrong normal index, a wrong
+    noise scale or a wrong observed component moves the states by about
+    sqrt(q) = 0.1 per component and the likelihood by far more than the bound."""
+    w = factory(P=1, T=4)
+    F, q, r, m0 = w.theta[0], 0.01, w.theta[2], -0.75
+    th = (F, q, r, m0, 0.0)
+    seed = 0x5EED1
+    x = np.full(w.N, m0)
+    x32 = np.full(w.N, m0, dtype=np.float32)
+    ll, tol = 0.0, 0.0
+    ny = len(range(w.N)[obs])
+    for i in range(1, w.T + 1):
+        z = np.array([_normal32_math(seed, 0, i, n) for n in range(w.N)])
+        x64_next = _rk4_l96(x, F, w.dt, w.substeps)
+        x32 = _rk4_l96(x32, F, w.dt, w.substeps)
+        delta = 10.0 * float(np.max(np.abs(x32.astype(np.float64) - x64_next))) + 1e-5
+        x = x64_next + math.sqrt(q) * z
+        x32 = (x32 + np.float32(math.sqrt(q)) * z.astype(np.float32)).astype(np.float32)
+        d = w.y[i - 1] - x[obs]
+        ll += -0.5 * ny * math.log(2 * math.pi * r) - 0.5 * float(np.sum(d * d)) / r
+        tol += float(np.sum((np.abs(d) + delta) * delta)) / r
+    assert tol < 0.05
+    res = O.pf_run(_om(w), th, w.y, seed, 1, w.T)
+    assert res["status"] == O.OK
+    assert abs(res["loglik"] - ll) <= tol, (res["loglik"], ll, tol)
+    assert np.allclose(res["x"][:, 0], x, rtol=0, atol=1e-3)
+
+
+def test_mixed_lorenz96_unbiased_against_fp64():
+    """Over 64 seeds, the mixed filter's log-likelihood minus the FP64
+    filter's on the same seeds has mean zero within four standard errors
+    (FP32 propagation changes the estimator by rounding, not systematically)."""
+    w = W.lorenz96_8(P=512, T=40)
+    m64, m32 = _om(w, prec=O.FP64), _om(w, prec=O.MIXED)
+    d = np.array([O.pf_run(m32, w.theta, w.y, s, w.P, w.T, want_x=False, want_anc=False,
+                           want_diag=False)["loglik"] -
+                  O.pf_run(m64, w.theta, w.y, s, w.P, w.T, want_x=False, want_anc=False,
+                           want_diag=False)["loglik"] for s in range(1, 65)])
+    se = d.std(ddof=1) / math.sqrt(len(d))
+    assert abs(d.mean()) < 4 * se + 1e-9, (d.mean(), se)
+    assert np.all(np.isfinite(d))

@@ -119,11 +119,6 @@ def _uniform(seed, j, i, blk, open_zero=False):
     return Fraction(v + (1 if open_zero else 0), 1 << 53)
 
 
-def _uniform24(seed, j, i, blk):
-    """((w0 >> 8) + 1) 2^-24 of Philox block (j, i, RESAMPLE << 16 | blk, 0)."""
-    w = O.philox4x32_10([j, i, (O.PURPOSE_RESAMPLE << 16) | blk, 0],
-                        [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF])
-    return ((int(w[0]) >> 8) + 1) / float(1 << 24)
 
 
 def test_stratified_matches_exact_rational():
@@ -153,14 +148,14 @@ def test_multinomial_matches_order_statistics_of_exponential_spacings():
         ell = rng.normal(0, 2, P)
         seed, i = int(rng.integers(1, 2 ** 40)), int(rng.integers(1, 50))
         anc, near = O.resample(ell, O.RESAMPLE_MULTINOMIAL, seed, i)
-        e = [-math.log(_uniform24(seed, l, i, 2)) for l in range(P + 1)]
+        e = [-math.log(float(_uniform(seed, l, i, 2, open_zero=True))) for l in range(P + 1)]
         G = [math.fsum(e[:j + 1]) for j in range(P + 1)]
         M = ell.max()
         w = [math.exp(x - M) for x in ell]
         C = [math.fsum(w[:k + 1]) for k in range(P)]
         targets = [G[j] / G[P] * C[-1] for j in range(P)]
         gap = min(abs(t - c) for t in targets for c in C) / C[-1]
-        if near or gap < 1e-5:  # the oracle's spacings use its FP32 logf (<= 2 ulp)
+        if near or gap < 1e-12:  # the oracle's own log is within 2 ulp of math.log
             continue
         ref = [next((k for k in range(P) if C[k] > t), P - 1) for t in targets]
         assert anc.tolist() == ref
@@ -203,3 +198,49 @@ def test_filter_with_other_resamplers_converges_to_kalman(kind):
                              want_diag=False)["loglik"] for s in range(1, 25)])
     se = math.sqrt(lls.var(ddof=1) / len(lls))
     assert abs(lls.mean() - (kf - lls.var(ddof=1) / 2)) < 4 * se + 0.02
+
+
+def _chi2_pvalue(obs, expected):
+    from scipy import stats
+    obs, expected = np.asarray(obs, float), np.asarray(expected, float)
+    chi2 = float(np.sum((obs - expected) ** 2 / expected))
+    return stats.chi2.sf(chi2, len(obs) - 1)
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+def test_multinomial_offspring_chi2_at_large_P(seed):
+    """P = 2^16 (Algorithm 2's multinomial ancestor draw): one draw's offspring
+    counts o_k against Multinomial(P, wbar).  Consecutive particles are pooled
+    into bins of expected count >= 64 and Pearson's chi^2 (df = bins - 1) must
+    not reject at 1e-6; with equal weights the histogram of o_k over 0..4 and
+    >= 5 must match Binomial(P, 1/P) the same way (the deterministic schemes
+    would give every particle exactly one offspring)."""
+    from scipy import stats
+    P = 1 << 16
+    rng = np.random.default_rng(seed)
+    ell = rng.normal(0, 1.5, P)
+    anc, _ = O.resample(ell, O.RESAMPLE_MULTINOMIAL, 0xC0FFEE + seed, 7)
+    o = np.bincount(anc, minlength=P)
+    assert o.sum() == P and np.all(np.diff(anc) >= 0)
+    wbar = np.exp(ell - ell.max())
+    wbar /= wbar.sum()
+    obs, exp_, acc_o, acc_e = [], [], 0, 0.0
+    for k in range(P):
+        acc_o += int(o[k])
+        acc_e += P * wbar[k]
+        if acc_e >= 64:
+            obs.append(acc_o)
+            exp_.append(acc_e)
+            acc_o, acc_e = 0, 0.0
+    obs[-1] += acc_o
+    exp_[-1] += acc_e
+    assert len(obs) > 500
+    assert _chi2_pvalue(obs, exp_) > 1e-6
+    # equal weights: counts ~ Binomial(P, 1/P)
+    anc, _ = O.resample(np.zeros(P), O.RESAMPLE_MULTINOMIAL, 0xBEEF + seed, 3)
+    o = np.bincount(anc, minlength=P)
+    hist = [int(np.sum(o == c)) for c in range(5)] + [int(np.sum(o >= 5))]
+    pmf = [stats.binom.pmf(c, P, 1.0 / P) for c in range(5)]
+    pmf.append(1.0 - sum(pmf))
+    assert _chi2_pvalue(hist, [P * p for p in pmf]) > 1e-6
+    assert abs(hist[0] / P - math.exp(-1)) < 0.01
