@@ -341,8 +341,10 @@ pf_status pf_server_destroy(pf_server* s);
 
 /* ---- allocation-free run (no counterpart in the paper) ------------------- */
 
-/* Size of the fixed device array pf_run_noalloc works in: 32 MiB, reserved on
- * every GPU that loads this library until the process exits. */
+/* Size of the fixed device array pf_run_noalloc works in: 32 MiB.  The array
+ * is reserved on a device by the first pf_run_noalloc call there (CUDA loads
+ * the module that holds it lazily, on first use) and kept until the process
+ * exits. */
 #define PF_NOALLOC_SCRATCH_BYTES (32u << 20)
 
 /* One run of the filter, exactly as pf_create + pf_run + pf_destroy would give
@@ -352,7 +354,10 @@ pf_status pf_server_destroy(pf_server* s);
  * (an allocation may synchronise the device or fail under fragmentation), or
  * real-time loops that must not enter the allocator.  It calls no
  * cudaMalloc, cudaFree or other allocating routine: every internal buffer is
- * carved out of one fixed array of PF_NOALLOC_SCRATCH_BYTES.
+ * carved out of one fixed array of PF_NOALLOC_SCRATCH_BYTES.  The first call
+ * on a device loads the array there (that load takes its 32 MiB of device
+ * memory): make it at set-up, before the caller's own pool takes the device
+ * budget and before any stream capture.
  *   m, P, T, dt   as for pf_create; a filter whose buffers do not fit in the
  *                 array is rejected with PF_EINVAL and a message giving the
  *                 bytes it needs (use pf_create/pf_run for it).
@@ -367,13 +372,41 @@ pf_status pf_server_destroy(pf_server* s);
  * Every call on a device shares the one array, which keeps the previous
  * call's contents (the run clears what must start at zero): calls that
  * overlap on the GPU (different streams, or several host threads) race and
- * must be serialised by the caller.  The first call on a device looks up the
- * array's device address; make that first call before any stream capture. */
+ * must be serialised by the caller.  Every call looks up the array's device
+ * address on the current device (so a device reset does not leave a stale
+ * one).  theta, y, loglik, status and final_particles must be device (or
+ * managed) memory of the current device: a host pointer is refused with
+ * PF_EINVAL before anything is enqueued. */
 pf_status pf_run_noalloc(const pf_model* m, int64_t P, int32_t T, double dt,
                          const double* theta, const double* y, uint64_t seed, double* loglik,
                          int32_t* status, void* final_particles, void* cuda_stream);
 
 /* ---- diagnostics (no counterpart in the paper) -------------------------- */
+
+/* Teacher-forced step: observation i (1 <= i <= T) of Algorithm 2's loop --
+ * propagate, weight, log-sum-exp and likelihood increment, ESS test and the
+ * resampling after it -- run by the same launches as step i of pf_run (the
+ * propagate kernel, then the resample kernel), but from a state given from
+ * outside, so that each step can be checked on its own against a reference
+ * fed the same state.
+ *   theta, y, seed  as for pf_run (y: all T rows; row i-1 is used).
+ *   x_prev         x(t_{i-1}), [N][P] in the filter's state precision, HOST
+ *                  or device.
+ *   anc            a(t_i), [P] int32, HOST or device: the ancestors that
+ *                  propagate into t_i; NULL: the identity.  The carried
+ *                  log-weights start at zero, as after a resampling.
+ *   x_out          x(t_i), [N][P] (or NULL).
+ *   incr           the likelihood increment log Z_i of step i (or NULL).
+ *   anc_next       [P] int32 (or NULL): the ancestors step i + 1 takes from
+ *                  step i's resampling, as the resample kernel wrote them (the
+ *                  identity when step i carried its weights); untouched for
+ *                  i = T or a degenerate step.
+ * Synchronous; returns PF_OK, PF_EDEGENERATE (a degenerate step) or an error.
+ * The filter is left standing at t_i: pf_run_range(f, ..., i, s) continues
+ * from it. */
+pf_status pf_debug_step(pf_filter* f, const double* theta, const double* y, uint64_t seed,
+                        int32_t i, const void* x_prev, const int32_t* anc, void* x_out,
+                        double* incr, int32_t* anc_next);
 
 /* Profiling mode: while enabled, pf_run launches the filter's kernels one by
  * one instead of as one CUDA graph and brackets every launch with CUDA events

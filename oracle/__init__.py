@@ -152,6 +152,10 @@ def lib():
                               ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(Param), _dp,
                               ctypes.c_uint64, ctypes.c_int32, _dp, _dp, _dp, _dp, _ip, _ip]
         L.or_smc2.restype = ctypes.c_int32
+        L.or_pf_step.argtypes = [ctypes.POINTER(Model), _dp, _dp, ctypes.c_uint64, ctypes.c_int64,
+                                 ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _dp, _ip, _dp,
+                                 _dp, _ip, _dp]
+        L.or_pf_step.restype = ctypes.c_int32
         L.or_sample_path.argtypes = [ctypes.POINTER(Model), _dp, _dp, ctypes.c_uint64,
                                      ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _dp, _dp, _ip]
         L.or_sample_path.restype = ctypes.c_int32
@@ -296,6 +300,24 @@ def pf_run_ex(m, theta, y, seed, P, T, nthreads=0):
                             ctypes.byref(ll), None, _ptr(anc, _ip), None, _ptr(xh, _dp),
                             _ptr(ellT, _dp))
     return dict(status=st, loglik=ll.value, xhist=xh, ellT=ellT, anc=anc)
+
+
+def pf_step(m, theta, y, seed, P, T, i, x_prev, anc=None, nthreads=0):
+    """Teacher-forced step i from x(t_{i-1}) [N][P] and a(t_i) [P] (None:
+    identity): dict(status, incr, x [N][P], anc_next [P] or None, diag [8])."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    xp = np.ascontiguousarray(x_prev, dtype=np.float64)
+    a = None if anc is None else np.ascontiguousarray(anc, dtype=np.int32)
+    x = np.zeros((m.N, P), dtype=np.float64)
+    inc = ctypes.c_double()
+    nxt = np.zeros(P, dtype=np.int32) if i < T else None
+    dg = np.zeros(8, dtype=np.float64)
+    st = lib().or_pf_step(ctypes.byref(m), _ptr(th, _dp), _ptr(yy, _dp), seed, P, T, i, nthreads,
+                          _ptr(xp, _dp), None if a is None else _ptr(a, _ip), _ptr(x, _dp),
+                          ctypes.byref(inc), None if nxt is None else _ptr(nxt, _ip),
+                          _ptr(dg, _dp))
+    return dict(status=st, incr=inc.value, x=x, anc_next=nxt, diag=dg)
 
 
 def sample_path(m, theta, y, seed, P, T, nthreads=0):

@@ -838,32 +838,119 @@ int32_t or_pf_run_ex(const or_model *m, const double *th, const double *y, uint6
  * the resampling after it) uses sched[i], i = 1..T; this is the run that
  * advancing a filter interval by interval with a new key per interval
  * gives.  With sched NULL every draw uses seed. */
-int32_t or_pf_run_sched(const or_model *m, const double *th, const double *y, uint64_t seed,
-                        const uint64_t *sched, int64_t P, int32_t T, int32_t nthreads,
-                        double *loglik, double *xfinal, int32_t *anc, double *diag,
-                        double *xhist, double *ellT) {
+/* The state of one filter between observations: the particles x(t_{i-1})
+ * (array a; b receives x(t_i)), the ancestors that propagate into t_i
+ * (identity or acur), the carried log-weights lam with their normaliser L,
+ * and the likelihood so far. */
+typedef struct {
+  const or_model *m;
+  or_ctx cx;
+  int64_t P;
+  int32_t T, N, every, mixed;
+  double c_obs;
+  double *xa, *xb;   /* FP64 state, SoA [N][P] */
+  float *fa, *fb;    /* FP32 state, SoA [N][P] */
+  double *ell, *lam, *w, *Cbuf;
+  int32_t *acur;
+  double ll, L;
+  int lam_zero, anc_identity;
+} or_state;
+
+/* Observation i (the loop body of Algorithm 2): propagate every particle from
+ * its ancestor and weight it; then, at an observed step, the log-sum-exp,
+ * the likelihood increment, the ESS test and the resampling (or the carry of
+ * the weights).  dg[8] receives (M, S, Q, ESS, resampled, u, increment, near
+ * targets).  Returns OR_OK, or OR_EDEGENERATE (ll set to -inf). */
+static int32_t or_step(or_state *r, int32_t i, const double *yi, double *dg) {
+  const int64_t P = r->P;
+  const int32_t N = r->N;
+  const int observed = (i % r->every) == 0;
+  double M, S, Q, ess, incr, u = 0.0;
+  int resample;
+  int64_t j, near = 0;
+  /* propagate and weight every particle from its ancestor */
+#pragma omp parallel
+  {
+    double xloc[4 * 256];
+    float floc[4 * 256];
+#pragma omp for schedule(static)
+    for (j = 0; j < P; ++j) {
+      int64_t a = r->anc_identity ? j : (int64_t)r->acur[j];
+      int32_t n;
+      double lw, e;
+      if (r->mixed) {
+        for (n = 0; n < N; ++n) floc[n] = r->fa[(int64_t)n * P + a];
+        lw = or_prop_weight32(&r->cx, (uint32_t)j, i, floc, floc + N, yi);
+        for (n = 0; n < N; ++n) r->fb[(int64_t)n * P + j] = floc[n];
+      } else {
+        for (n = 0; n < N; ++n) xloc[n] = r->xa[(int64_t)n * P + a];
+        lw = or_prop_weight64(&r->cx, (uint32_t)j, i, xloc, xloc + N, yi);
+        for (n = 0; n < N; ++n) r->xb[(int64_t)n * P + j] = xloc[n];
+      }
+      if (!observed) lw = 0.0;
+      e = r->lam_zero ? lw : r->lam[j] + lw;
+      if (e != e) e = -INFINITY;
+      r->ell[j] = e;
+    }
+  }
+  if (r->mixed) { float *t = r->fa; r->fa = r->fb; r->fb = t; }
+  else { double *t = r->xa; r->xa = r->xb; r->xb = t; }
+  if (!observed) {
+    /* a step without an observation only propagates: no weight, no
+     * likelihood term, no resampling, carried weights unchanged */
+    r->anc_identity = 1;
+    if (dg) dg[0] = dg[1] = dg[2] = dg[3] = dg[4] = dg[5] = dg[6] = dg[7] = 0.0;
+    return OR_OK;
+  }
+  or_lse(r->ell, P, &M, &S, &Q);
+  if (!(M > -INFINITY) || !(S > 0.0) || M == INFINITY) {
+    r->ll = -INFINITY;
+    if (dg) {
+      dg[0] = M; dg[1] = S; dg[2] = Q; dg[3] = 0.0; dg[4] = 0.0; dg[5] = 0.0;
+      dg[6] = -INFINITY; dg[7] = 0.0;
+    }
+    return OR_EDEGENERATE;
+  }
+  incr = ((M + log(S)) - r->L) + r->c_obs;
+  r->ll += incr;
+  ess = (S * S) / Q;
+  resample = (i < r->T) && (r->m->ess_threshold >= 1.0 || ess < r->m->ess_threshold * (double)P);
+  if (resample) {
+    for (j = 0; j < P; ++j) r->w[j] = exp(r->ell[j] - M);
+    if (r->m->resampler == OR_RESAMPLE_SYSTEMATIC) {
+      u = or_resample_uniform(r->cx.seed, (uint32_t)i);
+      near = or_systematic_from_w(r->w, P, u, r->acur, r->Cbuf);
+    } else {
+      near = or_resample_other(r->w, P, r->m->resampler, r->cx.seed, (uint32_t)i, r->acur,
+                               r->Cbuf);
+    }
+    r->anc_identity = 0;
+    r->lam_zero = 1;
+    r->L = log((double)P);
+  } else if (i < r->T) {
+    for (j = 0; j < P; ++j) r->lam[j] = r->ell[j] - M;
+    r->anc_identity = 1;
+    r->lam_zero = 0;
+    r->L = log(S);
+  }
+  if (dg) {
+    dg[0] = M; dg[1] = S; dg[2] = Q; dg[3] = ess; dg[4] = resample ? 1.0 : 0.0;
+    dg[5] = u; dg[6] = incr; dg[7] = (double)near;
+  }
+  return OR_OK;
+}
+
+/* Shape checks, buffers and constants of a filter state (x0 not drawn). */
+static int32_t or_state_open(or_state *r, const or_model *m, const double *th, uint64_t seed,
+                             int64_t P, int32_t T, int32_t nthreads) {
   const int32_t N = m->N, s = m->substeps;
-  const int mixed = (m->prec == OR_MIXED);
   const int32_t stride = OR_IS_L96(m->kind) ? m->obs_stride : 1;
   const int32_t Nys = OR_IS_L96(m->kind) ? (N + stride - 1) / stride : 1;
   const int32_t Ny = (OR_IS_L96(m->kind) && m->obs_count > 0 && m->obs_count < Nys)
                          ? m->obs_count : Nys;
-  const int32_t every = m->obs_every > 1 ? m->obs_every : 1;
-  const double r = OR_IS_L96(m->kind) ? th[2] : th[4];
-  const double m0 = OR_IS_L96(m->kind) ? th[3] : th[5];
-  const double s0 = OR_IS_L96(m->kind) ? th[4] : th[6];
-  const double c_obs = -0.5 * (double)Ny * log(2.0 * M_PI * r);
+  const double rv = OR_IS_L96(m->kind) ? th[2] : th[4];
   double *flow = NULL;
-  double *xa = NULL, *xb = NULL;   /* FP64 state, SoA [N][P] */
-  float *fa = NULL, *fb = NULL;    /* FP32 state, SoA [N][P] */
-  double *ell, *lam, *w, *Cbuf;
-  int32_t *acur;
-  double ll = 0.0, L = log((double)P);
-  int lam_zero = 1, anc_identity = 1, status = OR_OK;
-  int32_t i;
-  int64_t j;
-  or_ctx cx;
-
+  memset(r, 0, sizeof *r);
   if (P <= 0 || T <= 0 || N <= 0 || s <= 0) return OR_EINVAL;
   if (m->kind < OR_WINDKESSEL || m->kind > OR_LORENZ96_SDE) return OR_EINVAL;
   if (OR_IS_WK(m->kind) && N != 1) return OR_EINVAL;
@@ -878,144 +965,149 @@ int32_t or_pf_run_sched(const or_model *m, const double *th, const double *y, ui
 #else
   (void)nthreads;
 #endif
-
   if (OR_IS_WK(m->kind)) {
     flow = (double *)malloc(sizeof(double) * (size_t)((int64_t)T * s + 1));
     or_flow_table(m->flow_peak, m->flow_period, m->dt, (int64_t)T * s + 1, flow);
   }
-  if (mixed) {
-    fa = (float *)malloc(sizeof(float) * (size_t)(N * P));
-    fb = (float *)malloc(sizeof(float) * (size_t)(N * P));
+  r->m = m;
+  r->P = P;
+  r->T = T;
+  r->N = N;
+  r->every = m->obs_every > 1 ? m->obs_every : 1;
+  r->mixed = (m->prec == OR_MIXED);
+  r->c_obs = -0.5 * (double)Ny * log(2.0 * M_PI * rv);
+  if (r->mixed) {
+    r->fa = (float *)malloc(sizeof(float) * (size_t)(N * P));
+    r->fb = (float *)malloc(sizeof(float) * (size_t)(N * P));
   } else {
-    xa = (double *)malloc(sizeof(double) * (size_t)(N * P));
-    xb = (double *)malloc(sizeof(double) * (size_t)(N * P));
+    r->xa = (double *)malloc(sizeof(double) * (size_t)(N * P));
+    r->xb = (double *)malloc(sizeof(double) * (size_t)(N * P));
   }
-  ell = (double *)malloc(sizeof(double) * (size_t)P);
-  lam = (double *)malloc(sizeof(double) * (size_t)P);
-  w = (double *)malloc(sizeof(double) * (size_t)P);
-  Cbuf = (double *)malloc(sizeof(double) * (size_t)P);
-  acur = (int32_t *)malloc(sizeof(int32_t) * (size_t)P);
+  r->ell = (double *)malloc(sizeof(double) * (size_t)P);
+  r->lam = (double *)malloc(sizeof(double) * (size_t)P);
+  r->w = (double *)malloc(sizeof(double) * (size_t)P);
+  r->Cbuf = (double *)malloc(sizeof(double) * (size_t)P);
+  r->acur = (int32_t *)malloc(sizeof(int32_t) * (size_t)P);
+  r->cx.m = m;
+  r->cx.th = th;
+  r->cx.flow = flow;
+  r->cx.seed = seed;
+  r->cx.Ny = Ny;
+  r->cx.r = rv;
+  r->ll = 0.0;
+  r->L = log((double)P);
+  r->lam_zero = 1;
+  r->anc_identity = 1;
+  return OR_OK;
+}
 
-  if (sched) seed = sched[0];
-  cx.m = m; cx.th = th; cx.flow = flow; cx.seed = seed; cx.Ny = Ny; cx.r = r;
+static void or_state_close(or_state *r) {
+  free((void *)r->cx.flow);
+  free(r->xa); free(r->xb); free(r->fa); free(r->fb);
+  free(r->ell); free(r->lam); free(r->w); free(r->Cbuf); free(r->acur);
+}
 
-  /* initialisation (Algorithm 2, init lines) */
+/* Particle j's component n of the current state, as a double. */
+static double or_state_x(const or_state *r, int64_t k) {
+  return r->mixed ? (double)r->fa[k] : r->xa[k];
+}
+
+int32_t or_pf_run_sched(const or_model *m, const double *th, const double *y, uint64_t seed,
+                        const uint64_t *sched, int64_t P, int32_t T, int32_t nthreads,
+                        double *loglik, double *xfinal, int32_t *anc, double *diag,
+                        double *xhist, double *ellT) {
+  const double m0 = OR_IS_L96(m->kind) ? th[3] : th[5];
+  const double s0 = OR_IS_L96(m->kind) ? th[4] : th[6];
+  or_state r;
+  int32_t i, status = OR_OK;
+  int64_t j;
+  int32_t st = or_state_open(&r, m, th, sched ? sched[0] : seed, P, T, nthreads);
+  if (st != OR_OK) {
+    or_state_close(&r);
+    return st;
+  }
+  {
+    const int32_t N = r.N;
+    const uint64_t key0 = r.cx.seed;
+    /* initialisation (Algorithm 2, init lines) */
 #pragma omp parallel for schedule(static)
-  for (j = 0; j < P; ++j) {
-    int32_t n;
-    for (n = 0; n < N; ++n) {
-      if (mixed) {
-        float z = or_normal32(seed, (uint32_t)j, 0u, OR_PURPOSE_INIT, (uint32_t)n);
-        fa[(int64_t)n * P + j] = fmaf((float)s0, z, (float)m0);
-      } else {
-        double z = or_normal64(seed, (uint32_t)j, 0u, OR_PURPOSE_INIT, (uint32_t)n);
-        xa[(int64_t)n * P + j] = fma(s0, z, m0);
+    for (j = 0; j < P; ++j) {
+      int32_t n;
+      for (n = 0; n < N; ++n) {
+        if (r.mixed) {
+          float z = or_normal32(key0, (uint32_t)j, 0u, OR_PURPOSE_INIT, (uint32_t)n);
+          r.fa[(int64_t)n * P + j] = fmaf((float)s0, z, (float)m0);
+        } else {
+          double z = or_normal64(key0, (uint32_t)j, 0u, OR_PURPOSE_INIT, (uint32_t)n);
+          r.xa[(int64_t)n * P + j] = fma(s0, z, m0);
+        }
       }
     }
   }
-
   if (xhist) {
-    for (j = 0; j < (int64_t)N * P; ++j) xhist[j] = mixed ? (double)fa[j] : xa[j];
+    for (j = 0; j < (int64_t)r.N * P; ++j) xhist[j] = or_state_x(&r, j);
   }
   for (i = 1; i <= T; ++i) {
-    const double *yi = y + (int64_t)(i - 1) * Ny;
-    double M, S, Q, ess, incr, u = 0.0;
-    int resample;
-    int64_t near = 0;
-    /* a step without an observation only propagates: no weight, no
-     * likelihood term, no resampling, carried weights unchanged */
-    const int observed = (i % every) == 0;
-    if (sched) cx.seed = sched[i];
+    if (sched) r.cx.seed = sched[i];
     if (anc) {
-      for (j = 0; j < P; ++j) anc[(int64_t)(i - 1) * P + j] = anc_identity ? (int32_t)j : acur[j];
+      for (j = 0; j < P; ++j)
+        anc[(int64_t)(i - 1) * P + j] = r.anc_identity ? (int32_t)j : r.acur[j];
     }
-    /* propagate and weight every particle from its ancestor */
-#pragma omp parallel
-    {
-      double xloc[4 * 256];
-      float floc[4 * 256];
-#pragma omp for schedule(static)
-      for (j = 0; j < P; ++j) {
-        int64_t a = anc_identity ? j : (int64_t)acur[j];
-        int32_t n;
-        double lw, e;
-        if (mixed) {
-          for (n = 0; n < N; ++n) floc[n] = fa[(int64_t)n * P + a];
-          lw = or_prop_weight32(&cx, (uint32_t)j, i, floc, floc + N, yi);
-          for (n = 0; n < N; ++n) fb[(int64_t)n * P + j] = floc[n];
-        } else {
-          for (n = 0; n < N; ++n) xloc[n] = xa[(int64_t)n * P + a];
-          lw = or_prop_weight64(&cx, (uint32_t)j, i, xloc, xloc + N, yi);
-          for (n = 0; n < N; ++n) xb[(int64_t)n * P + j] = xloc[n];
-        }
-        if (!observed) lw = 0.0;
-        e = lam_zero ? lw : lam[j] + lw;
-        if (e != e) e = -INFINITY;
-        ell[j] = e;
-      }
-    }
-    if (mixed) { float *t = fa; fa = fb; fb = t; }
-    else { double *t = xa; xa = xb; xb = t; }
+    status = or_step(&r, i, y + (int64_t)(i - 1) * r.cx.Ny,
+                     diag ? diag + (int64_t)(i - 1) * 8 : NULL);
     if (xhist) {
-      double *xr = xhist + (int64_t)i * N * P;
-      for (j = 0; j < (int64_t)N * P; ++j) xr[j] = mixed ? (double)fa[j] : xa[j];
+      double *xr = xhist + (int64_t)i * r.N * P;
+      for (j = 0; j < (int64_t)r.N * P; ++j) xr[j] = or_state_x(&r, j);
     }
-    if (ellT && i == T) memcpy(ellT, ell, sizeof(double) * (size_t)P);
-    if (!observed) {
-      anc_identity = 1;
-      if (diag) {
-        double *dg = diag + (int64_t)(i - 1) * 8;
-        dg[0] = dg[1] = dg[2] = dg[3] = dg[4] = dg[5] = dg[6] = dg[7] = 0.0;
-      }
-      continue;
-    }
-
-    or_lse(ell, P, &M, &S, &Q);
-    if (!(M > -INFINITY) || !(S > 0.0) || M == INFINITY) {
-      status = OR_EDEGENERATE;
-      ll = -INFINITY;
-      if (diag) {
-        double *dg = diag + (int64_t)(i - 1) * 8;
-        dg[0] = M; dg[1] = S; dg[2] = Q; dg[3] = 0.0; dg[4] = 0.0; dg[5] = 0.0;
-        dg[6] = -INFINITY; dg[7] = 0.0;
-      }
-      break;
-    }
-    incr = ((M + log(S)) - L) + c_obs;
-    ll += incr;
-    ess = (S * S) / Q;
-    resample = (i < T) && (m->ess_threshold >= 1.0 || ess < m->ess_threshold * (double)P);
-    if (resample) {
-      for (j = 0; j < P; ++j) w[j] = exp(ell[j] - M);
-      if (m->resampler == OR_RESAMPLE_SYSTEMATIC) {
-        u = or_resample_uniform(cx.seed, (uint32_t)i);
-        near = or_systematic_from_w(w, P, u, acur, Cbuf);
-      } else {
-        near = or_resample_other(w, P, m->resampler, cx.seed, (uint32_t)i, acur, Cbuf);
-      }
-      anc_identity = 0;
-      lam_zero = 1;
-      L = log((double)P);
-    } else if (i < T) {
-      for (j = 0; j < P; ++j) lam[j] = ell[j] - M;
-      anc_identity = 1;
-      lam_zero = 0;
-      L = log(S);
-    }
-    if (diag) {
-      double *dg = diag + (int64_t)(i - 1) * 8;
-      dg[0] = M; dg[1] = S; dg[2] = Q; dg[3] = ess; dg[4] = resample ? 1.0 : 0.0;
-      dg[5] = u; dg[6] = incr; dg[7] = (double)near;
-    }
+    if (ellT && i == T) memcpy(ellT, r.ell, sizeof(double) * (size_t)P);
+    if (status != OR_OK) break;
   }
-
-  *loglik = ll;
+  *loglik = r.ll;
   if (xfinal && status == OR_OK) {
-    for (j = 0; j < (int64_t)N * P; ++j) xfinal[j] = mixed ? (double)fa[j] : xa[j];
+    for (j = 0; j < (int64_t)r.N * P; ++j) xfinal[j] = or_state_x(&r, j);
   }
-  free(flow); free(xa); free(xb); free(fa); free(fb);
-  free(ell); free(lam); free(w); free(Cbuf); free(acur);
+  or_state_close(&r);
   return status;
+}
+
+/* Teacher-forced step: observation i of Algorithm 2 from a given state --
+ * x(t_{i-1}) in x_prev [N][P] (values of the state precision), the ancestors
+ * a(t_i) in anc [P] (NULL: identity), carried log-weights zero (as after a
+ * resampling) -- by the same step function the whole run uses.  Outputs
+ * x(t_i) in x_next [N][P], the likelihood increment in *incr, the ancestors
+ * of step i + 1 in anc_next [P] (the identity when step i carried its
+ * weights; untouched for i = T) and the step's diagnostics in diag[8]. */
+int32_t or_pf_step(const or_model *m, const double *th, const double *y, uint64_t seed,
+                   int64_t P, int32_t T, int32_t i, int32_t nthreads, const double *x_prev,
+                   const int32_t *anc, double *x_next, double *incr, int32_t *anc_next,
+                   double *diag) {
+  or_state r;
+  int64_t j;
+  int32_t st;
+  if (i < 1 || i > T) return OR_EINVAL;
+  st = or_state_open(&r, m, th, seed, P, T, nthreads);
+  if (st != OR_OK) {
+    or_state_close(&r);
+    return st;
+  }
+  for (j = 0; j < (int64_t)r.N * P; ++j) {
+    if (r.mixed) r.fa[j] = (float)x_prev[j];
+    else r.xa[j] = x_prev[j];
+  }
+  if (anc) {
+    memcpy(r.acur, anc, sizeof(int32_t) * (size_t)P);
+    r.anc_identity = 0;
+  }
+  st = or_step(&r, i, y + (int64_t)(i - 1) * r.cx.Ny, diag);
+  if (incr) *incr = r.ll;
+  if (x_next) {
+    for (j = 0; j < (int64_t)r.N * P; ++j) x_next[j] = or_state_x(&r, j);
+  }
+  if (anc_next && st == OR_OK && i < T) {
+    for (j = 0; j < P; ++j) anc_next[j] = r.anc_identity ? (int32_t)j : r.acur[j];
+  }
+  or_state_close(&r);
+  return st;
 }
 
 /* ======================================================================

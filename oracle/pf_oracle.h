@@ -110,6 +110,13 @@ int32_t or_pf_run_sched(const or_model *m, const double *theta, const double *y,
                         const uint64_t *sched, int64_t P, int32_t T, int32_t nthreads,
                         double *loglik, double *xfinal, int32_t *anc, double *diag,
                         double *xhist, double *ellT);
+/* teacher-forced step i from x(t_{i-1}) = x_prev [N][P] and a(t_i) = anc [P]
+ * (NULL: identity), carried log-weights zero: x_next [N][P] = x(t_i), *incr =
+ * log Z_i, anc_next [P] = a(t_{i+1}) (i < T), diag [8] as above */
+int32_t or_pf_step(const or_model *m, const double *theta, const double *y, uint64_t seed,
+                   int64_t P, int32_t T, int32_t i, int32_t nthreads, const double *x_prev,
+                   const int32_t *anc, double *x_next, double *incr, int32_t *anc_next,
+                   double *diag);
 /* one state path by ancestry (end of Algorithm 2); path [T+1][N], idx [T+1] */
 int32_t or_sample_path(const or_model *m, const double *theta, const double *y, uint64_t seed,
                        int64_t P, int32_t T, int32_t nthreads, double *loglik, double *path,

@@ -92,9 +92,11 @@ def lib():
         L.pf_run_range.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32,
                                    _vp, _vp, _vp]
         L.pf_sample_path.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, _vp, _vp, _vp, _vp]
+        L.pf_debug_step.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, ctypes.c_int32, _vp, _vp,
+                                    _vp, _vp, _vp]
         for name in ("pf_run", "pf_wait", "pf_destroy", "pf_create", "pf_batch_run",
                      "pf_profile_enable", "pf_profile_read", "pf_measure_fma_peak",
-                     "pf_run_range", "pf_sample_path", "pf_weight_exp",
+                     "pf_run_range", "pf_sample_path", "pf_weight_exp", "pf_debug_step",
                      "pf_debug_fail_allocation", "pf_debug_fail_server_wait",
                      "pf_debug_check_counts"):
             getattr(L, name).restype = ctypes.c_int
@@ -279,6 +281,22 @@ class Filter:
         st = pf_sample_path(self, theta, y, seed, ll, path, idx, stream)
         return st, float(ll[0]), path, idx
 
+    def debug_step(self, theta, y, seed, i, x_prev, anc=None):
+        """Teacher-forced step i from x(t_{i-1}) and a(t_i) (None: identity):
+        returns (status, increment log Z_i, x(t_i) [N][P], a(t_{i+1}) [P] or
+        None for i = T)."""
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        x_prev = np.ascontiguousarray(x_prev, dtype=self.state_dtype)
+        anc = None if anc is None else np.ascontiguousarray(anc, dtype=np.int32)
+        x = np.zeros((self.N, self.P), dtype=self.state_dtype)
+        inc = np.zeros(1, dtype=np.float64)
+        nxt = np.zeros(self.P, dtype=np.int32) if i < self.T else None
+        st = lib().pf_debug_step(self.h, _ptr(theta), _ptr(y), ctypes.c_uint64(seed), i,
+                                 _ptr(x_prev), _ptr(anc), _ptr(x), _ptr(inc), _ptr(nxt))
+        st = _check(st, ok=(PF_OK, PF_EDEGENERATE))
+        return st, float(inc[0]), x, nxt
+
     def destroy(self):
         if self.h:
             lib().pf_destroy(self.h)
@@ -323,7 +341,12 @@ def pf_run_noalloc(m, P, T, dt, theta, y, seed, loglik, status=None, final_parti
                    stream=None):
     """Allocation-free run: every array is a device pointer (torch CUDA tensor);
     only enqueues on `stream`.  Raises PFError (PF_EINVAL) if the filter does not
-    fit in the library's fixed scratch array."""
+    fit in the library's fixed scratch array, and ValueError for an array that
+    is not a CUDA tensor (the library also refuses host pointers)."""
+    for name, a in (("theta", theta), ("y", y), ("loglik", loglik), ("status", status),
+                    ("final_particles", final_particles)):
+        if a is not None and not getattr(a, "is_cuda", False):
+            raise ValueError("pf_run_noalloc: %s must be a CUDA tensor" % name)
     st = lib().pf_run_noalloc(ctypes.byref(m), P, T, dt, _ptr(theta), _ptr(y),
                               ctypes.c_uint64(seed), _ptr(loglik), _ptr(status),
                               _ptr(final_particles), _stream_ptr(stream))

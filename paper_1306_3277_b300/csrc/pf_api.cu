@@ -756,6 +756,65 @@ extern "C" pf_status pf_sample_path(pf_filter* f, const double* theta, const dou
   return int(p->h_res[1]) == ST_OK ? PF_OK : PF_EDEGENERATE;
 }
 
+// ---------------------------------------------------------------------------
+// teacher-forced step (diagnostic)
+// ---------------------------------------------------------------------------
+extern "C" pf_status pf_debug_step(pf_filter* f, const double* theta, const double* y,
+                                   uint64_t seed, int32_t i, const void* x_prev,
+                                   const int32_t* anc, void* x_out, double* incr,
+                                   int32_t* anc_next) {
+  if (!f) return fail(PF_EINVAL, "filter is NULL");
+  if (!theta || !y || !x_prev) return fail(PF_EINVAL, "theta, y and x_prev are required");
+  if (i < 1 || i > f->T) return fail(PF_EINVAL, "step %d is not in [1, %d]", i, f->T);
+  pf_status ps = ensure_plan(f);
+  if (ps != PF_OK) return ps;
+  Plan* p = f->plan;
+  cudaStream_t st = f->own;
+  f->range_pos = -1;
+  CK(cudaEventSynchronize(p->ev_staged));
+  FilterDev& d = p->h_fds[0];
+  d = f->desc;
+  d.y = p->d_ycat;
+  d.seed = seed;
+  const int nth = pf_theta_size(f->m.kind);
+  const bool dev_theta = is_device_ptr(theta);
+  if (!dev_theta) memcpy(d.theta, theta, sizeof(double) * nth);
+  CK(cudaMemcpyAsync(p->d_fds, p->h_fds, sizeof(FilterDev), cudaMemcpyHostToDevice, st));
+  if (dev_theta)
+    CK(cudaMemcpyAsync(p->d_fds[0].theta, theta, sizeof(double) * nth, cudaMemcpyDeviceToDevice,
+                       st));
+  const size_t ny = size_t(f->T) * f->sh.Ny;
+  if (is_device_ptr(y)) {
+    CK(cudaMemcpyAsync(p->d_ycat, y, sizeof(double) * ny, cudaMemcpyDeviceToDevice, st));
+  } else {
+    memcpy(p->h_ycat, y, sizeof(double) * ny);
+    CK(cudaMemcpyAsync(p->d_ycat, p->h_ycat, sizeof(double) * ny, cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaEventRecord(p->ev_staged, st));
+  const size_t xs = size_t(f->m.N) * size_t(f->P) * f->sh.state_bytes;
+  CK(cudaMemcpyAsync(f->x[(i - 1) & 1], x_prev, xs, cudaMemcpyDefault, st));
+  if (anc) CK(cudaMemcpyAsync(f->anc, anc, size_t(f->P) * 4, cudaMemcpyDefault, st));
+  CK(launch_debug_ctl(p->d_fds, i, anc ? 0 : 1, st));
+  // step i's propagate and resample launches, as in a run
+  CK(enqueue_plan_steps(p, i, i, false, st));
+  if (anc_next && i < f->T) {
+    CK(launch_next_ancestors(p->d_fds, f->sh.ntiles, f->anc, st));
+    CK(cudaMemcpyAsync(anc_next, f->anc, size_t(f->P) * 4, cudaMemcpyDefault, st));
+  }
+  CK(cudaMemcpyAsync(p->h_res, p->d_res, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
+  if (x_out) CK(cudaMemcpyAsync(x_out, f->x[i & 1], xs, cudaMemcpyDefault, st));
+  CK(cudaEventRecord(p->ev_done, st));
+  CK(cudaEventSynchronize(p->ev_done));
+  const double ll = p->h_res[0];
+  if (incr) {
+    if (is_device_ptr(incr)) CK(cudaMemcpy(incr, &ll, sizeof(double), cudaMemcpyHostToDevice));
+    else *incr = ll;
+  }
+  // the filter now stands at t_i; a continuation resumes from here
+  f->range_pos = int(p->h_res[1]) == ST_OK ? i : -1;
+  return int(p->h_res[1]) == ST_OK ? PF_OK : PF_EDEGENERATE;
+}
+
 extern "C" pf_status pf_wait(pf_filter* f) {
   if (!f) return fail(PF_EINVAL, "filter is NULL");
   if (!f->plan) return PF_OK;

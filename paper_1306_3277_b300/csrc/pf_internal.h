@@ -18,6 +18,12 @@ cudaError_t launch_init(int kind, int N, int prec, const FilterDev* fds, const i
 cudaError_t launch_propagate(int kind, int N, int prec, const FilterDev* fds, const int2* tmap,
                              int nblocks, cudaStream_t st);
 cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks, cudaStream_t st);
+// the control block of fds[0] set to propagate to t_step from a loaded state,
+// ancestors from the array (anc_identity 0) or the identity (diagnostic)
+cudaError_t launch_debug_ctl(const FilterDev* fds, int step, int anc_identity, cudaStream_t st);
+// the ancestors the next propagation of fds[0] takes, into out [P] (diagnostic)
+cudaError_t launch_next_ancestors(const FilterDev* fds, int ntiles, int32_t* out,
+                                  cudaStream_t st);
 // one thread-block cluster of cluster_size CTAs per listed filter runs its
 // whole run (initial draw and all steps); the filters have at most
 // cluster_size tiles

@@ -1471,6 +1471,47 @@ __global__ void k_flow(double* __restrict__ flow, int64_t n, double peak, double
   flow[k] = v;
 }
 
+// Filter fds[0] about to propagate to t_step from a state loaded from outside
+// (a diagnostic for teacher-forced checks): the control block as after a
+// resampling (carried log-weights zero, no likelihood accumulated yet),
+// ancestors from the array or the identity, group tickets cleared.
+__global__ void k_debug_ctl(const FilterDev* __restrict__ fds, int step, int anc_identity) {
+  const FilterDev& fd = fds[0];
+  if (threadIdx.x == 0) {
+    Ctl* c = fd.ctl;
+    const double r = wk_kind(fd.kind) ? fd.theta[4] : fd.theta[2];
+    c->step = step;
+    c->rs_step = step - 1;
+    c->rs_flag = 0;
+    c->anc_identity = anc_identity;
+    c->lam_zero = 1;
+    c->status = ST_OK;
+    c->gticket = 0u;
+    c->ll = 0.0;
+    c->logP = log(double(fd.P));
+    c->L = c->logP;
+    c->c_obs = -0.5 * double(fd.Ny) * log(2.0 * 3.141592653589793 * r);
+    c->cw = -0.5 / r;
+    c->M = 0.0;
+    c->S = 0.0;
+    c->u = 0.0;
+    c->ratio = 0.0;
+  }
+  for (int g = threadIdx.x; g < fd.ngroups; g += blockDim.x) fd.gp[g].ticket = 0u;
+}
+
+// The ancestors the next propagation of filter fds[0] takes (diagnostic): the
+// array the resample kernel wrote, or the identity after a step that carried
+// its weights; nothing once the filter has finished or degenerated.
+__global__ void k_next_ancestors(const FilterDev* __restrict__ fds, int32_t* __restrict__ out) {
+  const FilterDev& fd = fds[0];
+  const Ctl* c = fd.ctl;
+  if (ldcg(&c->status) != ST_OK || ldcg(&c->step) > fd.T) return;
+  const int identity = ldcg(&c->anc_identity);
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < fd.P) out[j] = identity ? j : fd.anc[j];
+}
+
 // Copy (loglik, status, next step) of nf filters into out[3k .. 3k+2];
 // descriptors without a control block (empty server slots) give NaNs.
 __global__ void k_results(const FilterDev* __restrict__ fds, int nf, double* __restrict__ out) {
@@ -1658,6 +1699,18 @@ cudaError_t launch_mn_scan(const FilterDev* fds, const int2* tmap, int ntiles, i
   k_mn_tiles<<<ntiles, TILE, 0, st>>>(fds, tmap);
   k_mn_total<<<nf, TILE, 0, st>>>(fds, nf);
   k_mn_targets<<<ntiles, TILE, 0, st>>>(fds, tmap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_debug_ctl(const FilterDev* fds, int step, int anc_identity, cudaStream_t st) {
+  k_debug_ctl<<<1, TILE, 0, st>>>(fds, step, anc_identity);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_next_ancestors(const FilterDev* fds, int ntiles, int32_t* out,
+                                  cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  k_next_ancestors<<<ntiles, TILE, 0, st>>>(fds, out);
   return cudaGetLastError();
 }
 

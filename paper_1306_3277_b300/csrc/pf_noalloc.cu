@@ -8,15 +8,20 @@
 // all.  For them this entry point runs the same kernels as pf_run, with every
 // internal buffer (descriptor, tile map, particle state, weights, ancestors,
 // partial sums, control block) carved out of one file-scope device array of
-// fixed size, g_noalloc_scratch, which the library reserves on each GPU that
-// loads it and keeps until the process exits.
+// fixed size, g_noalloc_scratch, kept until the process exits.
+//
+// The array belongs to this file's device module, which CUDA loads on a
+// device lazily: the first call on each device loads it there, and that load
+// is what reserves the array's device memory.  So a caller should make one
+// call on every device it uses at set-up, before its own pool takes the
+// device budget and before any stream capture.
 //
 // The host never dereferences the array's name: on the host that name is
-// only a stand-in, so its device address is looked up once per device with
-// cudaGetSymbolAddress (the first call on a device does this set-up; make it
-// before any stream capture) and only that address is handed to the kernels.
+// only a stand-in, so every call looks up the array's device address on the
+// current device with cudaGetSymbolAddress (cheap once the module is loaded,
+// and never stale after a device reset) and hands only that address to the
+// kernels.
 #include <cstring>
-#include <mutex>
 
 #include "pf.h"
 #include "pf_internal.h"
@@ -28,9 +33,6 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[PF_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
 
 // Copy the descriptor (by value) and theta (device pointer) into the scratch
 // descriptor, and write the single-filter tile map (0, t).
@@ -59,19 +61,27 @@ pf_status scratch_address(void** out) {
     cudaGetLastError();
     return fail(PF_ECUDA, "pf_run_noalloc: no current CUDA device");
   }
-  if (dev < 0 || dev >= kMaxDevices) return fail(PF_EINVAL, "pf_run_noalloc: device %d", dev);
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return fail(PF_ECUDA, "pf_run_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-    }
-    g_scratch_addr[dev] = p;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return fail(PF_ECUDA, "pf_run_noalloc: cudaGetSymbolAddress on device %d: %s", dev,
+                cudaGetErrorString(e));
   }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return PF_OK;
+}
+
+// True when ptr is memory the current device's kernels can address (device or
+// managed memory).  cudaPointerGetAttributes allocates nothing; a host array
+// passed by mistake is refused here instead of faulting in a kernel.
+bool device_addressable(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 // Bump allocator over the scratch array (256-byte aligned regions).
@@ -118,6 +128,14 @@ extern "C" pf_status pf_run_noalloc(const pf_model* m, int64_t P, int32_t T, dou
   if (m->resampler == PF_RESAMPLE_MULTINOMIAL)
     return fail(PF_EINVAL, "pf_run_noalloc does not take the multinomial resampler");
   if (!theta || !y || !loglik) return fail(PF_EINVAL, "pf_run_noalloc: theta, y, loglik required");
+  {
+    const void* ptrs[] = {theta, y, loglik, status, final_particles};
+    const char* names[] = {"theta", "y", "loglik", "status", "final_particles"};
+    for (int k = 0; k < 5; ++k)
+      if (ptrs[k] && !device_addressable(ptrs[k]))
+        return fail(PF_EINVAL, "pf_run_noalloc: %s is not device memory of the current device",
+                    names[k]);
+  }
   const size_t need = layout_bytes(m, sh, P);
   if (need > size_t(PF_NOALLOC_SCRATCH_BYTES))
     return fail(PF_EINVAL,

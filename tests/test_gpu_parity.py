@@ -49,7 +49,9 @@ def test_parity(name, factory, seeds):
         o = run_oracle(w, seed)
         g = run_gpu(w, seed)
         rows, first_near = compare(w, g, o)
-        assert rows >= 1
+        # these seeds meet no near-boundary target, so every step is compared;
+        # steps after such a target are covered by the teacher-forced tests
+        assert rows == w.T and first_near is None
 
 
 def test_parity_large_config_full_particle_count():

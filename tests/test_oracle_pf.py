@@ -344,3 +344,31 @@ def test_mixed_lorenz96_unbiased_against_fp64():
     se = d.std(ddof=1) / math.sqrt(len(d))
     assert abs(d.mean()) < 4 * se + 1e-9, (d.mean(), se)
     assert np.all(np.isfinite(d))
+
+
+@pytest.mark.parametrize("prec", [O.FP64, O.MIXED])
+@pytest.mark.parametrize("thr", [1.0, 0.5])
+def test_teacher_forced_step_chain_is_the_run(prec, thr):
+    """The oracle's one-step entry (the reference of the teacher-forced GPU
+    checks) chained on its own outputs reproduces the whole run: the same
+    states, ancestors and, summed, the same log-likelihood.  With adaptive
+    resampling the chain is only followed while every step resamples (a
+    step's carried weights are not part of the one-step state)."""
+    w = W.lorenz96_8(P=300, T=12, prec=prec, ess_threshold=thr)
+    m = _om(w)
+    full = O.pf_run_ex(m, w.theta, w.y, 5, w.P, w.T)
+    run = O.pf_run(m, w.theta, w.y, 5, w.P, w.T)
+    x, anc, ll = full["xhist"][0], None, 0.0
+    for i in range(1, w.T + 1):
+        r = O.pf_step(m, w.theta, w.y, 5, w.P, w.T, i, x, anc)
+        assert r["status"] == O.OK
+        assert np.array_equal(r["x"], full["xhist"][i])
+        ll += r["incr"]
+        assert r["incr"] == run["diag"][i - 1, 6]
+        if i < w.T:
+            assert np.array_equal(r["anc_next"], full["anc"][i])
+        x, anc = r["x"], r["anc_next"]
+        if run["diag"][i - 1, 4] == 0:
+            break  # carried weights: the chain stops here
+    else:
+        assert ll == pytest.approx(run["loglik"], rel=1e-13)
