@@ -314,32 +314,39 @@ def secondary(pf, torch, dev):
     tp = time.perf_counter() - t0
     maxrel = max(abs(a - b) / abs(b) for a, b in zip(lls_b, lls_p))
     psteps = sum(w.P * w.T for w in ws)
-    # the autotuned split: small filters run whole, one thread-block cluster each
+    # the autotuned launch shape: cluster bound, branches, resample grid
     chosen = pf.pf_batch_autotune(fs, ths, ys, seeds)
+    shape = pf.pf_batch_get_shape(fs)
     t0 = time.perf_counter()
     for _ in range(reps):
         lls_a, _ = pf.pf_batch_run(fs, ths, ys, seeds)
     ta = (time.perf_counter() - t0) / reps
     maxrel_a = max(abs(a - b) / abs(b) for a, b in zip(lls_a, lls_p))
-    # the batch at each candidate cluster bound (what the autotuner compares)
-    sweep = {}
-    for bound in (0, 256, 512, 1024, 2048):
-        pf.pf_batch_configure(fs, bound)
+
+    def batch_ms(cta, branches, rs):
+        pf.pf_batch_set_shape(fs, cta, branches, rs)
         pf.pf_batch_run(fs, ths, ys, seeds)  # plan + graph build
         t0 = time.perf_counter()
         for _ in range(reps):
             pf.pf_batch_run(fs, ths, ys, seeds)
-        sweep[str(bound)] = (time.perf_counter() - t0) / reps * 1e3
-    pf.pf_batch_configure(fs, chosen)
+        return (time.perf_counter() - t0) / reps * 1e3
+
+    # the batch at candidate shapes (one field at a time, as the autotuner searches)
+    sweep_cta = {str(b): batch_ms(b, 1, 8) for b in (0, 256, 1024, 2048)}
+    sweep_br = {str(k): batch_ms(0, k, 8) for k in (1, 2, 4, 8, 16)}
+    pf.pf_batch_set_shape(fs, shape["cta_max_particles"], shape["branches"],
+                          shape["resample_blocks_per_sm"])
     out["batched_256"] = {"filters": len(ws), "batched_evals_per_s": len(ws) / tb,
                           "plain_evals_per_s": len(ws) / tp, "speedup": tp / tb,
                           "batched_particle_steps_per_s": psteps / tb,
                           "max_rel_loglik_diff_vs_plain": maxrel,
+                          "autotuned_shape": shape,
                           "autotuned_cluster_max_particles": chosen,
                           "autotuned_evals_per_s": len(ws) / ta,
                           "autotuned_speedup_vs_plain": tp / ta,
                           "autotuned_max_rel_loglik_diff_vs_plain": maxrel_a,
-                          "batch_ms_by_cluster_bound": sweep}
+                          "batch_ms_by_cluster_bound": sweep_cta,
+                          "batch_ms_by_branches": sweep_br}
     for f in fs:
         f.destroy()
     # one small filter alone: the tiled launches against one cluster per filter

@@ -221,13 +221,38 @@ pf_status pf_batch_run(int32_t nfilt, pf_filter* const* f, const double* const* 
  * twice, or cta_max_particles < 0. */
 pf_status pf_batch_configure(int32_t nfilt, pf_filter* const* f, int64_t cta_max_particles);
 
-/* Autotuner of that split: runs the batch (inputs as for pf_batch_run, on the
- * default stream, synchronously) with each candidate bound (0, 256, 512, 1024,
- * 2048 particles), one untimed and two timed runs each on the host clock,
- * keeps the fastest for the filter list (as pf_batch_configure would) and
- * returns it in *chosen (may be NULL).  The filters' results are those of
- * their last run, identical for every bound.  Errors: those of
- * pf_batch_configure and pf_batch_run, returned as soon as one occurs. */
+/* The whole launch shape of a batch.  No field changes any result: every
+ * filter is computed by the same functions in the same order whatever the
+ * shape; only how the filters share the GPU changes. */
+typedef struct {
+  int64_t cta_max_particles;      /* the cluster path's bound, as pf_batch_configure (0: none)    */
+  int32_t branches;               /* >= 1: the tiled filters, longest runs first, are dealt in turn
+                                     into this many independent chains of per-step launches; the
+                                     chains run concurrently as parallel branches of the plan's
+                                     CUDA graph, each at its own pace, and meet only at the end of
+                                     the run (capped at the number of tiled filters; one chain
+                                     when some filter resamples multinomially)                  */
+  int32_t resample_blocks_per_sm; /* blocks per SM in the resample kernel's grid, 1..8            */
+} pf_batch_shape;
+
+/* Set / read the launch shape used for this exact filter list (as
+ * pf_batch_configure: host-only; a cached plan is rebuilt on its next use).
+ * The default shape is {0, 1, 8}.  PF_EINVAL for a bad list (as
+ * pf_batch_configure), a NULL shape, cta_max_particles < 0, branches < 1 or
+ * resample_blocks_per_sm outside 1..8. */
+pf_status pf_batch_set_shape(int32_t nfilt, pf_filter* const* f, const pf_batch_shape* shape);
+pf_status pf_batch_get_shape(int32_t nfilt, pf_filter* const* f, pf_batch_shape* shape);
+
+/* Autotuner of the launch shape: runs the batch (inputs as for pf_batch_run,
+ * on the default stream, synchronously), one untimed and two timed runs per
+ * candidate on the host clock, searching one field at a time from the
+ * default: the cluster bound (0, 256, 512, 1024, 2048 particles), then the
+ * number of branches (1, 2, 4, 8, 16), then the resample grid (2, 4, 8 blocks
+ * per SM).  It keeps the fastest shape for the filter list (as
+ * pf_batch_set_shape would; pf_batch_get_shape reads it back) and returns its
+ * cluster bound in *chosen (may be NULL).  The filters' results are those of
+ * their last run, identical for every shape.  Errors: those of
+ * pf_batch_set_shape and pf_batch_run, returned as soon as one occurs. */
 pf_status pf_batch_autotune(int32_t nfilt, pf_filter* const* f, const double* const* theta,
                             const double* const* y, const uint64_t* seeds, int64_t* chosen);
 

@@ -39,6 +39,16 @@ class pf_model(ctypes.Structure):
                 ("obs_every", ctypes.c_int32), ("obs_count", ctypes.c_int32)]
 
 
+class pf_batch_shape(ctypes.Structure):
+    """Launch shape of a batch (include/pf.h): no field changes any result."""
+    _fields_ = [("cta_max_particles", ctypes.c_int64), ("branches", ctypes.c_int32),
+                ("resample_blocks_per_sm", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {"cta_max_particles": int(self.cta_max_particles), "branches": int(self.branches),
+                "resample_blocks_per_sm": int(self.resample_blocks_per_sm)}
+
+
 _lib = None
 _vp = ctypes.c_void_p
 
@@ -85,6 +95,12 @@ def lib():
         L.pf_smc2_run.restype = ctypes.c_int
         L.pf_batch_configure.argtypes = [ctypes.c_int32, ctypes.POINTER(_vp), ctypes.c_int64]
         L.pf_batch_configure.restype = ctypes.c_int
+        L.pf_batch_set_shape.argtypes = [ctypes.c_int32, ctypes.POINTER(_vp),
+                                         ctypes.POINTER(pf_batch_shape)]
+        L.pf_batch_set_shape.restype = ctypes.c_int
+        L.pf_batch_get_shape.argtypes = [ctypes.c_int32, ctypes.POINTER(_vp),
+                                         ctypes.POINTER(pf_batch_shape)]
+        L.pf_batch_get_shape.restype = ctypes.c_int
         L.pf_batch_autotune.argtypes = [ctypes.c_int32, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                         ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.POINTER(ctypes.c_int64)]
@@ -425,8 +441,27 @@ def pf_batch_configure(filters, cta_max_particles):
     _check(lib().pf_batch_configure(nf, hs, int(cta_max_particles)))
 
 
+def pf_batch_set_shape(filters, cta_max_particles=0, branches=1, resample_blocks_per_sm=8):
+    """Set the launch shape used for this filter list (results do not change)."""
+    nf = len(filters)
+    hs = (_vp * nf)(*[f.h for f in filters])
+    sh = pf_batch_shape(int(cta_max_particles), int(branches), int(resample_blocks_per_sm))
+    _check(lib().pf_batch_set_shape(nf, hs, ctypes.byref(sh)))
+
+
+def pf_batch_get_shape(filters):
+    """The launch shape used for this filter list, as a dict."""
+    nf = len(filters)
+    hs = (_vp * nf)(*[f.h for f in filters])
+    sh = pf_batch_shape()
+    _check(lib().pf_batch_get_shape(nf, hs, ctypes.byref(sh)))
+    return sh.as_dict()
+
+
 def pf_batch_autotune(filters, thetas, ys, seeds):
-    """Time the candidate splits on these inputs, keep the fastest, return it."""
+    """Time candidate launch shapes on these inputs (cluster bound, branches,
+    resample grid, one field at a time), keep the fastest for the list and
+    return its cluster bound (pf_batch_get_shape gives the whole shape)."""
     nf = len(filters)
     hs = (_vp * nf)(*[f.h for f in filters])
     th = [np.ascontiguousarray(t, dtype=np.float64) if not hasattr(t, "data_ptr") else t

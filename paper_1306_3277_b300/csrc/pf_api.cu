@@ -255,8 +255,9 @@ extern "C" pf_status pf_create(const pf_model* m, int64_t P, int32_t T, double d
 // ---------------------------------------------------------------------------
 static std::mutex g_plan_mu;
 static std::map<std::vector<pf_filter*>, Plan*> g_plans;  // cached batch plans
-// per filter list: the largest particle count sent to the cluster path
-static std::map<std::vector<pf_filter*>, int64_t> g_cta_choice;
+// per filter list: its launch shape (cluster bound, branches, resample grid)
+static const pf_batch_shape kDefaultShape = {0, 1, 8};
+static std::map<std::vector<pf_filter*>, pf_batch_shape> g_shapes;
 
 static void destroy_plan(Plan* p) {
   if (!p) return;
@@ -273,23 +274,22 @@ static void destroy_plan(Plan* p) {
   if (p->ev_done) cudaEventDestroy(p->ev_done);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->ev_fork_br) cudaEventDestroy(p->ev_fork_br);
+  for (Branch& b : p->branches) {
+    if (b.st) cudaStreamSynchronize(b.st);
+    if (b.ev_join) cudaEventDestroy(b.ev_join);
+    if (b.st) cudaStreamDestroy(b.st);
+  }
   if (p->st2) cudaStreamDestroy(p->st2);
   if (p->st) cudaStreamDestroy(p->st);
   delete p;
 }
 
-// The launch sequence of steps first..last of a plan: the initial draw when
-// `init` (normally first == 1), then for every step one propagate launch per
-// class and one resample launch (only over the filters that are still
-// running), then the results gather.  hook(i) is called after the propagate
-// launches of step i (and hook(0) after init), to enqueue work that reads
-// x(t_i).  With a profiler, every launch is bracketed by CUDA events on the
-// same stream.
-static cudaError_t no_hook(int) { return cudaSuccess; }
-
+// Steps first..last of one branch on st (the initial draw of its filters when
+// init).
 template <typename Hook>
-static cudaError_t enqueue_steps(Plan* p, int first, int last, cudaStream_t st, Profiler* prof,
-                                 Hook&& hook, bool init, bool results = true) {
+static cudaError_t enqueue_branch(Plan* p, const Branch& b, int first, int last,
+                                  cudaStream_t st, Profiler* prof, Hook&& hook, bool init) {
   cudaError_t le = cudaSuccess;
   auto timed = [&](int kind, auto&& launch) {
     if (prof) prof->begin(kind, st);
@@ -297,9 +297,10 @@ static cudaError_t enqueue_steps(Plan* p, int first, int last, cudaStream_t st, 
     if (prof) prof->end(st);
     return r;
   };
+  const int2* tall = p->d_tmap + b.all_offset;
   if (init) {
-    for (size_t c = 0; c < p->classes.size() && le == cudaSuccess; ++c) {
-      const PlanClass& pc = p->classes[c];
+    for (size_t c = 0; c < b.classes.size() && le == cudaSuccess; ++c) {
+      const PlanClass& pc = b.classes[c];
       le = timed(PROF_INIT, [&] {
         return launch_init(pc.kind, pc.N, pc.prec, p->d_fds, p->d_tmap + pc.offset, pc.ntiles,
                            st);
@@ -307,26 +308,65 @@ static cudaError_t enqueue_steps(Plan* p, int first, int last, cudaStream_t st, 
     }
     if (le == cudaSuccess) le = hook(0);
   }
-  for (int i = first; i <= last && le == cudaSuccess; ++i) {
-    for (size_t c = 0; c < p->classes.size() && le == cudaSuccess; ++c) {
-      const PlanClass& pc = p->classes[c];
-      if (p->cnt_cls[c][i] == 0) continue;
+  for (int i = first; i <= std::min(last, b.maxT) && le == cudaSuccess; ++i) {
+    for (size_t c = 0; c < b.classes.size() && le == cudaSuccess; ++c) {
+      const PlanClass& pc = b.classes[c];
+      if (b.cnt_cls[c][i] == 0) continue;
       le = timed(PROF_PROPAGATE, [&] {
         return launch_propagate(pc.kind, pc.N, pc.prec, p->d_fds, p->d_tmap + pc.offset,
-                                p->cnt_cls[c][i], st);
+                                b.cnt_cls[c][i], st);
       });
     }
     if (le == cudaSuccess) le = hook(i);
-    if (le == cudaSuccess && p->has_mn && p->cnt_all[i + 1] > 0)
-      le = timed(PROF_RESAMPLE, [&] {
-        return launch_mn_scan(p->d_fds, p->d_tmap, p->cnt_all[i + 1], p->nf, st);
-      });
-    if (le == cudaSuccess && p->cnt_all[i + 1] > 0)
+    if (le == cudaSuccess && b.has_mn && b.cnt_all[i + 1] > 0)
       le = timed(PROF_RESAMPLE,
-                 [&] { return launch_resample(p->d_fds, p->d_tmap, p->cnt_all[i + 1], st); });
+                 [&] { return launch_mn_scan(p->d_fds, tall, b.cnt_all[i + 1], p->nf, st); });
+    if (le == cudaSuccess && b.cnt_all[i + 1] > 0)
+      le = timed(PROF_RESAMPLE, [&] {
+        return launch_resample(p->d_fds, tall, b.cnt_all[i + 1], st,
+                               p->shape.resample_blocks_per_sm);
+      });
   }
-  if (le == cudaSuccess && results)
-    le = timed(PROF_RESULTS, [&] { return launch_results(p->d_fds, p->nf, p->d_res, st); });
+  return le;
+}
+
+// The launch sequence of steps first..last of a plan: the initial draw when
+// `init` (normally first == 1), then for every step of every branch one
+// propagate launch per class and one resample launch (only over the branch's
+// filters that are still running), then the results gather.  Branches after
+// the first are forked off st with an event and joined back before the
+// results (with a profiler, or a single branch, everything runs on st, one
+// launch after the other).  hook(i) is called after the propagate launches of
+// step i (and hook(0) after init), to enqueue work that reads x(t_i); it is
+// only used with single-filter plans.  With a profiler, every launch is
+// bracketed by CUDA events on the same stream.
+static cudaError_t no_hook(int) { return cudaSuccess; }
+
+template <typename Hook>
+static cudaError_t enqueue_steps(Plan* p, int first, int last, cudaStream_t st, Profiler* prof,
+                                 Hook&& hook, bool init, bool results = true) {
+  cudaError_t le = cudaSuccess;
+  const size_t nb = p->branches.size();
+  if (nb <= 1 || prof) {
+    for (size_t b = 0; b < nb && le == cudaSuccess; ++b)
+      le = enqueue_branch(p, p->branches[b], first, last, st, prof, hook, init);
+  } else {
+    le = cudaEventRecord(p->ev_fork_br, st);
+    for (size_t b = 1; b < nb && le == cudaSuccess; ++b) {
+      const Branch& br = p->branches[b];
+      le = cudaStreamWaitEvent(br.st, p->ev_fork_br, 0);
+      if (le == cudaSuccess) le = enqueue_branch(p, br, first, last, br.st, nullptr, hook, init);
+      if (le == cudaSuccess) le = cudaEventRecord(br.ev_join, br.st);
+    }
+    if (le == cudaSuccess) le = enqueue_branch(p, p->branches[0], first, last, st, nullptr, hook, init);
+    for (size_t b = 1; b < nb && le == cudaSuccess; ++b)
+      le = cudaStreamWaitEvent(st, p->branches[b].ev_join, 0);
+  }
+  if (le == cudaSuccess && results) {
+    if (prof) prof->begin(PROF_RESULTS, st);
+    le = launch_results(p->d_fds, p->nf, p->d_res, st);
+    if (prof) prof->end(st);
+  }
   return le;
 }
 
@@ -376,21 +416,16 @@ static bool cta_eligible(const pf_filter* f, int64_t cta_max_p) {
          f->m.resampler != PF_RESAMPLE_MULTINOMIAL;
 }
 
-pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out, int64_t cta_max_p) {
+pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out,
+                          const pf_batch_shape& shape) {
   Plan* p = new Plan();
   p->filters = fl;
-  p->cta_max_p = cta_max_p;
+  p->shape = shape;
+  const int64_t cta_max_p = shape.cta_max_particles;
   const int nf = int(fl.size());
   std::vector<int> order(nf);
   for (int k = 0; k < nf; ++k) order[k] = k;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return fl[a]->T > fl[b]->T; });
-  // classes: (kind, N, prec)
-  std::map<std::tuple<int, int, int>, int> cls_index;
-  std::vector<std::vector<int2>> cls_tiles;
-  std::vector<std::vector<int>> cls_T;
-  std::vector<int2> all_tiles;
-  std::vector<int> all_T;
-  int maxT = 0;
   size_t ytot = 0;
   p->yoff.resize(nf);
   for (int k = 0; k < nf; ++k) {
@@ -414,42 +449,23 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out, int64_t
     cta_all.insert(cta_all.end(), v.begin(), v.end());
   }
   p->cta_total = int(cta_all.size());
-  for (int k : order) {
-    pf_filter* f = fl[k];
-    if (cta_eligible(f, cta_max_p)) continue;
-    auto key = std::make_tuple(f->m.kind, f->m.N, f->m.prec);
-    auto it = cls_index.find(key);
-    int c;
-    if (it == cls_index.end()) {
-      c = int(cls_tiles.size());
-      cls_index[key] = c;
-      cls_tiles.emplace_back();
-      cls_T.emplace_back();
-      p->classes.push_back({f->m.kind, f->m.N, f->m.prec, 0, 0});
-    } else {
-      c = it->second;
-    }
-    for (int t = 0; t < f->sh.ntiles; ++t) {
-      cls_tiles[c].push_back(make_int2(k, t));
-      cls_T[c].push_back(f->T);
-      all_tiles.push_back(make_int2(k, t));
-      all_T.push_back(f->T);
-    }
-    maxT = std::max(maxT, f->T);
-  }
-  // one device array: all tiles, then each class's tiles
-  std::vector<int2> tm(all_tiles);
-  for (size_t c = 0; c < cls_tiles.size(); ++c) {
-    p->classes[c].offset = int(tm.size());
-    p->classes[c].ntiles = int(cls_tiles[c].size());
-    tm.insert(tm.end(), cls_tiles[c].begin(), cls_tiles[c].end());
-  }
-  p->nf = nf;
-  p->maxT = maxT;
+  // the tiled filters, longest runs first, dealt in turn into the branches
+  std::vector<int> tiled;
+  for (int k : order)
+    if (!cta_eligible(fl[k], cta_max_p)) tiled.push_back(k);
   for (pf_filter* f : fl) p->has_mn = p->has_mn || f->m.resampler == PF_RESAMPLE_MULTINOMIAL;
-  p->ntiles_all = int(all_tiles.size());
-  // per-step counts: tiles of filters with T >= i
-  auto counts = [&](const std::vector<int>& Ts, std::vector<int>& cnt) {
+  // the multinomial spacing kernels walk every filter of the plan: one branch
+  int nbr = p->has_mn ? 1 : std::max(1, std::min<int>(shape.branches, int(tiled.size())));
+  std::vector<std::vector<int>> members(nbr);
+  for (size_t r = 0; r < tiled.size(); ++r) members[r % nbr].push_back(tiled[r]);
+  // one device array: every tiled filter's tiles (sorted by T), then per
+  // branch its tiles and each of its classes' tiles (all sorted by T)
+  std::vector<int2> tm;
+  for (int k : tiled)
+    for (int t = 0; t < fl[k]->sh.ntiles; ++t) tm.push_back(make_int2(k, t));
+  p->ntiles_all = int(tm.size());
+  // per-step counts: entries of a T-sorted list with T >= i
+  auto counts = [](const std::vector<int>& Ts, int maxT, std::vector<int>& cnt) {
     cnt.assign(maxT + 2, 0);
     for (int i = 1; i <= maxT + 1; ++i) {
       int n = 0;
@@ -457,9 +473,50 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out, int64_t
       cnt[i] = n;
     }
   };
-  counts(all_T, p->cnt_all);
-  p->cnt_cls.resize(cls_tiles.size());
-  for (size_t c = 0; c < cls_tiles.size(); ++c) counts(cls_T[c], p->cnt_cls[c]);
+  int maxT = 0;
+  p->branches.resize(nbr);
+  for (int bi = 0; bi < nbr; ++bi) {
+    Branch& br = p->branches[bi];
+    std::map<std::tuple<int, int, int>, int> cls_index;
+    std::vector<std::vector<int2>> cls_tiles;
+    std::vector<std::vector<int>> cls_T;
+    std::vector<int> all_T;
+    br.all_offset = int(tm.size());
+    for (int k : members[bi]) {
+      pf_filter* f = fl[k];
+      auto key = std::make_tuple(f->m.kind, f->m.N, f->m.prec);
+      auto it = cls_index.find(key);
+      int c;
+      if (it == cls_index.end()) {
+        c = int(cls_tiles.size());
+        cls_index[key] = c;
+        cls_tiles.emplace_back();
+        cls_T.emplace_back();
+        br.classes.push_back({f->m.kind, f->m.N, f->m.prec, 0, 0});
+      } else {
+        c = it->second;
+      }
+      for (int t = 0; t < f->sh.ntiles; ++t) {
+        cls_tiles[c].push_back(make_int2(k, t));
+        cls_T[c].push_back(f->T);
+        tm.push_back(make_int2(k, t));
+        all_T.push_back(f->T);
+      }
+      br.maxT = std::max(br.maxT, f->T);
+      br.has_mn = br.has_mn || f->m.resampler == PF_RESAMPLE_MULTINOMIAL;
+    }
+    for (size_t c = 0; c < cls_tiles.size(); ++c) {
+      br.classes[c].offset = int(tm.size());
+      br.classes[c].ntiles = int(cls_tiles[c].size());
+      tm.insert(tm.end(), cls_tiles[c].begin(), cls_tiles[c].end());
+    }
+    counts(all_T, br.maxT, br.cnt_all);
+    br.cnt_cls.resize(cls_tiles.size());
+    for (size_t c = 0; c < cls_tiles.size(); ++c) counts(cls_T[c], br.maxT, br.cnt_cls[c]);
+    maxT = std::max(maxT, br.maxT);
+  }
+  p->nf = nf;
+  p->maxT = maxT;
 
   cudaError_t e = cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_staged, cudaEventDisableTiming);
@@ -479,6 +536,14 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out, int64_t
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(p->d_cta, cta_all.data(), sizeof(int) * cta_all.size(),
                           cudaMemcpyHostToDevice, p->st);
+  }
+  if (e == cudaSuccess && p->branches.size() > 1) {
+    e = cudaEventCreateWithFlags(&p->ev_fork_br, cudaEventDisableTiming);
+    for (size_t b = 1; b < p->branches.size() && e == cudaSuccess; ++b) {
+      e = cudaStreamCreateWithFlags(&p->branches[b].st, cudaStreamNonBlocking);
+      if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&p->branches[b].ev_join, cudaEventDisableTiming);
+    }
   }
   if (e == cudaSuccess && !tm.empty())
     e = cudaMemcpyAsync(p->d_tmap, tm.data(), sizeof(int2) * tm.size(), cudaMemcpyHostToDevice,
@@ -603,7 +668,7 @@ extern "C" pf_status pf_run(pf_filter* f, const double* theta, const double* y, 
   }
   if (!f->plan) {
     std::vector<pf_filter*> one{f};
-    pf_status ps = build_plan(one, &f->plan, 0);
+    pf_status ps = build_plan(one, &f->plan, kDefaultShape);
     if (ps != PF_OK) return ps;
   }
   Plan* p = f->plan;
@@ -649,7 +714,7 @@ static pf_status ensure_history(pf_filter* f) {
 static pf_status ensure_plan(pf_filter* f) {
   if (f->plan) return PF_OK;
   std::vector<pf_filter*> one{f};
-  return build_plan(one, &f->plan, 0);
+  return build_plan(one, &f->plan, kDefaultShape);
 }
 
 extern "C" pf_status pf_run_range(pf_filter* f, const double* theta, const double* y,
@@ -840,9 +905,9 @@ extern "C" pf_status pf_destroy(pf_filter* f) {
         ++it;
       }
     }
-    for (auto it = g_cta_choice.begin(); it != g_cta_choice.end();) {
+    for (auto it = g_shapes.begin(); it != g_shapes.end();) {
       if (std::find(it->first.begin(), it->first.end(), f) != it->first.end())
-        it = g_cta_choice.erase(it);
+        it = g_shapes.erase(it);
       else
         ++it;
     }
@@ -860,7 +925,7 @@ extern "C" pf_status pf_destroy(pf_filter* f) {
 // The cached launch plan of a filter list (built on first use; at most eight
 // are kept, the oldest evicted).  The filters must be distinct.
 pf_status pfb::batch_plan(const std::vector<pf_filter*>& key, Plan** out) {
-  int64_t cta_max_p = 0;
+  pf_batch_shape shape = kDefaultShape;
   {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto it = g_plans.find(key);
@@ -868,11 +933,11 @@ pf_status pfb::batch_plan(const std::vector<pf_filter*>& key, Plan** out) {
       *out = it->second;
       return PF_OK;
     }
-    auto c = g_cta_choice.find(key);
-    if (c != g_cta_choice.end()) cta_max_p = c->second;
+    auto c = g_shapes.find(key);
+    if (c != g_shapes.end()) shape = c->second;
   }
   Plan* p = nullptr;
-  pf_status ps = build_plan(key, &p, cta_max_p);
+  pf_status ps = build_plan(key, &p, shape);
   if (ps != PF_OK) return ps;
   std::lock_guard<std::mutex> lk(g_plan_mu);
   if (g_plans.size() >= 8) {
@@ -925,48 +990,104 @@ static pf_status batch_key(int32_t nfilt, pf_filter* const* f, std::vector<pf_fi
   return PF_OK;
 }
 
-extern "C" pf_status pf_batch_configure(int32_t nfilt, pf_filter* const* f,
-                                        int64_t cta_max_particles) {
+static bool same_shape(const pf_batch_shape& a, const pf_batch_shape& b) {
+  return a.cta_max_particles == b.cta_max_particles && a.branches == b.branches &&
+         a.resample_blocks_per_sm == b.resample_blocks_per_sm;
+}
+
+extern "C" pf_status pf_batch_set_shape(int32_t nfilt, pf_filter* const* f,
+                                        const pf_batch_shape* shape) {
   std::vector<pf_filter*> key;
   pf_status ps = batch_key(nfilt, f, &key);
   if (ps != PF_OK) return ps;
-  if (cta_max_particles < 0) return fail(PF_EINVAL, "cta_max_particles must be >= 0");
+  if (!shape) return fail(PF_EINVAL, "shape is NULL");
+  if (shape->cta_max_particles < 0) return fail(PF_EINVAL, "cta_max_particles must be >= 0");
+  if (shape->branches < 1) return fail(PF_EINVAL, "branches must be >= 1");
+  if (shape->resample_blocks_per_sm < 1 || shape->resample_blocks_per_sm > 8)
+    return fail(PF_EINVAL, "resample_blocks_per_sm must be in 1..8");
   std::lock_guard<std::mutex> lk(g_plan_mu);
-  g_cta_choice[key] = cta_max_particles;
+  g_shapes[key] = *shape;
   auto it = g_plans.find(key);
-  if (it != g_plans.end() && it->second->cta_max_p != cta_max_particles) {
-    destroy_plan(it->second);  // rebuilt with the new split on its next use
+  if (it != g_plans.end() && !same_shape(it->second->shape, *shape)) {
+    destroy_plan(it->second);  // rebuilt with the new shape on its next use
     g_plans.erase(it);
   }
+  return PF_OK;
+}
+
+extern "C" pf_status pf_batch_get_shape(int32_t nfilt, pf_filter* const* f,
+                                        pf_batch_shape* shape) {
+  std::vector<pf_filter*> key;
+  pf_status ps = batch_key(nfilt, f, &key);
+  if (ps != PF_OK) return ps;
+  if (!shape) return fail(PF_EINVAL, "shape is NULL");
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  auto it = g_shapes.find(key);
+  *shape = it != g_shapes.end() ? it->second : kDefaultShape;
+  return PF_OK;
+}
+
+extern "C" pf_status pf_batch_configure(int32_t nfilt, pf_filter* const* f,
+                                        int64_t cta_max_particles) {
+  pf_batch_shape shape = kDefaultShape;
+  pf_status ps = pf_batch_get_shape(nfilt, f, &shape);
+  if (ps != PF_OK) return ps;
+  shape.cta_max_particles = cta_max_particles;
+  return pf_batch_set_shape(nfilt, f, &shape);
+}
+
+// Host-clock time of the list's batch run with the given shape: one untimed
+// run (plan and graph), then the mean of two timed ones.
+static pf_status time_shape(int32_t nfilt, pf_filter* const* f, const double* const* theta,
+                            const double* const* y, const uint64_t* seeds,
+                            const pf_batch_shape& shape, double* ms) {
+  std::vector<double> ll(nfilt > 0 ? nfilt : 1);
+  std::vector<int32_t> st(nfilt > 0 ? nfilt : 1);
+  pf_status ps = pf_batch_set_shape(nfilt, f, &shape);
+  if (ps != PF_OK) return ps;
+  double acc = 0.0;
+  for (int rep = 0; rep < 3; ++rep) {
+    const auto t0 = std::chrono::steady_clock::now();
+    ps = pf_batch_run(nfilt, f, theta, y, seeds, ll.data(), st.data(), nullptr);
+    if (ps != PF_OK) return ps;
+    const auto t1 = std::chrono::steady_clock::now();
+    if (rep > 0) acc += std::chrono::duration<double, std::milli>(t1 - t0).count();
+  }
+  *ms = acc / 2.0;
   return PF_OK;
 }
 
 extern "C" pf_status pf_batch_autotune(int32_t nfilt, pf_filter* const* f,
                                        const double* const* theta, const double* const* y,
                                        const uint64_t* seeds, int64_t* chosen) {
-  static const int64_t candidates[] = {0, 256, 512, 1024, 2048};
-  std::vector<double> ll(nfilt > 0 ? nfilt : 1);
-  std::vector<int32_t> st(nfilt > 0 ? nfilt : 1);
+  static const int64_t cta_bounds[] = {0, 256, 512, 1024, 2048};
+  static const int32_t branch_counts[] = {1, 2, 4, 8, 16};
+  static const int32_t rs_grids[] = {2, 4, 8};
+  pf_batch_shape best = kDefaultShape;
   double best_ms = 0.0;
-  int64_t best = 0;
-  for (int64_t c : candidates) {
-    pf_status ps = pf_batch_configure(nfilt, f, c);
-    if (ps != PF_OK) return ps;
-    double ms = 0.0;
-    for (int rep = 0; rep < 3; ++rep) {  // plan and graph, then two timed runs
-      const auto t0 = std::chrono::steady_clock::now();
-      ps = pf_batch_run(nfilt, f, theta, y, seeds, ll.data(), st.data(), nullptr);
+  pf_status ps = time_shape(nfilt, f, theta, y, seeds, best, &best_ms);
+  if (ps != PF_OK) return ps;
+  // one field at a time, from the default
+  for (int field = 0; field < 3; ++field) {
+    const int n = field == 0 ? 5 : field == 1 ? 5 : 3;
+    const pf_batch_shape base = best;
+    for (int c = 0; c < n; ++c) {
+      pf_batch_shape cand = base;
+      if (field == 0) cand.cta_max_particles = cta_bounds[c];
+      else if (field == 1) cand.branches = branch_counts[c];
+      else cand.resample_blocks_per_sm = rs_grids[c];
+      if (same_shape(cand, base)) continue;
+      double ms = 0.0;
+      ps = time_shape(nfilt, f, theta, y, seeds, cand, &ms);
       if (ps != PF_OK) return ps;
-      const auto t1 = std::chrono::steady_clock::now();
-      if (rep > 0) ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
-    }
-    if (c == candidates[0] || ms < best_ms) {
-      best_ms = ms;
-      best = c;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = cand;
+      }
     }
   }
-  pf_status ps = pf_batch_configure(nfilt, f, best);
-  if (ps == PF_OK && chosen) *chosen = best;
+  ps = pf_batch_set_shape(nfilt, f, &best);
+  if (ps == PF_OK && chosen) *chosen = best.cta_max_particles;
   return ps;
 }
 

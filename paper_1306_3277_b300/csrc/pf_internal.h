@@ -17,7 +17,10 @@ cudaError_t launch_init(int kind, int N, int prec, const FilterDev* fds, const i
                         int nblocks, cudaStream_t st);
 cudaError_t launch_propagate(int kind, int N, int prec, const FilterDev* fds, const int2* tmap,
                              int nblocks, cudaStream_t st);
-cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks, cudaStream_t st);
+// resample kernel over the listed tiles, its grid at most blocks_per_sm (1..8)
+// blocks per SM
+cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks, cudaStream_t st,
+                            int blocks_per_sm = 8);
 // the control block of fds[0] set to propagate to t_step from a loaded state,
 // ancestors from the array (anc_identity 0) or the identity (diagnostic)
 cudaError_t launch_debug_ctl(const FilterDev* fds, int step, int anc_identity, cudaStream_t st);

@@ -76,38 +76,6 @@ __device__ __forceinline__ void l96_rk4_step(R (&x)[N], R F, R dt, R h2, R h3, R
   l96_rk4_step_f<N, R>(x, [F](int) { return F; }, dt, h2, h3, h6);
 }
 
-// ---------------------------------------------------------------------------
-// Packed FP32 pairs (sm_100-family f32x2 instructions): one instruction does
-// the same IEEE single-precision operation on both halves of a 64-bit
-// register, so a packed computation gives bit for bit the scalar results
-// with half the instructions issued.
-// ---------------------------------------------------------------------------
-typedef unsigned long long f32x2;
-
-__device__ __forceinline__ f32x2 pk(float lo, float hi) {
-  f32x2 d;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
-  return d;
-}
-__device__ __forceinline__ void upk(f32x2 v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f32x2 swp(f32x2 v) {
-  float a, b;
-  upk(v, a, b);
-  return pk(b, a);
-}
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
-  f32x2 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
-  f32x2 d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-
 // Lorenz '96 right-hand side for the component pair p = (p, p + H) of a state
 // stored as H = N/2 pairs; the cyclic neighbours of the first and last pairs
 // are the swapped halves of the pairs at the other end.
@@ -174,14 +142,12 @@ __device__ __forceinline__ void normals(float (&z)[N], uint64_t seed, uint32_t j
                                         uint32_t purpose, uint32_t b0 = 0) {
 #pragma unroll
   for (int b = 0; b < (N + 3) / 4; ++b) {
-    const uint4 w = rng_block(seed, j, i, purpose, b0 + b);
-    float z0, z1, z2, z3;
-    normal_pair32(w.x, w.y, &z0, &z1);
-    normal_pair32(w.z, w.w, &z2, &z3);
-    z[4 * b] = z0;
-    if (4 * b + 1 < N) z[4 * b + 1] = z1;
-    if (4 * b + 2 < N) z[4 * b + 2] = z2;
-    if (4 * b + 3 < N) z[4 * b + 3] = z3;
+    float q[4];
+    normal_quad32(rng_block(seed, j, i, purpose, b0 + b), q);
+    z[4 * b] = q[0];
+    if (4 * b + 1 < N) z[4 * b + 1] = q[1];
+    if (4 * b + 2 < N) z[4 * b + 2] = q[2];
+    if (4 * b + 3 < N) z[4 * b + 3] = q[3];
   }
 }
 
@@ -1664,7 +1630,7 @@ cudaError_t launch_filter_cluster(int kind, int N, int prec, const FilterDev* fd
 }
 
 cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks,
-                            cudaStream_t st) {
+                            cudaStream_t st, int blocks_per_sm) {
   if (nblocks <= 0) return cudaSuccess;
   static int sms = 0;
   if (sms == 0) {
@@ -1673,7 +1639,8 @@ cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks,
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       sms = 148;
   }
-  const int grid = std::min(nblocks, sms * RESAMPLE_BLOCKS_PER_SM);
+  const int bps = std::min(std::max(blocks_per_sm, 1), RESAMPLE_BLOCKS_PER_SM);
+  const int grid = std::min(nblocks, sms * bps);
   const cudaError_t e = launch_chained(k_resample, unsigned(grid), st, fds, tmap, nblocks);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

@@ -110,15 +110,31 @@ struct pf_filter {
 
 namespace pfb {
 
-// A launch plan: descriptors of its filters, tile maps sorted by T
-// (descending) and one instantiated CUDA graph covering the whole run.
+// One independent chain of per-step launches over some of a plan's tiled
+// filters: its tile maps (sorted by T, descending) and per-step tile counts.
+// The branches of a plan run concurrently, each at its own pace (branch 0 on
+// the launching stream, the others on their own streams, forked and joined
+// with events, so a captured graph holds them as parallel branches).
+struct Branch {
+  std::vector<PlanClass> classes;           // offset / ntiles into Plan::d_tmap
+  int all_offset = 0;                       // the branch's all-tiles map in Plan::d_tmap
+  int maxT = 0;
+  bool has_mn = false;                      // some filter resamples multinomially
+  std::vector<int> cnt_all;                 // [i]: tiles of the branch's filters with T >= i
+  std::vector<std::vector<int>> cnt_cls;    // per class
+  cudaStream_t st = nullptr;                // branches 1..: their own stream
+  cudaEvent_t ev_join = nullptr;
+};
+
+// A launch plan: descriptors of its filters, tile maps and one instantiated
+// CUDA graph covering the whole run.
 struct Plan {
   std::vector<pf_filter*> filters;
-  int nf = 0, maxT = 0, ntiles_all = 0;
+  int nf = 0, maxT = 0, ntiles_all = 0;     // d_tmap[0, ntiles_all): every tiled filter's tiles
   bool has_mn = false;                      // some filter resamples multinomially
-  std::vector<PlanClass> classes;
-  std::vector<int> cnt_all;                 // [i]: tiles of filters with T >= i
-  std::vector<std::vector<int>> cnt_cls;    // per class
+  pf_batch_shape shape{0, 1, 8};            // the launch shape the plan was built for
+  std::vector<Branch> branches;
+  cudaEvent_t ev_fork_br = nullptr;         // forks the branches off the launching stream
   std::vector<size_t> yoff;                 // offset of each filter's y in d_ycat
   FilterDev* d_fds = nullptr;
   FilterDev* h_fds = nullptr;               // pinned
@@ -133,7 +149,6 @@ struct Plan {
   // cluster path: filters with at most cta_max_p particles (0: none) and at
   // most MAX_CLUSTER_TILES tiles run whole, one thread-block cluster each, on
   // a side branch of the graph
-  int64_t cta_max_p = 0;
   int cta_total = 0;
   std::vector<PlanClass> cta_classes;       // offset / ntiles = first / count in d_cta
   std::vector<int> cta_cluster;             // cluster size (= tiles) of each of those
@@ -150,7 +165,7 @@ bool injected_alloc_failure();
 // scheduler chosen to report a CUDA error.
 bool injected_wait_failure();
 pf_status check_shape(const pf_model* m, int64_t P, int32_t T, double dt, Shape* sh);
-pf_status build_plan(const std::vector<pf_filter*>& fl, Plan** out, int64_t cta_max_p);
+pf_status build_plan(const std::vector<pf_filter*>& fl, Plan** out, const pf_batch_shape& shape);
 pf_status stage_plan(Plan* p, const double* const* theta, const double* const* y,
                      const uint64_t* seeds, const int32_t* hist_on, cudaStream_t st);
 pf_status run_plan(Plan* p, const double* const* theta, const double* const* y,

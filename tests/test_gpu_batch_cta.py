@@ -1,8 +1,9 @@
-"""GPU tests of the batched form's cluster path: filters sent to it (one
-thread-block cluster runs a whole filter, one CTA per tile, on a side branch
-of the plan's graph) give the bits of their single runs, whatever the split
-and whatever the autotuner chooses; PMMH chains over such a batch are
-unchanged too."""
+"""GPU tests of the batched form's launch shapes: filters sent to the cluster
+path (one thread-block cluster runs a whole filter, one CTA per tile, on a
+side branch of the plan's graph) or dealt into several independent branches of
+per-step launches give the bits of their single runs, whatever the shape and
+whatever the autotuner chooses; PMMH chains over such batches are unchanged
+too."""
 import math
 
 import numpy as np
@@ -82,6 +83,10 @@ def test_autotuner_choice_keeps_results_and_pmmh():
         chosen = pf.pf_batch_autotune(fs, [w.theta for w in ws], [w.y for w in ws],
                                       [w.seed for w in ws])
         assert chosen in (0, 256, 512, 1024, 2048)
+        shape = pf.pf_batch_get_shape(fs)
+        assert shape["cta_max_particles"] == chosen
+        assert shape["branches"] in (1, 2, 4, 8, 16)
+        assert shape["resample_blocks_per_sm"] in (2, 4, 8)
         lls, sts = pf.pf_batch_run(fs, [w.theta for w in ws], [w.y for w in ws],
                                    [w.seed for w in ws])
         assert [(int(a), b) for a, b in zip(sts, lls)] == [(int(a), b) for a, b in ref]
@@ -99,6 +104,70 @@ def test_autotuner_choice_keeps_results_and_pmmh():
         try:
             pf.pf_batch_configure(fs, cta)
             out.append(pf.pf_pmmh_run(fs, w.y, spec, th0, 15, 3))
+        finally:
+            for f in fs:
+                f.destroy()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("branches,cta,rs", [(2, 0, 8), (3, 0, 4), (8, 1024, 2), (64, 0, 1)])
+def test_branches_are_bit_identical(branches, cta, rs):
+    """The tiled filters dealt into independent launch chains (parallel branches
+    of the captured graph) give the bits of their single runs; the first run
+    builds and captures the plan, the second replays it."""
+    import paper_1306_3277_b300 as pf
+    ws = [w for w in _mix() if w.resampler != 2]
+    fs = [pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt) for w in ws]
+    try:
+        ref = _single(pf, ws, fs)
+        pf.pf_batch_set_shape(fs, cta, branches, rs)
+        assert pf.pf_batch_get_shape(fs) == {"cta_max_particles": cta, "branches": branches,
+                                             "resample_blocks_per_sm": rs}
+        for _ in range(2):
+            lls, sts = pf.pf_batch_run(fs, [w.theta for w in ws], [w.y for w in ws],
+                                       [w.seed for w in ws])
+            for k, (st, ll) in enumerate(ref):
+                assert sts[k] == st and lls[k] == ll, (k, ws[k].name, lls[k], ll)
+    finally:
+        for f in fs:
+            f.destroy()
+
+
+def test_branches_with_a_multinomial_filter_and_invalid_shapes():
+    """A multinomial filter keeps the plan on one chain (same bits); shapes out
+    of range are refused."""
+    import paper_1306_3277_b300 as pf
+    ws = _mix()
+    fs = [pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt) for w in ws]
+    try:
+        ref = _single(pf, ws, fs)
+        pf.pf_batch_set_shape(fs, 0, 4, 8)
+        lls, sts = pf.pf_batch_run(fs, [w.theta for w in ws], [w.y for w in ws],
+                                   [w.seed for w in ws])
+        assert [(int(a), b) for a, b in zip(sts, lls)] == [(int(a), b) for a, b in ref]
+        for bad in ((-1, 1, 8), (0, 0, 8), (0, 1, 0), (0, 1, 9)):
+            with pytest.raises(pf.PFError) as e:
+                pf.pf_batch_set_shape(fs, *bad)
+            assert e.value.status == pf.PF_EINVAL
+    finally:
+        for f in fs:
+            f.destroy()
+
+
+def test_samplers_unchanged_by_branches():
+    """PMMH chains run their filters through a batch plan: dealing the chains
+    into branches changes none of their samples."""
+    import paper_1306_3277_b300 as pf
+    w = W.windkessel(P=512, T=30)
+    spec = [(3, 1, 2.0, 0.9, 0.03, 0.0, math.inf), (0, 0), (3, 1, 2.0, 0.03, 0.002, 0.0, math.inf),
+            (4, 2, 2.0, 0.01, 2.0, 3.0), (0, 0), (0, 0), (0, 0)]
+    th0 = np.tile(np.array(w.theta), (8, 1))
+    out = []
+    for branches in (1, 4):
+        fs = [pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt) for _ in range(8)]
+        try:
+            pf.pf_batch_set_shape(fs, 0, branches, 8)
+            out.append(pf.pf_pmmh_run(fs, w.y, spec, th0, 10, 5))
         finally:
             for f in fs:
                 f.destroy()
