@@ -35,7 +35,7 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 PROFILES = os.path.join(ROOT, "profiles")
-DESCRIPTOR_BYTES = 256  # per-filter descriptor the library uploads with every run
+DESCRIPTOR_BYTES = 272  # per-filter descriptor the library uploads with every run
 
 
 def _code_only(text):
@@ -363,6 +363,86 @@ def secondary(pf, torch, dev):
             small[name + "_ms_per_run"] = (time.perf_counter() - t0) / 20 * 1e3
         f.destroy()
         out["small_filter_" + w.name] = small
+    # serving: a compact sweep (5 s of Poisson arrivals per rate, at most 5 s
+    # more to drain), beside the same request mix one pf_run at a time
+    fp32_peak = pf.pf_measure_fma_peak(pf.PF_MIXED)
+    serving = {"rates": [serve_at_rate(pf, rate, 5.0, 5.0, 64 << 30, 64, fp32_peak)
+                         for rate in (250.0, 1000.0)]}
+    reqs = W.serving_requests(40, 100.0, seed=7)
+    fs = [(pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt), w) for _, w in reqs]
+    for f, w in fs[:3]:
+        f.run(w.theta, w.y, w.seed)
+    t0 = time.perf_counter()
+    for f, w in fs:
+        f.run(w.theta, w.y, w.seed)
+    serving["plain_requests_per_s"] = len(fs) / (time.perf_counter() - t0)
+    for f, _ in fs:
+        f.destroy()
+    out["serving"] = serving
+    return out
+
+
+def request_flops(w):
+    """Algorithmic FP32 flops of one served request (Lorenz '96 RK4 and noise;
+    the windkessel's few FP64 operations are not counted)."""
+    if w.kind == W.LORENZ96:
+        return l96_flops_per_particle_step(w) * w.P * w.T
+    return 0
+
+
+def serve_at_rate(pf, rate, duration, drain, budget_bytes, slots, fp32_peak=None):
+    """Poisson arrivals at `rate` per second for `duration` seconds into one
+    server, then up to `drain` seconds for the queue to empty: goodput,
+    latency quantiles of the completed requests, queue length (sampled every
+    10 ms), rejected and unfinished requests."""
+    n = max(1, int(rate * duration))
+    reqs = W.serving_requests(n, rate, seed=int(rate))
+    srv = pf.pf_server_create(budget_bytes, slots)
+    pending = {}
+    lat = []
+    psteps_done = flops_done = 0
+    rejected, max_queued, queued_at_end, last_stat = 0, 0, None, -1.0
+    t0 = time.perf_counter()
+    k = 0
+    while k < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while k < len(reqs) and reqs[k][0] <= now:
+            w = reqs[k][1]
+            try:
+                t = srv.submit(pf.model_from_workload(w), w.P, w.T, w.dt, w.theta, w.y, w.seed)
+                pending[t] = w
+            except pf.PFError:
+                rejected += 1
+            k += 1
+        if now - last_stat >= 0.01:  # queue length, sampled every 10 ms
+            queued = srv.stats()["queued"]
+            max_queued = max(max_queued, queued)
+            if queued_at_end is None and k == len(reqs):
+                queued_at_end = queued
+            last_stat = now
+        for t in list(pending):
+            r = srv.poll(t)
+            if r is not None:
+                w = pending.pop(t)
+                lat.append(r[2])
+                psteps_done += w.P * w.T
+                flops_done += request_flops(w)
+        if now > duration + drain:
+            break
+        time.sleep(0.0005)
+    elapsed = time.perf_counter() - t0
+    st = srv.stats()
+    srv.destroy()
+    lat.sort()
+    q = (lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None)
+    out = {"offered_per_s": rate, "submitted": k, "rejected": rejected, "completed": len(lat),
+           "unfinished": len(pending), "max_queued": max_queued,
+           "queued_when_arrivals_end": queued_at_end, "goodput_per_s": len(lat) / elapsed,
+           "particle_steps_per_s": psteps_done / elapsed, "p50_s": q(0.5), "p99_s": q(0.99),
+           "elapsed_s": elapsed, "iterations": st["iterations"],
+           "fp32_tflops": flops_done / elapsed / 1e12}
+    if fp32_peak:
+        out["fp32_roof_frac"] = flops_done / elapsed / fp32_peak
     return out
 
 
@@ -374,56 +454,11 @@ def run_serving(args):
     import paper_1306_3277_b300 as pf
     torch.cuda.set_device(0)
     rates = [float(r) for r in args.rates.split(",")]
+    fp32_peak = None if args.no_peak else pf.pf_measure_fma_peak(pf.PF_MIXED)
     sweep = []
     for rate in rates:
-        n = max(1, int(rate * args.duration))
-        reqs = W.serving_requests(n, rate, seed=int(rate))
-        srv = pf.pf_server_create(int(args.budget_gb * (1 << 30)), args.slots)
-        pending = {}
-        lat, done_ll = [], 0
-        psteps_done = 0
-        rejected, max_queued, queued_at_end, last_stat = 0, 0, None, -1.0
-        t0 = time.perf_counter()
-        k = 0
-        while k < len(reqs) or pending:
-            now = time.perf_counter() - t0
-            while k < len(reqs) and reqs[k][0] <= now:
-                w = reqs[k][1]
-                try:
-                    t = srv.submit(pf.model_from_workload(w), w.P, w.T, w.dt, w.theta, w.y,
-                                   w.seed)
-                    pending[t] = w
-                except pf.PFError:
-                    rejected += 1
-                k += 1
-            if now - last_stat >= 0.01:  # queue length, sampled every 10 ms
-                queued = srv.stats()["queued"]
-                max_queued = max(max_queued, queued)
-                if queued_at_end is None and k == len(reqs):
-                    queued_at_end = queued
-                last_stat = now
-            for t in list(pending):
-                r = srv.poll(t)
-                if r is not None:
-                    w = pending.pop(t)
-                    lat.append(r[2])
-                    psteps_done += w.P * w.T
-                    done_ll += 1
-            if now > args.duration + args.drain:
-                break
-            time.sleep(0.0005)
-        elapsed = time.perf_counter() - t0
-        st = srv.stats()
-        srv.destroy()
-        lat.sort()
-        q = (lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None)
-        sweep.append({"offered_per_s": rate, "submitted": k, "rejected": rejected,
-                      "completed": len(lat), "unfinished": len(pending),
-                      "max_queued": max_queued, "queued_when_arrivals_end": queued_at_end,
-                      "goodput_per_s": len(lat) / elapsed,
-                      "particle_steps_per_s": psteps_done / elapsed,
-                      "p50_s": q(0.5), "p99_s": q(0.99), "elapsed_s": elapsed,
-                      "iterations": st["iterations"]})
+        sweep.append(serve_at_rate(pf, rate, args.duration, args.drain,
+                                   int(args.budget_gb * (1 << 30)), args.slots, fp32_peak))
         print(json.dumps({"rate": rate, **sweep[-1]}), file=sys.stderr, flush=True)
     # plain form: the same kind of requests one pf_run at a time
     reqs = W.serving_requests(args.plain_sample, 100.0, seed=7)
@@ -647,7 +682,7 @@ def main():
     ap.add_argument("--cluster-bound", type=int, default=0,
                     help="batched: largest filter (particles) run on one thread-block cluster")
     ap.add_argument("--rates", default="250,500,1000,1500,2000", help="serving: offered rates")
-    ap.add_argument("--duration", type=float, default=4.0, help="serving: seconds of arrivals")
+    ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--drain", type=float, default=20.0, help="serving: extra seconds to finish")
     ap.add_argument("--slots", type=int, default=64, help="serving: concurrent filters")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: device memory budget")

@@ -126,6 +126,17 @@ pf_status pfb::check_shape(const pf_model* m, int64_t P, int32_t T, double dt, S
   return PF_OK;
 }
 
+// A small FP64 windkessel filter draws its normals ahead, in one launch over the
+// whole GPU at the start of a run, instead of on the FP64 unit of the few SMs
+// its tiles occupy: entries of that table (0 when the filter does not).
+static constexpr int64_t kNoiseMaxP = int64_t(1) << 14;
+static constexpr int64_t kNoiseMaxEntries = int64_t(8) << 20;  // 64 MiB of doubles
+static int64_t noise_entries(const pf_model* m, int64_t P, int32_t T) {
+  if (!wk_kind(m->kind) || m->prec != PF_FP64 || P > kNoiseMaxP) return 0;
+  const int64_t n = int64_t(T) * m->substeps * P;
+  return n <= kNoiseMaxEntries ? n : 0;
+}
+
 static size_t bytes_for(const pf_model* m, const Shape& sh, int64_t P, int32_t T, int hist) {
   size_t b = 2 * size_t(m->N) * size_t(P) * sh.state_bytes;
   b += size_t(P) * 8;                                     // ctil
@@ -133,6 +144,7 @@ static size_t bytes_for(const pf_model* m, const Shape& sh, int64_t P, int32_t T
   b += size_t(P) * 4;                                     // anc
   if (hist) b += size_t(T) * size_t(P) * 4;               // history
   b += size_t(sh.nflow) * 8;                              // flow
+  b += size_t(noise_entries(m, P, T)) * 8;                 // FP64 normals drawn ahead
   b += size_t(sh.ntiles) * sizeof(TilePart) + size_t(sh.ngroups) * sizeof(GroupPart);
   b += sizeof(Ctl);
   b += size_t(T) * size_t(sh.Ny) * 8;                     // observations (plan side)
@@ -153,7 +165,8 @@ extern "C" size_t pf_device_bytes(const pf_model* m, int64_t P, int32_t T, int32
 // ---------------------------------------------------------------------------
 static void free_filter_buffers(pf_filter* f) {
   void* ptrs[] = {f->x[0], f->x[1], f->ctil, f->ell, f->lam, f->anc, f->hist,
-                  f->flow, f->tp, f->gp, f->ctl, f->path, f->path_idx, f->mn_t, f->mn_part};
+                  f->flow, f->tp, f->gp, f->ctl, f->path, f->path_idx, f->mn_t, f->mn_part,
+                  f->znoise};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (f->h_res) cudaFreeHost(f->h_res);
@@ -191,6 +204,7 @@ extern "C" pf_status pf_create(const pf_model* m, int64_t P, int32_t T, double d
     ok = ok && alloc((void**)&f->ell, size_t(P) * 8) && alloc((void**)&f->lam, size_t(P) * 8);
   ok = ok && alloc((void**)&f->anc, size_t(P) * 4);
   ok = ok && alloc((void**)&f->flow, size_t(sh.nflow) * 8);
+  ok = ok && alloc((void**)&f->znoise, size_t(noise_entries(m, P, T)) * 8);
   ok = ok && alloc((void**)&f->tp, size_t(sh.ntiles) * sizeof(TilePart));
   ok = ok && alloc((void**)&f->gp, size_t(sh.ngroups) * sizeof(GroupPart));
   ok = ok && alloc((void**)&f->ctl, sizeof(Ctl));
@@ -245,6 +259,7 @@ extern "C" pf_status pf_create(const pf_model* m, int64_t P, int32_t T, double d
   d.ctl = f->ctl;
   d.mn_t = f->mn_t;
   d.mn_part = f->mn_part;
+  d.znoise = f->znoise;
   f->bytes = bytes_for(m, sh, P, T, 0);
   *out = f;
   return PF_OK;
@@ -298,6 +313,11 @@ static cudaError_t enqueue_branch(Plan* p, const Branch& b, int first, int last,
     return r;
   };
   const int2* tall = p->d_tmap + b.all_offset;
+  for (size_t q = 0; q < b.noise.size() && le == cudaSuccess; ++q) {
+    const pf_filter* f = p->filters[b.noise[q]];
+    le = launch_noise(p->d_fds, b.noise[q], std::max(first, 1), std::min(last, f->T), int(f->P),
+                      f->m.substeps, st);
+  }
   if (init) {
     for (size_t c = 0; c < b.classes.size() && le == cudaSuccess; ++c) {
       const PlanClass& pc = b.classes[c];
@@ -378,7 +398,12 @@ static cudaError_t enqueue_run(Plan* p, cudaStream_t st, Profiler* prof) {
   if (p->cta_total == 0) return enqueue_steps(p, 1, p->maxT, st, prof, no_hook, true);
   cudaStream_t side = prof ? st : p->st2;
   cudaError_t le = cudaSuccess;
-  if (!prof) {
+  // the cluster filters' FP64 normals, drawn ahead before the fork
+  for (size_t q = 0; q < p->cta_noise.size() && le == cudaSuccess; ++q) {
+    const pf_filter* f = p->filters[p->cta_noise[q]];
+    le = launch_noise(p->d_fds, p->cta_noise[q], 1, f->T, int(f->P), f->m.substeps, st);
+  }
+  if (!prof && le == cudaSuccess) {
     le = cudaEventRecord(p->ev_fork, st);
     if (le == cudaSuccess) le = cudaStreamWaitEvent(side, p->ev_fork, 0);
   }
@@ -448,6 +473,8 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out,
     p->cta_cluster.push_back(std::get<3>(kv.first));
     cta_all.insert(cta_all.end(), v.begin(), v.end());
   }
+  for (int k : cta_all)
+    if (fl[k]->znoise) p->cta_noise.push_back(k);
   p->cta_total = int(cta_all.size());
   // the tiled filters, longest runs first, dealt in turn into the branches
   std::vector<int> tiled;
@@ -504,6 +531,7 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out,
       }
       br.maxT = std::max(br.maxT, f->T);
       br.has_mn = br.has_mn || f->m.resampler == PF_RESAMPLE_MULTINOMIAL;
+      if (f->znoise) br.noise.push_back(k);
     }
     for (size_t c = 0; c < cls_tiles.size(); ++c) {
       br.classes[c].offset = int(tm.size());
@@ -666,12 +694,17 @@ extern "C" pf_status pf_run(pf_filter* f, const double* theta, const double* y, 
                   (long long)(size_t(f->T) * size_t(f->P) * 4));
     }
   }
-  if (!f->plan) {
+  if (!f->wplan) {
+    // a filter of at most MAX_CLUSTER_TILES tiles runs whole on one
+    // thread-block cluster (no per-step launches); others take the tiled path
     std::vector<pf_filter*> one{f};
-    pf_status ps = build_plan(one, &f->plan, kDefaultShape);
+    pf_batch_shape shape = kDefaultShape;
+    if (cta_eligible(f, f->P)) shape.cta_max_particles = f->P;
+    pf_status ps = build_plan(one, &f->wplan, shape);
     if (ps != PF_OK) return ps;
   }
-  Plan* p = f->plan;
+  Plan* p = f->wplan;
+  f->last = p;
   const int32_t hist_on = ancestors ? 1 : 0;
   f->range_pos = -1;
   pf_status ps = run_plan(p, &theta, &y, &seed, &hist_on, st, f->prof);
@@ -731,6 +764,7 @@ extern "C" pf_status pf_run_range(pf_filter* f, const double* theta, const doubl
   pf_status ps = ensure_plan(f);
   if (ps != PF_OK) return ps;
   Plan* p = f->plan;
+  f->last = p;
   cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : f->own;
   f->range_pos = -1;
   CK(cudaEventSynchronize(p->ev_staged));
@@ -792,6 +826,7 @@ extern "C" pf_status pf_sample_path(pf_filter* f, const double* theta, const dou
     }
   }
   Plan* p = f->plan;
+  f->last = p;
   cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : f->own;
   f->range_pos = -1;
   // pass 1: the filter with its ancestor history, then the pick and the trace
@@ -834,6 +869,7 @@ extern "C" pf_status pf_debug_step(pf_filter* f, const double* theta, const doub
   pf_status ps = ensure_plan(f);
   if (ps != PF_OK) return ps;
   Plan* p = f->plan;
+  f->last = p;
   cudaStream_t st = f->own;
   f->range_pos = -1;
   CK(cudaEventSynchronize(p->ev_staged));
@@ -882,10 +918,10 @@ extern "C" pf_status pf_debug_step(pf_filter* f, const double* theta, const doub
 
 extern "C" pf_status pf_wait(pf_filter* f) {
   if (!f) return fail(PF_EINVAL, "filter is NULL");
-  if (!f->plan) return PF_OK;
-  CK(cudaEventSynchronize(f->plan->ev_done));
+  if (!f->last) return PF_OK;
+  CK(cudaEventSynchronize(f->last->ev_done));
   f->pending = false;
-  return int(f->plan->h_res[1]) == ST_OK ? PF_OK : PF_EDEGENERATE;
+  return int(f->last->h_res[1]) == ST_OK ? PF_OK : PF_EDEGENERATE;
 }
 
 extern "C" pf_status pf_destroy(pf_filter* f) {
@@ -894,6 +930,7 @@ extern "C" pf_status pf_destroy(pf_filter* f) {
   // ev_done, set-up work runs on f->own, and destroy_plan drains the streams
   // of every plan the filter is part of (the batched forms are synchronous)
   if (f->plan && f->plan->ev_done) cudaEventSynchronize(f->plan->ev_done);
+  if (f->wplan && f->wplan->ev_done) cudaEventSynchronize(f->wplan->ev_done);
   if (f->own) cudaStreamSynchronize(f->own);
   {
     std::lock_guard<std::mutex> lk(g_plan_mu);
@@ -913,6 +950,7 @@ extern "C" pf_status pf_destroy(pf_filter* f) {
     }
   }
   destroy_plan(f->plan);
+  destroy_plan(f->wplan);
   free_filter_buffers(f);
   delete f->prof;
   delete f;

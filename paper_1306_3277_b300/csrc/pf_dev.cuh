@@ -102,8 +102,9 @@ struct alignas(16) FilterDev {
   Ctl* ctl;
   double* mn_t;       // multinomial: in-tile inclusive sums of the spacings [P]
   double* mn_part;    // multinomial: tile offsets [ntiles], then P / (sum of all P + 1)
+  const double* znoise;  // FP64 windkessel: normals drawn ahead, [T * s][P], or null
 };
-static_assert(sizeof(FilterDev) == 256, "descriptor layout");
+static_assert(sizeof(FilterDev) == 272, "descriptor layout");
 
 // -------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two

@@ -21,6 +21,10 @@ cudaError_t launch_propagate(int kind, int N, int prec, const FilterDev* fds, co
 // blocks per SM
 cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks, cudaStream_t st,
                             int blocks_per_sm = 8);
+// the FP64 windkessel normals of filter fds[k] (P particles, s substeps) for
+// steps first..last drawn ahead into its table
+cudaError_t launch_noise(const FilterDev* fds, int k, int first, int last, int P, int s,
+                         cudaStream_t st);
 // the control block of fds[0] set to propagate to t_step from a loaded state,
 // ancestors from the array (anc_identity 0) or the identity (diagnostic)
 cudaError_t launch_debug_ctl(const FilterDev* fds, int step, int anc_identity, cudaStream_t st);

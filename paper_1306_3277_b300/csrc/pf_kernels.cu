@@ -252,6 +252,21 @@ __device__ __forceinline__ double exp_weight(double d) {
 // a = exp(-dt/(RC)) (own exponential), b = R (1 - a), sd = dt sqrt(sigma2),
 // z_mm = normal number mm of stream (j, i, PROP); a, b, sd in FP64, rounded to
 // the state precision.
+// Normal numbers mm and mm + 1 of stream (j, i, PROP) of an FP64 windkessel
+// filter: read from its table when they were drawn ahead (k_noise_wk64: the
+// same Philox block and Box-Muller pair), else drawn here.
+__device__ __forceinline__ void wk_normals64(const FilterDev& fd, uint32_t j, int i, int mm,
+                                             double (&z)[2]) {
+  if (fd.znoise) {
+    const double* zr = fd.znoise + (int64_t(i - 1) * fd.s + mm) * fd.P + j;
+    z[0] = zr[0];
+    z[1] = mm + 1 < fd.s ? zr[fd.P] : 0.0;
+  } else {
+    normal_pair64(rng_block(fd.seed, j, uint32_t(i), PURPOSE_PROP, uint32_t(mm >> 1)), &z[0],
+                  &z[1]);
+  }
+}
+
 // The filter's constants (a, b, sd) of the exact windkessel transition, computed
 // by one thread per block: an FP64 exponential, a division and a square root
 // that every particle shares.
@@ -273,7 +288,7 @@ __device__ __forceinline__ void wkx_propagate(const FilterDev& fd, uint32_t j, i
   if constexpr (sizeof(R) == 8) {
     for (int mm = 0; mm < s; mm += 2) {
       double z[2];
-      normal_pair64(rng_block(fd.seed, j, uint32_t(i), PURPOSE_PROP, uint32_t(mm >> 1)), &z[0], &z[1]);
+      wk_normals64(fd, j, i, mm, z);
 #pragma unroll
       for (int e = 0; e < 2; ++e)
         if (mm + e < s) xv = fmaR(a, xv, b * fmaR(sd, R(z[e]), R(fl[mm + e])));
@@ -304,7 +319,7 @@ __device__ __forceinline__ void wk_propagate(const FilterDev& fd, uint32_t j, in
   if constexpr (sizeof(R) == 8) {
     for (int mm = 0; mm < s; mm += 2) {
       double z[2];
-      normal_pair64(rng_block(fd.seed, j, uint32_t(i), PURPOSE_PROP, uint32_t(mm >> 1)), &z[0], &z[1]);
+      wk_normals64(fd, j, i, mm, z);
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         if (mm + e < s) {
@@ -1420,6 +1435,34 @@ __global__ void k_path_copy(const void* __restrict__ x, int prec, int N, int P,
   path[int64_t(i) * N + n] = v;
 }
 
+// The normals of the FP64 windkessel transition of filter fds[k] for steps
+// first..last, drawn ahead into its table: znoise[(i - 1) s + mm][j] is normal
+// number mm of stream (j, i, PROP), from the same Philox block and Box-Muller
+// pair as the propagate kernel would draw.  One thread per particle and pair
+// of substeps, over the whole GPU: a small filter's propagation then reads
+// its normals instead of spending B300's FP64 unit (1/64 of the FP32 rate)
+// on them in the few SMs its tiles occupy.  The key is read from the device
+// descriptor, so samplers that rewrite it on the device get their own draws.
+__global__ void k_noise_wk64(const FilterDev* __restrict__ fds, int k, int first, int last) {
+  const FilterDev& fd = fds[k];
+  const int P = fd.P, s = fd.s, hb = (s + 1) / 2;
+  const uint64_t seed = fd.seed;
+  double* zt = const_cast<double*>(fd.znoise);
+  const int64_t n = int64_t(last - first + 1) * hb * P;
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < n;
+       q += int64_t(gridDim.x) * blockDim.x) {
+    const int j = int(q % P);
+    const int64_t r = q / P;
+    const int b = int(r % hb);
+    const int i = first + int(r / hb);
+    double z0, z1;
+    normal_pair64(rng_block(seed, uint32_t(j), uint32_t(i), PURPOSE_PROP, uint32_t(b)), &z0, &z1);
+    double* zr = zt + (int64_t(i - 1) * s + 2 * b) * P + j;
+    zr[0] = z0;
+    if (2 * b + 1 < s) zr[P] = z1;
+  }
+}
+
 // Windkessel input table F(k dt), k < n: half sine of the given peak and period.
 __global__ void k_flow(double* __restrict__ flow, int64_t n, double peak, double period,
                        double dt) {
@@ -1666,6 +1709,23 @@ cudaError_t launch_mn_scan(const FilterDev* fds, const int2* tmap, int ntiles, i
   k_mn_tiles<<<ntiles, TILE, 0, st>>>(fds, tmap);
   k_mn_total<<<nf, TILE, 0, st>>>(fds, nf);
   k_mn_targets<<<ntiles, TILE, 0, st>>>(fds, tmap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_noise(const FilterDev* fds, int k, int first, int last, int P, int s,
+                         cudaStream_t st) {
+  if (last < first) return cudaSuccess;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 148;
+  }
+  const int64_t n = int64_t(last - first + 1) * ((s + 1) / 2) * P;
+  const int64_t nb = (n + 255) / 256;
+  k_noise_wk64<<<unsigned(std::min<int64_t>(nb, int64_t(sms) * 8)), 256, 0, st>>>(fds, k, first,
+                                                                                  last);
   return cudaGetLastError();
 }
 

@@ -96,12 +96,15 @@ struct pf_filter {
   double* path = nullptr;        // [T+1][N] sampled path (pf_sample_path)
   int32_t* path_idx = nullptr;   // [T+1] its particle indices
   double* flow = nullptr;
+  double* znoise = nullptr;      // FP64 windkessel: normals drawn ahead [T * s][P] (small filters)
   pfb::TilePart* tp = nullptr;
   pfb::GroupPart* gp = nullptr;
   pfb::Ctl* ctl = nullptr;
   double* h_res = nullptr;
   pfb::FilterDev desc{};
-  pfb::Plan* plan = nullptr;
+  pfb::Plan* plan = nullptr;      // tiled single-filter plan: intervals, paths, debug steps
+  pfb::Plan* wplan = nullptr;     // whole runs (pf_run): the cluster path for a small filter
+  pfb::Plan* last = nullptr;      // the plan of the last pf_run (pf_wait)
   pfb::Profiler* prof = nullptr;
   bool pending = false;
   int32_t range_pos = -1;        // t_s reached by the last pf_run_range, else -1
@@ -117,6 +120,7 @@ namespace pfb {
 // with events, so a captured graph holds them as parallel branches).
 struct Branch {
   std::vector<PlanClass> classes;           // offset / ntiles into Plan::d_tmap
+  std::vector<int> noise;                   // filters whose FP64 normals are drawn ahead
   int all_offset = 0;                       // the branch's all-tiles map in Plan::d_tmap
   int maxT = 0;
   bool has_mn = false;                      // some filter resamples multinomially
@@ -152,6 +156,7 @@ struct Plan {
   int cta_total = 0;
   std::vector<PlanClass> cta_classes;       // offset / ntiles = first / count in d_cta
   std::vector<int> cta_cluster;             // cluster size (= tiles) of each of those
+  std::vector<int> cta_noise;               // cluster filters whose FP64 normals are drawn ahead
   int* d_cta = nullptr;                     // filter indices, per class
   cudaStream_t st2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
