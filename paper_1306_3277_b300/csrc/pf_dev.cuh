@@ -326,17 +326,6 @@ __device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
-__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
-  f32x2 d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
-  f32x2 d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f32x2 splat2(float v) { return pk(v, v); }
 
 // FP32: one 32-bit word pair (a, b) gives one pair: u1 = ((a>>8)+1) 2^-24,
 // u2 = (b>>8) 2^-24.
@@ -348,89 +337,6 @@ __device__ __forceinline__ void normal_pair32(uint32_t a, uint32_t b, float* z0,
   sincos_2pif(u2, &sn, &cs);
   *z0 = __fmul_rn(rho, cs);
   *z1 = __fmul_rn(rho, sn);
-}
-
-// The two FP32 pairs of one Philox block, (w.x, w.y) and (w.z, w.w), in
-// packed f32x2 arithmetic: lane 0 carries the first pair, lane 1 the second,
-// and every packed add, sub, mul and fma is the IEEE single-precision
-// operation of normal_pair32 (log_posf, sincos_2pif) on each lane, in the
-// same order; the steps without a packed instruction (integer-to-float
-// conversions, reading the exponent and mantissa off the bits, the division,
-// the square root, the rounding to a quarter turn and the quadrant
-// rotation) run per lane.  So z holds exactly the bits of two normal_pair32
-// calls: z[0], z[1] from (w.x, w.y) and z[2], z[3] from (w.z, w.w).
-__device__ __forceinline__ void split_logf_arg(float x, float* m, int* e) {
-  const int bits = __float_as_int(x);
-  int ee = ((bits >> 23) & 0xff) - 126;
-  float mm = __int_as_float((bits & 0x007fffff) | 0x3f000000);
-  if (mm < 0x1.6a09e6p-1f) {
-    mm = __fadd_rn(mm, mm);
-    ee -= 1;
-  }
-  *m = mm;
-  *e = ee;
-}
-__device__ __forceinline__ void quarter_turn(int q, float sinx, float cosx, float* sn, float* cs) {
-  const int quarter = q & 3;
-  *sn = quarter == 0 ? sinx : quarter == 1 ? cosx : quarter == 2 ? -sinx : -cosx;
-  *cs = quarter == 0 ? cosx : quarter == 1 ? -sinx : quarter == 2 ? -cosx : sinx;
-}
-__device__ __forceinline__ void normal_quad32(uint4 w, float (&z)[4]) {
-  const f32x2 u1 = mul2(pk(float((w.x >> 8) + 1u), float((w.z >> 8) + 1u)), splat2(0x1.0p-24f));
-  const f32x2 u2 = mul2(pk(float(w.y >> 8), float(w.w >> 8)), splat2(0x1.0p-24f));
-  // log u1 (log_posf)
-  float ua, ub, ma, mb;
-  int ea, eb;
-  upk(u1, ua, ub);
-  split_logf_arg(ua, &ma, &ea);
-  split_logf_arg(ub, &mb, &eb);
-  const f32x2 m = pk(ma, mb);
-  float na, nb, da, db;
-  upk(sub2(m, splat2(1.0f)), na, nb);
-  upk(add2(m, splat2(1.0f)), da, db);
-  const f32x2 f = pk(__fdiv_rn(na, da), __fdiv_rn(nb, db));
-  const f32x2 two_f = add2(f, f);
-  const f32x2 f2 = mul2(f, f);
-  f32x2 p = splat2(1.0f / 11.0f);
-  p = fma2(p, f2, splat2(1.0f / 9.0f));
-  p = fma2(p, f2, splat2(1.0f / 7.0f));
-  p = fma2(p, f2, splat2(1.0f / 5.0f));
-  p = fma2(p, f2, splat2(1.0f / 3.0f));
-  const f32x2 lm = fma2(mul2(two_f, f2), p, two_f);
-  const f32x2 de = pk(float(ea), float(eb));
-  const f32x2 lg = fma2(de, splat2(0x1.62e430p-1f), fma2(de, splat2(-0x1.05c610p-29f), lm));
-  // rho = sqrt(-2 log u1)
-  float ta, tb;
-  upk(mul2(splat2(-2.0f), lg), ta, tb);
-  const f32x2 rho = pk(__fsqrt_rn(ta), __fsqrt_rn(tb));
-  // sin, cos of 2 pi u2 (sincos_2pif)
-  const f32x2 v = mul2(splat2(4.0f), u2);
-  float va, vb;
-  upk(v, va, vb);
-  const float qa = rintf(va), qb = rintf(vb);
-  const f32x2 r = sub2(v, pk(qa, qb));
-  const f32x2 x = fma2(r, splat2(0x1.921fb6p+0f), mul2(r, splat2(-0x1.777a5cp-25f)));
-  const f32x2 x2 = mul2(x, x);
-  f32x2 s = splat2(-1.0f / 39916800.0f);
-  s = fma2(s, x2, splat2(1.0f / 362880.0f));
-  s = fma2(s, x2, splat2(-1.0f / 5040.0f));
-  s = fma2(s, x2, splat2(1.0f / 120.0f));
-  s = fma2(s, x2, splat2(-1.0f / 6.0f));
-  const f32x2 sinx = fma2(mul2(x, x2), s, x);
-  f32x2 c = splat2(1.0f / 479001600.0f);
-  c = fma2(c, x2, splat2(-1.0f / 3628800.0f));
-  c = fma2(c, x2, splat2(1.0f / 40320.0f));
-  c = fma2(c, x2, splat2(-1.0f / 720.0f));
-  c = fma2(c, x2, splat2(1.0f / 24.0f));
-  c = fma2(c, x2, splat2(-0.5f));
-  const f32x2 cosx = fma2(x2, c, splat2(1.0f));
-  float sa, sb, ca, cb, sna, snb, csa, csb;
-  upk(sinx, sa, sb);
-  upk(cosx, ca, cb);
-  quarter_turn(int(qa), sa, ca, &sna, &csa);
-  quarter_turn(int(qb), sb, cb, &snb, &csb);
-  upk(mul2(rho, pk(csa, csb)), z[0], z[2]);
-  upk(mul2(rho, pk(sna, snb)), z[1], z[3]);
 }
 
 // -------------------------------------------------------------------------

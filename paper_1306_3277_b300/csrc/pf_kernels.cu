@@ -142,12 +142,14 @@ __device__ __forceinline__ void normals(float (&z)[N], uint64_t seed, uint32_t j
                                         uint32_t purpose, uint32_t b0 = 0) {
 #pragma unroll
   for (int b = 0; b < (N + 3) / 4; ++b) {
-    float q[4];
-    normal_quad32(rng_block(seed, j, i, purpose, b0 + b), q);
-    z[4 * b] = q[0];
-    if (4 * b + 1 < N) z[4 * b + 1] = q[1];
-    if (4 * b + 2 < N) z[4 * b + 2] = q[2];
-    if (4 * b + 3 < N) z[4 * b + 3] = q[3];
+    const uint4 w = rng_block(seed, j, i, purpose, b0 + b);
+    float z0, z1, z2, z3;
+    normal_pair32(w.x, w.y, &z0, &z1);
+    normal_pair32(w.z, w.w, &z2, &z3);
+    z[4 * b] = z0;
+    if (4 * b + 1 < N) z[4 * b + 1] = z1;
+    if (4 * b + 2 < N) z[4 * b + 2] = z2;
+    if (4 * b + 3 < N) z[4 * b + 3] = z3;
   }
 }
 
@@ -307,9 +309,12 @@ __device__ __forceinline__ void wkx_propagate(const FilterDev& fd, uint32_t j, i
 }
 
 // Windkessel propagation: s Euler substeps x <- x + dt (F_k/C - x/(RC)) +
-// sqrt(q) z_mm (normal number mm of stream (j, i, PROP)).
+// sqrt(q) z_mm (normal number mm of stream (j, i, PROP)).  fc, when given,
+// holds the step's F_k/C (the same division, made once per block: every
+// particle shares it).
 template <typename R>
-__device__ __forceinline__ void wk_propagate(const FilterDev& fd, uint32_t j, int i, R& xv) {
+__device__ __forceinline__ void wk_propagate(const FilterDev& fd, uint32_t j, int i, R& xv,
+                                             const R* fc) {
   const int s = fd.s;
   const R Rr = from_double<R>(fd.theta[0]);
   const R Cc = from_double<R>(fd.theta[1]);
@@ -323,8 +328,8 @@ __device__ __forceinline__ void wk_propagate(const FilterDev& fd, uint32_t j, in
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         if (mm + e < s) {
-          const R Fk = fl[mm + e];
-          const R drift = Fk / Cc - xv / (Rr * Cc);
+          const R fkc = fc ? fc[mm + e] : R(fl[mm + e]) / Cc;
+          const R drift = fkc - xv / (Rr * Cc);
           xv = fmaR(dt, drift, xv);
           xv = fmaR(sq, R(z[e]), xv);
         }
@@ -339,8 +344,8 @@ __device__ __forceinline__ void wk_propagate(const FilterDev& fd, uint32_t j, in
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         if (mm + e < s) {
-          const R Fk = from_double<R>(fl[mm + e]);
-          const R drift = Fk / Cc - xv / (Rr * Cc);
+          const R fkc = fc ? fc[mm + e] : from_double<R>(fl[mm + e]) / Cc;
+          const R drift = fkc - xv / (Rr * Cc);
           xv = fmaR(dt, drift, xv);
           xv = fmaR(sq, R(z[e]), xv);
         }
@@ -726,6 +731,18 @@ __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i
     if (tid == 0) wkx_constants<R>(fd, kc);
     __syncthreads();
   }
+  // Euler windkessel: F(t_k)/C of the step's substeps, one division each
+  __shared__ R fcs[KIND == KIND_WK ? TILE : 1];
+  const R* fc = nullptr;
+  if constexpr (KIND == KIND_WK) {
+    if (fd.s <= TILE) {
+      if (tid < fd.s)
+        fcs[tid] = from_double<R>(fd.flow[int64_t(i - 1) * fd.s + tid]) /
+                   from_double<R>(fd.theta[1]);
+      __syncthreads();
+      fc = fcs;
+    }
+  }
   R x[N];
   if (valid) {
     int a = anc_identity ? j : (fd.hist ? fd.anc[int64_t(i - 1) * P + j] : a_spec);
@@ -739,7 +756,7 @@ __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i
     R* xout = static_cast<R*>(fd.x[i & 1]);
 #pragma unroll
     for (int n = 0; n < N; ++n) x[n] = xin[int64_t(n) * P + a];
-    if constexpr (KIND == KIND_WK) wk_propagate<R>(fd, uint32_t(j), i, x[0]);
+    if constexpr (KIND == KIND_WK) wk_propagate<R>(fd, uint32_t(j), i, x[0], fc);
     else if constexpr (KIND == KIND_WKX) wkx_propagate<R>(fd, uint32_t(j), i, x[0], kc);
     else if constexpr (KIND == KIND_L96W) l96w_propagate<N, R>(fd, uint32_t(j), i, x);
     else l96_propagate<N, R>(fd, uint32_t(j), i, x);
