@@ -467,6 +467,8 @@ struct CombineScratch {
   BlockScratch b;
   double incl[TILE];
   double gM, gS, gQ;  // thread 0's group partials, for a one-group filter's combine
+  double tg[MAX_CLUSTER_TILES], tbase[MAX_CLUSTER_TILES];  // warp path: the first tiles' g, base
+  double G;           // one-group filter: the group scale the filter combine took
   int last;
 };
 
@@ -477,8 +479,16 @@ struct CombineScratch {
 // combined by warp 0 alone, and the only group of a filter skips the group
 // ticket (it is the last by construction); both give the same bits as the
 // block path.
+// The tile partials (M, S, Q) of a cluster's tiles, gathered in CTA 0's shared
+// memory (the values propagate_tile also writes to tp); src = nullptr: read
+// them from tp.
+struct TileTriples {
+  double M[MAX_CLUSTER_TILES], S[MAX_CLUSTER_TILES], Q[MAX_CLUSTER_TILES];
+};
+
 template <bool WARP>
-__device__ bool combine_group(const FilterDev& fd, int g, CombineScratch& cs) {
+__device__ bool combine_group(const FilterDev& fd, int g, CombineScratch& cs,
+                              const TileTriples* src = nullptr) {
   const int tid = threadIdx.x;
   const int t0 = g * GROUP;
   const int ntg = min(GROUP, fd.ntiles - t0);
@@ -488,9 +498,15 @@ __device__ bool combine_group(const FilterDev& fd, int g, CombineScratch& cs) {
     if (tid < 32) {
       double Mt = -INFINITY, St = 0.0, Qt = 0.0;
       if (tid < ntg) {
-        Mt = ldcg(&fd.tp[t0 + tid].M);
-        St = ldcg(&fd.tp[t0 + tid].S);
-        Qt = ldcg(&fd.tp[t0 + tid].Q);
+        if (src) {
+          Mt = src->M[tid];
+          St = src->S[tid];
+          Qt = src->Q[tid];
+        } else {
+          Mt = ldcg(&fd.tp[t0 + tid].M);
+          St = ldcg(&fd.tp[t0 + tid].S);
+          Qt = ldcg(&fd.tp[t0 + tid].Q);
+        }
       }
       Mg = warp_max(Mt);
       // exp(0) = 1 exactly: the maximal tile (and a one-tile group) skips the call
@@ -501,6 +517,10 @@ __device__ bool combine_group(const FilterDev& fd, int g, CombineScratch& cs) {
       if (tid < ntg) {
         fd.tp[t0 + tid].g = gt;
         fd.tp[t0 + tid].base = tid == 0 ? 0.0 : before;
+      }
+      if (tid < MAX_CLUSTER_TILES) {  // warp 0's lanes keep their tile's g and base
+        cs.tg[tid] = gt;
+        cs.tbase[tid] = tid == 0 ? 0.0 : before;
       }
     }
   } else {
@@ -546,9 +566,13 @@ __device__ bool combine_group(const FilterDev& fd, int g, CombineScratch& cs) {
 }
 
 // Combine the groups of the filter and take the step's decisions (with WARP,
-// by warp 0 alone for at most 32 groups: the same bits).
+// by warp 0 alone for at most 32 groups: the same bits).  sctl, when given, is
+// a copy of the control block in shared memory (the cluster path's): the
+// decisions are read from and taken in it, then the whole block is stored to
+// fd.ctl at once.
 template <bool WARP>
-__device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs) {
+__device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs,
+                               Ctl* sctl = nullptr) {
   const int tid = threadIdx.x;
   const int ng = fd.ngroups;
   double M, S, Q = 0.0;
@@ -562,6 +586,7 @@ __device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs) {
     if (fd.mode == MODE_ADAPTIVE) Q = cs.gQ * (G * G);
     fd.gp[0].G = G;
     fd.gp[0].B = 0.0;
+    cs.G = G;
   } else if (WARP && ng <= 32) {
     // warp 0 alone (the same bits as the block reductions)
     if (tid >= 32) return;
@@ -599,7 +624,7 @@ __device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs) {
     }
   }
   if (tid == 0) {
-    Ctl* c = fd.ctl;
+    Ctl* c = sctl ? sctl : fd.ctl;
     c->gticket = 0u;
     c->rs_step = i;
     if (!(M > -INFINITY) || M == INFINITY || !(S > 0.0)) {
@@ -643,6 +668,7 @@ __device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs) {
       }
       c->step = i + 1;
     }
+    if (sctl) *fd.ctl = *sctl;
   }
 }
 
@@ -719,7 +745,7 @@ struct PropagateOccupancy {
 template <int KIND, int N, typename R>
 __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i, int anc_identity,
                                                int lam_zero, double cw, int a_spec, double* ys,
-                                               CombineScratch& cs) {
+                                               CombineScratch& cs, TileTriples* tri = nullptr) {
   const int P = fd.P;
   const int tid = threadIdx.x;
   const int j = t * TILE + tid;
@@ -805,6 +831,11 @@ __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i
     tp.M = Mt;
     tp.S = St;
     tp.Q = Qt;
+    if (tri) {  // the cluster path: also into CTA 0's shared memory
+      tri->M[t] = Mt;
+      tri->S[t] = St;
+      tri->Q[t] = Qt;
+    }
   }
 }
 
@@ -1212,6 +1243,23 @@ __device__ __forceinline__ void cluster_sync() {
                "barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// Address of the same shared-memory object in CTA `rank` of the cluster
+// (distributed shared memory: a generic pointer the other CTA can store to).
+template <typename T>
+__device__ __forceinline__ T* cluster_peer(T* local, unsigned rank) {
+  unsigned long long out;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(reinterpret_cast<unsigned long long>(local)),
+               "r"(rank));
+  return reinterpret_cast<T*>(out);
+}
+
+// A tile's place in the filter's cumulative weights after a combine (what
+// tile_base would read from the partials): base and scale of the tile, base of
+// the next tile (S after the last).
+struct TileGeo {
+  double base, scale, base_next;
+};
+
 // Filter list[blockIdx.x / CS] runs whole on a cluster of CS CTAs, CTA r
 // owning tile r (CTAs past the filter's tiles only take part in the
 // barriers): its initial draw, then per step its tiles propagated in parallel
@@ -1220,71 +1268,81 @@ __device__ __forceinline__ void cluster_sync() {
 // carried (carry_tile), with a cluster barrier between the phases.  These are
 // the tiled kernels' own functions in their order, so every result is
 // bit-identical to the tiled path's; the two launches and the last-block
-// hand-offs of every step disappear.  Every CTA of a cluster reads the same
-// control block after the same barrier, so all take the same branches and
-// reach the same barriers.
+// hand-offs of every step disappear.
+// What the phases hand each other travels through distributed shared memory
+// instead of L2: every CTA stores its tile partials (M, S, Q) into CTA 0's
+// shared memory, and CTA 0 stores the step's control block and every tile's
+// place in the cumulative weights (TileGeo) into each CTA's shared memory
+// (the same values as the global copies, which are kept up to date).  Every
+// CTA reads the same control block after the same barrier, so all take the
+// same branches and reach the same barriers.
 template <int KIND, int N, typename R>
 __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __restrict__ fds,
                                                          const int* __restrict__ list, int cs_size) {
   __shared__ CombineScratch cs;
   __shared__ double ys[64];
-  __shared__ int s_step, s_ok, s_anc_identity, s_lam_zero, s_go, s_flag, s_lo, s_hi, nlong;
+  __shared__ Ctl sctl;          // this CTA's copy of the control block
+  __shared__ TileGeo geo;       // this CTA's tile in the step's cumulative weights
+  __shared__ TileTriples tri;   // CTA 0: the tile partials of the cluster's tiles
+  __shared__ int s_lo, s_hi, nlong;
   __shared__ int s_nlast[WARPS];
-  __shared__ double s_cw, s_M, s_u, s_ratio, s_S, s_e0, s_scale_r;
+  __shared__ double s_e0, s_scale_r;
   __shared__ int3 longr[TILE];
   const FilterDev& fd = fds[list[blockIdx.x / cs_size]];
   const int t = blockIdx.x % cs_size;
   const int tid = threadIdx.x;
   const int P = fd.P, T = fd.T, rs = fd.resampler;
   const bool mine = t < fd.ntiles;
+  TileTriples* tri0 = cluster_peer(&tri, 0u);
   if (mine) init_tile<KIND, N, R>(fd, t);
   cluster_sync();
+  if (tid == 0) {  // the initial control block, once from global memory
+    const uint4* src = reinterpret_cast<const uint4*>(fd.ctl);
+    uint4* dst = reinterpret_cast<uint4*>(&sctl);
+    for (int k = 0; k < int(sizeof(Ctl) / sizeof(uint4)); ++k) dst[k] = ldcg(src + k);
+  }
+  __syncthreads();
   for (int i = 1; i <= T; ++i) {
-    if (tid == 0) {
-      const Ctl* ctl = fd.ctl;
-      s_step = ldcg(&ctl->step);
-      s_ok = ldcg(&ctl->status) == ST_OK;
-      s_anc_identity = ldcg(&ctl->anc_identity);
-      s_lam_zero = ldcg(&ctl->lam_zero);
-      s_cw = ldcg(&ctl->cw);
-    }
-    __syncthreads();
-    if (!s_ok || s_step != i) break;  // a degenerate step ended the run (same in every CTA)
+    if (sctl.status != ST_OK || sctl.step != i) break;  // a degenerate step ended the run
     if (mine) {
       const int j = t * TILE + tid;
       const int a_spec = (j < P && !fd.hist) ? fd.anc[j] : j;
-      propagate_tile<KIND, N, R>(fd, t, i, s_anc_identity, s_lam_zero, s_cw, a_spec, ys, cs);
+      propagate_tile<KIND, N, R>(fd, t, i, sctl.anc_identity, sctl.lam_zero, sctl.cw, a_spec, ys,
+                                 cs, tri0);
     }
-    cluster_sync();  // the tile partials of every CTA
+    cluster_sync();  // the tile partials of every CTA, in CTA 0's shared memory
     if (t == 0) {
-      if (combine_group<true>(fd, 0, cs)) combine_filter<true>(fd, i, cs);
+      if (combine_group<true>(fd, 0, cs, &tri)) combine_filter<true>(fd, i, cs, &sctl);
+      __syncthreads();  // thread 0's decisions in sctl
+      if (tid < cs_size) {  // lane r hands CTA r the control block and its tile's place
+        const int r = tid;
+        const double G = cs.G;
+        TileGeo gr{0.0, 0.0, 0.0};
+        if (r < fd.ntiles) {
+          gr.base = fma(G, cs.tbase[r], 0.0);  // tile_base: fma(gG, base_t, B) with B = 0
+          gr.scale = G * cs.tg[r];
+          gr.base_next = r + 1 < fd.ntiles ? fma(G, cs.tbase[r + 1], 0.0) : sctl.S;
+        }
+        *cluster_peer(&geo, unsigned(r)) = gr;
+        if (r != 0) *cluster_peer(&sctl, unsigned(r)) = sctl;
+      }
     }
-    cluster_sync();  // the group partials and the step's decisions
-    if (tid == 0) {
-      const Ctl* ctl = fd.ctl;
-      const int i0 = ldcg(&ctl->rs_step);
-      s_go = ldcg(&ctl->status) == ST_OK && i0 == i && i < T && ldcg(&ctl->step) == i + 1;
-      s_flag = ldcg(&ctl->rs_flag);
-      s_M = ldcg(&ctl->M);
-      s_u = rs == RS_SYSTEMATIC ? ldcg(&ctl->u) : 0.0;
-      s_ratio = ldcg(&ctl->ratio);
-      s_S = ldcg(&ctl->S);
-      nlong = 0;
-    }
-    __syncthreads();
-    if (s_go && mine) {
-      if (!s_flag) {
-        carry_tile(fd, t, i, s_M);
+    cluster_sync();  // every CTA's control block and tile place
+    const bool go = sctl.status == ST_OK && sctl.rs_step == i && i < T && sctl.step == i + 1;
+    if (tid == 0) nlong = 0;
+    if (go && mine) {
+      if (!sctl.rs_flag) {
+        carry_tile(fd, t, i, sctl.M);
       } else {
         const int j = t * TILE + tid;
         const double ct = j < P ? fd.ctil[j] : 0.0;
+        const double u = rs == RS_SYSTEMATIC ? sctl.u : 0.0;
         if (tid == 0 || tid == 32) {
-          double base = 0.0, scale = 0.0;
-          tile_base(fd, t, tid == 0 ? 0 : 1, s_S, &base, &scale);
-          const int n0 = range_count(fd, rs, base, s_ratio, s_u, i);
+          const double base = tid == 0 ? geo.base : geo.base_next;
+          const int n0 = range_count(fd, rs, base, sctl.ratio, u, i);
           if (tid == 0) {
-            s_e0 = base * s_ratio - s_u;
-            s_scale_r = scale * s_ratio;
+            s_e0 = base * sctl.ratio - u;
+            s_scale_r = geo.scale * sctl.ratio;
             s_lo = n0;
           } else {
             s_hi = n0;
