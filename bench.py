@@ -572,17 +572,23 @@ def run_variants(args):
 
 def run_batched(args):
     """The batched form on its own: 256 uneven filters (Lorenz '96 N=8 and
-    windkessel, P 2^8..2^14, T 50..500, mixed precision) as one plan, the
-    small ones on thread-block clusters up to --cluster-bound particles (0: all
-    tiled).  K timed batch runs after W warm-ups; unless --no-secondary, the
-    same filters one pf_run at a time for comparison."""
+    windkessel, P 2^8..2^14, T 50..500, mixed precision) as one plan, in the
+    launch shape the autotuner picks (or, with --branches, that many launch
+    chains, the small filters on thread-block clusters up to --cluster-bound
+    particles and --rs-grid resample blocks per SM).  K timed batch runs after
+    W warm-ups; unless --no-secondary, the same filters one pf_run at a time
+    for comparison."""
     import torch
     import paper_1306_3277_b300 as pf
     torch.cuda.set_device(0)
     ws = W.batched()
     fs = [pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt) for w in ws]
     ths, ys, seeds = [w.theta for w in ws], [w.y for w in ws], [w.seed for w in ws]
-    pf.pf_batch_configure(fs, args.cluster_bound)
+    if args.branches > 0:
+        pf.pf_batch_set_shape(fs, args.cluster_bound, args.branches, args.rs_grid)
+    else:
+        pf.pf_batch_autotune(fs, ths, ys, seeds)
+    shape = pf.pf_batch_get_shape(fs)
     for _ in range(max(args.warmup, 1)):  # the first run builds the plan and its graph
         pf.pf_batch_run(fs, ths, ys, seeds)
     t0 = time.perf_counter()
@@ -593,7 +599,7 @@ def run_batched(args):
     line = {"metric": "batched evaluations/s", "value": len(ws) / tb, "unit": "evals/s",
             "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_batch": tb * 1e3,
             "particle_steps_per_s": psteps / tb, "filters": len(ws),
-            "cluster_bound": args.cluster_bound,
+            "shape": shape, "shape_from": "given" if args.branches > 0 else "autotuner",
             "degenerate": int(sum(1 for st in sts if int(st) != 0))}
     if not args.no_secondary:
         for f, w in zip(fs, ws):  # the single-filter plans
@@ -681,6 +687,10 @@ def main():
                              "precision", "variants", "samplers"])
     ap.add_argument("--cluster-bound", type=int, default=0,
                     help="batched: largest filter (particles) run on one thread-block cluster")
+    ap.add_argument("--branches", type=int, default=0,
+                    help="batched: independent launch chains (0: the autotuner picks the shape)")
+    ap.add_argument("--rs-grid", type=int, default=4,
+                    help="batched: resample blocks per SM (with --branches)")
     ap.add_argument("--rates", default="250,500,1000,1500,2000", help="serving: offered rates")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--drain", type=float, default=20.0, help="serving: extra seconds to finish")
@@ -795,6 +805,12 @@ def main():
             flop_launch = 6 * w.substeps * w.P
         prop_bytes = propagate_bytes_per_particle(w) * w.P
         res_bytes = RESAMPLE_BYTES_PER_PARTICLE * w.P
+        tag = "k_propagate<%s,%d,%s>" % ("L96" if w.kind else "WK", w.N,
+                                          "f32" if w.prec else "f64")
+        if prop_n == args.steps:  # a small filter: one cluster launch runs the whole run
+            tag = "k_filter_cluster" + tag[len("k_propagate"):]
+            flop_launch *= w.T
+            prop_bytes *= w.T
         fp32_peak = fp64_peak = None
         if not args.no_peak:
             fp32_peak = pf.pf_measure_fma_peak(pf.PF_MIXED)
@@ -802,11 +818,11 @@ def main():
         achieved_tf = flop_launch / (avg_prop_ms * 1e-3) / 1e12
         alu_peak = fp32_peak if w.prec == W.MIXED else fp64_peak
         alu_peak_tf = alu_peak / 1e12 if alu_peak else None
-        tag = "k_propagate<%s,%d,%s>" % ("L96" if w.kind else "WK", w.N,
-                                          "f32" if w.prec else "f64")
         res_gbs = res_bytes / (avg_res_ms * 1e-3) / 1e9 if avg_res_ms > 0 else None
         roof = {"kernel": tag + " (fused gather, %s substeps, noise, FP64 weight, tile prefix "
-                                "sums)" % ("RK4" if w.kind == W.LORENZ96 else "Euler"),
+                                "sums%s)" % ("RK4" if w.kind == W.LORENZ96 else "Euler",
+                                             "; whole run per launch" if prop_n == args.steps
+                                             else ""),
                 "bound": "alu", "achieved": achieved_tf, "peak": alu_peak_tf, "unit": "TFLOP/s",
                 "frac": (achieved_tf / alu_peak_tf) if alu_peak_tf else None,
                 "traffic": read_traffic(tag, w.P),
