@@ -366,7 +366,7 @@ def secondary(pf, torch, dev):
     # serving: a compact sweep (5 s of Poisson arrivals per rate, at most 5 s
     # more to drain), beside the same request mix one pf_run at a time
     fp32_peak = pf.pf_measure_fma_peak(pf.PF_MIXED)
-    serving = {"rates": [serve_at_rate(pf, rate, 5.0, 5.0, 64 << 30, 64, fp32_peak)
+    serving = {"rates": [serve_at_rate(pf, rate, 5.0, 5.0, 64 << 30, 128, fp32_peak)
                          for rate in (250.0, 1000.0)]}
     reqs = W.serving_requests(40, 100.0, seed=7)
     fs = [(pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt), w) for _, w in reqs]
@@ -694,7 +694,7 @@ def main():
     ap.add_argument("--rates", default="250,500,1000,1500,2000", help="serving: offered rates")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--drain", type=float, default=20.0, help="serving: extra seconds to finish")
-    ap.add_argument("--slots", type=int, default=64, help="serving: concurrent filters")
+    ap.add_argument("--slots", type=int, default=128, help="serving: concurrent filters")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: device memory budget")
     ap.add_argument("--plain-sample", type=int, default=60, help="serving: plain-form sample")
     ap.add_argument("--seeds", type=int, default=64, help="precision: seeds per configuration")

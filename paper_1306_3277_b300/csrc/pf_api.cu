@@ -473,8 +473,11 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out,
     p->cta_cluster.push_back(std::get<3>(kv.first));
     cta_all.insert(cta_all.end(), v.begin(), v.end());
   }
+  // drawn-ahead normals serve a filter that runs alone (latency-bound); a batch
+  // fills the GPU anyway, and would redraw every filter's table per launch sequence
+  p->use_noise = nf == 1;
   for (int k : cta_all)
-    if (fl[k]->znoise) p->cta_noise.push_back(k);
+    if (fl[k]->znoise && p->use_noise) p->cta_noise.push_back(k);
   p->cta_total = int(cta_all.size());
   // the tiled filters, longest runs first, dealt in turn into the branches
   std::vector<int> tiled;
@@ -531,7 +534,7 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out,
       }
       br.maxT = std::max(br.maxT, f->T);
       br.has_mn = br.has_mn || f->m.resampler == PF_RESAMPLE_MULTINOMIAL;
-      if (f->znoise) br.noise.push_back(k);
+      if (f->znoise && p->use_noise) br.noise.push_back(k);
     }
     for (size_t c = 0; c < cls_tiles.size(); ++c) {
       br.classes[c].offset = int(tm.size());
@@ -584,6 +587,7 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out,
   }
   for (int k = 0; k < nf; ++k) {
     p->h_fds[k] = fl[k]->desc;
+    if (!p->use_noise) p->h_fds[k].znoise = nullptr;
     p->h_fds[k].y = p->d_ycat + p->yoff[k];
   }
   // capture the whole run: init, then T x (propagate per class, resample)
@@ -625,6 +629,7 @@ pf_status pfb::stage_plan(Plan* p, const double* const* theta, const double* con
     FilterDev& d = p->h_fds[k];
     d = f->desc;
     d.y = p->d_ycat + p->yoff[k];
+    if (!p->use_noise) d.znoise = nullptr;
     d.seed = seeds[k];
     if (hist_on && hist_on[k]) {
       d.hist = 1;

@@ -136,6 +136,7 @@ struct Plan {
   std::vector<pf_filter*> filters;
   int nf = 0, maxT = 0, ntiles_all = 0;     // d_tmap[0, ntiles_all): every tiled filter's tiles
   bool has_mn = false;                      // some filter resamples multinomially
+  bool use_noise = false;                   // single filter: FP64 normals drawn ahead
   pf_batch_shape shape{0, 1, 8};            // the launch shape the plan was built for
   std::vector<Branch> branches;
   cudaEvent_t ev_fork_br = nullptr;         // forks the branches off the launching stream
