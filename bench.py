@@ -35,6 +35,7 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 PROFILES = os.path.join(ROOT, "profiles")
+SERVER_BRANCHES = 4  # concurrent launch groups per server iteration (the library default)
 DESCRIPTOR_BYTES = 272  # per-filter descriptor the library uploads with every run
 
 
@@ -375,8 +376,8 @@ def secondary(pf, torch, dev):
     # serving: a compact sweep (5 s of Poisson arrivals per rate, at most 5 s
     # more to drain), beside the same request mix one pf_run at a time
     fp32_peak = pf.pf_measure_fma_peak(pf.PF_MIXED)
-    serving = {"rates": [serve_at_rate(pf, rate, 5.0, 5.0, 64 << 30, 128, fp32_peak)
-                         for rate in (250.0, 1000.0)]}
+    serving = {"rates": [serve_at_rate(pf, rate, 5.0, 5.0, 64 << 30, 128, fp32_peak,
+                                       SERVER_BRANCHES) for rate in (250.0, 1000.0)]}
     reqs = W.serving_requests(40, 100.0, seed=7)
     fs = [(pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt), w) for _, w in reqs]
     for f, w in fs[:3]:
@@ -399,14 +400,15 @@ def request_flops(w):
     return 0
 
 
-def serve_at_rate(pf, rate, duration, drain, budget_bytes, slots, fp32_peak=None):
+def serve_at_rate(pf, rate, duration, drain, budget_bytes, slots, fp32_peak=None,
+                  branches=None):
     """Poisson arrivals at `rate` per second for `duration` seconds into one
     server, then up to `drain` seconds for the queue to empty: goodput,
     latency quantiles of the completed requests, queue length (sampled every
     10 ms), rejected and unfinished requests."""
     n = max(1, int(rate * duration))
     reqs = W.serving_requests(n, rate, seed=int(rate))
-    srv = pf.pf_server_create(budget_bytes, slots)
+    srv = pf.pf_server_create(budget_bytes, slots, branches=branches)
     pending = {}
     lat = []
     psteps_done = flops_done = 0
@@ -448,7 +450,7 @@ def serve_at_rate(pf, rate, duration, drain, budget_bytes, slots, fp32_peak=None
            "unfinished": len(pending), "max_queued": max_queued,
            "queued_when_arrivals_end": queued_at_end, "goodput_per_s": len(lat) / elapsed,
            "particle_steps_per_s": psteps_done / elapsed, "p50_s": q(0.5), "p99_s": q(0.99),
-           "elapsed_s": elapsed, "iterations": st["iterations"],
+           "elapsed_s": elapsed, "iterations": st["iterations"], "branches": branches,
            "fp32_tflops": flops_done / elapsed / 1e12}
     if fp32_peak:
         out["fp32_roof_frac"] = flops_done / elapsed / fp32_peak
@@ -467,7 +469,8 @@ def run_serving(args):
     sweep = []
     for rate in rates:
         sweep.append(serve_at_rate(pf, rate, args.duration, args.drain,
-                                   int(args.budget_gb * (1 << 30)), args.slots, fp32_peak))
+                                   int(args.budget_gb * (1 << 30)), args.slots, fp32_peak,
+                                   args.server_branches))
         print(json.dumps({"rate": rate, **sweep[-1]}), file=sys.stderr, flush=True)
     # plain form: the same kind of requests one pf_run at a time
     reqs = W.serving_requests(args.plain_sample, 100.0, seed=7)
@@ -486,7 +489,8 @@ def run_serving(args):
            "vs_baseline": None, "dtype": "f32 state / f64 weights", "data": "synthetic",
            "config": {"workload": "serving: Poisson arrivals, models windkessel / L96 N=8 / "
                                   "L96 N=40, P=2^U{10..16}, T~U{50..1000}",
-                      "slots": args.slots, "budget_gb": args.budget_gb,
+                      "slots": args.slots, "launch_groups": args.server_branches,
+                      "budget_gb": args.budget_gb,
                       "duration_s": args.duration, "drain_s": args.drain},
            "sweep": sweep,
            "plain_one_run_at_a_time": {"requests": len(fs), "requests_per_s": len(fs) / tp,
@@ -704,6 +708,8 @@ def main():
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--drain", type=float, default=20.0, help="serving: extra seconds to finish")
     ap.add_argument("--slots", type=int, default=128, help="serving: concurrent filters")
+    ap.add_argument("--server-branches", type=int, default=SERVER_BRANCHES,
+                    help="serving: concurrent launch groups per scheduler iteration")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: device memory budget")
     ap.add_argument("--plain-sample", type=int, default=60, help="serving: plain-form sample")
     ap.add_argument("--seeds", type=int, default=64, help="precision: seeds per configuration")

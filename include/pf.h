@@ -359,6 +359,15 @@ pf_status pf_server_submit(pf_server* s, const pf_model* m, int64_t P, int32_t T
  * A finished ticket can be collected once: polling it again, or polling a
  * ticket this server never issued, gives PF_EINVAL. */
 pf_status pf_server_poll(pf_server* s, uint64_t ticket, double* loglik, double* latency_s);
+/* Launch groups per scheduler iteration, 1..8 (default 4, the best measured
+ * on a mixed serving workload).  With b > 1 the running filters are dealt into
+ * b groups of about equal work per step (longest first, each to the
+ * least-loaded group) and each group's launches of an iteration run on a
+ * stream of their own, forked from the scheduler's stream and joined back
+ * before the iteration's results; with b = 1 every launch runs on one stream.
+ * Results do not depend on b.  Takes effect at the next iteration; PF_EINVAL
+ * outside 1..8. */
+pf_status pf_server_configure(pf_server* s, int32_t branches);
 /* Counters: queued, running, completed requests and scheduler iterations. */
 pf_status pf_server_stats(pf_server* s, int64_t* queued, int64_t* running, int64_t* completed,
                           int64_t* iterations);

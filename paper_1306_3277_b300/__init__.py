@@ -128,9 +128,10 @@ def lib():
             L.pf_server_poll.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double)]
             L.pf_server_stats.argtypes = [_vp] + [ctypes.POINTER(ctypes.c_int64)] * 4
+            L.pf_server_configure.argtypes = [_vp, ctypes.c_int32]
             L.pf_server_destroy.argtypes = [_vp]
             for name in ("pf_server_create", "pf_server_submit", "pf_server_poll",
-                         "pf_server_stats", "pf_server_destroy"):
+                         "pf_server_stats", "pf_server_configure", "pf_server_destroy"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -526,6 +527,10 @@ class Server:
         _check(st, ok=(PF_OK, PF_EDEGENERATE))
         return st, ll.value, lat.value
 
+    def configure(self, branches):
+        """Launch groups per scheduler iteration (1..8); results do not depend on it."""
+        _check(lib().pf_server_configure(self.h, int(branches)))
+
     def stats(self):
         v = [ctypes.c_int64() for _ in range(4)]
         _check(lib().pf_server_stats(self.h, *[ctypes.byref(x) for x in v]))
@@ -544,5 +549,8 @@ class Server:
             pass
 
 
-def pf_server_create(device_mem_budget, max_slots=64):
-    return Server(device_mem_budget, max_slots)
+def pf_server_create(device_mem_budget, max_slots=64, branches=None):
+    s = Server(device_mem_budget, max_slots)
+    if branches is not None:
+        s.configure(branches)
+    return s

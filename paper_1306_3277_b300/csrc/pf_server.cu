@@ -13,8 +13,16 @@
 //      the descriptor table and tile map are uploaded only when a slot
 //      changed, and results are copied back only by iterations that launch
 //      some filter's last observation or every RESULTS_EVERY-th one.
+// With more than one branch (pf_server_configure), the running filters are
+// dealt into that many groups of about equal work per step, and each group's
+// launches of an iteration (init, propagate per model class, resample) run on
+// a stream of their own, forked from and joined back into the scheduler's
+// stream: one group's launches fill the SMs that another's leave idle (the
+// tail of a wave, a class bound by the FP64 unit beside one bound by FP32).
 // The same kernels and per-filter reduction order as pf_run are used, so a
 // request's log-likelihood is bit-identical to pf_run of the same request.
+#include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -64,6 +72,19 @@ struct Request {
 };
 
 constexpr size_t ARENA_HALF = size_t(16) << 20;  // pinned staging per iteration parity
+constexpr int MAX_BRANCHES = 8;
+constexpr int DEFAULT_BRANCHES = 4;
+
+// Relative device time of one step of one tile of a request's model class
+// (per-launch times at 2^20 particles, mixed precision: windkessel 76 us,
+// Lorenz '96 N = 8 120 us, N = 40 425 us; FP64 Lorenz '96 about 4x its mixed
+// form).  Only the balance of the branches depends on it.
+double tile_cost(const Request* r) {
+  if (r->m.kind == PF_WINDKESSEL || r->m.kind == PF_WINDKESSEL_EXP) return 75.0;
+  double c = 100.0 + double(r->m.N) * double(r->m.substeps);
+  if (r->m.kind == PF_LORENZ96_SDE) c *= 3.5;  // the normals of every substep
+  return r->m.prec == PF_FP64 ? 4.0 * c : c;
+}
 
 }  // namespace
 
@@ -81,8 +102,13 @@ struct pf_server {
   bool stop = false;
   bool broken = false;  // a CUDA error ended the scheduler's work: requests fail with PF_ECUDA
   std::thread thr;
+  std::atomic<int> branches{DEFAULT_BRANCHES};  // launch groups per iteration
+  bool regroup = false;  // under mu: branches changed, rebuild the tile map
   // scheduler-owned
   cudaStream_t st = nullptr;
+  cudaStream_t st_br[MAX_BRANCHES] = {};  // the branches' streams
+  cudaEvent_t ev_fork = nullptr;          // forks the branches off st
+  cudaEvent_t ev_join[MAX_BRANCHES] = {};
   cudaMemPool_t pool = nullptr;
   std::vector<Request*> slots;
   size_t used = 0;
@@ -103,8 +129,14 @@ struct pf_server {
   struct Seg {
     int kind, N, prec;
     size_t off, n;
+    int br;  // branch
   };
-  std::vector<Seg> run_seg;  // the running filters' tile-map segments, by model class
+  struct Range {
+    size_t off, n;
+    int br;
+  };
+  std::vector<Seg> run_seg;    // the running filters' tile-map segments, by branch and class
+  std::vector<Range> run_br;   // each branch's running tiles (contiguous in the tile map)
   size_t n_run = 0;
   int64_t iter = 0;
 };
@@ -299,6 +331,10 @@ void scheduler(pf_server* s) {
     std::vector<Request*> admitted;
     {
       std::unique_lock<std::mutex> lk(s->mu);
+      if (s->regroup) {
+        s->map_dirty = true;
+        s->regroup = false;
+      }
       bool any_running = false;
       for (Request* r : s->slots) any_running = any_running || r;
       if (s->broken || (!any_running && s->queue.empty() && !s->ev_live[0] && !s->ev_live[1])) {
@@ -349,9 +385,12 @@ void scheduler(pf_server* s) {
     std::vector<pf_server::Seg> new_seg;
     if (s->map_dirty) {
       // descriptors and tile map of this iteration:
-      // [running tiles by class | new tiles by class]
+      // [running tiles by branch, then class | new tiles by branch, then class]
       FilterDev* hf = s->h_fds[parity];
-      std::map<std::tuple<int, int, int>, std::vector<int2>> run_cls, new_cls;
+      const int nb = std::min(std::max(s->branches.load(), 1), MAX_BRANCHES);
+      // deal the filters into the branches, longest per-step work first, each
+      // to the branch with the least work so far
+      std::vector<std::pair<double, int>> order;
       for (int k = 0; k < s->max_slots; ++k) {
         Request* r = s->slots[k];
         if (!r) {
@@ -359,15 +398,28 @@ void scheduler(pf_server* s) {
           continue;
         }
         hf[k] = r->desc;
+        order.push_back({-tile_cost(r) * r->sh.ntiles, k});
+      }
+      std::sort(order.begin(), order.end());
+      std::vector<double> load(nb, 0.0);
+      typedef std::map<std::tuple<int, int, int>, std::vector<int2>> ClassTiles;
+      std::vector<ClassTiles> run_cls(nb), new_cls(nb);
+      for (const auto& o : order) {
+        const int k = o.second;
+        Request* r = s->slots[k];
+        const int b = int(std::min_element(load.begin(), load.end()) - load.begin());
+        load[b] -= o.first;
         auto key = std::make_tuple(r->m.kind, r->m.N, r->m.prec);
         for (int t = 0; t < r->sh.ntiles; ++t) {
-          run_cls[key].push_back(make_int2(k, t));
-          if (r->fresh) new_cls[key].push_back(make_int2(k, t));
+          run_cls[b][key].push_back(make_int2(k, t));
+          if (r->fresh) new_cls[b][key].push_back(make_int2(k, t));
         }
       }
       size_t ntm = 0;
-      for (auto& kv : run_cls) ntm += kv.second.size();
-      for (auto& kv : new_cls) ntm += kv.second.size();
+      for (int b = 0; b < nb; ++b) {
+        for (auto& kv : run_cls[b]) ntm += kv.second.size();
+        for (auto& kv : new_cls[b]) ntm += kv.second.size();
+      }
       if (ntm == 0) {  // nothing running: drain the other parity and wait for work
         retire(s, parity ^ 1);
         continue;
@@ -380,20 +432,26 @@ void scheduler(pf_server* s) {
       }
       int2* tm = s->h_tmap[parity];
       s->run_seg.clear();
+      s->run_br.clear();
       size_t off = 0;
-      for (auto& kv : run_cls) {
-        memcpy(tm + off, kv.second.data(), kv.second.size() * sizeof(int2));
-        s->run_seg.push_back({std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
-                              off, kv.second.size()});
-        off += kv.second.size();
+      for (int b = 0; b < nb; ++b) {
+        const size_t b0 = off;
+        for (auto& kv : run_cls[b]) {
+          memcpy(tm + off, kv.second.data(), kv.second.size() * sizeof(int2));
+          s->run_seg.push_back({std::get<0>(kv.first), std::get<1>(kv.first),
+                                std::get<2>(kv.first), off, kv.second.size(), b});
+          off += kv.second.size();
+        }
+        if (off > b0) s->run_br.push_back({b0, off - b0, b});
       }
       s->n_run = off;
-      for (auto& kv : new_cls) {
-        memcpy(tm + off, kv.second.data(), kv.second.size() * sizeof(int2));
-        new_seg.push_back({std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
-                           off, kv.second.size()});
-        off += kv.second.size();
-      }
+      for (int b = 0; b < nb; ++b)
+        for (auto& kv : new_cls[b]) {
+          memcpy(tm + off, kv.second.data(), kv.second.size() * sizeof(int2));
+          new_seg.push_back({std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                             off, kv.second.size(), b});
+          off += kv.second.size();
+        }
       cudaMemcpyAsync(s->d_fds, hf, sizeof(FilterDev) * s->max_slots, cudaMemcpyHostToDevice,
                       s->st);
       cudaMemcpyAsync(s->d_tmap, tm, sizeof(int2) * off, cudaMemcpyHostToDevice, s->st);
@@ -401,11 +459,29 @@ void scheduler(pf_server* s) {
       // tiles are in it) or a slot change make it stale
       s->map_dirty = !new_seg.empty();
     }
-    for (const pf_server::Seg& g : new_seg)
-      launch_init(g.kind, g.N, g.prec, s->d_fds, s->d_tmap + g.off, int(g.n), s->st);
-    for (const pf_server::Seg& g : s->run_seg)
-      launch_propagate(g.kind, g.N, g.prec, s->d_fds, s->d_tmap + g.off, int(g.n), s->st);
-    launch_resample(s->d_fds, s->d_tmap, int(s->n_run), s->st);
+    if (s->run_br.size() <= 1) {
+      for (const pf_server::Seg& g : new_seg)
+        launch_init(g.kind, g.N, g.prec, s->d_fds, s->d_tmap + g.off, int(g.n), s->st);
+      for (const pf_server::Seg& g : s->run_seg)
+        launch_propagate(g.kind, g.N, g.prec, s->d_fds, s->d_tmap + g.off, int(g.n), s->st);
+      launch_resample(s->d_fds, s->d_tmap, int(s->n_run), s->st);
+    } else {
+      cudaEventRecord(s->ev_fork, s->st);
+      for (size_t q = 0; q < s->run_br.size(); ++q) {
+        cudaStream_t sb = s->st_br[q];
+        const int b = s->run_br[q].br;
+        cudaStreamWaitEvent(sb, s->ev_fork, 0);
+        for (const pf_server::Seg& g : new_seg)
+          if (g.br == b)
+            launch_init(g.kind, g.N, g.prec, s->d_fds, s->d_tmap + g.off, int(g.n), sb);
+        for (const pf_server::Seg& g : s->run_seg)
+          if (g.br == b)
+            launch_propagate(g.kind, g.N, g.prec, s->d_fds, s->d_tmap + g.off, int(g.n), sb);
+        launch_resample(s->d_fds, s->d_tmap + s->run_br[q].off, int(s->run_br[q].n), sb);
+        cudaEventRecord(s->ev_join[q], sb);
+        cudaStreamWaitEvent(s->st, s->ev_join[q], 0);
+      }
+    }
     bool fetch = s->iter % RESULTS_EVERY == 0;
     for (Request* r : s->slots)
       if (r && ++r->launched_steps >= r->T) fetch = true;
@@ -469,6 +545,11 @@ extern "C" pf_status pf_server_create(size_t device_mem_budget, int32_t max_slot
     if (e == cudaSuccess) e = cudaMallocHost((void**)&s->h_res[q], sizeof(double) * 3 * max_slots);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&s->arena[q], ARENA_HALF);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev[q], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
+  for (int b = 0; b < MAX_BRANCHES && e == cudaSuccess; ++b) {
+    e = cudaStreamCreateWithFlags(&s->st_br[b], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_join[b], cudaEventDisableTiming);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -540,6 +621,16 @@ extern "C" pf_status pf_server_poll(pf_server* s, uint64_t ticket, double* logli
   return st;
 }
 
+extern "C" pf_status pf_server_configure(pf_server* s, int32_t branches) {
+  if (!s) return fail(PF_EINVAL, "server is NULL");
+  if (branches < 1 || branches > MAX_BRANCHES)
+    return fail(PF_EINVAL, "pf_server_configure: branches must be 1..%d", MAX_BRANCHES);
+  s->branches.store(branches);
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->regroup = true;
+  return PF_OK;
+}
+
 extern "C" pf_status pf_server_stats(pf_server* s, int64_t* queued, int64_t* running,
                                      int64_t* completed, int64_t* iterations) {
   if (!s) return fail(PF_EINVAL, "server is NULL");
@@ -579,6 +670,11 @@ extern "C" pf_status pf_server_destroy(pf_server* s) {
     if (s->arena[q]) cudaFreeHost(s->arena[q]);
     if (s->ev[q]) cudaEventDestroy(s->ev[q]);
   }
+  for (int b = 0; b < MAX_BRANCHES; ++b) {
+    if (s->st_br[b]) cudaStreamDestroy(s->st_br[b]);
+    if (s->ev_join[b]) cudaEventDestroy(s->ev_join[b]);
+  }
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
   if (s->pool) cudaMemPoolDestroy(s->pool);
   if (s->st) cudaStreamDestroy(s->st);
   delete s;

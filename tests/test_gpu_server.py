@@ -32,13 +32,15 @@ def _mix(n, seed):
     return out
 
 
-def _serve(pf, ws, budget, slots, stagger=0.0):
-    srv = pf.pf_server_create(budget, slots)
+def _serve(pf, ws, budget, slots, stagger=0.0, branches=None, regroup_to=None):
+    srv = pf.pf_server_create(budget, slots, branches=branches)
     tickets = []
-    for w in ws:
+    for n, w in enumerate(ws):
         tickets.append(srv.submit(pf.model_from_workload(w), w.P, w.T, w.dt, w.theta, w.y, w.seed))
         if stagger:
             time.sleep(stagger)
+        if regroup_to is not None and n == len(ws) // 2:
+            srv.configure(regroup_to)  # while filters run
     res = {}
     deadline = time.time() + 120
     while len(res) < len(tickets) and time.time() < deadline:
@@ -83,6 +85,39 @@ def test_server_alone_equals_in_mix():
     mixed, _ = _serve(pf, ws, 8 << 30, 32)
     for a, m in zip(alone, mixed[:3]):
         assert a[0] == m[0] and a[1] == m[1]
+
+
+@pytest.mark.parametrize("branches,regroup_to", [(2, None), (3, None), (8, None), (4, 1),
+                                                 (1, 5)])
+def test_server_branches_equal_pf_run(branches, regroup_to):
+    """Filters dealt into concurrent launch groups (and regrouped while they
+    run) give pf_run's results bit for bit."""
+    import paper_1306_3277_b300 as pf
+    ws = _mix(20, 5)
+    ref = []
+    for w in ws:
+        f = pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt)
+        st, ll, _, _ = f.run(w.theta, w.y, w.seed)
+        f.destroy()
+        ref.append((st, ll))
+    got, stats = _serve(pf, ws, 8 << 30, 12, stagger=0.002, branches=branches,
+                        regroup_to=regroup_to)
+    for (st, ll), (gst, gll, _) in zip(ref, got):
+        assert gst == st and gll == ll
+    assert stats["completed"] == len(ws)
+
+
+def test_server_configure_rejects_bad_branch_counts():
+    import paper_1306_3277_b300 as pf
+    srv = pf.pf_server_create(1 << 30, 2)
+    try:
+        for b in (0, -1, 9):
+            with pytest.raises(pf.PFError) as e:
+                srv.configure(b)
+            assert e.value.status == pf.PF_EINVAL
+        srv.configure(8)
+    finally:
+        srv.destroy()
 
 
 def test_server_rejects_oversized_and_bad_requests():
