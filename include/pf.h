@@ -469,6 +469,19 @@ pf_status pf_measure_fma_peak(int32_t prec, double* flops_per_s, double* ms);
  * n < 0, n > 2^28 or a NULL array with n > 0; PF_ECUDA on a CUDA error. */
 pf_status pf_weight_exp(const double* d, double* w, int64_t n);
 
+/* The step combine's logarithm of the weight sum (Algorithm 2, likelihood
+ * line: log Z_i = M + log S - log P with S = sum_j e^(ell_j - M) >= 1),
+ * evaluated on the device for n given arguments: y[i] = log s[i].  A
+ * diagnostic that lets a test compare the kernels' logarithm (an FP32
+ * logarithm refined by one Newton step in FP64 with the weight exponential,
+ * absolute error a few units of 2^-53 for 1 <= s <= 2^120; the library
+ * logarithm elsewhere) with correctly rounded values.  s and y are HOST arrays
+ * of n doubles owned by the caller (they may not overlap); n = 0 does nothing.
+ * Synchronous, on the current device; allocates 16 n bytes of device memory
+ * for the call.  PF_EINVAL for n < 0, n > 2^28 or a NULL array with n > 0;
+ * PF_ECUDA on a CUDA error. */
+pf_status pf_weight_sum_log(const double* s, double* y, int64_t n);
+
 /* Host-side fault injection for tests: the k-th next device allocation made
  * for a filter (pf_create) or for a request the server admits fails as if
  * the device were out of memory -- once; k = 0 disarms.  pf_create then

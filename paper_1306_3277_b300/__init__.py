@@ -81,6 +81,7 @@ def lib():
         L.pf_measure_fma_peak.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]
         L.pf_weight_exp.argtypes = [_vp, _vp, ctypes.c_int64]
+        L.pf_weight_sum_log.argtypes = [_vp, _vp, ctypes.c_int64]
         L.pf_debug_fail_allocation.argtypes = [ctypes.c_int32]
         L.pf_debug_fail_server_wait.argtypes = [ctypes.c_int32]
         L.pf_debug_check_counts.argtypes = [ctypes.POINTER(ctypes.c_uint64),
@@ -112,7 +113,8 @@ def lib():
                                     _vp, _vp, _vp]
         for name in ("pf_run", "pf_wait", "pf_destroy", "pf_create", "pf_batch_run",
                      "pf_profile_enable", "pf_profile_read", "pf_measure_fma_peak",
-                     "pf_run_range", "pf_sample_path", "pf_weight_exp", "pf_debug_step",
+                     "pf_run_range", "pf_sample_path", "pf_weight_exp", "pf_weight_sum_log",
+                     "pf_debug_step",
                      "pf_debug_fail_allocation", "pf_debug_fail_server_wait",
                      "pf_debug_check_counts"):
             getattr(L, name).restype = ctypes.c_int
@@ -423,6 +425,15 @@ def pf_debug_check_counts():
     names = ("ancestor_out_of_range", "state_not_finite", "prefix_not_monotone",
              "offspring_range_invalid")
     return bool(chk.value), {n: int(v) for n, v in zip(names, c)}
+
+
+def pf_weight_sum_log(s):
+    """log s evaluated on the GPU by the step combine's weight-sum logarithm
+    (diagnostic; s: float64 array, returns a new float64 array)."""
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    y = np.empty_like(s)
+    _check(lib().pf_weight_sum_log(s.ctypes.data, y.ctypes.data, s.size))
+    return y
 
 
 def pf_weight_exp(d):

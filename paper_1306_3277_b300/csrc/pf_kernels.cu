@@ -250,6 +250,46 @@ __device__ __forceinline__ double exp_weight(double d) {
   return __longlong_as_double(__double_as_longlong(W) + (static_cast<long long>(k >> 8) << 52));
 }
 
+// log S of a filter's weight sum S = sum_j e^(ell_j - M) >= 1 (the maximal
+// particle contributes e^0 = 1), for the likelihood increment M + log S.  The
+// library's FP64 logarithm is a long chain of FP64 operations, which B300 runs
+// at 1/64 of the FP32 rate, on the serial path of every step's combine.  Here:
+// y0 = logf(S) in FP32 (the library's single-precision logarithm, within one
+// FP32 ulp of log S), then one Newton step for e^y = S in FP64,
+// t = S e^(-y0) - 1 with the weight exponential (relative error about 2^-52),
+// log S = y0 + log1p(t) = y0 + (t - t^2/2).  |t| is about y0's error, at most
+// 2^-17 (2^-19 for S <= 2^31), so the omitted t^3/3 stays below 2^-52
+// (2^-58).  Absolute error a few units of 2^-53 times max(1, log S) (tests
+// compare it with correctly rounded values); seven FP64-pipe operations.
+// log 1 = 0 exactly; outside 1 <= S <= 2^120 (never reached by a filter) the
+// library logarithm.
+__device__ __forceinline__ double log_sum(double S) {
+  if (S == 1.0) return 0.0;
+  if (!(S > 1.0 && S <= 0x1p120)) return log(S);
+  const double y0 = to_double(logf(__double2float_rn(S)));
+  const double t = fma(S, exp_weight(-y0), -1.0);
+  return y0 + fma(-0.5 * t, t, t);
+}
+
+// The combines' exponential and logarithm: the two functions above (OWN), or
+// the library's for the large states, whose register-bound propagate kernel
+// measurably slows (0.7 %) when their code is compiled into it.  A model class
+// uses one choice in every launch form, so every form gives the same bits.
+template <bool OWN>
+__device__ __forceinline__ double combine_exp(double d) {
+  if constexpr (OWN) return exp_weight(d);
+  else return exp(d);
+}
+template <bool OWN>
+__device__ __forceinline__ double combine_log(double s) {
+  if constexpr (OWN) return log_sum(s);
+  else return log(s);
+}
+template <int KIND, int N>
+struct OwnCombineMath {
+  static constexpr bool value = !(l96_kind(KIND) && N >= 16);
+};
+
 // The paper's windkessel transition: s steps x <- a x + b (F_k + sd z_mm),
 // a = exp(-dt/(RC)) (own exponential), b = R (1 - a), sd = dt sqrt(sigma2),
 // z_mm = normal number mm of stream (j, i, PROP); a, b, sd in FP64, rounded to
@@ -486,9 +526,12 @@ struct TileTriples {
   double M[MAX_CLUSTER_TILES], S[MAX_CLUSTER_TILES], Q[MAX_CLUSTER_TILES];
 };
 
-template <bool WARP>
+// store = false (the cluster path's CTAs other than the first, which combine
+// the same partials for themselves): the global copies (tp, gp) are left to
+// the CTA that stores them.
+template <bool WARP, bool OWN>
 __device__ bool combine_group(const FilterDev& fd, int g, CombineScratch& cs,
-                              const TileTriples* src = nullptr) {
+                              const TileTriples* src = nullptr, bool store = true) {
   const int tid = threadIdx.x;
   const int t0 = g * GROUP;
   const int ntg = min(GROUP, fd.ntiles - t0);
@@ -510,11 +553,11 @@ __device__ bool combine_group(const FilterDev& fd, int g, CombineScratch& cs,
       }
       Mg = warp_max(Mt);
       // exp(0) = 1 exactly: the maximal tile (and a one-tile group) skips the call
-      const double gt = (Mt == -INFINITY) ? 0.0 : (Mt == Mg ? 1.0 : exp(Mt - Mg));
+      const double gt = (Mt == -INFINITY) ? 0.0 : (Mt == Mg ? 1.0 : combine_exp<OWN>(Mt - Mg));
       const double incl = warp_scan(St * gt, &Sg);
       if (fd.mode == MODE_ADAPTIVE) Qg = warp_sum(Qt * (gt * gt));
       const double before = __shfl_up_sync(0xffffffffu, incl, 1);
-      if (tid < ntg) {
+      if (store && tid < ntg) {
         fd.tp[t0 + tid].g = gt;
         fd.tp[t0 + tid].base = tid == 0 ? 0.0 : before;
       }
@@ -531,7 +574,7 @@ __device__ bool combine_group(const FilterDev& fd, int g, CombineScratch& cs,
       Qt = ldcg(&fd.tp[t0 + tid].Q);
     }
     Mg = block_max(Mt, cs.b);
-    const double gt = (Mt == -INFINITY) ? 0.0 : exp(Mt - Mg);
+    const double gt = (Mt == -INFINITY) ? 0.0 : combine_exp<OWN>(Mt - Mg);
     const double incl = block_scan(St * gt, cs.b, &Sg);
     cs.incl[tid] = incl;
     if (fd.mode == MODE_ADAPTIVE) Qg = block_sum(Qt * (gt * gt), cs.b);
@@ -542,11 +585,13 @@ __device__ bool combine_group(const FilterDev& fd, int g, CombineScratch& cs,
     }
   }
   if (tid == 0) {
-    GroupPart& gp = fd.gp[g];
-    gp.M = Mg;
-    gp.S = Sg;
-    gp.Q = Qg;
-    gp.ticket = 0u;
+    if (store) {
+      GroupPart& gp = fd.gp[g];
+      gp.M = Mg;
+      gp.S = Sg;
+      gp.Q = Qg;
+      gp.ticket = 0u;
+    }
     cs.gM = Mg;
     cs.gS = Sg;
     cs.gQ = Qg;
@@ -569,10 +614,10 @@ __device__ bool combine_group(const FilterDev& fd, int g, CombineScratch& cs,
 // by warp 0 alone for at most 32 groups: the same bits).  sctl, when given, is
 // a copy of the control block in shared memory (the cluster path's): the
 // decisions are read from and taken in it, then the whole block is stored to
-// fd.ctl at once.
-template <bool WARP>
+// fd.ctl at once (only with store; store = false also leaves gp alone).
+template <bool WARP, bool OWN>
 __device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs,
-                               Ctl* sctl = nullptr) {
+                               Ctl* sctl = nullptr, bool store = true) {
   const int tid = threadIdx.x;
   const int ng = fd.ngroups;
   double M, S, Q = 0.0;
@@ -584,8 +629,10 @@ __device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs,
     const double G = (M == -INFINITY) ? 0.0 : 1.0;
     S = cs.gS * G;
     if (fd.mode == MODE_ADAPTIVE) Q = cs.gQ * (G * G);
-    fd.gp[0].G = G;
-    fd.gp[0].B = 0.0;
+    if (store) {
+      fd.gp[0].G = G;
+      fd.gp[0].B = 0.0;
+    }
     cs.G = G;
   } else if (WARP && ng <= 32) {
     // warp 0 alone (the same bits as the block reductions)
@@ -597,7 +644,7 @@ __device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs,
       Qg = ldcg(&fd.gp[tid].Q);
     }
     M = warp_max(Mg);
-    const double G = (Mg == -INFINITY) ? 0.0 : exp(Mg - M);
+    const double G = (Mg == -INFINITY) ? 0.0 : combine_exp<OWN>(Mg - M);
     const double incl = warp_scan(Sg * G, &S);
     if (fd.mode == MODE_ADAPTIVE) Q = warp_sum(Qg * (G * G));
     const double before = __shfl_up_sync(0xffffffffu, incl, 1);
@@ -613,7 +660,7 @@ __device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs,
       Qg = ldcg(&fd.gp[tid].Q);
     }
     M = block_max(Mg, cs.b);
-    const double G = (Mg == -INFINITY) ? 0.0 : exp(Mg - M);
+    const double G = (Mg == -INFINITY) ? 0.0 : combine_exp<OWN>(Mg - M);
     const double incl = block_scan(Sg * G, cs.b, &S);
     cs.incl[tid] = incl;
     if (fd.mode == MODE_ADAPTIVE) Q = block_sum(Qg * (G * G), cs.b);
@@ -641,7 +688,7 @@ __device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs,
       if (i < fd.T) c->anc_identity = 1;
       c->step = i + 1;
     } else {
-      const double incr = ((M + log(S)) - c->L) + c->c_obs;
+      const double incr = ((M + combine_log<OWN>(S)) - c->L) + c->c_obs;
       c->ll = c->ll + incr;
       bool resample = false;
       if (i < fd.T) {
@@ -663,12 +710,12 @@ __device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs,
         if (i < fd.T) {
           c->anc_identity = 1;
           c->lam_zero = 0;
-          c->L = log(S);
+          c->L = combine_log<OWN>(S);
         }
       }
       c->step = i + 1;
     }
-    if (sctl) *fd.ctl = *sctl;
+    if (sctl && store) *fd.ctl = *sctl;
   }
 }
 
@@ -737,15 +784,28 @@ struct PropagateOccupancy {
                                                                  : 1;
 };
 
+// Address of the same shared-memory object in CTA `rank` of the cluster
+// (distributed shared memory: a generic pointer the other CTA can store to).
+template <typename T>
+__device__ __forceinline__ T* cluster_peer(T* local, unsigned rank) {
+  unsigned long long out;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(reinterpret_cast<unsigned long long>(local)),
+               "r"(rank));
+  return reinterpret_cast<T*>(out);
+}
+
 // Step i of tile t (Algorithm 2, propagate and weight lines): gather the
 // ancestors' states, propagate, store, weight with y(t_i) in FP64 (skipped at a
 // step without an observation), then the tile partials: max, inclusive prefix
 // of exp(ell - M_t) (ctil) and its total; thread 0 writes them to tp[t].
 // a_spec is the ancestor row's entry when there is no history (loaded early).
+// tri (the cluster path): this CTA's TileTriples; thread 0 also stores the
+// tile's partials into that object in each of the cluster's first ncopies CTAs.
 template <int KIND, int N, typename R>
 __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i, int anc_identity,
                                                int lam_zero, double cw, int a_spec, double* ys,
-                                               CombineScratch& cs, TileTriples* tri = nullptr) {
+                                               CombineScratch& cs, TileTriples* tri = nullptr,
+                                               int ncopies = 0) {
   const int P = fd.P;
   const int tid = threadIdx.x;
   const int j = t * TILE + tid;
@@ -831,10 +891,11 @@ __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i
     tp.M = Mt;
     tp.S = St;
     tp.Q = Qt;
-    if (tri) {  // the cluster path: also into CTA 0's shared memory
-      tri->M[t] = Mt;
-      tri->S[t] = St;
-      tri->Q[t] = Qt;
+    for (int r = 0; r < ncopies; ++r) {  // the cluster path: into every CTA's shared memory
+      TileTriples* dst = cluster_peer(tri, unsigned(r));
+      dst->M[t] = Mt;
+      dst->S[t] = St;
+      dst->Q[t] = Qt;
     }
   }
 }
@@ -892,7 +953,8 @@ __global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value))
   // the large states keep the block reductions only: the extra code of the
   // warp paths measurably slows their register-bound main loop (same bits)
   constexpr bool WARP = !(l96_kind(KIND) && N >= 16);
-  if (combine_group<WARP>(fd, t / GROUP, cs)) combine_filter<WARP>(fd, i, cs);
+  constexpr bool OWN = OwnCombineMath<KIND, N>::value;
+  if (combine_group<WARP, OWN>(fd, t / GROUP, cs)) combine_filter<WARP, OWN>(fd, i, cs);
 }
 
 // Number of systematic targets j in [0, P) below cumulative weight b: target
@@ -1243,47 +1305,30 @@ __device__ __forceinline__ void cluster_sync() {
                "barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// Address of the same shared-memory object in CTA `rank` of the cluster
-// (distributed shared memory: a generic pointer the other CTA can store to).
-template <typename T>
-__device__ __forceinline__ T* cluster_peer(T* local, unsigned rank) {
-  unsigned long long out;
-  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(reinterpret_cast<unsigned long long>(local)),
-               "r"(rank));
-  return reinterpret_cast<T*>(out);
-}
-
-// A tile's place in the filter's cumulative weights after a combine (what
-// tile_base would read from the partials): base and scale of the tile, base of
-// the next tile (S after the last).
-struct TileGeo {
-  double base, scale, base_next;
-};
-
 // Filter list[blockIdx.x / CS] runs whole on a cluster of CS CTAs, CTA r
-// owning tile r (CTAs past the filter's tiles only take part in the
-// barriers): its initial draw, then per step its tiles propagated in parallel
-// (propagate_tile), CTA 0 combining the group and the filter (combine_group,
+// owning tile r (CTAs past the filter's tiles take part in the barriers and
+// the combine only): its initial draw, then per step its tiles propagated in
+// parallel (propagate_tile), the group and the filter combined (combine_group,
 // combine_filter), and its tiles resampled in parallel (resample_particles) or
-// carried (carry_tile), with a cluster barrier between the phases.  These are
-// the tiled kernels' own functions in their order, so every result is
-// bit-identical to the tiled path's; the two launches and the last-block
-// hand-offs of every step disappear.
-// What the phases hand each other travels through distributed shared memory
-// instead of L2: every CTA stores its tile partials (M, S, Q) into CTA 0's
-// shared memory, and CTA 0 stores the step's control block and every tile's
-// place in the cumulative weights (TileGeo) into each CTA's shared memory
-// (the same values as the global copies, which are kept up to date).  Every
-// CTA reads the same control block after the same barrier, so all take the
-// same branches and reach the same barriers.
+// carried (carry_tile).  These are the tiled kernels' own functions in their
+// order, so every result is bit-identical to the tiled path's; the two
+// launches and the last-block hand-offs of every step disappear.
+// Every CTA stores its tile partials (M, S, Q) into every CTA's shared memory
+// (distributed shared memory) before the step's first cluster barrier; after
+// it, every CTA combines the same partials with the same code, so each takes
+// the same decisions in its own copy of the control block and finds its own
+// tile's place in the cumulative weights, with no second barrier and no
+// hand-off from one CTA to the others.  CTA 0 alone keeps the global copies
+// (tile and group partials, control block) up to date.  The second barrier
+// of the step orders the ancestors each CTA writes for the others' targets
+// before the next step's gathers.
 template <int KIND, int N, typename R>
 __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __restrict__ fds,
                                                          const int* __restrict__ list, int cs_size) {
   __shared__ CombineScratch cs;
   __shared__ double ys[64];
   __shared__ Ctl sctl;          // this CTA's copy of the control block
-  __shared__ TileGeo geo;       // this CTA's tile in the step's cumulative weights
-  __shared__ TileTriples tri;   // CTA 0: the tile partials of the cluster's tiles
+  __shared__ TileTriples tri;   // the tile partials of the cluster's tiles
   __shared__ int s_lo, s_hi, nlong;
   __shared__ int s_nlast[WARPS];
   __shared__ double s_e0, s_scale_r;
@@ -1293,7 +1338,6 @@ __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __rest
   const int tid = threadIdx.x;
   const int P = fd.P, T = fd.T, rs = fd.resampler;
   const bool mine = t < fd.ntiles;
-  TileTriples* tri0 = cluster_peer(&tri, 0u);
   if (mine) init_tile<KIND, N, R>(fd, t);
   cluster_sync();
   if (tid == 0) {  // the initial control block, once from global memory
@@ -1308,26 +1352,14 @@ __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __rest
       const int j = t * TILE + tid;
       const int a_spec = (j < P && !fd.hist) ? fd.anc[j] : j;
       propagate_tile<KIND, N, R>(fd, t, i, sctl.anc_identity, sctl.lam_zero, sctl.cw, a_spec, ys,
-                                 cs, tri0);
+                                 cs, &tri, cs_size);
     }
-    cluster_sync();  // the tile partials of every CTA, in CTA 0's shared memory
-    if (t == 0) {
-      if (combine_group<true>(fd, 0, cs, &tri)) combine_filter<true>(fd, i, cs, &sctl);
-      __syncthreads();  // thread 0's decisions in sctl
-      if (tid < cs_size) {  // lane r hands CTA r the control block and its tile's place
-        const int r = tid;
-        const double G = cs.G;
-        TileGeo gr{0.0, 0.0, 0.0};
-        if (r < fd.ntiles) {
-          gr.base = fma(G, cs.tbase[r], 0.0);  // tile_base: fma(gG, base_t, B) with B = 0
-          gr.scale = G * cs.tg[r];
-          gr.base_next = r + 1 < fd.ntiles ? fma(G, cs.tbase[r + 1], 0.0) : sctl.S;
-        }
-        *cluster_peer(&geo, unsigned(r)) = gr;
-        if (r != 0) *cluster_peer(&sctl, unsigned(r)) = sctl;
-      }
-    }
-    cluster_sync();  // every CTA's control block and tile place
+    cluster_sync();  // the tile partials of every CTA, in every CTA's shared memory
+    const bool first = t == 0;
+    constexpr bool OWN = OwnCombineMath<KIND, N>::value;
+    if (combine_group<true, OWN>(fd, 0, cs, &tri, first))
+      combine_filter<true, OWN>(fd, i, cs, &sctl, first);
+    __syncthreads();  // thread 0's decisions in sctl, the tiles' g and base in cs
     const bool go = sctl.status == ST_OK && sctl.rs_step == i && i < T && sctl.step == i + 1;
     if (tid == 0) nlong = 0;
     if (go && mine) {
@@ -1338,11 +1370,15 @@ __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __rest
         const double ct = j < P ? fd.ctil[j] : 0.0;
         const double u = rs == RS_SYSTEMATIC ? sctl.u : 0.0;
         if (tid == 0 || tid == 32) {
-          const double base = tid == 0 ? geo.base : geo.base_next;
+          // this tile's place (what tile_base reads from the global partials):
+          // base fma(G, base_t, 0), scale G g_t; the next tile's base, or S
+          const double G = cs.G;
+          const double base = tid == 0 ? fma(G, cs.tbase[t], 0.0)
+                                       : (t + 1 < fd.ntiles ? fma(G, cs.tbase[t + 1], 0.0) : sctl.S);
           const int n0 = range_count(fd, rs, base, sctl.ratio, u, i);
           if (tid == 0) {
             s_e0 = base * sctl.ratio - u;
-            s_scale_r = geo.scale * sctl.ratio;
+            s_scale_r = (G * cs.tg[t]) * sctl.ratio;
             s_lo = n0;
           } else {
             s_hi = n0;
@@ -1720,6 +1756,20 @@ __global__ void k_weight_exp(const double* __restrict__ d, double* __restrict__ 
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
        i += int64_t(gridDim.x) * blockDim.x)
     w[i] = exp_weight(d[i]);
+}
+
+// The weight-sum logarithm on n given arguments (diagnostic entry point).
+__global__ void k_log_sum(const double* __restrict__ s, double* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    y[i] = log_sum(s[i]);
+}
+
+cudaError_t launch_log_sum(const double* s, double* y, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t nb = (n + TILE - 1) / TILE;
+  k_log_sum<<<unsigned(nb < 4096 ? nb : 4096), TILE, 0, st>>>(s, y, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_weight_exp(const double* d, double* w, int64_t n, cudaStream_t st) {

@@ -157,6 +157,23 @@ extern "C" pf_status pf_weight_exp(const double* d, double* w, int64_t n) {
   return PF_OK;
 }
 
+extern "C" pf_status pf_weight_sum_log(const double* s, double* y, int64_t n) {
+  if (n < 0) return pfb::fail(PF_EINVAL, "n = %lld < 0", static_cast<long long>(n));
+  if (n == 0) return PF_OK;
+  if (!s || !y) return pfb::fail(PF_EINVAL, "s or y is NULL");
+  if (n > (int64_t(1) << 28)) return pfb::fail(PF_EINVAL, "n = %lld > 2^28", static_cast<long long>(n));
+  double* buf = nullptr;
+  const size_t bytes = size_t(n) * sizeof(double);
+  cudaError_t e = cudaMalloc(&buf, 2 * bytes);
+  if (e != cudaSuccess) return pfb::fail(PF_ECUDA, "cudaMalloc: %s", cudaGetErrorString(e));
+  e = cudaMemcpy(buf, s, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = pfb::launch_log_sum(buf, buf + n, n, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(y, buf + n, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) return pfb::fail(PF_ECUDA, "weight-sum logarithm: %s", cudaGetErrorString(e));
+  return PF_OK;
+}
+
 extern "C" pf_status pf_debug_check_counts(uint64_t* counts, int32_t* checked) {
   if (!counts) return pfb::fail(PF_EINVAL, "counts is NULL");
   unsigned long long c[pfb::CHK_KINDS];

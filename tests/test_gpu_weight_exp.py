@@ -1,7 +1,10 @@
 """The propagate kernels' weight exponential (Algorithm 2, weight line:
-w = exp(ell - M) with ell - M <= 0), evaluated on the GPU through the C ABI and
-compared with correctly rounded values: within 2.5 units of 2^-53 relative on
--700 < d <= 0, exact at the special points, the library exponential below."""
+w = exp(ell - M) with ell - M <= 0) and the step combine's weight-sum
+logarithm (likelihood line: log S), evaluated on the GPU through the C ABI and
+compared with correctly rounded values: the exponential within 2.5 units of
+2^-53 relative on -700 < d <= 0, exact at the special points, the library
+exponential below; the logarithm within 4 units of 2^-53 times max(1, log S)
+on 1 <= S <= 2^120, the library logarithm outside."""
 import math
 
 import mpmath
@@ -73,3 +76,43 @@ def test_weight_exp_rejects_bad_arguments():
     assert pf.pf_weight_exp(np.zeros(0)).size == 0
     assert pf.lib().pf_weight_exp(None, None, -1) == pf.PF_EINVAL
     assert pf.lib().pf_weight_exp(None, None, 4) == pf.PF_EINVAL
+
+
+# ---------------------------------------------------------------------------
+# The step combine's weight-sum logarithm (Algorithm 2, likelihood line:
+# log Z_i = M + log S - log P, S >= 1): an FP32 logarithm refined by one
+# Newton step with the weight exponential.  Absolute error within 4 units of
+# 2^-53 times max(1, log S) against correctly rounded values.
+# ---------------------------------------------------------------------------
+def _log_err_units(y, s):
+    e = mpmath.log(mpmath.mpf(s))
+    return float(abs(mpmath.mpf(y) - e)) / (2.0 ** -53 * max(1.0, float(abs(e))))
+
+
+def test_weight_sum_log_accuracy():
+    import paper_1306_3277_b300 as pf
+    rng = np.random.default_rng(11)
+    s = np.concatenate([
+        2.0 ** rng.uniform(0.0, 31.0, 6000),               # weight sums of up to 2^31 particles
+        1.0 + rng.uniform(0.0, 1e-3, 1000),                 # one dominant particle
+        1.0 + np.arange(1, 400) * 2.0 ** -52,               # next to 1
+        2.0 ** np.arange(0, 121),                           # powers of two
+        np.nextafter(2.0 ** np.arange(1, 60), 0.0),
+        rng.uniform(1.0, 2.0 ** 120, 500),
+    ])
+    y = pf.pf_weight_sum_log(s)
+    worst = max(_log_err_units(yi, si) for yi, si in zip(y, s))
+    assert worst <= 4.0, worst
+    assert pf.pf_weight_sum_log(np.array([1.0]))[0] == 0.0  # one particle carries all the weight
+
+
+def test_weight_sum_log_outside_the_fast_range():
+    import paper_1306_3277_b300 as pf
+    s = np.array([0.5, 1e-300, 2.0 ** 121, 1e300, 0.0, np.inf, np.nan, -1.0])
+    y = pf.pf_weight_sum_log(s)
+    for k in range(4):  # the library logarithm
+        assert _log_err_units(y[k], s[k]) <= 2.0, (s[k], y[k])
+    assert y[4] == -np.inf and y[5] == np.inf and np.isnan(y[6]) and np.isnan(y[7])
+    assert pf.pf_weight_sum_log(np.zeros(0)).size == 0
+    assert pf.lib().pf_weight_sum_log(None, None, -1) == pf.PF_EINVAL
+    assert pf.lib().pf_weight_sum_log(None, None, 4) == pf.PF_EINVAL
