@@ -290,6 +290,13 @@ struct OwnCombineMath {
   static constexpr bool value = !(l96_kind(KIND) && N >= 16);
 };
 
+// The systematic resampling uniform of step i: u in [0, 1) from words 1:0 of
+// Philox block (0, i, RESAMPLE, 0).
+__device__ __forceinline__ double resample_uniform(const FilterDev& fd, int i) {
+  const uint4 w = rng_block(fd.seed, 0u, uint32_t(i), PURPOSE_RESAMPLE, 0u);
+  return u53_closed_open(w.x, w.y);
+}
+
 // The paper's windkessel transition: s steps x <- a x + b (F_k + sd z_mm),
 // a = exp(-dt/(RC)) (own exponential), b = R (1 - a), sd = dt sqrt(sigma2),
 // z_mm = normal number mm of stream (j, i, PROP); a, b, sd in FP64, rounded to
@@ -615,9 +622,12 @@ __device__ bool combine_group(const FilterDev& fd, int g, CombineScratch& cs,
 // a copy of the control block in shared memory (the cluster path's): the
 // decisions are read from and taken in it, then the whole block is stored to
 // fd.ctl at once (only with store; store = false also leaves gp alone).
+// u_pre, when given, is the step's resampling uniform drawn ahead by another
+// thread (the same value this function would draw).
 template <bool WARP, bool OWN>
 __device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs,
-                               Ctl* sctl = nullptr, bool store = true) {
+                               Ctl* sctl = nullptr, bool store = true,
+                               const double* u_pre = nullptr) {
   const int tid = threadIdx.x;
   const int ng = fd.ngroups;
   double M, S, Q = 0.0;
@@ -698,8 +708,7 @@ __device__ void combine_filter(const FilterDev& fd, int i, CombineScratch& cs,
       c->M = M;
       c->S = S;
       if (resample) {
-        const uint4 w = rng_block(fd.seed, 0u, uint32_t(i), PURPOSE_RESAMPLE, 0u);
-        c->u = u53_closed_open(w.x, w.y);
+        c->u = u_pre ? *u_pre : resample_uniform(fd, i);
         c->ratio = double(fd.P) / S;
         c->rs_flag = 1;
         c->anc_identity = 0;
@@ -1331,7 +1340,7 @@ __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __rest
   __shared__ TileTriples tri;   // the tile partials of the cluster's tiles
   __shared__ int s_lo, s_hi, nlong;
   __shared__ int s_nlast[WARPS];
-  __shared__ double s_e0, s_scale_r;
+  __shared__ double s_e0, s_scale_r, s_u;
   __shared__ int3 longr[TILE];
   const FilterDev& fd = fds[list[blockIdx.x / cs_size]];
   const int t = blockIdx.x % cs_size;
@@ -1348,6 +1357,9 @@ __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __rest
   __syncthreads();
   for (int i = 1; i <= T; ++i) {
     if (sctl.status != ST_OK || sctl.step != i) break;  // a degenerate step ended the run
+    // the step's resampling uniform, drawn by the last thread while the others
+    // gather and propagate (off the combine's serial path)
+    if (tid == TILE - 1) s_u = resample_uniform(fd, i);
     if (mine) {
       const int j = t * TILE + tid;
       const int a_spec = (j < P && !fd.hist) ? fd.anc[j] : j;
@@ -1358,7 +1370,7 @@ __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __rest
     const bool first = t == 0;
     constexpr bool OWN = OwnCombineMath<KIND, N>::value;
     if (combine_group<true, OWN>(fd, 0, cs, &tri, first))
-      combine_filter<true, OWN>(fd, i, cs, &sctl, first);
+      combine_filter<true, OWN>(fd, i, cs, &sctl, first, &s_u);
     __syncthreads();  // thread 0's decisions in sctl, the tiles' g and base in cs
     const bool go = sctl.status == ST_OK && sctl.rs_step == i && i < T && sctl.step == i + 1;
     if (tid == 0) nlong = 0;
