@@ -357,16 +357,17 @@ __device__ __forceinline__ void wkx_propagate(const FilterDev& fd, uint32_t j, i
 
 // Windkessel propagation: s Euler substeps x <- x + dt (F_k/C - x/(RC)) +
 // sqrt(q) z_mm (normal number mm of stream (j, i, PROP)).  fc, when given,
-// holds the step's F_k/C (the same division, made once per block: every
-// particle shares it).
+// holds the step's F_k/C, and kc the filter's sqrt(q) and RC (the same
+// operations, made once per block: every particle shares them; in FP64 the
+// square root is a long chain on B300's 1/64-rate FP64 unit).
 template <typename R>
 __device__ __forceinline__ void wk_propagate(const FilterDev& fd, uint32_t j, int i, R& xv,
-                                             const R* fc) {
+                                             const R* fc, const R* kc) {
   const int s = fd.s;
-  const R Rr = from_double<R>(fd.theta[0]);
   const R Cc = from_double<R>(fd.theta[1]);
   const R dt = from_double<R>(fd.dt);
-  const R sq = sqrt(from_double<R>(fd.theta[3]));
+  const R sq = kc ? kc[0] : sqrt(from_double<R>(fd.theta[3]));
+  const R RC = kc ? kc[1] : from_double<R>(fd.theta[0]) * Cc;
   const double* fl = fd.flow + int64_t(i - 1) * s;
   if constexpr (sizeof(R) == 8) {
     for (int mm = 0; mm < s; mm += 2) {
@@ -376,7 +377,7 @@ __device__ __forceinline__ void wk_propagate(const FilterDev& fd, uint32_t j, in
       for (int e = 0; e < 2; ++e) {
         if (mm + e < s) {
           const R fkc = fc ? fc[mm + e] : R(fl[mm + e]) / Cc;
-          const R drift = fkc - xv / (Rr * Cc);
+          const R drift = fkc - xv / RC;
           xv = fmaR(dt, drift, xv);
           xv = fmaR(sq, R(z[e]), xv);
         }
@@ -392,7 +393,7 @@ __device__ __forceinline__ void wk_propagate(const FilterDev& fd, uint32_t j, in
       for (int e = 0; e < 4; ++e) {
         if (mm + e < s) {
           const R fkc = fc ? fc[mm + e] : from_double<R>(fl[mm + e]) / Cc;
-          const R drift = fkc - xv / (Rr * Cc);
+          const R drift = fkc - xv / RC;
           xv = fmaR(dt, drift, xv);
           xv = fmaR(sq, R(z[e]), xv);
         }
@@ -826,17 +827,23 @@ __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i
     if (tid == 0) wkx_constants<R>(fd, kc);
     __syncthreads();
   }
-  // Euler windkessel: F(t_k)/C of the step's substeps, one division each
+  // Euler windkessel: F(t_k)/C of the step's substeps, one division each, and
+  // the filter's sqrt(q) and RC
   __shared__ R fcs[KIND == KIND_WK ? TILE : 1];
+  __shared__ R wkc[2];
   const R* fc = nullptr;
   if constexpr (KIND == KIND_WK) {
+    if (tid == TILE - 2) {
+      wkc[0] = sqrt(from_double<R>(fd.theta[3]));
+      wkc[1] = from_double<R>(fd.theta[0]) * from_double<R>(fd.theta[1]);
+    }
     if (fd.s <= TILE) {
       if (tid < fd.s)
         fcs[tid] = from_double<R>(fd.flow[int64_t(i - 1) * fd.s + tid]) /
                    from_double<R>(fd.theta[1]);
-      __syncthreads();
       fc = fcs;
     }
+    __syncthreads();
   }
   R x[N];
   if (valid) {
@@ -851,7 +858,7 @@ __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i
     R* xout = static_cast<R*>(fd.x[i & 1]);
 #pragma unroll
     for (int n = 0; n < N; ++n) x[n] = xin[int64_t(n) * P + a];
-    if constexpr (KIND == KIND_WK) wk_propagate<R>(fd, uint32_t(j), i, x[0], fc);
+    if constexpr (KIND == KIND_WK) wk_propagate<R>(fd, uint32_t(j), i, x[0], fc, wkc);
     else if constexpr (KIND == KIND_WKX) wkx_propagate<R>(fd, uint32_t(j), i, x[0], kc);
     else if constexpr (KIND == KIND_L96W) l96w_propagate<N, R>(fd, uint32_t(j), i, x);
     else l96_propagate<N, R>(fd, uint32_t(j), i, x);
