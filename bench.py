@@ -327,14 +327,15 @@ def secondary(pf, torch, dev):
     # the autotuned launch shape: cluster bound, branches, resample grid
     chosen = pf.pf_batch_autotune(fs, ths, ys, seeds)
     shape = pf.pf_batch_get_shape(fs)
+    pf.pf_batch_run(fs, ths, ys, seeds)  # the chosen shape's plan and graph
     t0 = time.perf_counter()
     for _ in range(reps):
         lls_a, _ = pf.pf_batch_run(fs, ths, ys, seeds)
     ta = (time.perf_counter() - t0) / reps
     maxrel_a = max(abs(a - b) / abs(b) for a, b in zip(lls_a, lls_p))
 
-    def batch_ms(cta, branches, rs):
-        pf.pf_batch_set_shape(fs, cta, branches, rs)
+    def batch_ms(cta, branches, rs, persistent=0, kt=1):
+        pf.pf_batch_set_shape(fs, cta, branches, rs, persistent, kt)
         pf.pf_batch_run(fs, ths, ys, seeds)  # plan + graph build
         t0 = time.perf_counter()
         for _ in range(reps):
@@ -344,8 +345,12 @@ def secondary(pf, torch, dev):
     # the batch at candidate shapes (one field at a time, as the autotuner searches)
     sweep_cta = {str(b): batch_ms(b, 1, 8) for b in (0, 256, 1024, 2048)}
     sweep_br = {str(k): batch_ms(0, k, 8) for k in (1, 2, 4, 8, 16)}
+    # the persistent launch: CTAs per SM x tiles per propagate item
+    sweep_pe = {"%d_%d" % (b, kt): batch_ms(0, 1, 8, b, kt)
+                for b, kt in ((2, 1), (3, 1), (4, 1), (4, 2), (4, 4))}
     pf.pf_batch_set_shape(fs, shape["cta_max_particles"], shape["branches"],
-                          shape["resample_blocks_per_sm"])
+                          shape["resample_blocks_per_sm"], shape["persistent_blocks_per_sm"],
+                          shape["tiles_per_item"])
     out["batched_256"] = {"filters": len(ws), "batched_evals_per_s": len(ws) / tb,
                           "plain_evals_per_s": len(ws) / tp, "speedup": tp / tb,
                           "batched_particle_steps_per_s": psteps / tb,
@@ -356,7 +361,8 @@ def secondary(pf, torch, dev):
                           "autotuned_speedup_vs_plain": tp / ta,
                           "autotuned_max_rel_loglik_diff_vs_plain": maxrel_a,
                           "batch_ms_by_cluster_bound": sweep_cta,
-                          "batch_ms_by_branches": sweep_br}
+                          "batch_ms_by_branches": sweep_br,
+                          "batch_ms_persistent_by_ctas_per_sm_and_tiles_per_item": sweep_pe}
     for f in fs:
         f.destroy()
     # one small filter alone: the tiled launches against one cluster per filter
@@ -588,7 +594,9 @@ def run_batched(args):
     windkessel, P 2^8..2^14, T 50..500, mixed precision) as one plan, in the
     launch shape the autotuner picks (or, with --branches, that many launch
     chains, the small filters on thread-block clusters up to --cluster-bound
-    particles and --rs-grid resample blocks per SM).  K timed batch runs after
+    particles, --rs-grid resample blocks per SM, and with --persistent that
+    many CTAs per SM of the persistent launch, --tiles-per-item tiles per work
+    item).  K timed batch runs after
     W warm-ups; unless --no-secondary, the same filters one pf_run at a time
     for comparison."""
     import torch
@@ -598,7 +606,8 @@ def run_batched(args):
     fs = [pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt) for w in ws]
     ths, ys, seeds = [w.theta for w in ws], [w.y for w in ws], [w.seed for w in ws]
     if args.branches > 0:
-        pf.pf_batch_set_shape(fs, args.cluster_bound, args.branches, args.rs_grid)
+        pf.pf_batch_set_shape(fs, args.cluster_bound, args.branches, args.rs_grid,
+                              args.persistent, args.tiles_per_item)
     else:
         pf.pf_batch_autotune(fs, ths, ys, seeds)
     shape = pf.pf_batch_get_shape(fs)
@@ -704,6 +713,10 @@ def main():
                     help="batched: independent launch chains (0: the autotuner picks the shape)")
     ap.add_argument("--rs-grid", type=int, default=4,
                     help="batched: resample blocks per SM (with --branches)")
+    ap.add_argument("--persistent", type=int, default=0,
+                    help="batched: CTAs per SM of the persistent launch (0: launch chains)")
+    ap.add_argument("--tiles-per-item", type=int, default=1,
+                    help="batched: tiles per work item of the persistent launch (1, 2, 4, 8)")
     ap.add_argument("--rates", default="250,500,1000,1500,2000", help="serving: offered rates")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: seconds of arrivals")
     ap.add_argument("--drain", type=float, default=20.0, help="serving: extra seconds to finish")

@@ -56,7 +56,7 @@ typedef enum {
   PF_ENOMEM = 2,       /* device allocation failed / over the memory budget  */
   PF_ECUDA = 3,        /* a CUDA runtime call failed                         */
   PF_EDEGENERATE = 4,  /* every particle weight was zero or not a number     */
-  PF_ETIMEOUT = 5,     /* a bounded wait ran out (reserved: no kernel waits) */
+  PF_ETIMEOUT = 5,     /* a bounded wait ran out (the persistent batch launch) */
   PF_EBUSY = 6         /* result not ready / no capacity right now           */
 } pf_status;
 
@@ -200,7 +200,9 @@ const char* pf_last_error(void);
  * memory; logliks and per_filter_status are host arrays of nfilt entries.
  * The launch plan (tile map, CUDA graph) is cached for a repeated filter list.
  * Returns PF_OK if every filter ran (per-filter outcomes in
- * per_filter_status), else the first error. */
+ * per_filter_status), else the first error; PF_ETIMEOUT if a CTA of the
+ * persistent launch (pf_batch_shape) waited more than 4 s for a work item
+ * (the results are then not valid). */
 pf_status pf_batch_run(int32_t nfilt, pf_filter* const* f, const double* const* theta,
                        const double* const* y, const uint64_t* seeds, double* logliks,
                        int32_t* per_filter_status, void* cuda_stream);
@@ -233,13 +235,25 @@ typedef struct {
                                      the run (capped at the number of tiled filters; one chain
                                      when some filter resamples multinomially)                  */
   int32_t resample_blocks_per_sm; /* blocks per SM in the resample kernel's grid, 1..8            */
+  int32_t persistent_blocks_per_sm; /* 0: the tiled filters run as the chains above.  1..8: they
+                                     run in one persistent launch instead, this many CTAs per SM
+                                     (capped at the kernel's occupancy): the CTAs take (filter,
+                                     phase, tiles) work items from a device queue, and the CTA that
+                                     finishes a filter's step or resampling queues the filter's next
+                                     phase, so no filter waits for another.  Used when every tiled
+                                     filter is a windkessel or a Lorenz '96 N = 8 filter of one
+                                     precision, none resampled multinomially; otherwise ignored  */
+  int32_t tiles_per_item;         /* persistent launch: tiles of 256 particles per work item, 1, 2,
+                                     4 or 8; a filter of at most this many tiles runs whole on the
+                                     CTA that takes its first item                               */
 } pf_batch_shape;
 
 /* Set / read the launch shape used for this exact filter list (as
  * pf_batch_configure: host-only; a cached plan is rebuilt on its next use).
- * The default shape is {0, 1, 8}.  PF_EINVAL for a bad list (as
- * pf_batch_configure), a NULL shape, cta_max_particles < 0, branches < 1 or
- * resample_blocks_per_sm outside 1..8. */
+ * The default shape is {0, 1, 8, 0, 1}.  PF_EINVAL for a bad list (as
+ * pf_batch_configure), a NULL shape, cta_max_particles < 0, branches < 1,
+ * resample_blocks_per_sm or persistent_blocks_per_sm outside 1..8 and 0..8,
+ * or tiles_per_item not 1, 2, 4 or 8. */
 pf_status pf_batch_set_shape(int32_t nfilt, pf_filter* const* f, const pf_batch_shape* shape);
 pf_status pf_batch_get_shape(int32_t nfilt, pf_filter* const* f, pf_batch_shape* shape);
 
@@ -248,7 +262,9 @@ pf_status pf_batch_get_shape(int32_t nfilt, pf_filter* const* f, pf_batch_shape*
  * candidate on the host clock, searching one field at a time from the
  * default: the cluster bound (0, 256, 512, 1024, 2048 particles), then the
  * number of branches (1, 2, 4, 8, 16), then the resample grid (2, 4, 8 blocks
- * per SM).  It keeps the fastest shape for the filter list (as
+ * per SM), then the persistent launch's CTAs per SM (0 = off, 1, 2, 3, 4) and,
+ * when it is on, its tiles per item (1, 2, 4, 8).  It keeps the fastest shape
+ * for the filter list (as
  * pf_batch_set_shape would; pf_batch_get_shape reads it back) and returns its
  * cluster bound in *chosen (may be NULL).  The filters' results are those of
  * their last run, identical for every shape.  Errors: those of

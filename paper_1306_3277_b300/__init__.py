@@ -42,11 +42,14 @@ class pf_model(ctypes.Structure):
 class pf_batch_shape(ctypes.Structure):
     """Launch shape of a batch (include/pf.h): no field changes any result."""
     _fields_ = [("cta_max_particles", ctypes.c_int64), ("branches", ctypes.c_int32),
-                ("resample_blocks_per_sm", ctypes.c_int32)]
+                ("resample_blocks_per_sm", ctypes.c_int32),
+                ("persistent_blocks_per_sm", ctypes.c_int32), ("tiles_per_item", ctypes.c_int32)]
 
     def as_dict(self):
         return {"cta_max_particles": int(self.cta_max_particles), "branches": int(self.branches),
-                "resample_blocks_per_sm": int(self.resample_blocks_per_sm)}
+                "resample_blocks_per_sm": int(self.resample_blocks_per_sm),
+                "persistent_blocks_per_sm": int(self.persistent_blocks_per_sm),
+                "tiles_per_item": int(self.tiles_per_item)}
 
 
 _lib = None
@@ -453,11 +456,13 @@ def pf_batch_configure(filters, cta_max_particles):
     _check(lib().pf_batch_configure(nf, hs, int(cta_max_particles)))
 
 
-def pf_batch_set_shape(filters, cta_max_particles=0, branches=1, resample_blocks_per_sm=8):
+def pf_batch_set_shape(filters, cta_max_particles=0, branches=1, resample_blocks_per_sm=8,
+                       persistent_blocks_per_sm=0, tiles_per_item=1):
     """Set the launch shape used for this filter list (results do not change)."""
     nf = len(filters)
     hs = (_vp * nf)(*[f.h for f in filters])
-    sh = pf_batch_shape(int(cta_max_particles), int(branches), int(resample_blocks_per_sm))
+    sh = pf_batch_shape(int(cta_max_particles), int(branches), int(resample_blocks_per_sm),
+                        int(persistent_blocks_per_sm), int(tiles_per_item))
     _check(lib().pf_batch_set_shape(nf, hs, ctypes.byref(sh)))
 
 
@@ -472,7 +477,8 @@ def pf_batch_get_shape(filters):
 
 def pf_batch_autotune(filters, thetas, ys, seeds):
     """Time candidate launch shapes on these inputs (cluster bound, branches,
-    resample grid, one field at a time), keep the fastest for the list and
+    resample grid, persistent launch and its tiles per item, one field at a
+    time), keep the fastest for the list and
     return its cluster bound (pf_batch_get_shape gives the whole shape)."""
     nf = len(filters)
     hs = (_vp * nf)(*[f.h for f in filters])

@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -271,7 +272,7 @@ extern "C" pf_status pf_create(const pf_model* m, int64_t P, int32_t T, double d
 static std::mutex g_plan_mu;
 static std::map<std::vector<pf_filter*>, Plan*> g_plans;  // cached batch plans
 // per filter list: its launch shape (cluster bound, branches, resample grid)
-static const pf_batch_shape kDefaultShape = {0, 1, 8};
+static const pf_batch_shape kDefaultShape = {0, 1, 8, 0, 1};
 static std::map<std::vector<pf_filter*>, pf_batch_shape> g_shapes;
 
 static void destroy_plan(Plan* p) {
@@ -279,10 +280,11 @@ static void destroy_plan(Plan* p) {
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->st) cudaStreamSynchronize(p->st);
   if (p->st2) cudaStreamSynchronize(p->st2);
-  void* dptrs[] = {p->d_fds, p->d_tmap, p->d_ycat, p->d_res, p->d_cta};
+  void* dptrs[] = {p->d_fds, p->d_tmap, p->d_ycat, p->d_res, p->d_cta, p->d_pq, p->d_slots,
+                   p->d_slots_init};
   for (void* q : dptrs)
     if (q) cudaFree(q);
-  void* hptrs[] = {p->h_fds, p->h_ycat, p->h_res};
+  void* hptrs[] = {p->h_fds, p->h_ycat, p->h_res, p->h_perr};
   for (void* q : hptrs)
     if (q) cudaFreeHost(q);
   if (p->ev_staged) cudaEventDestroy(p->ev_staged);
@@ -390,12 +392,47 @@ static cudaError_t enqueue_steps(Plan* p, int first, int last, cudaStream_t st, 
   return le;
 }
 
+// The tiled filters' whole run: the per-step chains, or the persistent launch
+// (the queue reset to the plan's first items, the initial draw per class, one
+// k_persist launch), then the results gather when `results`.
+static cudaError_t enqueue_tiled_run(Plan* p, cudaStream_t st, Profiler* prof, bool results) {
+  if (p->persist_set == 0) return enqueue_steps(p, 1, p->maxT, st, prof, no_hook, true, results);
+  cudaError_t le = cudaMemsetAsync(p->d_slots, 0, sizeof(unsigned long long) * p->persist_total, st);
+  if (le == cudaSuccess)
+    le = cudaMemcpyAsync(p->d_slots, p->d_slots_init,
+                         sizeof(unsigned long long) * p->persist_first, cudaMemcpyDeviceToDevice,
+                         st);
+  if (le == cudaSuccess)  // the run's header; err_any is kept
+    le = cudaMemcpyAsync(p->d_pq, p->d_pq_init, offsetof(PersistQueue, err_any),
+                         cudaMemcpyDeviceToDevice, st);
+  for (size_t b = 0; b < p->branches.size() && le == cudaSuccess; ++b) {
+    for (const PlanClass& pc : p->branches[b].classes) {
+      if (prof) prof->begin(PROF_INIT, st);
+      le = launch_init(pc.kind, pc.N, pc.prec, p->d_fds, p->d_tmap + pc.offset, pc.ntiles, st);
+      if (prof) prof->end(st);
+      if (le != cudaSuccess) break;
+    }
+  }
+  if (le == cudaSuccess) {
+    if (prof) prof->begin(PROF_PROPAGATE, st);
+    le = launch_persist(p->persist_set, p->d_fds, p->d_pq, p->d_slots, p->persist_kt,
+                        p->shape.persistent_blocks_per_sm, st);
+    if (prof) prof->end(st);
+  }
+  if (le == cudaSuccess && results) {
+    if (prof) prof->begin(PROF_RESULTS, st);
+    le = launch_results(p->d_fds, p->nf, p->d_res, st);
+    if (prof) prof->end(st);
+  }
+  return le;
+}
+
 // The launch sequence of one whole run of a plan.  The cluster filters run on
 // a side branch (their own stream, forked and joined with events, so a
 // captured graph holds two parallel branches) next to the tiled steps of the
 // others; with a profiler everything runs on st, one launch after the other.
 static cudaError_t enqueue_run(Plan* p, cudaStream_t st, Profiler* prof) {
-  if (p->cta_total == 0) return enqueue_steps(p, 1, p->maxT, st, prof, no_hook, true);
+  if (p->cta_total == 0) return enqueue_tiled_run(p, st, prof, true);
   cudaStream_t side = prof ? st : p->st2;
   cudaError_t le = cudaSuccess;
   // the cluster filters' FP64 normals, drawn ahead before the fork
@@ -415,7 +452,7 @@ static cudaError_t enqueue_run(Plan* p, cudaStream_t st, Profiler* prof) {
     if (prof) prof->end(st);
   }
   if (le == cudaSuccess && !prof) le = cudaEventRecord(p->ev_join, side);
-  if (le == cudaSuccess) le = enqueue_steps(p, 1, p->maxT, st, prof, no_hook, true, false);
+  if (le == cudaSuccess) le = enqueue_tiled_run(p, st, prof, false);
   if (le == cudaSuccess && !prof) le = cudaStreamWaitEvent(st, p->ev_join, 0);
   if (le == cudaSuccess) {
     if (prof) prof->begin(PROF_RESULTS, st);
@@ -548,6 +585,38 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out,
   }
   p->nf = nf;
   p->maxT = maxT;
+  // the persistent launch: every tiled filter of a class the kernel is
+  // compiled for (in one of its class sets), none resampled multinomially
+  std::vector<unsigned long long> persist_init;
+  if (shape.persistent_blocks_per_sm > 0 && !tiled.empty()) {
+    int set = 0;
+    bool ok = true;
+    for (int k : tiled) {
+      const int bit = persist_class_bit(fl[k]->m.kind, fl[k]->m.N, fl[k]->m.prec);
+      ok = ok && bit != 0 && fl[k]->m.resampler != PF_RESAMPLE_MULTINOMIAL;
+      set |= bit;
+    }
+    if (ok && persist_set_supported(set)) {
+      const int kt = shape.tiles_per_item;
+      unsigned long long total = 0;
+      for (int k : tiled) {  // longest runs first
+        const int nt = fl[k]->sh.ntiles, T = fl[k]->T;
+        const int nP = (nt + kt - 1) / kt;              // propagate items per step
+        const int nR = (nt + RS_CHUNK - 1) / RS_CHUNK;  // resample items per step
+        if (nt <= kt) {  // the whole run on the CTA that takes its first item
+          total += 1;
+          persist_init.push_back(persist_item(k, PHASE_PROP, 0));
+        } else {  // every phase through the queue: T propagate, T - 1 resample phases
+          total += static_cast<unsigned long long>(T) * nP + static_cast<unsigned long long>(T - 1) * nR;
+          for (int q = 0; q < nP; ++q) persist_init.push_back(persist_item(k, PHASE_PROP, q));
+        }
+      }
+      p->persist_set = set;
+      p->persist_kt = kt;
+      p->persist_total = total;
+      p->persist_first = persist_init.size();
+    }
+  }
 
   cudaError_t e = cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_staged, cudaEventDisableTiming);
@@ -579,6 +648,30 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out,
   if (e == cudaSuccess && !tm.empty())
     e = cudaMemcpyAsync(p->d_tmap, tm.data(), sizeof(int2) * tm.size(), cudaMemcpyHostToDevice,
                         p->st);
+  PersistQueue pq0{};
+  if (e == cudaSuccess && p->persist_set != 0) {
+    pq0.tail = p->persist_first;
+    pq0.total = p->persist_total;
+    pq0.cap = p->persist_total;
+    e = cudaMalloc((void**)&p->d_pq, 2 * sizeof(PersistQueue));
+    if (e == cudaSuccess) {
+      p->d_pq_init = p->d_pq + 1;
+      e = cudaMalloc((void**)&p->d_slots, sizeof(unsigned long long) * p->persist_total);
+    }
+    if (e == cudaSuccess)
+      e = cudaMalloc((void**)&p->d_slots_init, sizeof(unsigned long long) * p->persist_first);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_perr, sizeof(int));
+    if (e == cudaSuccess) {
+      *p->h_perr = 0;
+      e = cudaMemcpyAsync(p->d_pq, &pq0, sizeof(PersistQueue), cudaMemcpyHostToDevice, p->st);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->d_pq_init, &pq0, sizeof(PersistQueue), cudaMemcpyHostToDevice, p->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->d_slots_init, persist_init.data(),
+                          sizeof(unsigned long long) * p->persist_first, cudaMemcpyHostToDevice,
+                          p->st);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
   if (e != cudaSuccess) {
     destroy_plan(p);
@@ -671,8 +764,18 @@ pf_status pfb::run_plan(Plan* p, const double* const* theta, const double* const
   if (prof) CK(enqueue_run(p, st, prof));
   else CK(cudaGraphLaunch(p->exec, st));
   CK(cudaMemcpyAsync(p->h_res, p->d_res, sizeof(double) * 3 * p->nf, cudaMemcpyDeviceToHost, st));
+  if (p->persist_set != 0)
+    CK(cudaMemcpyAsync(p->h_perr, &p->d_pq->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaEventRecord(p->ev_done, st));
   return PF_OK;
+}
+
+// After a run of the plan has completed: the persistent launch's failure, if
+// any, as a status (PF_OK otherwise).
+pf_status pfb::persist_status(const Plan* p, int err) {
+  if (p->persist_set == 0 || err == 0) return PF_OK;
+  if (err == 1) return fail(PF_ETIMEOUT, "persistent batch launch: a wait for a work item ran out");
+  return fail(PF_ECUDA, "persistent batch launch: inconsistent work queue (code %d)", err);
 }
 
 // ---------------------------------------------------------------------------
@@ -1014,6 +1117,10 @@ extern "C" pf_status pf_batch_run(int32_t nfilt, pf_filter* const* f, const doub
   pf_status ps = run_plan(p, theta, y, seeds, nullptr, st, nullptr);
   if (ps != PF_OK) return ps;
   CK(cudaEventSynchronize(p->ev_done));
+  if (p->persist_set != 0) {
+    ps = persist_status(p, *p->h_perr);
+    if (ps != PF_OK) return ps;
+  }
   for (int k = 0; k < nfilt; ++k) {
     logliks[k] = p->h_res[3 * k];
     per_filter_status[k] = int(p->h_res[3 * k + 1]) == ST_OK ? PF_OK : PF_EDEGENERATE;
@@ -1035,7 +1142,9 @@ static pf_status batch_key(int32_t nfilt, pf_filter* const* f, std::vector<pf_fi
 
 static bool same_shape(const pf_batch_shape& a, const pf_batch_shape& b) {
   return a.cta_max_particles == b.cta_max_particles && a.branches == b.branches &&
-         a.resample_blocks_per_sm == b.resample_blocks_per_sm;
+         a.resample_blocks_per_sm == b.resample_blocks_per_sm &&
+         a.persistent_blocks_per_sm == b.persistent_blocks_per_sm &&
+         a.tiles_per_item == b.tiles_per_item;
 }
 
 extern "C" pf_status pf_batch_set_shape(int32_t nfilt, pf_filter* const* f,
@@ -1048,6 +1157,11 @@ extern "C" pf_status pf_batch_set_shape(int32_t nfilt, pf_filter* const* f,
   if (shape->branches < 1) return fail(PF_EINVAL, "branches must be >= 1");
   if (shape->resample_blocks_per_sm < 1 || shape->resample_blocks_per_sm > 8)
     return fail(PF_EINVAL, "resample_blocks_per_sm must be in 1..8");
+  if (shape->persistent_blocks_per_sm < 0 || shape->persistent_blocks_per_sm > 8)
+    return fail(PF_EINVAL, "persistent_blocks_per_sm must be in 0..8");
+  const int kt = shape->tiles_per_item;
+  if (kt != 1 && kt != 2 && kt != 4 && kt != 8)
+    return fail(PF_EINVAL, "tiles_per_item must be 1, 2, 4 or 8");
   std::lock_guard<std::mutex> lk(g_plan_mu);
   g_shapes[key] = *shape;
   auto it = g_plans.find(key);
@@ -1106,19 +1220,25 @@ extern "C" pf_status pf_batch_autotune(int32_t nfilt, pf_filter* const* f,
   static const int64_t cta_bounds[] = {0, 256, 512, 1024, 2048};
   static const int32_t branch_counts[] = {1, 2, 4, 8, 16};
   static const int32_t rs_grids[] = {2, 4, 8};
+  static const int32_t persist_bps[] = {0, 1, 2, 3, 4};
+  static const int32_t tiles_items[] = {1, 2, 4, 8};
   pf_batch_shape best = kDefaultShape;
   double best_ms = 0.0;
   pf_status ps = time_shape(nfilt, f, theta, y, seeds, best, &best_ms);
   if (ps != PF_OK) return ps;
   // one field at a time, from the default
-  for (int field = 0; field < 3; ++field) {
-    const int n = field == 0 ? 5 : field == 1 ? 5 : 3;
+  for (int field = 0; field < 5; ++field) {
+    // tiles per item only matter for the persistent launch
+    if (field == 4 && best.persistent_blocks_per_sm == 0) break;
+    const int n = field <= 1 ? 5 : field == 2 ? 3 : field == 3 ? 5 : 4;
     const pf_batch_shape base = best;
     for (int c = 0; c < n; ++c) {
       pf_batch_shape cand = base;
       if (field == 0) cand.cta_max_particles = cta_bounds[c];
       else if (field == 1) cand.branches = branch_counts[c];
-      else cand.resample_blocks_per_sm = rs_grids[c];
+      else if (field == 2) cand.resample_blocks_per_sm = rs_grids[c];
+      else if (field == 3) cand.persistent_blocks_per_sm = persist_bps[c];
+      else cand.tiles_per_item = tiles_items[c];
       if (same_shape(cand, base)) continue;
       double ms = 0.0;
       ps = time_shape(nfilt, f, theta, y, seeds, cand, &ms);

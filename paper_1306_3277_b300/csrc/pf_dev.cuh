@@ -18,6 +18,7 @@ constexpr int GROUP = 256;       // tiles per group (two-level combine)
 constexpr int WARPS = TILE / 32;
 constexpr int64_t MAX_P = int64_t(1) << 24;  // GROUP * GROUP * TILE
 constexpr int MAX_CLUSTER_TILES = 8;          // the portable thread-block cluster size
+constexpr int RS_CHUNK = 4;   // tiles a resample block (or persistent resample item) takes at once
 
 // Checked builds (-DPF_CHECKED=1, libpf_b300_checked.so) count violations of
 // the path's invariants on the device instead of assuming them: an ancestor
@@ -69,7 +70,7 @@ struct alignas(16) Ctl {
   int32_t lam_zero;      // propagate kernel: carried log-weights are all zero
   int32_t status;        // ST_OK / ST_DEGENERATE
   uint32_t gticket;      // groups finished in the current step
-  int32_t pad;
+  uint32_t rticket;      // persistent launch: tiles resampled in the current step
   double ll;             // log-likelihood accumulated so far
   double L;              // log sum_j exp(lam_j) of the carried log-weights
   double M, S;           // max and scaled sum of the current step
@@ -105,6 +106,31 @@ struct alignas(16) FilterDev {
   const double* znoise;  // FP64 windkessel: normals drawn ahead, [T * s][P], or null
 };
 static_assert(sizeof(FilterDev) == 272, "descriptor layout");
+
+// Work queue of the batched form's persistent launch (k_persist).  Items are
+// 64-bit words (filter + 1) << 32 | phase << 24 | q: the tiles
+// [q kt, (q + 1) kt) of one filter, to propagate (PHASE_PROP) or resample
+// (PHASE_RS) at the filter's current step; 0 marks a slot not yet filled.
+// Slots are filled once per run in order of reservation (tail) and taken in
+// order (head); total is the number of items the run fills, lowered when a
+// filter ends early (a degenerate step).
+struct alignas(16) PersistQueue {
+  unsigned long long head;   // next slot to take
+  unsigned long long tail;   // next slot to fill
+  unsigned long long total;  // slots the run fills
+  unsigned long long cap;    // slots allocated
+  int err;                   // this run: a wait ran out (1), a push overflowed (2), an
+                             // item of a stopped filter or a class outside the kernel's (3)
+  int err_any;               // every run since the plan was built (not reset per run)
+  int pad[2];
+};
+enum { PHASE_PROP = 1, PHASE_RS = 2 };
+__host__ __device__ constexpr unsigned long long persist_item(int k, int phase, int q) {
+  return (static_cast<unsigned long long>(k + 1) << 32) |
+         (static_cast<unsigned long long>(phase) << 24) | static_cast<unsigned long long>(q);
+}
+// Model classes the persistent kernel is compiled for, as bits of its class set.
+enum { PC_WK64 = 1, PC_WK32 = 2, PC_L8_64 = 4, PC_L8_32 = 8 };
 
 // -------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two

@@ -38,6 +38,16 @@ cudaError_t launch_next_ancestors(const FilterDev* fds, int ntiles, int32_t* out
 cudaError_t launch_filter_cluster(int kind, int N, int prec, const FilterDev* fds,
                                   const int* list, int nfilters, int cluster_size,
                                   cudaStream_t st);
+// The batched form's persistent launch (k_persist): the model-class bit of
+// the persistent kernel for (kind, N, prec), 0 when it has none; whether a set
+// of class bits has a compiled kernel; the launch over queue q (kt tiles per
+// item, a power of two up to MAX_CLUSTER_TILES; blocks_per_sm CTAs per SM,
+// capped at the kernel's occupancy).
+int persist_class_bit(int kind, int N, int prec);
+bool persist_set_supported(int set);
+cudaError_t launch_persist(int set, const FilterDev* fds, PersistQueue* q,
+                           unsigned long long* slots, int kt, int blocks_per_sm,
+                           cudaStream_t st);
 cudaError_t launch_flow(double* flow, int64_t n, double peak, double period, double dt,
                         cudaStream_t st);
 cudaError_t launch_results(const FilterDev* fds, int nf, double* out, cudaStream_t st);

@@ -760,6 +760,7 @@ __device__ __forceinline__ void init_tile(const FilterDev& fd, int t) {
     c->lam_zero = 1;
     c->status = ST_OK;
     c->gticket = 0u;
+    c->rticket = 0u;
     c->ll = 0.0;
     c->logP = log(double(P));
     c->L = c->logP;
@@ -1208,105 +1209,119 @@ __device__ __forceinline__ void carry_tile(const FilterDev& fd, int t, int i, do
 // every particle's count in every tile of the chunk is taken, and each warp's
 // last count passes through shared memory to the next warp's lane 0 (its
 // predecessor), so no lane recomputes a count; then the tiles' offspring are
-// written (or the tiles carried) one after the other.
-constexpr int RS_CHUNK = 4;
+// written (or the tiles carried) one after the other (RS_CHUNK: pf_dev.cuh).
 
-__global__ void __launch_bounds__(TILE, RESAMPLE_BLOCKS_PER_SM)
-    k_resample(const FilterDev* __restrict__ fds, const int2* __restrict__ tmap, int ntiles) {
-  __shared__ int2 s_ft[RS_CHUNK];
-  __shared__ int s_i[RS_CHUNK], s_go[RS_CHUNK], s_flag[RS_CHUNK], s_lo[RS_CHUNK], s_hi[RS_CHUNK];
-  __shared__ int nlong[RS_CHUNK];
-  __shared__ double s_M[RS_CHUNK], s_e0[RS_CHUNK], s_sr[RS_CHUNK];
-  __shared__ int s_nlast[RS_CHUNK][WARPS];
-  __shared__ int3 longr[2][TILE];
+// Shared scratch of one chunk of resampled tiles.
+struct RsChunk {
+  int2 ft[RS_CHUNK];
+  int i[RS_CHUNK], go[RS_CHUNK], flag[RS_CHUNK], lo[RS_CHUNK], hi[RS_CHUNK];
+  int nlong[RS_CHUNK];
+  double M[RS_CHUNK], e0[RS_CHUNK], sr[RS_CHUNK];
+  int nlast[RS_CHUNK][WARPS];
+  int3 longr[2][TILE];
+};
+
+// The chunk of the nq <= RS_CHUNK tiles tile_of(0..nq-1) (filter, tile),
+// resampled or carried as described above; it counts the resampled tiles in
+// it (its parity picks the long-range list).  Every thread of the block calls
+// it; it ends with a block barrier.
+template <typename TileOf>
+__device__ __forceinline__ void resample_chunk(const FilterDev* __restrict__ fds, TileOf tile_of,
+                                               int nq, RsChunk& c, int& it) {
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int w = tid >> 5;
+  double ct[RS_CHUNK];
+#pragma unroll
+  for (int m = 0; m < RS_CHUNK; ++m) {
+    ct[m] = 0.0;
+    if (m < nq) {
+      const int2 ft = tile_of(m);
+      const FilterDev& fd = fds[ft.x];
+      const int j = ft.y * TILE + tid;
+      if (j < fd.P) ct[m] = fd.ctil[j];
+    }
+  }
+  if (tid < RS_CHUNK) c.nlong[tid] = 0;
+  if (tid < 2 * nq) {
+    const int m = tid >> 1, which = tid & 1;
+    const int2 ft = tile_of(m);
+    const FilterDev& fd = fds[ft.x];
+    const Ctl* ctl = fd.ctl;
+    const int rs = fd.resampler;
+    const int i = ldcg(&ctl->rs_step);
+    const int go = ldcg(&ctl->status) == ST_OK && i >= 1 && i < fd.T && ldcg(&ctl->step) == i + 1;
+    const int flag = ldcg(&ctl->rs_flag);
+    const double u = rs == RS_SYSTEMATIC ? ldcg(&ctl->u) : 0.0;
+    const double ratio = ldcg(&ctl->ratio);
+    double base = 0.0, scale = 0.0;
+    tile_base(fd, ft.y, which, ldcg(&ctl->S), &base, &scale);
+    const int n0 = (go && flag) ? range_count(fd, rs, base, ratio, u, i) : 0;
+    if (which == 0) {
+      c.ft[m] = ft;
+      c.i[m] = i;
+      c.go[m] = go;
+      c.flag[m] = flag;
+      c.M[m] = ldcg(&ctl->M);
+      c.e0[m] = base * ratio - u;
+      c.sr[m] = scale * ratio;
+      c.lo[m] = n0;
+    } else {
+      c.hi[m] = n0;
+    }
+  }
+  __syncthreads();
+  // every particle's count in every tile of the chunk; each warp's last one
+  // goes through shared memory to the next warp's lane 0
+  int nn[RS_CHUNK];
+#pragma unroll
+  for (int m = 0; m < RS_CHUNK; ++m) {
+    nn[m] = 0;
+    if (m < nq && c.go[m] && c.flag[m]) {
+      const int2 ft = c.ft[m];
+      const FilterDev& fd = fds[ft.x];
+      const int nvalid = min(TILE, fd.P - ft.y * TILE);
+      nn[m] = (tid < nvalid && tid != nvalid - 1)
+                  ? particle_count(fd, c.i[m], fd.resampler, c.lo[m], c.hi[m], c.e0[m], c.sr[m],
+                                   ct[m])
+                  : c.hi[m];
+      nn[m] = warp_running_max(nn[m]);
+      if (lane == 31) c.nlast[m][w] = nn[m];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < RS_CHUNK; ++m) {
+    if (m < nq) {
+      const int2 ft = c.ft[m];
+      const FilterDev& fd = fds[ft.x];
+      if (c.go[m] && c.flag[m]) {  // uniform over the block
+        // the counts of the warps before this one bound this warp's below
+        int run = c.lo[m];
+        for (int q = 0; q < w; ++q) run = max(run, c.nlast[m][q]);
+        nn[m] = max(nn[m], run);
+        int prev = __shfl_up_sync(0xffffffffu, nn[m], 1);
+        if (lane == 0) prev = run;
+        const bool valid = tid < min(TILE, fd.P - ft.y * TILE);
+        write_offspring(fd, ft.y, c.i[m], prev, nn[m], valid, &c.nlong[m], c.longr[it & 1]);
+        ++it;
+      } else if (c.go[m]) {
+        carry_tile(fd, ft.y, c.i[m], c.M[m]);
+      }
+    }
+  }
+  __syncthreads();  // the chunk's shared values are rewritten by the next chunk
+}
+
+__global__ void __launch_bounds__(TILE, RESAMPLE_BLOCKS_PER_SM)
+    k_resample(const FilterDev* __restrict__ fds, const int2* __restrict__ tmap, int ntiles) {
+  __shared__ RsChunk c;
   const int G = gridDim.x;
   wait_prior_grid();
   int it = 0;  // resampled tiles so far: its parity picks the long-range list
   for (int q0 = blockIdx.x; q0 < ntiles; q0 += RS_CHUNK * G) {
     const int nq = min(RS_CHUNK, (ntiles - q0 + G - 1) / G);  // q0 + m G < ntiles for m < nq
-    double ct[RS_CHUNK];
-#pragma unroll
-    for (int m = 0; m < RS_CHUNK; ++m) {
-      ct[m] = 0.0;
-      if (m < nq) {
-        const int2 ft = tmap[q0 + m * G];
-        const FilterDev& fd = fds[ft.x];
-        const int j = ft.y * TILE + tid;
-        if (j < fd.P) ct[m] = fd.ctil[j];
-      }
-    }
-    if (tid < RS_CHUNK) nlong[tid] = 0;
-    if (tid < 2 * nq) {
-      const int m = tid >> 1, which = tid & 1;
-      const int2 ft = tmap[q0 + m * G];
-      const FilterDev& fd = fds[ft.x];
-      const Ctl* ctl = fd.ctl;
-      const int rs = fd.resampler;
-      const int i = ldcg(&ctl->rs_step);
-      const int go = ldcg(&ctl->status) == ST_OK && i >= 1 && i < fd.T && ldcg(&ctl->step) == i + 1;
-      const int flag = ldcg(&ctl->rs_flag);
-      const double u = rs == RS_SYSTEMATIC ? ldcg(&ctl->u) : 0.0;
-      const double ratio = ldcg(&ctl->ratio);
-      double base = 0.0, scale = 0.0;
-      tile_base(fd, ft.y, which, ldcg(&ctl->S), &base, &scale);
-      const int n0 = (go && flag) ? range_count(fd, rs, base, ratio, u, i) : 0;
-      if (which == 0) {
-        s_ft[m] = ft;
-        s_i[m] = i;
-        s_go[m] = go;
-        s_flag[m] = flag;
-        s_M[m] = ldcg(&ctl->M);
-        s_e0[m] = base * ratio - u;
-        s_sr[m] = scale * ratio;
-        s_lo[m] = n0;
-      } else {
-        s_hi[m] = n0;
-      }
-    }
-    __syncthreads();
-    // every particle's count in every tile of the chunk; each warp's last one
-    // goes through shared memory to the next warp's lane 0
-    int nn[RS_CHUNK];
-#pragma unroll
-    for (int m = 0; m < RS_CHUNK; ++m) {
-      nn[m] = 0;
-      if (m < nq && s_go[m] && s_flag[m]) {
-        const int2 ft = s_ft[m];
-        const FilterDev& fd = fds[ft.x];
-        const int nvalid = min(TILE, fd.P - ft.y * TILE);
-        nn[m] = (tid < nvalid && tid != nvalid - 1)
-                    ? particle_count(fd, s_i[m], fd.resampler, s_lo[m], s_hi[m], s_e0[m], s_sr[m],
-                                     ct[m])
-                    : s_hi[m];
-        nn[m] = warp_running_max(nn[m]);
-        if (lane == 31) s_nlast[m][w] = nn[m];
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int m = 0; m < RS_CHUNK; ++m) {
-      if (m < nq) {
-        const int2 ft = s_ft[m];
-        const FilterDev& fd = fds[ft.x];
-        if (s_go[m] && s_flag[m]) {  // uniform over the block
-          // the counts of the warps before this one bound this warp's below
-          int run = s_lo[m];
-          for (int q = 0; q < w; ++q) run = max(run, s_nlast[m][q]);
-          nn[m] = max(nn[m], run);
-          int prev = __shfl_up_sync(0xffffffffu, nn[m], 1);
-          if (lane == 0) prev = run;
-          const bool valid = tid < min(TILE, fd.P - ft.y * TILE);
-          write_offspring(fd, ft.y, s_i[m], prev, nn[m], valid, &nlong[m], longr[it & 1]);
-          ++it;
-        } else if (s_go[m]) {
-          carry_tile(fd, ft.y, s_i[m], s_M[m]);
-        }
-      }
-    }
-    __syncthreads();  // the chunk's shared values are rewritten by the next chunk
+    resample_chunk(fds, [&](int m) { return tmap[q0 + m * G]; }, nq, c, it);
   }
 }
 
@@ -1408,6 +1423,281 @@ __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __rest
       }
     }
     cluster_sync();  // the ancestors and carried weights of the next step
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The batched form's persistent launch: one grid of resident CTAs works off a
+// device queue of (filter, phase, tiles) items until every listed filter has
+// run all its steps.
+// ---------------------------------------------------------------------------
+// A CTA takes the next slot (head), waits until it is filled, and processes
+// the item with the tiled kernels' own functions, in their order: for a
+// propagate item propagate_tile and, in the CTA that finishes the step's last
+// tile (the tickets gp[g].ticket and gticket), the group and filter combines;
+// for a resample item the per-tile resampling of k_resample (or the carry of
+// the weights).  So every filter's results are bit-identical to the per-step
+// launches'.  The CTA that finishes a phase pushes the filter's next one: its
+// resample items after the combine, its propagate items of the next step after
+// the last resampled tile (rticket).  A propagate item covers kt tiles, a
+// resample item RS_CHUNK tiles (k_resample's chunk).  A filter of at most kt
+// tiles is one item per phase, and the CTA that holds it goes on with the next
+// phase itself, without the queue: its whole run stays on that CTA.
+//
+// No CTA waits while it holds work: a CTA waits only for the slot it has
+// taken, between items, and every slot below the final total is filled by a
+// CTA that is processing an item.  So the run completes whatever the number
+// of resident CTAs.  Every wait is bounded (PERSIST_WAIT_NS on the global
+// timer); a wait that runs out sets err, and the other CTAs stop at their
+// next wait.
+//
+// Memory ordering: a tile's writes are released by its ticket (the block's
+// barrier, then a fence and the atomic) and a phase's by the push (the
+// block's barrier, then st.release of each slot); the thread that takes a
+// slot acquires it (ld.acquire) and the block's barrier passes that on to the
+// other threads before they read anything the item depends on.
+//
+// Latency: thread 0 reserves the slot of its CTA's next item (the atomic on
+// head) as soon as it holds the current one, so the reservation overlaps the
+// item's work; a CTA running a small filter's whole run reserves nothing
+// ahead (the reserved item would wait for that run).
+constexpr unsigned long long PERSIST_WAIT_NS = 4000000000ull;  // 4 s
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// Record a failure of this run (err) and of the plan's runs so far (err_any).
+__device__ __forceinline__ void persist_fail(PersistQueue* q, int code) {
+  atomicExch(&q->err, code);
+  atomicExch(&q->err_any, code);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// The item in slot idx once it is filled; 0 when the run fills no slot idx
+// (every item is taken) or has failed.
+__device__ unsigned long long persist_wait(PersistQueue* q, const unsigned long long* slots,
+                                           unsigned long long idx) {
+  const unsigned long long t0 = global_ns();
+  unsigned ns = 32;
+  for (;;) {
+    if (idx >= ld_acquire_u64(&q->total)) return 0ull;
+    const unsigned long long v = ld_acquire_u64(&slots[idx]);
+    if (v != 0ull) return v;
+    if (ld_relaxed_s32(&q->err) != 0) return 0ull;
+    if (global_ns() - t0 > PERSIST_WAIT_NS) {
+      persist_fail(q, 1);
+      return 0ull;
+    }
+    __nanosleep(ns);
+    if (ns < 256) ns <<= 1;
+  }
+}
+
+struct PersistShared {
+  CombineScratch cs;
+  double ys[64];
+  unsigned long long item, next, base;
+  int last, cont;
+  RsChunk rc;  // resample items
+};
+
+// Fill n slots with the items (k, phase, 0..n-1).  Every thread of the block
+// calls it; the barrier orders the block's writes before the releases.
+__device__ void persist_push(PersistQueue* q, unsigned long long* slots, int k, int phase, int n,
+                             PersistShared& sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) sh.base = atomicAdd(&q->tail, static_cast<unsigned long long>(n));
+  __syncthreads();
+  const unsigned long long b = sh.base;
+  if (b + static_cast<unsigned long long>(n) > q->cap) {
+    // the plan's count rules this out; refuse rather than write past the array
+    if (threadIdx.x == 0) persist_fail(q, 2);
+    return;
+  }
+  for (int r = threadIdx.x; r < n; r += TILE) st_release_u64(&slots[b + r], persist_item(k, phase, r));
+}
+
+// Propagate item: tiles [qi kt, (qi + 1) kt) of filter k at its current step.
+template <int KIND, int N, typename R>
+__device__ void persist_propagate(const FilterDev& fd, int k, int qi, int kt, PersistQueue* q,
+                                  unsigned long long* slots, PersistShared& sh) {
+  const int tid = threadIdx.x;
+  const int t0 = qi * kt, t1 = min(t0 + kt, fd.ntiles);
+  // every thread reads the control block (L2) with its first tile's ancestor
+  // row entry, so the two loads overlap
+  const Ctl* ctl = fd.ctl;
+  const int j0 = t0 * TILE + tid;
+  int a_spec = (j0 < fd.P && !fd.hist) ? fd.anc[j0] : j0;
+  const int i = ldcg(&ctl->step);
+  const bool ok = ldcg(&ctl->status) == ST_OK;
+  const int anc_identity = ldcg(&ctl->anc_identity);
+  const int lam_zero = ldcg(&ctl->lam_zero);
+  const double cw = ldcg(&ctl->cw);
+  if (i > fd.T || !ok) {  // items are pushed only for running filters
+    if (tid == 0) persist_fail(q, 3);
+    return;
+  }
+  constexpr bool WARP = !(l96_kind(KIND) && N >= 16);
+  constexpr bool OWN = OwnCombineMath<KIND, N>::value;
+  bool finished = false;
+  for (int t = t0; t < t1; ++t) {
+    const int j = t * TILE + tid;
+    if (t > t0) a_spec = (j < fd.P && !fd.hist) ? fd.anc[j] : j;
+    propagate_tile<KIND, N, R>(fd, t, i, anc_identity, lam_zero, cw, a_spec, sh.ys, sh.cs);
+    __syncthreads();  // the tile's states, prefixes and partials, before its ticket
+    if (tid == 0) {
+      __threadfence();
+      const int g = t / GROUP;
+      const int ntg = min(GROUP, fd.ntiles - g * GROUP);
+      sh.last = atomicAdd(&fd.gp[g].ticket, 1u) == unsigned(ntg - 1);
+    }
+    __syncthreads();
+    if (sh.last) {
+      __threadfence();
+      if (combine_group<WARP, OWN>(fd, t / GROUP, sh.cs)) {
+        combine_filter<WARP, OWN>(fd, i, sh.cs);
+        finished = true;
+      }
+    }
+  }
+  if (!finished) return;  // uniform over the block
+  __syncthreads();        // thread 0's decisions in the control block
+  const int nR = (fd.ntiles + RS_CHUNK - 1) / RS_CHUNK;
+  if (tid == 0) {
+    const Ctl* c = fd.ctl;  // written by this thread
+    sh.cont = c->status == ST_OK && c->step == i + 1 && i < fd.T;
+    // a filter that ends before its last step fills none of its remaining
+    // (T - i) (nP + nR) slots
+    if (!sh.cont && i < fd.T && fd.ntiles > kt) {
+      const long long nP = (fd.ntiles + kt - 1) / kt;
+      atomicAdd(&q->total, static_cast<unsigned long long>(-(fd.T - i) * (nP + nR)));
+    }
+  }
+  __syncthreads();
+  if (!sh.cont) return;
+  if (fd.ntiles <= kt) {
+    if (tid == 0) sh.next = persist_item(k, PHASE_RS, 0);
+  } else {
+    persist_push(q, slots, k, PHASE_RS, nR, sh);
+  }
+}
+
+// Resample item: tiles [qi RS_CHUNK, (qi + 1) RS_CHUNK) of filter k after its
+// current step, or all its tiles for a filter run whole on this CTA, in
+// k_resample's chunks (resample_chunk: the same computation).
+__device__ void persist_resample(const FilterDev* __restrict__ fds, int k, int qi, int kt,
+                                 PersistQueue* q, unsigned long long* slots, PersistShared& sh) {
+  const int tid = threadIdx.x;
+  const FilterDev& fd = fds[k];
+  const bool whole = fd.ntiles <= kt;
+  const int t0 = whole ? 0 : qi * RS_CHUNK;
+  const int t1 = whole ? fd.ntiles : min(t0 + RS_CHUNK, fd.ntiles);
+  int it = 0;
+  for (int c0 = t0; c0 < t1; c0 += RS_CHUNK)
+    resample_chunk(fds, [&](int m) { return make_int2(k, c0 + m); }, min(RS_CHUNK, t1 - c0),
+                   sh.rc, it);
+  // resample_chunk ended with the block's barrier: the tiles' ancestors (or
+  // carried weights) are written before the ticket
+  if (tid == 0) {
+    __threadfence();
+    const unsigned n = unsigned(t1 - t0);
+    sh.last = atomicAdd(&fd.ctl->rticket, n) == unsigned(fd.ntiles) - n;
+  }
+  __syncthreads();
+  if (!sh.last) return;
+  __threadfence();
+  if (tid == 0) fd.ctl->rticket = 0u;  // for the next step (ordered by the push)
+  if (whole) {
+    if (tid == 0) sh.next = persist_item(k, PHASE_PROP, 0);
+  } else {
+    persist_push(q, slots, k, PHASE_PROP, (fd.ntiles + kt - 1) / kt, sh);
+  }
+}
+
+// Blocks per SM the persistent kernel is compiled for: that of its largest
+// class's propagate kernel (registers without spills); the sets with the FP32
+// Lorenz '96 state are also compiled for four (64 registers, a few words
+// spilled), which the launch takes when asked for four CTAs per SM.
+template <int SET>
+struct PersistOccupancy {
+  static constexpr int value = (SET & PC_L8_64) ? 2 : (SET & PC_L8_32) ? 3 : 4;
+};
+
+template <int SET, int MINB>
+__global__ void __launch_bounds__(TILE, MINB)
+    k_persist(const FilterDev* __restrict__ fds, PersistQueue* q, unsigned long long* slots,
+              int kt) {
+  __shared__ PersistShared sh;
+  const int tid = threadIdx.x;
+  if (tid == 0) sh.next = 0ull;
+  unsigned long long ahead = ~0ull;  // thread 0: the slot reserved for the next item
+  for (;;) {
+    __syncthreads();  // the previous item's shared values are consumed
+    if (tid == 0) {
+      unsigned long long it = sh.next;
+      sh.next = 0ull;
+      if (it == 0ull) {
+        const unsigned long long h = ahead != ~0ull ? ahead : atomicAdd(&q->head, 1ull);
+        ahead = ~0ull;
+        it = persist_wait(q, slots, h);  // acquires the slot
+      }
+      sh.item = it;
+    }
+    __syncthreads();
+    const unsigned long long it = sh.item;
+    if (it == 0ull) return;
+    const int k = int(it >> 32) - 1;
+    const int phase = int((it >> 24) & 0xffu);
+    const int qi = int(it & 0xffffffu);
+    const FilterDev& fd = fds[k];
+    // reserve the next slot now, unless this CTA runs the filter whole
+    if (tid == 0 && fd.ntiles > kt) ahead = atomicAdd(&q->head, 1ull);
+    if (phase == PHASE_RS) {
+      persist_resample(fds, k, qi, kt, q, slots, sh);
+      continue;
+    }
+    const bool dp = fd.prec == PREC_FP64;
+    if constexpr ((SET & PC_WK64) != 0) {
+      if (fd.kind == KIND_WK && dp) {
+        persist_propagate<KIND_WK, 1, double>(fd, k, qi, kt, q, slots, sh);
+        continue;
+      }
+    }
+    if constexpr ((SET & PC_WK32) != 0) {
+      if (fd.kind == KIND_WK && !dp) {
+        persist_propagate<KIND_WK, 1, float>(fd, k, qi, kt, q, slots, sh);
+        continue;
+      }
+    }
+    if constexpr ((SET & PC_L8_64) != 0) {
+      if (fd.kind == KIND_L96 && fd.N == 8 && dp) {
+        persist_propagate<KIND_L96, 8, double>(fd, k, qi, kt, q, slots, sh);
+        continue;
+      }
+    }
+    if constexpr ((SET & PC_L8_32) != 0) {
+      if (fd.kind == KIND_L96 && fd.N == 8 && !dp) {
+        persist_propagate<KIND_L96, 8, float>(fd, k, qi, kt, q, slots, sh);
+        continue;
+      }
+    }
+    if (tid == 0) persist_fail(q, 3);  // a class outside the set: never queued by a plan
+    return;
   }
 }
 
@@ -1626,6 +1916,7 @@ __global__ void k_debug_ctl(const FilterDev* __restrict__ fds, int step, int anc
     c->lam_zero = 1;
     c->status = ST_OK;
     c->gticket = 0u;
+    c->rticket = 0u;
     c->ll = 0.0;
     c->logP = log(double(fd.P));
     c->L = c->logP;
@@ -1831,6 +2122,66 @@ cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks,
   const cudaError_t e = launch_chained(k_resample, unsigned(grid), st, fds, tmap, nblocks);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+int persist_class_bit(int kind, int N, int prec) {
+  if (kind == KIND_WK && N == 1) return prec == PREC_FP64 ? PC_WK64 : PC_WK32;
+  if (kind == KIND_L96 && N == 8) return prec == PREC_FP64 ? PC_L8_64 : PC_L8_32;
+  return 0;
+}
+
+// The class sets the persistent kernel is compiled for: each model class
+// alone, and the windkessel with Lorenz '96 N = 8 in one precision.
+#define PF_PERSIST_SETS(X)                                                       \
+  X(PC_WK64) X(PC_WK32) X(PC_L8_64) X(PC_L8_32) X(PC_WK64 | PC_L8_64) X(PC_WK32 | PC_L8_32)
+
+bool persist_set_supported(int set) {
+#define PF_CASE(m) if (set == (m)) return true;
+  PF_PERSIST_SETS(PF_CASE)
+#undef PF_CASE
+  return false;
+}
+
+template <int SET, int MINB>
+static cudaError_t launch_persist_occ(const FilterDev* fds, PersistQueue* q,
+                                      unsigned long long* slots, int kt, int blocks_per_sm,
+                                      cudaStream_t st) {
+  static int sms = 0, occ = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 148;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persist<SET, MINB>, TILE, 0) !=
+            cudaSuccess ||
+        occ < 1)
+      occ = 1;
+  }
+  const int bps = std::min(std::max(blocks_per_sm, 1), occ);
+  k_persist<SET, MINB><<<sms * bps, TILE, 0, st>>>(fds, q, slots, kt);
+  return cudaGetLastError();
+}
+
+template <int SET>
+static cudaError_t launch_persist_set(const FilterDev* fds, PersistQueue* q,
+                                      unsigned long long* slots, int kt, int blocks_per_sm,
+                                      cudaStream_t st) {
+  constexpr int occ = PersistOccupancy<SET>::value;
+  if constexpr (occ == 3) {
+    if (blocks_per_sm >= 4)
+      return launch_persist_occ<SET, 4>(fds, q, slots, kt, blocks_per_sm, st);
+  }
+  return launch_persist_occ<SET, occ>(fds, q, slots, kt, blocks_per_sm, st);
+}
+
+cudaError_t launch_persist(int set, const FilterDev* fds, PersistQueue* q,
+                           unsigned long long* slots, int kt, int blocks_per_sm,
+                           cudaStream_t st) {
+  if (kt < 1 || kt > MAX_CLUSTER_TILES || (kt & (kt - 1)) != 0) return cudaErrorInvalidValue;
+#define PF_CASE(m) \
+  if (set == (m)) return launch_persist_set<(m)>(fds, q, slots, kt, blocks_per_sm, st);
+  PF_PERSIST_SETS(PF_CASE)
+#undef PF_CASE
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_flow(double* flow, int64_t n, double peak, double period, double dt,

@@ -175,6 +175,8 @@ extern "C" pf_status pf_pmmh_run(int32_t nc, pf_filter* const* f, const double* 
   }
   CKP(cudaMemcpyAsync(ch.theta_p, th_pad.data(), th_pad.size() * sizeof(double),
                       cudaMemcpyHostToDevice, st));
+  if (p->persist_set != 0)  // failures of this call's persistent launches, checked at the end
+    CKP(cudaMemsetAsync(&p->d_pq->err_any, 0, sizeof(int), st));
   k_pmmh_start<<<blocks, threads, 0, st>>>(sp, p->d_fds, nc, ch, seed);
   CKP(cudaGetLastError());
   CKP(cudaGraphLaunch(p->exec, st));
@@ -193,7 +195,10 @@ extern "C" pf_status pf_pmmh_run(int32_t nc, pf_filter* const* f, const double* 
   CKP(cudaMemcpyAsync(logliks, d_ll, n_ll * sizeof(double), cudaMemcpyDefault, st));
   if (accepted)
     CKP(cudaMemcpyAsync(accepted, ch.acc, size_t(nc) * sizeof(int32_t), cudaMemcpyDefault, st));
+  if (p->persist_set != 0)
+    CKP(cudaMemcpyAsync(p->h_perr, &p->d_pq->err_any, sizeof(int), cudaMemcpyDeviceToHost, st));
   CKP(cudaStreamSynchronize(st));
+  if (p->persist_set != 0) ps = persist_status(p, *p->h_perr);
 done:
   if (block) {
     cudaStreamSynchronize(st);

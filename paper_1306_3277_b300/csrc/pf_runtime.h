@@ -161,6 +161,19 @@ struct Plan {
   int* d_cta = nullptr;                     // filter indices, per class
   cudaStream_t st2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // persistent launch (k_persist) of the tiled filters, when the shape asks
+  // for it and the plan qualifies: the class set of the kernel (0: the
+  // per-step chains), tiles per item, the queue and its slots, the initial
+  // slots (every tiled filter's first propagate items, longest runs first) and
+  // the queue header every run starts from
+  int persist_set = 0;
+  int persist_kt = 1;
+  unsigned long long persist_total = 0, persist_first = 0;
+  PersistQueue* d_pq = nullptr;
+  PersistQueue* d_pq_init = nullptr;
+  unsigned long long* d_slots = nullptr;
+  unsigned long long* d_slots_init = nullptr;
+  int* h_perr = nullptr;                    // pinned: the run's queue error
 };
 
 pf_status fail(pf_status st, const char* fmt, ...);
@@ -178,6 +191,9 @@ pf_status run_plan(Plan* p, const double* const* theta, const double* const* y,
                    const uint64_t* seeds, const int32_t* hist_on, cudaStream_t st,
                    Profiler* prof);
 pf_status batch_plan(const std::vector<pf_filter*>& key, Plan** out);
+// After a run of the plan has completed: err (the run's queue error word, read
+// back by run_plan into h_perr) as a status, PF_OK without a persistent launch.
+pf_status persist_status(const Plan* p, int err);
 // Direct launches of steps first..last of a plan (with the initial draw when
 // init), then the results gather; no staging, no graph.
 cudaError_t enqueue_plan_steps(Plan* p, int first, int last, bool init, cudaStream_t st);

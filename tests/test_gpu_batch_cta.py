@@ -122,7 +122,9 @@ def test_branches_are_bit_identical(branches, cta, rs):
         ref = _single(pf, ws, fs)
         pf.pf_batch_set_shape(fs, cta, branches, rs)
         assert pf.pf_batch_get_shape(fs) == {"cta_max_particles": cta, "branches": branches,
-                                             "resample_blocks_per_sm": rs}
+                                             "resample_blocks_per_sm": rs,
+                                             "persistent_blocks_per_sm": 0,
+                                             "tiles_per_item": 1}
         for _ in range(2):
             lls, sts = pf.pf_batch_run(fs, [w.theta for w in ws], [w.y for w in ws],
                                        [w.seed for w in ws])
