@@ -397,11 +397,10 @@ static cudaError_t enqueue_steps(Plan* p, int first, int last, cudaStream_t st, 
 // k_persist launch), then the results gather when `results`.
 static cudaError_t enqueue_tiled_run(Plan* p, cudaStream_t st, Profiler* prof, bool results) {
   if (p->persist_set == 0) return enqueue_steps(p, 1, p->maxT, st, prof, no_hook, true, results);
-  cudaError_t le = cudaMemsetAsync(p->d_slots, 0, sizeof(unsigned long long) * p->persist_total, st);
-  if (le == cudaSuccess)
-    le = cudaMemcpyAsync(p->d_slots, p->d_slots_init,
-                         sizeof(unsigned long long) * p->persist_first, cudaMemcpyDeviceToDevice,
-                         st);
+  // every level's first items, the rest of the slots empty
+  cudaError_t le = cudaMemcpyAsync(p->d_slots, p->d_slots_init,
+                                   sizeof(unsigned long long) * p->persist_total,
+                                   cudaMemcpyDeviceToDevice, st);
   if (le == cudaSuccess)  // the run's header; err_any is kept
     le = cudaMemcpyAsync(p->d_pq, p->d_pq_init, offsetof(PersistQueue, err_any),
                          cudaMemcpyDeviceToDevice, st);
@@ -587,7 +586,8 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out,
   p->maxT = maxT;
   // the persistent launch: every tiled filter of a class the kernel is
   // compiled for (in one of its class sets), none resampled multinomially
-  std::vector<unsigned long long> persist_init;
+  std::vector<unsigned long long> persist_init;  // the slot array every run starts from
+  PersistQueue pq0{};                             // and its queue header
   if (shape.persistent_blocks_per_sm > 0 && !tiled.empty()) {
     int set = 0;
     bool ok = true;
@@ -598,23 +598,42 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out,
     }
     if (ok && persist_set_supported(set)) {
       const int kt = shape.tiles_per_item;
-      unsigned long long total = 0;
-      for (int k : tiled) {  // longest runs first
+      int tmax = 1;
+      for (int k : tiled) tmax = std::max(tmax, fl[k]->T);
+      // the items of every level over the whole run, and each level's first
+      // ones (the longest runs first within a level)
+      unsigned long long cnt[PERSIST_LEVELS] = {};
+      std::vector<unsigned long long> first[PERSIST_LEVELS];
+      for (int k : tiled) {
         const int nt = fl[k]->sh.ntiles, T = fl[k]->T;
         const int nP = (nt + kt - 1) / kt;              // propagate items per step
         const int nR = (nt + RS_CHUNK - 1) / RS_CHUNK;  // resample items per step
+        const int l0 = persist_level(T, tmax);
         if (nt <= kt) {  // the whole run on the CTA that takes its first item
-          total += 1;
-          persist_init.push_back(persist_item(k, PHASE_PROP, 0));
-        } else {  // every phase through the queue: T propagate, T - 1 resample phases
-          total += static_cast<unsigned long long>(T) * nP + static_cast<unsigned long long>(T - 1) * nR;
-          for (int q = 0; q < nP; ++q) persist_init.push_back(persist_item(k, PHASE_PROP, q));
+          cnt[l0] += 1;
+          first[l0].push_back(persist_item(k, PHASE_PROP, 0));
+        } else {  // every phase through the queue: propagate at 1..T, resample at 1..T-1
+          for (int i = 1; i <= T; ++i) cnt[persist_level(T - i + 1, tmax)] += nP;
+          for (int i = 1; i < T; ++i) cnt[persist_level(T - i, tmax)] += nR;
+          for (int q = 0; q < nP; ++q) first[l0].push_back(persist_item(k, PHASE_PROP, q));
         }
       }
+      unsigned long long base = 0;
+      for (int l = 0; l < PERSIST_LEVELS; ++l) {
+        PersistLevel& L = pq0.lv[l];
+        L.head = 0;
+        L.tail = first[l].size();
+        L.total = cnt[l];
+        L.base = base;
+        L.cap = cnt[l];
+        persist_init.resize(base + cnt[l], 0ull);
+        std::copy(first[l].begin(), first[l].end(), persist_init.begin() + base);
+        base += cnt[l];
+      }
+      pq0.maxT = tmax;
       p->persist_set = set;
       p->persist_kt = kt;
-      p->persist_total = total;
-      p->persist_first = persist_init.size();
+      p->persist_total = base;
     }
   }
 
@@ -648,18 +667,14 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out,
   if (e == cudaSuccess && !tm.empty())
     e = cudaMemcpyAsync(p->d_tmap, tm.data(), sizeof(int2) * tm.size(), cudaMemcpyHostToDevice,
                         p->st);
-  PersistQueue pq0{};
   if (e == cudaSuccess && p->persist_set != 0) {
-    pq0.tail = p->persist_first;
-    pq0.total = p->persist_total;
-    pq0.cap = p->persist_total;
     e = cudaMalloc((void**)&p->d_pq, 2 * sizeof(PersistQueue));
     if (e == cudaSuccess) {
       p->d_pq_init = p->d_pq + 1;
       e = cudaMalloc((void**)&p->d_slots, sizeof(unsigned long long) * p->persist_total);
     }
     if (e == cudaSuccess)
-      e = cudaMalloc((void**)&p->d_slots_init, sizeof(unsigned long long) * p->persist_first);
+      e = cudaMalloc((void**)&p->d_slots_init, sizeof(unsigned long long) * p->persist_total);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_perr, sizeof(int));
     if (e == cudaSuccess) {
       *p->h_perr = 0;
@@ -669,7 +684,7 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out,
       e = cudaMemcpyAsync(p->d_pq_init, &pq0, sizeof(PersistQueue), cudaMemcpyHostToDevice, p->st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(p->d_slots_init, persist_init.data(),
-                          sizeof(unsigned long long) * p->persist_first, cudaMemcpyHostToDevice,
+                          sizeof(unsigned long long) * p->persist_total, cudaMemcpyHostToDevice,
                           p->st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);

@@ -109,21 +109,36 @@ static_assert(sizeof(FilterDev) == 272, "descriptor layout");
 
 // Work queue of the batched form's persistent launch (k_persist).  Items are
 // 64-bit words (filter + 1) << 32 | phase << 24 | q: the tiles
-// [q kt, (q + 1) kt) of one filter, to propagate (PHASE_PROP) or resample
-// (PHASE_RS) at the filter's current step; 0 marks a slot not yet filled.
-// Slots are filled once per run in order of reservation (tail) and taken in
-// order (head); total is the number of items the run fills, lowered when a
-// filter ends early (a degenerate step).
-struct alignas(16) PersistQueue {
+// [q kt, (q + 1) kt) of one filter to propagate (PHASE_PROP), or the tiles
+// [q RS_CHUNK, (q + 1) RS_CHUNK) to resample (PHASE_RS), at the filter's
+// current step; 0 marks a slot not yet filled.  An item goes to one of
+// PERSIST_LEVELS first-in-first-out levels by its filter's remaining phases
+// (persist_level: the longest remaining runs first).  Per level, slots are
+// filled once per run in order of reservation (tail) and taken in order
+// (head); total is the number of items the run puts in the level, lowered
+// when a filter ends early (a degenerate step); base is the level's first
+// slot in the slot array.
+constexpr int PERSIST_LEVELS = 8;
+struct alignas(128) PersistLevel {
   unsigned long long head;   // next slot to take
   unsigned long long tail;   // next slot to fill
   unsigned long long total;  // slots the run fills
+  unsigned long long base;   // first slot in the slot array
   unsigned long long cap;    // slots allocated
+};
+struct alignas(128) PersistQueue {
+  PersistLevel lv[PERSIST_LEVELS];
+  int maxT;                  // the longest listed run (levels scale with it)
   int err;                   // this run: a wait ran out (1), a push overflowed (2), an
                              // item of a stopped filter or a class outside the kernel's (3)
   int err_any;               // every run since the plan was built (not reset per run)
-  int pad[2];
 };
+// Level of an item whose filter has rem >= 1 phases of its kind left,
+// including this one (a propagate item of step i: T - i + 1; a resample
+// item of step i: T - i), in a launch whose longest run has maxT steps.
+__host__ __device__ constexpr int persist_level(int rem, int maxT) {
+  return int((static_cast<long long>(rem) * PERSIST_LEVELS) / (static_cast<long long>(maxT) + 1));
+}
 enum { PHASE_PROP = 1, PHASE_RS = 2 };
 __host__ __device__ constexpr unsigned long long persist_item(int k, int phase, int q) {
   return (static_cast<unsigned long long>(k + 1) << 32) |

@@ -1431,7 +1431,8 @@ __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __rest
 // device queue of (filter, phase, tiles) items until every listed filter has
 // run all its steps.
 // ---------------------------------------------------------------------------
-// A CTA takes the next slot (head), waits until it is filled, and processes
+// A CTA takes the first slot of the highest-priority level that has one
+// reserved, waits until it is filled, and processes
 // the item with the tiled kernels' own functions, in their order: for a
 // propagate item propagate_tile and, in the CTA that finishes the step's last
 // tile (the tickets gp[g].ticket and gticket), the group and filter combines;
@@ -1444,12 +1445,19 @@ __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __rest
 // tiles is one item per phase, and the CTA that holds it goes on with the next
 // phase itself, without the queue: its whole run stays on that CTA.
 //
-// No CTA waits while it holds work: a CTA waits only for the slot it has
-// taken, between items, and every slot below the final total is filled by a
-// CTA that is processing an item.  So the run completes whatever the number
-// of resident CTAs.  Every wait is bounded (PERSIST_WAIT_NS on the global
-// timer); a wait that runs out sets err, and the other CTAs stop at their
-// next wait.
+// Priority: the levels order items by their filter's remaining phases, the
+// longest remaining runs first.  With one first-in-first-out queue every
+// filter advanced one phase per pass through the whole queue, so the longest
+// runs of a batch were the last to finish, alone on an idle GPU.
+//
+// No CTA waits while it holds work: a CTA waits only between items, for a
+// slot it has taken (a race with another CTA can take a slot not yet
+// reserved, which then waits for the level's next push), and every slot
+// below a level's final total is filled by a CTA that is processing an item.
+// So the run completes whatever the number of resident CTAs; a CTA ends when
+// every level's items are taken.  Every wait is bounded (PERSIST_WAIT_NS on
+// the global timer); a wait that runs out sets err, and the other CTAs stop
+// at their next wait.
 //
 // Memory ordering: a tile's writes are released by its ticket (the block's
 // barrier, then a fence and the atomic) and a phase's by the push (the
@@ -1457,10 +1465,11 @@ __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __rest
 // slot acquires it (ld.acquire) and the block's barrier passes that on to the
 // other threads before they read anything the item depends on.
 //
-// Latency: thread 0 reserves the slot of its CTA's next item (the atomic on
-// head) as soon as it holds the current one, so the reservation overlaps the
-// item's work; a CTA running a small filter's whole run reserves nothing
-// ahead (the reserved item would wait for that run).
+// Latency: a take reads every level's counters at once (relaxed loads, one
+// round trip) and skips the levels this CTA has seen fully taken.  No slot
+// is claimed ahead of the current item's end: a slot claimed early waits for
+// the claiming CTA's item, which lengthened the longest runs' step chains
+// more than the overlap saved.
 constexpr unsigned long long PERSIST_WAIT_NS = 4000000000ull;  // 4 s
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
@@ -1470,6 +1479,11 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 }
 __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
 }
 __device__ __forceinline__ int ld_relaxed_s32(const int* p) {
   int v;
@@ -1488,15 +1502,18 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// The item in slot idx once it is filled; 0 when the run fills no slot idx
-// (every item is taken) or has failed.
-__device__ unsigned long long persist_wait(PersistQueue* q, const unsigned long long* slots,
+// The item in slot idx of level L once it is filled (acquired); 0 when the
+// level gets no item idx (its total fell below idx) or the run has failed.
+// The counters are read relaxed: only the slot itself synchronizes with the
+// push that fills it.
+__device__ unsigned long long persist_wait(PersistQueue* q, PersistLevel& L,
+                                           const unsigned long long* slots,
                                            unsigned long long idx) {
   const unsigned long long t0 = global_ns();
   unsigned ns = 32;
   for (;;) {
-    if (idx >= ld_acquire_u64(&q->total)) return 0ull;
-    const unsigned long long v = ld_acquire_u64(&slots[idx]);
+    if (idx >= ld_relaxed_u64(&L.total)) return 0ull;
+    const unsigned long long v = ld_acquire_u64(&slots[L.base + idx]);
     if (v != 0ull) return v;
     if (ld_relaxed_s32(&q->err) != 0) return 0ull;
     if (global_ns() - t0 > PERSIST_WAIT_NS) {
@@ -1508,6 +1525,69 @@ __device__ unsigned long long persist_wait(PersistQueue* q, const unsigned long 
   }
 }
 
+// Claim (thread 0) the first reserved slot of the highest-priority level that
+// has one: its level, its index in *idx; -1 when no level has a reserved slot
+// now, with *all_taken set when every level's items are taken.  The levels'
+// counters are read together (relaxed loads, one round trip); `closed` keeps
+// the levels this CTA found fully taken (head only grows and total only
+// falls, so they stay so).
+__device__ int persist_claim(PersistQueue* q, unsigned& closed, unsigned long long* idx,
+                             bool* all_taken) {
+  unsigned long long h[PERSIST_LEVELS], tot[PERSIST_LEVELS], tl[PERSIST_LEVELS];
+#pragma unroll
+  for (int l = 0; l < PERSIST_LEVELS; ++l) {
+    h[l] = 0ull;
+    tot[l] = 0ull;
+    tl[l] = 0ull;
+    if (!((closed >> l) & 1u)) {
+      h[l] = ld_relaxed_u64(&q->lv[l].head);
+      tot[l] = ld_relaxed_u64(&q->lv[l].total);
+      tl[l] = ld_relaxed_u64(&q->lv[l].tail);
+    }
+  }
+  *all_taken = true;
+#pragma unroll
+  for (int l = PERSIST_LEVELS - 1; l >= 0; --l) {
+    if ((closed >> l) & 1u) continue;
+    if (h[l] >= tot[l]) {
+      closed |= 1u << l;
+      continue;
+    }
+    *all_taken = false;
+    if (h[l] < tl[l]) {
+      *idx = atomicAdd(&q->lv[l].head, 1ull);
+      return l;
+    }
+  }
+  return -1;
+}
+
+// This CTA's next item (thread 0): claims and waits until one is filled; 0
+// once every level's items are taken (the run is over) or the run has failed.
+__device__ unsigned long long persist_take(PersistQueue* q, const unsigned long long* slots,
+                                           unsigned& closed) {
+  const unsigned long long t0 = global_ns();
+  unsigned ns = 32;
+  for (;;) {
+    unsigned long long idx = 0;
+    bool all_taken = false;
+    const int l = persist_claim(q, closed, &idx, &all_taken);
+    if (l >= 0) {
+      const unsigned long long v = persist_wait(q, q->lv[l], slots, idx);
+      if (v != 0ull) return v;
+      if (ld_relaxed_s32(&q->err) != 0) return 0ull;
+      continue;  // the level's total fell below the claimed slot: look again
+    }
+    if (all_taken || ld_relaxed_s32(&q->err) != 0) return 0ull;
+    if (global_ns() - t0 > PERSIST_WAIT_NS) {
+      persist_fail(q, 1);
+      return 0ull;
+    }
+    __nanosleep(ns);
+    if (ns < 512) ns <<= 1;
+  }
+}
+
 struct PersistShared {
   CombineScratch cs;
   double ys[64];
@@ -1516,20 +1596,23 @@ struct PersistShared {
   RsChunk rc;  // resample items
 };
 
-// Fill n slots with the items (k, phase, 0..n-1).  Every thread of the block
-// calls it; the barrier orders the block's writes before the releases.
+// Fill n slots of level `level` with the items (k, phase, 0..n-1).  Every
+// thread of the block calls it; the barrier orders the block's writes before
+// the releases.
 __device__ void persist_push(PersistQueue* q, unsigned long long* slots, int k, int phase, int n,
-                             PersistShared& sh) {
+                             int level, PersistShared& sh) {
+  PersistLevel& L = q->lv[level];
   __syncthreads();
-  if (threadIdx.x == 0) sh.base = atomicAdd(&q->tail, static_cast<unsigned long long>(n));
+  if (threadIdx.x == 0) sh.base = atomicAdd(&L.tail, static_cast<unsigned long long>(n));
   __syncthreads();
   const unsigned long long b = sh.base;
-  if (b + static_cast<unsigned long long>(n) > q->cap) {
-    // the plan's count rules this out; refuse rather than write past the array
+  if (b + static_cast<unsigned long long>(n) > L.cap) {
+    // the plan's count rules this out; refuse rather than write past the level
     if (threadIdx.x == 0) persist_fail(q, 2);
     return;
   }
-  for (int r = threadIdx.x; r < n; r += TILE) st_release_u64(&slots[b + r], persist_item(k, phase, r));
+  for (int r = threadIdx.x; r < n; r += TILE)
+    st_release_u64(&slots[L.base + b + r], persist_item(k, phase, r));
 }
 
 // Propagate item: tiles [qi kt, (qi + 1) kt) of filter k at its current step.
@@ -1581,11 +1664,16 @@ __device__ void persist_propagate(const FilterDev& fd, int k, int qi, int kt, Pe
   if (tid == 0) {
     const Ctl* c = fd.ctl;  // written by this thread
     sh.cont = c->status == ST_OK && c->step == i + 1 && i < fd.T;
-    // a filter that ends before its last step fills none of its remaining
-    // (T - i) (nP + nR) slots
+    // a filter that ends before its last step fills none of the slots of
+    // its remaining phases: propagate at steps i+1..T, resample at i..T-1
     if (!sh.cont && i < fd.T && fd.ntiles > kt) {
       const long long nP = (fd.ntiles + kt - 1) / kt;
-      atomicAdd(&q->total, static_cast<unsigned long long>(-(fd.T - i) * (nP + nR)));
+      for (int i2 = i + 1; i2 <= fd.T; ++i2)
+        atomicAdd(&q->lv[persist_level(fd.T - i2 + 1, q->maxT)].total,
+                  static_cast<unsigned long long>(-nP));
+      for (int i2 = i; i2 < fd.T; ++i2)
+        atomicAdd(&q->lv[persist_level(fd.T - i2, q->maxT)].total,
+                  static_cast<unsigned long long>(-static_cast<long long>(nR)));
     }
   }
   __syncthreads();
@@ -1593,7 +1681,7 @@ __device__ void persist_propagate(const FilterDev& fd, int k, int qi, int kt, Pe
   if (fd.ntiles <= kt) {
     if (tid == 0) sh.next = persist_item(k, PHASE_RS, 0);
   } else {
-    persist_push(q, slots, k, PHASE_RS, nR, sh);
+    persist_push(q, slots, k, PHASE_RS, nR, persist_level(fd.T - i, q->maxT), sh);
   }
 }
 
@@ -1624,8 +1712,9 @@ __device__ void persist_resample(const FilterDev* __restrict__ fds, int k, int q
   if (tid == 0) fd.ctl->rticket = 0u;  // for the next step (ordered by the push)
   if (whole) {
     if (tid == 0) sh.next = persist_item(k, PHASE_PROP, 0);
-  } else {
-    persist_push(q, slots, k, PHASE_PROP, (fd.ntiles + kt - 1) / kt, sh);
+  } else {  // the next step's items: T - i propagate phases left
+    persist_push(q, slots, k, PHASE_PROP, (fd.ntiles + kt - 1) / kt,
+                 persist_level(fd.T - sh.rc.i[0], q->maxT), sh);
   }
 }
 
@@ -1645,17 +1734,13 @@ __global__ void __launch_bounds__(TILE, MINB)
   __shared__ PersistShared sh;
   const int tid = threadIdx.x;
   if (tid == 0) sh.next = 0ull;
-  unsigned long long ahead = ~0ull;  // thread 0: the slot reserved for the next item
+  unsigned closed = 0u;  // thread 0: the levels found fully taken
   for (;;) {
     __syncthreads();  // the previous item's shared values are consumed
     if (tid == 0) {
       unsigned long long it = sh.next;
       sh.next = 0ull;
-      if (it == 0ull) {
-        const unsigned long long h = ahead != ~0ull ? ahead : atomicAdd(&q->head, 1ull);
-        ahead = ~0ull;
-        it = persist_wait(q, slots, h);  // acquires the slot
-      }
+      if (it == 0ull) it = persist_take(q, slots, closed);  // acquires the slot
       sh.item = it;
     }
     __syncthreads();
@@ -1665,8 +1750,6 @@ __global__ void __launch_bounds__(TILE, MINB)
     const int phase = int((it >> 24) & 0xffu);
     const int qi = int(it & 0xffffffu);
     const FilterDev& fd = fds[k];
-    // reserve the next slot now, unless this CTA runs the filter whole
-    if (tid == 0 && fd.ntiles > kt) ahead = atomicAdd(&q->head, 1ull);
     if (phase == PHASE_RS) {
       persist_resample(fds, k, qi, kt, q, slots, sh);
       continue;

@@ -163,12 +163,12 @@ struct Plan {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // persistent launch (k_persist) of the tiled filters, when the shape asks
   // for it and the plan qualifies: the class set of the kernel (0: the
-  // per-step chains), tiles per item, the queue and its slots, the initial
-  // slots (every tiled filter's first propagate items, longest runs first) and
-  // the queue header every run starts from
+  // per-step chains), tiles per item, the queue and its slots, the slot array
+  // every run starts from (each level's first items, the rest empty) and the
+  // queue header every run starts from
   int persist_set = 0;
   int persist_kt = 1;
-  unsigned long long persist_total = 0, persist_first = 0;
+  unsigned long long persist_total = 0;
   PersistQueue* d_pq = nullptr;
   PersistQueue* d_pq_init = nullptr;
   unsigned long long* d_slots = nullptr;
