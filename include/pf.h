@@ -515,6 +515,20 @@ pf_status pf_debug_fail_allocation(int32_t k);
  * still releases it.  The GPU itself is not touched.  PF_EINVAL for k < 0. */
 pf_status pf_debug_fail_server_wait(int32_t k);
 
+/* Failure detection of the batched form's persistent launch, for tests.
+ * pf_debug_persist_wait_limit sets how long (seconds, > 0; 4 at load) a CTA
+ * of any later persistent launch waits for a work item before it gives up:
+ * the launch then ends with PF_ETIMEOUT from pf_batch_run, every kernel
+ * having returned (no fault; the context stays usable).  It is set on the
+ * current device, synchronously; PF_EINVAL for seconds <= 0 or > 60,
+ * PF_ECUDA on a CUDA error.  pf_debug_persist_unfilled_slot(1) makes every
+ * persistent plan built afterwards count one slot more than its filters fill
+ * (a slot nothing ever fills: its wait runs out); 0 disarms.  Process-wide,
+ * host-side; PF_EINVAL for values other than 0 and 1.  Neither has a
+ * counterpart in the paper. */
+pf_status pf_debug_persist_wait_limit(double seconds);
+pf_status pf_debug_persist_unfilled_slot(int32_t on);
+
 /* Invariant counters of a checked build of this library (compiled with
  * PF_CHECKED=1: libpf_b300_checked.so), the sanitizer substitute: the kernels
  * count, instead of assuming, violations of the path's invariants.

@@ -87,6 +87,8 @@ def lib():
         L.pf_weight_sum_log.argtypes = [_vp, _vp, ctypes.c_int64]
         L.pf_debug_fail_allocation.argtypes = [ctypes.c_int32]
         L.pf_debug_fail_server_wait.argtypes = [ctypes.c_int32]
+        L.pf_debug_persist_wait_limit.argtypes = [ctypes.c_double]
+        L.pf_debug_persist_unfilled_slot.argtypes = [ctypes.c_int32]
         L.pf_debug_check_counts.argtypes = [ctypes.POINTER(ctypes.c_uint64),
                                             ctypes.POINTER(ctypes.c_int32)]
         L.pf_pmmh_run.argtypes = [ctypes.c_int32, ctypes.POINTER(_vp), _vp,
@@ -119,6 +121,7 @@ def lib():
                      "pf_run_range", "pf_sample_path", "pf_weight_exp", "pf_weight_sum_log",
                      "pf_debug_step",
                      "pf_debug_fail_allocation", "pf_debug_fail_server_wait",
+                     "pf_debug_persist_wait_limit", "pf_debug_persist_unfilled_slot",
                      "pf_debug_check_counts"):
             getattr(L, name).restype = ctypes.c_int
         L.pf_run_noalloc.argtypes = [ctypes.POINTER(pf_model), ctypes.c_int64, ctypes.c_int32,
@@ -410,6 +413,18 @@ def pf_debug_fail_allocation(k):
     """Fault injection: the k-th next device allocation of a filter or a served
     request fails as if the device were out of memory (once); 0 disarms."""
     _check(lib().pf_debug_fail_allocation(k))
+
+
+def pf_debug_persist_wait_limit(seconds):
+    """How long a CTA of a later persistent batch launch waits for a work item
+    before the launch ends with PF_ETIMEOUT (current device; 4 s at load)."""
+    _check(lib().pf_debug_persist_wait_limit(float(seconds)))
+
+
+def pf_debug_persist_unfilled_slot(on):
+    """Fault injection: persistent plans built afterwards count one slot that
+    nothing fills (its wait runs out); False disarms."""
+    _check(lib().pf_debug_persist_unfilled_slot(1 if on else 0))
 
 
 def pf_debug_fail_server_wait(k):

@@ -59,6 +59,22 @@ extern "C" pf_status pf_debug_fail_allocation(int32_t k) {
 
 // ... and the k-th next wait of a server's scheduler for one of its iterations
 // reports a CUDA error, as a failed kernel would
+static std::atomic<int> g_persist_unfilled{0};  // plans count one slot nothing fills
+
+extern "C" pf_status pf_debug_persist_wait_limit(double seconds) {
+  if (!(seconds > 0.0 && seconds <= 60.0))
+    return fail(PF_EINVAL, "the wait limit must be in (0, 60] seconds");
+  const cudaError_t e = set_persist_wait_limit(static_cast<unsigned long long>(seconds * 1e9));
+  if (e != cudaSuccess) return fail(PF_ECUDA, "wait limit: %s", cudaGetErrorString(e));
+  return PF_OK;
+}
+
+extern "C" pf_status pf_debug_persist_unfilled_slot(int32_t on) {
+  if (on != 0 && on != 1) return fail(PF_EINVAL, "on must be 0 or 1");
+  g_persist_unfilled.store(on);
+  return PF_OK;
+}
+
 static std::atomic<int> g_fail_wait_countdown{0};
 
 bool pfb::injected_wait_failure() {
@@ -618,6 +634,9 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out,
           for (int q = 0; q < nP; ++q) first[l0].push_back(persist_item(k, PHASE_PROP, q));
         }
       }
+      // fault injection for tests: one slot more than the filters fill, in
+      // the level of the longest runs' first items (its wait runs out)
+      if (g_persist_unfilled.load() != 0) cnt[persist_level(tmax, tmax)] += 1;
       unsigned long long base = 0;
       for (int l = 0; l < PERSIST_LEVELS; ++l) {
         PersistLevel& L = pq0.lv[l];

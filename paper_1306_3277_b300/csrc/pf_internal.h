@@ -44,6 +44,8 @@ cudaError_t launch_filter_cluster(int kind, int N, int prec, const FilterDev* fd
 // item, a power of two up to MAX_CLUSTER_TILES; blocks_per_sm CTAs per SM,
 // capped at the kernel's occupancy).
 int persist_class_bit(int kind, int N, int prec);
+// The persistent kernel's wait limit in global-timer ns (current device).
+cudaError_t set_persist_wait_limit(unsigned long long ns);
 bool persist_set_supported(int set);
 cudaError_t launch_persist(int set, const FilterDev* fds, PersistQueue* q,
                            unsigned long long* slots, int kt, int blocks_per_sm,

@@ -1455,7 +1455,7 @@ __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __rest
 // reserved, which then waits for the level's next push), and every slot
 // below a level's final total is filled by a CTA that is processing an item.
 // So the run completes whatever the number of resident CTAs; a CTA ends when
-// every level's items are taken.  Every wait is bounded (PERSIST_WAIT_NS on
+// every level's items are taken.  Every wait is bounded (g_persist_wait_ns on
 // the global timer); a wait that runs out sets err, and the other CTAs stop
 // at their next wait.
 //
@@ -1470,7 +1470,8 @@ __global__ void __launch_bounds__(TILE) k_filter_cluster(const FilterDev* __rest
 // is claimed ahead of the current item's end: a slot claimed early waits for
 // the claiming CTA's item, which lengthened the longest runs' step chains
 // more than the overlap saved.
-constexpr unsigned long long PERSIST_WAIT_NS = 4000000000ull;  // 4 s
+// How long a wait may last (global-timer ns): 4 s unless a test shortens it.
+__device__ unsigned long long g_persist_wait_ns = 4000000000ull;
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
   unsigned long long v;
@@ -1516,7 +1517,7 @@ __device__ unsigned long long persist_wait(PersistQueue* q, PersistLevel& L,
     const unsigned long long v = ld_acquire_u64(&slots[L.base + idx]);
     if (v != 0ull) return v;
     if (ld_relaxed_s32(&q->err) != 0) return 0ull;
-    if (global_ns() - t0 > PERSIST_WAIT_NS) {
+    if (global_ns() - t0 > g_persist_wait_ns) {
       persist_fail(q, 1);
       return 0ull;
     }
@@ -1579,7 +1580,7 @@ __device__ unsigned long long persist_take(PersistQueue* q, const unsigned long 
       continue;  // the level's total fell below the claimed slot: look again
     }
     if (all_taken || ld_relaxed_s32(&q->err) != 0) return 0ull;
-    if (global_ns() - t0 > PERSIST_WAIT_NS) {
+    if (global_ns() - t0 > g_persist_wait_ns) {
       persist_fail(q, 1);
       return 0ull;
     }
@@ -2205,6 +2206,10 @@ cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks,
   const cudaError_t e = launch_chained(k_resample, unsigned(grid), st, fds, tmap, nblocks);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+cudaError_t set_persist_wait_limit(unsigned long long ns) {
+  return cudaMemcpyToSymbol(g_persist_wait_ns, &ns, sizeof(ns));
 }
 
 int persist_class_bit(int kind, int N, int prec) {

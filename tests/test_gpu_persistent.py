@@ -5,8 +5,11 @@ next one.  Every filter must give the bits of its own single run, whatever
 the CTAs per SM and the tiles per item, on the first run (plan and graph
 built) and on a replay; filters that stop early (a degenerate step) must not
 hold up the others; shapes outside the kernel's classes fall back to the
-per-step chains with the same bits."""
+per-step chains with the same bits; a wait that runs out (a slot nothing
+fills, planted on the host) ends the launch with PF_ETIMEOUT and leaves the
+device usable."""
 import math
+import time
 
 import numpy as np
 import pytest
@@ -172,3 +175,46 @@ def test_pmmh_chains_on_the_persistent_launch():
                 f.destroy()
     for o in out[1:]:
         assert np.array_equal(out[0][0], o[0]) and np.array_equal(out[0][1], o[1])
+
+
+def test_persistent_wait_runs_out_and_the_device_stays_usable():
+    """A slot that nothing fills (one slot more than the filters fill, counted
+    by the host) makes a CTA's bounded wait run out: the launch ends with
+    PF_ETIMEOUT, every kernel having returned, and the next batch on the same
+    device gives the bits of the single runs."""
+    import paper_1306_3277_b300 as pf
+    def make():
+        ws = [W.windkessel(P=2000, T=12, seed=1, prec=W.MIXED),
+              W.lorenz96_8(P=1500, T=10, seed=2, prec=W.MIXED),
+              W.windkessel(P=256, T=9, seed=3, prec=W.MIXED)]
+        return ws, [pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt) for w in ws]
+    pf.pf_debug_persist_wait_limit(0.25)
+    try:
+        ws, fs = make()
+        try:
+            pf.pf_debug_persist_unfilled_slot(True)
+            pf.pf_batch_set_shape(fs, 0, 1, 8, 2, 1)
+            t0 = time.perf_counter()
+            with pytest.raises(pf.PFError) as e:
+                _run_batch(pf, fs, ws)
+            assert e.value.status == pf.PF_ETIMEOUT
+            assert time.perf_counter() - t0 < 10.0
+        finally:
+            pf.pf_debug_persist_unfilled_slot(False)
+            for f in fs:
+                f.destroy()
+        ws, fs = make()
+        try:
+            ref = [f.run(w.theta, w.y, w.seed)[:2] for w, f in zip(ws, fs)]
+            pf.pf_batch_set_shape(fs, 0, 1, 8, 2, 1)
+            lls, sts = _run_batch(pf, fs, ws)
+            assert [(int(a), b) for a, b in zip(sts, lls)] == [(int(a), b) for a, b in ref]
+        finally:
+            for f in fs:
+                f.destroy()
+        for bad in (0.0, -1.0, 61.0):
+            with pytest.raises(pf.PFError) as e:
+                pf.pf_debug_persist_wait_limit(bad)
+            assert e.value.status == pf.PF_EINVAL
+    finally:
+        pf.pf_debug_persist_wait_limit(4.0)
