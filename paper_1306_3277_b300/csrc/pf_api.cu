@@ -351,8 +351,8 @@ static cudaError_t enqueue_branch(Plan* p, const Branch& b, int first, int last,
       const PlanClass& pc = b.classes[c];
       if (b.cnt_cls[c][i] == 0) continue;
       le = timed(PROF_PROPAGATE, [&] {
-        return launch_propagate(pc.kind, pc.N, pc.prec, p->d_fds, p->d_tmap + pc.offset,
-                                b.cnt_cls[c][i], st);
+        return launch_propagate_sub(pc.kind, pc.N, pc.prec, pc.sub, p->d_fds,
+                                    p->d_tmap + pc.offset, b.cnt_cls[c][i], st);
       });
     }
     if (le == cudaSuccess) le = hook(i);
@@ -593,6 +593,10 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out,
       br.classes[c].ntiles = int(cls_tiles[c].size());
       tm.insert(tm.end(), cls_tiles[c].begin(), cls_tiles[c].end());
     }
+    // a filter running alone whose FP64 tiles would leave SMs idle spreads
+    // each tile's propagation over several blocks (k_propagate_sub)
+    if (nf == 1)
+      for (PlanClass& pc : br.classes) pc.sub = propagate_sub(pc.kind, pc.N, pc.prec, pc.ntiles);
     counts(all_T, br.maxT, br.cnt_all);
     br.cnt_cls.resize(cls_tiles.size());
     for (size_t c = 0; c < cls_tiles.size(); ++c) counts(cls_T[c], br.maxT, br.cnt_cls[c]);

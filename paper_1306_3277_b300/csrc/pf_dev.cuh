@@ -48,7 +48,8 @@ struct alignas(16) TilePart {
   double Q;     // sum exp(2 (ell - M)) (adaptive resampling only)
   double g;     // exp(M - M_group)
   double base;  // exclusive prefix of the scaled tile sums inside the group
-  double pad;
+  unsigned ticket;  // sub-tile propagate launch: parts of the tile finished this step
+  unsigned pad;
 };
 
 struct alignas(16) GroupPart {

@@ -18,6 +18,13 @@ cudaError_t launch_init(int kind, int N, int prec, const FilterDev* fds, const i
                         int nblocks, cudaStream_t st);
 cudaError_t launch_propagate(int kind, int N, int prec, const FilterDev* fds, const int2* tmap,
                              int nblocks, cudaStream_t st);
+// The sub-tile propagate launch (k_propagate_sub) for one filter's tiles:
+// propagate_sub gives the blocks per tile (1, 2 or 4) for a filter of ntiles
+// tiles of this class running alone; launch_propagate_sub launches with it
+// (sub = 1: launch_propagate).  Same results as launch_propagate.
+int propagate_sub(int kind, int N, int prec, int ntiles);
+cudaError_t launch_propagate_sub(int kind, int N, int prec, int sub, const FilterDev* fds,
+                                 const int2* tmap, int ntiles, cudaStream_t st);
 // resample kernel over the listed tiles, its grid at most blocks_per_sm (1..8)
 // blocks per SM
 cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks, cudaStream_t st,

@@ -750,6 +750,7 @@ __device__ __forceinline__ void init_tile(const FilterDev& fd, int t) {
     if (fd.hist) fd.anc[j] = j;
   }
   if (threadIdx.x == 0 && (t % GROUP) == 0) fd.gp[t / GROUP].ticket = 0u;
+  if (threadIdx.x == 0) fd.tp[t].ticket = 0u;
   if (threadIdx.x == 0 && t == 0) {
     Ctl* c = fd.ctl;
     const double r = wk_kind(KIND) ? fd.theta[4] : fd.theta[2];
@@ -805,22 +806,25 @@ __device__ __forceinline__ T* cluster_peer(T* local, unsigned rank) {
   return reinterpret_cast<T*>(out);
 }
 
-// Step i of tile t (Algorithm 2, propagate and weight lines): gather the
-// ancestors' states, propagate, store, weight with y(t_i) in FP64 (skipped at a
-// step without an observation), then the tile partials: max, inclusive prefix
-// of exp(ell - M_t) (ctil) and its total; thread 0 writes them to tp[t].
-// a_spec is the ancestor row's entry when there is no history (loaded early).
-// tri (the cluster path): this CTA's TileTriples; thread 0 also stores the
-// tile's partials into that object in each of the cluster's first ncopies CTAs.
+// Step i of tile t (Algorithm 2, propagate and weight lines), propagate_tile
+// below: gather the ancestors' states, propagate, store, weight with y(t_i) in
+// FP64 (skipped at a step without an observation), then the tile partials:
+// max, inclusive prefix of exp(ell - M_t) (ctil) and its total; thread 0
+// writes them to tp[t].  a_spec is the ancestor row's entry when there is no
+// history (loaded early).  tri (the cluster path): this CTA's TileTriples;
+// thread 0 also stores the tile's partials into that object in each of the
+// cluster's first ncopies CTAs.
+// Its two parts, which the sub-tile launch (k_propagate_sub) also calls:
+// propagate_ell (every thread of the block calls it; particle j, when valid,
+// is gathered, propagated, stored and weighted: its log-weight is returned,
+// -inf for an invalid slot) and tile_epilogue (the tile's reductions over the
+// 256 log-weights of tile t, thread k holding particle j = 256 t + k).
 template <int KIND, int N, typename R>
-__device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i, int anc_identity,
-                                               int lam_zero, double cw, int a_spec, double* ys,
-                                               CombineScratch& cs, TileTriples* tri = nullptr,
-                                               int ncopies = 0) {
+__device__ __forceinline__ double propagate_ell(const FilterDev& fd, int i, int j, bool valid,
+                                                int anc_identity, int lam_zero, double cw,
+                                                int a_spec, double* ys) {
   const int P = fd.P;
   const int tid = threadIdx.x;
-  const int j = t * TILE + tid;
-  const bool valid = j < P;
   if (tid < fd.Ny) ys[tid] = fd.y[int64_t(i - 1) * fd.Ny + tid];  // read after the barrier below
 
   __shared__ R kc[3];  // per-filter constants of the exact windkessel
@@ -886,7 +890,14 @@ __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i
     ell = e;
     if (fd.mode != MODE_ALWAYS) fd.ell[j] = e;
   }
+  return ell;
+}
 
+__device__ __forceinline__ void tile_epilogue(const FilterDev& fd, int t, int j, double ell,
+                                              CombineScratch& cs, TileTriples* tri = nullptr,
+                                              int ncopies = 0) {
+  const int P = fd.P;
+  const int tid = threadIdx.x;
   // tile partials: max, inclusive prefix of exp(ell - M_t), total
   const double Mt = block_max(ell, cs.b);
   const double w = (Mt == -INFINITY) ? 0.0 : exp_weight(ell - Mt);
@@ -915,6 +926,17 @@ __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i
       dst->Q[t] = Qt;
     }
   }
+}
+
+template <int KIND, int N, typename R>
+__device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i, int anc_identity,
+                                               int lam_zero, double cw, int a_spec, double* ys,
+                                               CombineScratch& cs, TileTriples* tri = nullptr,
+                                               int ncopies = 0) {
+  const int j = t * TILE + int(threadIdx.x);
+  const double ell =
+      propagate_ell<KIND, N, R>(fd, i, j, j < fd.P, anc_identity, lam_zero, cw, a_spec, ys);
+  tile_epilogue(fd, t, j, ell, cs, tri, ncopies);
 }
 
 // The step kernels are launched with programmatic stream serialization: the
@@ -969,6 +991,74 @@ __global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value))
   __threadfence();
   // the large states keep the block reductions only: the extra code of the
   // warp paths measurably slows their register-bound main loop (same bits)
+  constexpr bool WARP = !(l96_kind(KIND) && N >= 16);
+  constexpr bool OWN = OwnCombineMath<KIND, N>::value;
+  if (combine_group<WARP, OWN>(fd, t / GROUP, cs)) combine_filter<WARP, OWN>(fd, i, cs);
+}
+
+// The same step with each tile propagated by SUB blocks, block (t, h) taking
+// particles [256 t + h 256/SUB, 256 t + (h+1) 256/SUB) with its first 256/SUB
+// threads (the others only join the block's barriers): for a small filter of
+// FP64 state, whose tiles would leave most SMs idle while each runs its FP64
+// work (B300: 1/64 of the FP32 rate), the work of a tile spreads over SUB
+// SMs.  Each block parks its particles' log-weights in ctil; the last of the
+// tile's SUB blocks (tp[t].ticket) reads the tile's 256 back and runs
+// tile_epilogue and the combines exactly as k_propagate does, so every
+// result is bit-identical to k_propagate's.
+template <int KIND, int N, typename R, int SUB>
+__global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value))
+    k_propagate_sub(const FilterDev* __restrict__ fds, const int2* __restrict__ tmap) {
+  static_assert(SUB == 2 || SUB == 4, "two or four blocks per tile");
+  constexpr int PART = TILE / SUB;
+  __shared__ CombineScratch cs;
+  __shared__ double ys[64];
+  wait_prior_grid();
+  const int2 ft = tmap[blockIdx.x / SUB];
+  const int h = int(blockIdx.x % SUB);
+  const FilterDev& fd = fds[ft.x];
+  Ctl* ctl = fd.ctl;
+  const int P = fd.P;
+  const int t = ft.y;
+  const int tid = threadIdx.x;
+  const int j = t * TILE + h * PART + tid;
+  const bool valid = tid < PART && j < P;
+  const int a_spec = (valid && !fd.hist) ? fd.anc[j] : j;
+  __shared__ int s_step, s_ok, s_anc_identity, s_lam_zero;
+  __shared__ double s_cw;
+  if (tid == 0) {
+    s_step = ldcg(&ctl->step);
+    s_ok = ldcg(&ctl->status) == ST_OK;
+    s_anc_identity = ldcg(&ctl->anc_identity);
+    s_lam_zero = ldcg(&ctl->lam_zero);
+    s_cw = ldcg(&ctl->cw);
+  }
+  __syncthreads();
+  const int i = s_step;
+  if (i > fd.T || !s_ok) return;
+  const double ell =
+      propagate_ell<KIND, N, R>(fd, i, j, valid, s_anc_identity, s_lam_zero, s_cw, a_spec, ys);
+  if (valid) fd.ctil[j] = ell;  // parked for the tile's epilogue
+  __syncthreads();              // the part's states and log-weights, before its ticket
+  if (tid == 0) {
+    __threadfence();
+    cs.last = atomicAdd(&fd.tp[t].ticket, 1u) == unsigned(SUB - 1);
+  }
+  __syncthreads();
+  if (!cs.last) return;
+  __threadfence();
+  if (tid == 0) fd.tp[t].ticket = 0u;  // for the next step (ordered by the launch boundary)
+  const int jt = t * TILE + tid;
+  tile_epilogue(fd, t, jt, jt < P ? ldcg(&fd.ctil[jt]) : -INFINITY, cs);
+  if (tid == 0) {
+    __threadfence();
+    const int g = t / GROUP;
+    const int ntg = min(GROUP, fd.ntiles - g * GROUP);
+    const unsigned old = atomicAdd(&fd.gp[g].ticket, 1u);
+    cs.last = (old == unsigned(ntg - 1));
+  }
+  __syncthreads();
+  if (!cs.last) return;
+  __threadfence();
   constexpr bool WARP = !(l96_kind(KIND) && N >= 16);
   constexpr bool OWN = OwnCombineMath<KIND, N>::value;
   if (combine_group<WARP, OWN>(fd, t / GROUP, cs)) combine_filter<WARP, OWN>(fd, i, cs);
@@ -2012,6 +2102,7 @@ __global__ void k_debug_ctl(const FilterDev* __restrict__ fds, int step, int anc
     c->ratio = 0.0;
   }
   for (int g = threadIdx.x; g < fd.ngroups; g += blockDim.x) fd.gp[g].ticket = 0u;
+  for (int t = threadIdx.x; t < fd.ntiles; t += blockDim.x) fd.tp[t].ticket = 0u;
 }
 
 // The ancestors the next propagation of filter fds[0] takes (diagnostic): the
@@ -2171,6 +2262,68 @@ cudaError_t launch_weight_exp(const double* d, double* w, int64_t n, cudaStream_
   const int64_t nb = (n + TILE - 1) / TILE;
   k_weight_exp<<<unsigned(nb < 4096 ? nb : 4096), TILE, 0, st>>>(d, w, n);
   return cudaGetLastError();
+}
+
+// Blocks per tile of the sub-tile propagate launch for a single filter of
+// `ntiles` tiles: 4 or 2 when the filter's state is FP64 and that many blocks
+// per tile still fit the GPU's resident blocks at once, else 1 (k_propagate).
+template <int KIND, int N, typename R>
+static int sub_for(int ntiles) {
+  if constexpr (sizeof(R) != 8) {
+    return 1;
+  } else {
+    static int sms = 0;
+    if (sms == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 148;
+    }
+    const long long slots = static_cast<long long>(sms) * PropagateOccupancy<KIND, N, R>::value;
+    if (4ll * ntiles <= slots) return 4;
+    if (2ll * ntiles <= slots) return 2;
+    return 1;
+  }
+}
+
+template <int KIND, int N, typename R>
+static cudaError_t launch_sub(int sub, const FilterDev* fds, const int2* tmap, int ntiles,
+                              cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  if (sub == 4)
+    e = launch_chained(k_propagate_sub<KIND, N, R, 4>, unsigned(4 * ntiles), st, fds, tmap);
+  else if (sub == 2)
+    e = launch_chained(k_propagate_sub<KIND, N, R, 2>, unsigned(2 * ntiles), st, fds, tmap);
+  else
+    e = launch_chained(k_propagate<KIND, N, R>, unsigned(ntiles), st, fds, tmap);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// The classes with a sub-tile propagate kernel: FP64 windkessel (both forms)
+// and FP64 Lorenz '96 (both forms) up to N = 12.
+#define PF_SUB_CLASSES(X)                                                          \
+  X(KIND_WK, 1) X(KIND_WKX, 1) X(KIND_L96, 4) X(KIND_L96, 8) X(KIND_L96, 12)     \
+  X(KIND_L96W, 4) X(KIND_L96W, 8) X(KIND_L96W, 12)
+
+int propagate_sub(int kind, int N, int prec, int ntiles) {
+  if (prec != PREC_FP64) return 1;
+#define PF_CASE(k, n) \
+  if (kind == k && N == n) return sub_for<k, n, double>(ntiles);
+  PF_SUB_CLASSES(PF_CASE)
+#undef PF_CASE
+  return 1;
+}
+
+cudaError_t launch_propagate_sub(int kind, int N, int prec, int sub, const FilterDev* fds,
+                                 const int2* tmap, int ntiles, cudaStream_t st) {
+  if (sub <= 1 || prec != PREC_FP64) return launch_propagate(kind, N, prec, fds, tmap, ntiles, st);
+#define PF_CASE(k, n) \
+  if (kind == k && N == n) return launch_sub<k, n, double>(sub, fds, tmap, ntiles, st);
+  PF_SUB_CLASSES(PF_CASE)
+#undef PF_CASE
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_init(int kind, int N, int prec, const FilterDev* fds, const int2* tmap,

@@ -20,6 +20,7 @@ struct PlanClass {
   int kind, N, prec;
   int offset;   // first entry of the class's tiles in Plan::d_tmap
   int ntiles;
+  int sub = 1;  // propagate blocks per tile (k_propagate_sub; a filter running alone)
 };
 
 struct Plan;
