@@ -660,7 +660,8 @@ def run_samplers(args):
     t0 = time.perf_counter()
     _, _, acc = pf.pf_pmmh_run(fs, w.y, spec, th0, niter, 2)
     dt = time.perf_counter() - t0
-    pf.pf_batch_configure(fs, 0)  # the same chains on the tiled path alone
+    shape = pf.pf_batch_get_shape(fs)
+    pf.pf_batch_set_shape(fs, 0, 1, 8, 0, 1)  # the same chains in the default tiled shape
     pf.pf_pmmh_run(fs, w.y, spec, th0, 5, 1)
     t0 = time.perf_counter()
     pf.pf_pmmh_run(fs, w.y, spec, th0, niter, 2)
@@ -673,6 +674,7 @@ def run_samplers(args):
         "particle_steps_per_s": nc * (niter + 1) * w.P * w.T / dt,
         "acceptance": float(acc.sum()) / (nc * niter),
         "autotuned_cluster_max_particles": chosen,
+        "autotuned_shape": shape,
         "tiled_only_chain_iterations_per_s": nc * (niter + 1) / dt_tiled}
     w = W.windkessel(P=256, T=50)
     spec2 = [(0, 0), (0, 0), (3, 1, 2.0, 0.03, 0.005, 0.0, inf), (4, 2, 2.0, 0.01, 2.0, 3.0),

@@ -593,10 +593,11 @@ pf_status pfb::build_plan(const std::vector<pf_filter*>& fl, Plan** out,
       br.classes[c].ntiles = int(cls_tiles[c].size());
       tm.insert(tm.end(), cls_tiles[c].begin(), cls_tiles[c].end());
     }
-    // a filter running alone whose FP64 tiles would leave SMs idle spreads
-    // each tile's propagation over several blocks (k_propagate_sub)
-    if (nf == 1)
-      for (PlanClass& pc : br.classes) pc.sub = propagate_sub(pc.kind, pc.N, pc.prec, pc.ntiles);
+    // a plan whose tiles (all of its tiled filters', which the branches run
+    // at once) would leave SMs idle spreads each FP64 tile's propagation over
+    // several blocks (k_propagate_sub)
+    for (PlanClass& pc : br.classes)
+      pc.sub = propagate_sub(pc.kind, pc.N, pc.prec, p->ntiles_all);
     counts(all_T, br.maxT, br.cnt_all);
     br.cnt_cls.resize(cls_tiles.size());
     for (size_t c = 0; c < cls_tiles.size(); ++c) counts(cls_T[c], br.maxT, br.cnt_cls[c]);

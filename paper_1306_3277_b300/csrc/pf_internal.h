@@ -18,10 +18,10 @@ cudaError_t launch_init(int kind, int N, int prec, const FilterDev* fds, const i
                         int nblocks, cudaStream_t st);
 cudaError_t launch_propagate(int kind, int N, int prec, const FilterDev* fds, const int2* tmap,
                              int nblocks, cudaStream_t st);
-// The sub-tile propagate launch (k_propagate_sub) for one filter's tiles:
-// propagate_sub gives the blocks per tile (1, 2 or 4) for a filter of ntiles
-// tiles of this class running alone; launch_propagate_sub launches with it
-// (sub = 1: launch_propagate).  Same results as launch_propagate.
+// The sub-tile propagate launch (k_propagate_sub): propagate_sub gives the
+// blocks per tile (1, 2 or 4) for tiles of this class in a plan of ntiles
+// tiles in all; launch_propagate_sub launches with it (sub = 1:
+// launch_propagate).  Same results as launch_propagate.
 int propagate_sub(int kind, int N, int prec, int ntiles);
 cudaError_t launch_propagate_sub(int kind, int N, int prec, int sub, const FilterDev* fds,
                                  const int2* tmap, int ntiles, cudaStream_t st);

@@ -2264,9 +2264,10 @@ cudaError_t launch_weight_exp(const double* d, double* w, int64_t n, cudaStream_
   return cudaGetLastError();
 }
 
-// Blocks per tile of the sub-tile propagate launch for a single filter of
-// `ntiles` tiles: 4 or 2 when the filter's state is FP64 and that many blocks
-// per tile still fit the GPU's resident blocks at once, else 1 (k_propagate).
+// Blocks per tile of the sub-tile propagate launch for FP64 tiles of a plan
+// of `ntiles` tiles in all: 4 or 2 when the state is FP64 and that many
+// blocks per tile still fit the GPU's resident blocks at once, else 1
+// (k_propagate).
 template <int KIND, int N, typename R>
 static int sub_for(int ntiles) {
   if constexpr (sizeof(R) != 8) {
@@ -2301,11 +2302,13 @@ static cudaError_t launch_sub(int sub, const FilterDev* fds, const int2* tmap, i
   return cudaGetLastError();
 }
 
-// The classes with a sub-tile propagate kernel: FP64 windkessel (both forms)
-// and FP64 Lorenz '96 (both forms) up to N = 12.
+// The classes with a sub-tile propagate kernel: FP64 Lorenz '96 (both forms)
+// up to N = 12, whose RK4 substeps and normals make a tile's FP64 work long.
+// The FP64 windkessel's step is too light: split, its tiles only lengthened
+// each step's chain of dependent phases.
 #define PF_SUB_CLASSES(X)                                                          \
-  X(KIND_WK, 1) X(KIND_WKX, 1) X(KIND_L96, 4) X(KIND_L96, 8) X(KIND_L96, 12)     \
-  X(KIND_L96W, 4) X(KIND_L96W, 8) X(KIND_L96W, 12)
+  X(KIND_L96, 4) X(KIND_L96, 8) X(KIND_L96, 12) X(KIND_L96W, 4) X(KIND_L96W, 8)   \
+  X(KIND_L96W, 12)
 
 int propagate_sub(int kind, int N, int prec, int ntiles) {
   if (prec != PREC_FP64) return 1;

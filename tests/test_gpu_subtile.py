@@ -1,8 +1,9 @@
-"""GPU tests of the sub-tile propagate launch.  A filter of FP64 state running
-alone, whose tiles would leave most SMs idle, propagates each 256-particle
-tile with 2 or 4 blocks; the last block of the tile gathers the tile's
-log-weights and runs its reductions in the canonical order.  Results must be
-the bits of the same filter inside a batch (which keeps one block per tile),
+"""GPU tests of the sub-tile propagate launch.  FP64 filters whose plan's tiles
+would leave most SMs idle (a filter running alone, a small batch) propagate
+each 256-particle tile with 2 or 4 blocks; the last block of the tile gathers
+the tile's log-weights and runs its reductions in the canonical order.
+Results must be the bits of the same filter inside a batch whose tiles fill
+the GPU (one block per tile),
 on both sides of the 4 / 2 / 1 block-per-tile thresholds, with ragged last
 tiles, for every model class that has the kernel, and the oracle's (ancestors
 and particles bit-exact away from the near-boundary window, log-likelihood
@@ -23,8 +24,8 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-# tile counts 12 (4 blocks per tile), 77 and 130 (2 blocks per tile for the
-# two-blocks-per-SM Lorenz '96 kernels, 4 for the windkessel's four), 330 (one)
+# tile counts 12 and 20 (4 blocks per tile), 77 and 130 (2 blocks per tile for
+# the two-blocks-per-SM FP64 Lorenz '96 kernels), 330 (one)
 CASES = [
     ("l96_8_P3000", lambda: W.lorenz96_8(P=3000, T=12)),
     ("l96_8_P19700", lambda: W.lorenz96_8(P=19700, T=8)),
@@ -34,9 +35,7 @@ CASES = [
     ("l96_12_P9000", lambda: W.lorenz96_8(P=9000, T=6).with_(N=12, obs_stride=2)),
     ("l96_sparse_P4000", lambda: W.lorenz96_sparse(P=4000, T=12)),
     ("l96_sde_P3000", lambda: W.lorenz96_sde(P=3000, T=10)),
-    ("wk_P5000", lambda: W.windkessel(P=5000, T=30)),
-    ("wk_P70000", lambda: W.windkessel(P=70000, T=6)),
-    ("wkx_P4000", lambda: W.windkessel_exact(P=4000, T=20)),
+    ("wk_P5000_unsplit", lambda: W.windkessel(P=5000, T=30)),  # no sub-tile kernel
 ]
 
 
@@ -55,12 +54,33 @@ def test_subtile_equals_batch_and_oracle(name, factory):
     g = run_gpu(w, seed)  # alone: the sub-tile launch where it applies
     o = run_oracle(w, seed)
     compare(w, g, o)
-    # the same filter in a batch with a second one keeps one block per tile
-    other = W.windkessel(P=300, T=5, seed=2)
+    # the same filter in a batch whose tiles fill the GPU keeps one block per tile
+    other = W.windkessel(P=1 << 18, T=3, seed=2, prec=W.MIXED)
     fs = [pf.pf_create(pf.model_from_workload(x), x.P, x.T, x.dt) for x in (w, other)]
     try:
         lls, sts = pf.pf_batch_run(fs, [w.theta, other.theta], [w.y, other.y], [seed, 2])
         assert int(sts[0]) == g["status"] and lls[0] == g["loglik"], (lls[0], g["loglik"])
+    finally:
+        for f in fs:
+            f.destroy()
+
+
+def test_small_fp64_batch_on_subtiles_equals_single_runs():
+    """A batch of few FP64 Lorenz '96 filters takes the sub-tile launch too
+    (beside windkessel filters, which keep one block per tile): every filter
+    gives the bits of its single run."""
+    import paper_1306_3277_b300 as pf
+    ws = [W.lorenz96_8(P=1024, T=9, seed=50 + k) for k in range(6)]
+    ws += [W.lorenz96_sde(P=512, T=7, seed=60 + k) for k in range(4)]
+    ws += [W.windkessel(P=256, T=12, seed=k + 1) for k in range(10)]
+    fs = [pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt) for w in ws]
+    try:
+        ref = [f.run(w.theta, w.y, w.seed)[:2] for w, f in zip(ws, fs)]
+        for branches in (1, 3):
+            pf.pf_batch_set_shape(fs, 0, branches, 8)
+            lls, sts = pf.pf_batch_run(fs, [w.theta for w in ws], [w.y for w in ws],
+                                       [w.seed for w in ws])
+            assert [(int(a), b) for a, b in zip(sts, lls)] == [(int(a), b) for a, b in ref]
     finally:
         for f in fs:
             f.destroy()
