@@ -262,9 +262,9 @@ pf_status pf_batch_get_shape(int32_t nfilt, pf_filter* const* f, pf_batch_shape*
  * candidate on the host clock, searching one field at a time from the
  * default: the cluster bound (0, 256, 512, 1024, 2048 particles), then the
  * number of branches (1, 2, 4, 8, 16), then the resample grid (2, 4, 8 blocks
- * per SM), then the persistent launch's CTAs per SM (0 = off, 1, 2, 3, 4) and,
- * when it is on, its tiles per item (1, 2, 4, 8).  It keeps the fastest shape
- * for the filter list (as
+ * per SM), then the persistent launch: off, or CTAs per SM (2, 3, 4) jointly
+ * with tiles per item (1, 2, 4).  It keeps the fastest shape for the filter
+ * list (as
  * pf_batch_set_shape would; pf_batch_get_shape reads it back) and returns its
  * cluster bound in *chosen (may be NULL).  The filters' results are those of
  * their last run, identical for every shape.  Errors: those of

@@ -492,8 +492,8 @@ def pf_batch_get_shape(filters):
 
 def pf_batch_autotune(filters, thetas, ys, seeds):
     """Time candidate launch shapes on these inputs (cluster bound, branches,
-    resample grid, persistent launch and its tiles per item, one field at a
-    time), keep the fastest for the list and
+    resample grid, one field at a time, then the persistent launch's CTAs per
+    SM with its tiles per item, jointly), keep the fastest for the list and
     return its cluster bound (pf_batch_get_shape gives the whole shape)."""
     nf = len(filters)
     hs = (_vp * nf)(*[f.h for f in filters])

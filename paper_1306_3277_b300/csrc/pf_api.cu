@@ -1259,25 +1259,45 @@ extern "C" pf_status pf_batch_autotune(int32_t nfilt, pf_filter* const* f,
   static const int64_t cta_bounds[] = {0, 256, 512, 1024, 2048};
   static const int32_t branch_counts[] = {1, 2, 4, 8, 16};
   static const int32_t rs_grids[] = {2, 4, 8};
-  static const int32_t persist_bps[] = {0, 1, 2, 3, 4};
-  static const int32_t tiles_items[] = {1, 2, 4, 8};
+  static const int32_t persist_bps[] = {2, 3, 4};
+  static const int32_t tiles_items[] = {1, 2, 4};
   pf_batch_shape best = kDefaultShape;
   double best_ms = 0.0;
   pf_status ps = time_shape(nfilt, f, theta, y, seeds, best, &best_ms);
   if (ps != PF_OK) return ps;
-  // one field at a time, from the default
-  for (int field = 0; field < 5; ++field) {
-    // tiles per item only matter for the persistent launch
-    if (field == 4 && best.persistent_blocks_per_sm == 0) break;
-    const int n = field <= 1 ? 5 : field == 2 ? 3 : field == 3 ? 5 : 4;
+  // one field at a time, from the default; the persistent launch's CTAs per
+  // SM and tiles per item jointly (its best shape needs both)
+  for (int field = 0; field < 4; ++field) {
     const pf_batch_shape base = best;
-    for (int c = 0; c < n; ++c) {
-      pf_batch_shape cand = base;
-      if (field == 0) cand.cta_max_particles = cta_bounds[c];
-      else if (field == 1) cand.branches = branch_counts[c];
-      else if (field == 2) cand.resample_blocks_per_sm = rs_grids[c];
-      else if (field == 3) cand.persistent_blocks_per_sm = persist_bps[c];
-      else cand.tiles_per_item = tiles_items[c];
+    std::vector<pf_batch_shape> cands;
+    pf_batch_shape c = base;
+    if (field == 0) {
+      for (int64_t b : cta_bounds) {
+        c.cta_max_particles = b;
+        cands.push_back(c);
+      }
+    } else if (field == 1) {
+      for (int32_t b : branch_counts) {
+        c.branches = b;
+        cands.push_back(c);
+      }
+    } else if (field == 2) {
+      for (int32_t g : rs_grids) {
+        c.resample_blocks_per_sm = g;
+        cands.push_back(c);
+      }
+    } else {
+      c.persistent_blocks_per_sm = 0;
+      c.tiles_per_item = 1;
+      cands.push_back(c);
+      for (int32_t b : persist_bps)
+        for (int32_t k : tiles_items) {
+          c.persistent_blocks_per_sm = b;
+          c.tiles_per_item = k;
+          cands.push_back(c);
+        }
+    }
+    for (const pf_batch_shape& cand : cands) {
       if (same_shape(cand, base)) continue;
       double ms = 0.0;
       ps = time_shape(nfilt, f, theta, y, seeds, cand, &ms);
