@@ -66,6 +66,31 @@ def test_persistent_launch_is_bit_identical(prec, bps, kt):
             f.destroy()
 
 
+@pytest.mark.parametrize("kt", [1, 2])
+def test_persistent_edge_sizes(kt):
+    """One-particle filters, exact and ragged tiles, one- to three-step runs,
+    in both model classes and the queue's two forms (whole run on one CTA,
+    queued items): every filter gives its single run's bits."""
+    import paper_1306_3277_b300 as pf
+    ws = []
+    for k, (P, T) in enumerate([(1, 1), (1, 3), (2, 2), (255, 1), (256, 2), (257, 3), (513, 2),
+                                (769, 3), (1, 2), (300, 1)]):
+        if k % 2:
+            ws.append(W.lorenz96_8(P=P, T=T, prec=W.MIXED, seed=k + 1))
+        else:
+            ws.append(W.windkessel(P=P, T=T, prec=W.MIXED, seed=k + 1))
+    fs = [pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt) for w in ws]
+    try:
+        ref = [f.run(w.theta, w.y, w.seed)[:2] for w, f in zip(ws, fs)]
+        pf.pf_batch_set_shape(fs, 0, 1, 8, 3, kt)
+        for _ in range(2):
+            lls, sts = _run_batch(pf, fs, ws)
+            assert [(int(a), b) for a, b in zip(sts, lls)] == [(int(a), b) for a, b in ref]
+    finally:
+        for f in fs:
+            f.destroy()
+
+
 @pytest.mark.parametrize("kt", [1, 4])
 def test_persistent_degenerate_filters_end_early(kt):
     """Zero observation variance makes every weight zero at the first step: the

@@ -35,6 +35,8 @@ CASES = [
     ("l96_12_P9000", lambda: W.lorenz96_8(P=9000, T=6).with_(N=12, obs_stride=2)),
     ("l96_sparse_P4000", lambda: W.lorenz96_sparse(P=4000, T=12)),
     ("l96_sde_P3000", lambda: W.lorenz96_sde(P=3000, T=10)),
+    ("l96_8_P2305_one_in_last", lambda: W.lorenz96_8(P=2305, T=6)),  # empty sub-blocks
+    ("l96_8_P2433", lambda: W.lorenz96_8(P=2433, T=5)),  # 129 particles in the last tile
     ("wk_P5000_unsplit", lambda: W.windkessel(P=5000, T=30)),  # no sub-tile kernel
 ]
 
