@@ -1152,8 +1152,8 @@ __device__ __forceinline__ int mn_below(const FilterDev& fd, double e, int lo, i
 // FP64 (one fma per particle; ceilings and floors are taken on the bits).
 //
 // Barriers: two per chunk of tiles (after their ranges and scaled bases are
-// prepared, after the counts), one vote per resampled tile for very long
-// offspring ranges, one at the end of the chunk.  A particle's predecessor
+// prepared, after the counts), one vote per chunk for very long offspring
+// ranges (written by the whole block after it), one at the end of the chunk.  A particle's predecessor
 // count comes from the neighbouring lane (lane 0's from the running maximum
 // of the earlier warps' last counts, through shared memory); ranges up to
 // SHORT_RANGE are written by the particle's thread, up
@@ -1210,10 +1210,12 @@ __device__ __forceinline__ int particle_count(const FilterDev& fd, int i, int rs
 }
 
 // Particle j of tile t takes the targets [prev, n) as ancestor: written by its
-// thread, its warp or, for ranges longer than BLOCK_RANGE after a block vote,
-// the whole block.  Every thread of the block calls it (one barrier).
-__device__ __forceinline__ void write_offspring(const FilterDev& fd, int t, int i, int prev, int n,
-                                               bool valid, int* nlong, int3* longr) {
+// thread or its warp; a range longer than BLOCK_RANGE is only listed in
+// longr (returns true), for the whole block to write after a block vote.
+// Every thread of the warp calls it; no block barrier.
+__device__ __forceinline__ bool write_offspring_local(const FilterDev& fd, int t, int i, int prev,
+                                                      int n, bool valid, int* nlong,
+                                                      int3* longr) {
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int j0 = t * TILE;
@@ -1233,7 +1235,16 @@ __device__ __forceinline__ void write_offspring(const FilterDev& fd, int t, int 
     for (int jj = a + lane; jj < b; jj += 32) aout[jj] = who;
   }
   if (len > BLOCK_RANGE) longr[atomicAdd(nlong, 1)] = make_int3(prev, n, j);
-  if (__syncthreads_or(len > BLOCK_RANGE)) write_long_ranges(aout, *nlong, longr);
+  return len > BLOCK_RANGE;
+}
+
+// write_offspring_local, then the tile's long ranges written by the whole
+// block after a block vote.  Every thread of the block calls it (one barrier).
+__device__ __forceinline__ void write_offspring(const FilterDev& fd, int t, int i, int prev, int n,
+                                               bool valid, int* nlong, int3* longr) {
+  const bool lng = write_offspring_local(fd, t, i, prev, n, valid, nlong, longr);
+  if (__syncthreads_or(lng)) write_long_ranges(fd.anc + (fd.hist ? int64_t(i) * fd.P : 0), *nlong,
+                                               longr);
 }
 
 // The running maximum of a count over the lanes of a warp.  The canonical
@@ -1308,16 +1319,17 @@ struct RsChunk {
   int nlong[RS_CHUNK];
   double M[RS_CHUNK], e0[RS_CHUNK], sr[RS_CHUNK];
   int nlast[RS_CHUNK][WARPS];
-  int3 longr[2][TILE];
+  int3 longr[RS_CHUNK][TILE];  // each tile's offspring ranges longer than BLOCK_RANGE
 };
 
 // The chunk of the nq <= RS_CHUNK tiles tile_of(0..nq-1) (filter, tile),
-// resampled or carried as described above; it counts the resampled tiles in
-// it (its parity picks the long-range list).  Every thread of the block calls
-// it; it ends with a block barrier.
+// resampled or carried as described above.  The tiles' ranges longer than
+// BLOCK_RANGE are listed while their short and warp-length ranges are
+// written, then written by the whole block after one vote for the chunk.
+// Every thread of the block calls it; it ends with a block barrier.
 template <typename TileOf>
 __device__ __forceinline__ void resample_chunk(const FilterDev* __restrict__ fds, TileOf tile_of,
-                                               int nq, RsChunk& c, int& it) {
+                                               int nq, RsChunk& c) {
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int w = tid >> 5;
@@ -1380,6 +1392,7 @@ __device__ __forceinline__ void resample_chunk(const FilterDev* __restrict__ fds
     }
   }
   __syncthreads();
+  bool lng = false;
 #pragma unroll
   for (int m = 0; m < RS_CHUNK; ++m) {
     if (m < nq) {
@@ -1393,10 +1406,20 @@ __device__ __forceinline__ void resample_chunk(const FilterDev* __restrict__ fds
         int prev = __shfl_up_sync(0xffffffffu, nn[m], 1);
         if (lane == 0) prev = run;
         const bool valid = tid < min(TILE, fd.P - ft.y * TILE);
-        write_offspring(fd, ft.y, c.i[m], prev, nn[m], valid, &c.nlong[m], c.longr[it & 1]);
-        ++it;
+        lng |= write_offspring_local(fd, ft.y, c.i[m], prev, nn[m], valid, &c.nlong[m],
+                                     c.longr[m]);
       } else if (c.go[m]) {
         carry_tile(fd, ft.y, c.i[m], c.M[m]);
+      }
+    }
+  }
+  if (__syncthreads_or(lng)) {
+#pragma unroll
+    for (int m = 0; m < RS_CHUNK; ++m) {
+      if (m < nq && c.nlong[m] > 0) {
+        const FilterDev& fd = fds[c.ft[m].x];
+        write_long_ranges(fd.anc + (fd.hist ? int64_t(c.i[m]) * fd.P : 0), c.nlong[m],
+                          c.longr[m]);
       }
     }
   }
@@ -1408,10 +1431,9 @@ __global__ void __launch_bounds__(TILE, RESAMPLE_BLOCKS_PER_SM)
   __shared__ RsChunk c;
   const int G = gridDim.x;
   wait_prior_grid();
-  int it = 0;  // resampled tiles so far: its parity picks the long-range list
   for (int q0 = blockIdx.x; q0 < ntiles; q0 += RS_CHUNK * G) {
     const int nq = min(RS_CHUNK, (ntiles - q0 + G - 1) / G);  // q0 + m G < ntiles for m < nq
-    resample_chunk(fds, [&](int m) { return tmap[q0 + m * G]; }, nq, c, it);
+    resample_chunk(fds, [&](int m) { return tmap[q0 + m * G]; }, nq, c);
   }
 }
 
@@ -1786,10 +1808,9 @@ __device__ void persist_resample(const FilterDev* __restrict__ fds, int k, int q
   const bool whole = fd.ntiles <= kt;
   const int t0 = whole ? 0 : qi * RS_CHUNK;
   const int t1 = whole ? fd.ntiles : min(t0 + RS_CHUNK, fd.ntiles);
-  int it = 0;
   for (int c0 = t0; c0 < t1; c0 += RS_CHUNK)
     resample_chunk(fds, [&](int m) { return make_int2(k, c0 + m); }, min(RS_CHUNK, t1 - c0),
-                   sh.rc, it);
+                   sh.rc);
   // resample_chunk ended with the block's barrier: the tiles' ancestors (or
   // carried weights) are written before the ticket
   if (tid == 0) {
