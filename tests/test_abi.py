@@ -48,6 +48,19 @@ def test_shape_queries_without_a_device():
     assert pf.pf_device_bytes(pf.model(pf.PF_LORENZ96, N=7), 100, 10) == 0
 
 
+def test_persistent_diagnostics_validate_without_a_device():
+    """The persistent launch's test hooks refuse bad arguments on the host,
+    before any CUDA call."""
+    import paper_1306_3277_b300 as pf
+    for bad in (0.0, -1.0, 60.5):
+        with pytest.raises(pf.PFError) as e:
+            pf.pf_debug_persist_wait_limit(bad)
+        assert e.value.status == pf.PF_EINVAL
+    assert pf.lib().pf_debug_persist_unfilled_slot(2) == pf.PF_EINVAL
+    assert pf.lib().pf_debug_persist_unfilled_slot(-1) == pf.PF_EINVAL
+    pf.pf_debug_persist_unfilled_slot(False)  # host-only: accepted without a device
+
+
 def test_no_cpu_fallback_without_gpu():
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
