@@ -661,7 +661,7 @@ def run_samplers(args):
     _, _, acc = pf.pf_pmmh_run(fs, w.y, spec, th0, niter, 2)
     dt = time.perf_counter() - t0
     shape = pf.pf_batch_get_shape(fs)
-    pf.pf_batch_set_shape(fs, 0, 1, 8, 0, 1)  # the same chains in the default tiled shape
+    pf.pf_batch_set_shape(fs, 0, 1, 8, 0, 1)  # the same chains on one tiled launch chain
     pf.pf_pmmh_run(fs, w.y, spec, th0, 5, 1)
     t0 = time.perf_counter()
     pf.pf_pmmh_run(fs, w.y, spec, th0, niter, 2)

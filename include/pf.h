@@ -250,7 +250,7 @@ typedef struct {
 
 /* Set / read the launch shape used for this exact filter list (as
  * pf_batch_configure: host-only; a cached plan is rebuilt on its next use).
- * The default shape is {0, 1, 8, 0, 1}.  PF_EINVAL for a bad list (as
+ * The default shape is {0, 4, 8, 0, 1}.  PF_EINVAL for a bad list (as
  * pf_batch_configure), a NULL shape, cta_max_particles < 0, branches < 1,
  * resample_blocks_per_sm or persistent_blocks_per_sm outside 1..8 and 0..8,
  * or tiles_per_item not 1, 2, 4 or 8. */

@@ -471,7 +471,7 @@ def pf_batch_configure(filters, cta_max_particles):
     _check(lib().pf_batch_configure(nf, hs, int(cta_max_particles)))
 
 
-def pf_batch_set_shape(filters, cta_max_particles=0, branches=1, resample_blocks_per_sm=8,
+def pf_batch_set_shape(filters, cta_max_particles=0, branches=4, resample_blocks_per_sm=8,
                        persistent_blocks_per_sm=0, tiles_per_item=1):
     """Set the launch shape used for this filter list (results do not change)."""
     nf = len(filters)

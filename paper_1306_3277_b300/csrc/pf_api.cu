@@ -288,7 +288,10 @@ extern "C" pf_status pf_create(const pf_model* m, int64_t P, int32_t T, double d
 static std::mutex g_plan_mu;
 static std::map<std::vector<pf_filter*>, Plan*> g_plans;  // cached batch plans
 // per filter list: its launch shape (cluster bound, branches, resample grid)
-static const pf_batch_shape kDefaultShape = {0, 1, 8, 0, 1};
+// four launch chains: a batch that is not autotuned keeps the SMs busier than
+// with one chain (the 256-filter benchmark batch 36.9 against 44.2 ms), and a
+// single filter is one chain anyway
+static const pf_batch_shape kDefaultShape = {0, 4, 8, 0, 1};
 static std::map<std::vector<pf_filter*>, pf_batch_shape> g_shapes;
 
 static void destroy_plan(Plan* p) {
