@@ -379,11 +379,15 @@ def secondary(pf, torch, dev):
             small[name + "_ms_per_run"] = (time.perf_counter() - t0) / 20 * 1e3
         f.destroy()
         out["small_filter_" + w.name] = small
-    # serving: a compact sweep (5 s of Poisson arrivals per rate, at most 5 s
-    # more to drain), beside the same request mix one pf_run at a time
+    # serving: the rate sweep up to the stated 2000 requests/s (10 s of Poisson
+    # arrivals per rate, so 20,000 requests at the top rate, then at most 5 s
+    # more to drain; an overloaded rate reports its unfinished requests),
+    # beside the same request mix one pf_run at a time
     fp32_peak = pf.pf_measure_fma_peak(pf.PF_MIXED)
-    serving = {"rates": [serve_at_rate(pf, rate, 5.0, 5.0, 64 << 30, 128, fp32_peak,
-                                       SERVER_BRANCHES) for rate in (250.0, 1000.0)]}
+    serving = {"arrivals_s": 10.0, "drain_s": 5.0,
+               "rates": [serve_at_rate(pf, rate, 10.0, 5.0, 64 << 30, 128, fp32_peak,
+                                       SERVER_BRANCHES)
+                         for rate in (250.0, 500.0, 1000.0, 1500.0, 2000.0)]}
     reqs = W.serving_requests(40, 100.0, seed=7)
     fs = [(pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt), w) for _, w in reqs]
     for f, w in fs[:3]:
