@@ -2289,19 +2289,27 @@ cudaError_t launch_weight_exp(const double* d, double* w, int64_t n, cudaStream_
 // of `ntiles` tiles in all: 4 or 2 when the state is FP64 and that many
 // blocks per tile still fit the GPU's resident blocks at once, else 1
 // (k_propagate).
+// The current device's SM count, queried once per process (a function-local
+// static: its initialisation is thread-safe, so host threads launching at
+// the same time see one value).
+static int device_sms() {
+  static const int sms = [] {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    return cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0
+               ? n
+               : 148;
+  }();
+  return sms;
+}
+
 template <int KIND, int N, typename R>
 static int sub_for(int ntiles) {
   if constexpr (sizeof(R) != 8) {
     return 1;
   } else {
-    static int sms = 0;
-    if (sms == 0) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        sms = 148;
-    }
-    const long long slots = static_cast<long long>(sms) * PropagateOccupancy<KIND, N, R>::value;
+    const long long slots =
+        static_cast<long long>(device_sms()) * PropagateOccupancy<KIND, N, R>::value;
     if (4ll * ntiles <= slots) return 4;
     if (2ll * ntiles <= slots) return 2;
     return 1;
@@ -2371,13 +2379,7 @@ cudaError_t launch_filter_cluster(int kind, int N, int prec, const FilterDev* fd
 cudaError_t launch_resample(const FilterDev* fds, const int2* tmap, int nblocks,
                             cudaStream_t st, int blocks_per_sm) {
   if (nblocks <= 0) return cudaSuccess;
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 148;
-  }
+  const int sms = device_sms();
   const int bps = std::min(std::max(blocks_per_sm, 1), RESAMPLE_BLOCKS_PER_SM);
   const int grid = std::min(nblocks, sms * bps);
   const cudaError_t e = launch_chained(k_resample, unsigned(grid), st, fds, tmap, nblocks);
@@ -2411,16 +2413,14 @@ template <int SET, int MINB>
 static cudaError_t launch_persist_occ(const FilterDev* fds, PersistQueue* q,
                                       unsigned long long* slots, int kt, int blocks_per_sm,
                                       cudaStream_t st) {
-  static int sms = 0, occ = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 148;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_persist<SET, MINB>, TILE, 0) !=
-            cudaSuccess ||
-        occ < 1)
-      occ = 1;
-  }
+  const int sms = device_sms();
+  static const int occ = [] {  // resident CTAs per SM, once per instantiation (thread-safe)
+    int o = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_persist<SET, MINB>, TILE, 0) ==
+                       cudaSuccess && o >= 1
+               ? o
+               : 1;
+  }();
   const int bps = std::min(std::max(blocks_per_sm, 1), occ);
   k_persist<SET, MINB><<<sms * bps, TILE, 0, st>>>(fds, q, slots, kt);
   return cudaGetLastError();
@@ -2475,13 +2475,7 @@ cudaError_t launch_mn_scan(const FilterDev* fds, const int2* tmap, int ntiles, i
 cudaError_t launch_noise(const FilterDev* fds, int k, int first, int last, int P, int s,
                          cudaStream_t st) {
   if (last < first) return cudaSuccess;
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 148;
-  }
+  const int sms = device_sms();
   const int64_t n = int64_t(last - first + 1) * ((s + 1) / 2) * P;
   const int64_t nb = (n + 255) / 256;
   k_noise_wk64<<<unsigned(std::min<int64_t>(nb, int64_t(sms) * 8)), 256, 0, st>>>(fds, k, first,
