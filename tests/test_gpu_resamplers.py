@@ -69,11 +69,16 @@ def test_batch_mixing_schemes_equals_single_runs():
             ws.append(base.with_(resampler=rs, seed=10 * k + rs + 1))
     fs = [pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt) for w in ws]
     try:
-        lls, sts = pf.pf_batch_run(fs, [w.theta for w in ws], [w.y for w in ws],
-                                   [w.seed for w in ws])
-        for k, (w, f) in enumerate(zip(ws, fs)):
-            st, ll, _, _ = f.run(w.theta, w.y, w.seed)
-            assert sts[k] == st and lls[k] == ll, (k, w.resampler)
+        ref = [f.run(w.theta, w.y, w.seed)[:2] for w, f in zip(ws, fs)]
+        # the default shape, one launch chain, the cluster path for the small
+        # filters (multinomial ones stay tiled), the persistent launch
+        for shape in (None, (0, 1, 8, 0, 1), (4096, 2, 4, 0, 1), (0, 1, 8, 4, 2)):
+            if shape is not None:
+                pf.pf_batch_set_shape(fs, *shape)
+            lls, sts = pf.pf_batch_run(fs, [w.theta for w in ws], [w.y for w in ws],
+                                       [w.seed for w in ws])
+            for k, (st, ll) in enumerate(ref):
+                assert sts[k] == st and lls[k] == ll, (k, ws[k].resampler, shape)
     finally:
         for f in fs:
             f.destroy()

@@ -120,13 +120,20 @@ def test_exact_variants_in_batch_and_server():
           W.lorenz96_8(P=500, T=15, prec=W.MIXED)]
     fs = [pf.pf_create(pf.model_from_workload(w), w.P, w.T, w.dt) for w in ws]
     try:
-        lls, sts = pf.pf_batch_run(fs, [w.theta for w in ws], [w.y for w in ws],
-                                   [w.seed for w in ws])
-        ref = []
-        for k, (w, f) in enumerate(zip(ws, fs)):
+        ref, singles = [], []
+        for w, f in zip(ws, fs):
             st, ll, _, _ = f.run(w.theta, w.y, w.seed)
-            assert sts[k] == st and lls[k] == ll
+            singles.append((st, ll))
             ref.append(ll)
+        # the default shape, one launch chain, the cluster path, the persistent
+        # launch (whose classes these variants are not: they take launch chains)
+        for shape in (None, (0, 1, 8, 0, 1), (4096, 2, 4, 0, 1), (0, 1, 8, 4, 2)):
+            if shape is not None:
+                pf.pf_batch_set_shape(fs, *shape)
+            lls, sts = pf.pf_batch_run(fs, [w.theta for w in ws], [w.y for w in ws],
+                                       [w.seed for w in ws])
+            for k, (st, ll) in enumerate(singles):
+                assert sts[k] == st and lls[k] == ll, (k, shape)
     finally:
         for f in fs:
             f.destroy()
