@@ -27,7 +27,11 @@
  * the integrator and the process noise in FP32 and the observation
  * log-weights, log-sum-exp, cumulative-weight scan and likelihood in FP64.
  * In both, the weight exponential exp(ell - M) is evaluated on the FP32 unit
- * in double-float arithmetic to about 2^-52 relative (pf_weight_exp).
+ * in double-float arithmetic to about 2^-52 relative (pf_weight_exp).  A
+ * tile's cumulative weights are, for the windkessel and Lorenz '96 with
+ * N <= 12, exact sums in 2^-55 fixed point, each rounded once to FP64
+ * (pf_weight_prefix), and for Lorenz '96 with N >= 16 sums in a fixed tree of
+ * FP64 additions (a few ulp).
  *
  * Random numbers: Philox4x32-10 keyed by the 64-bit seed, counter
  * (particle, step, purpose << 16 | block, 0), Box-Muller normals.  A run is a
@@ -485,6 +489,22 @@ pf_status pf_measure_fma_peak(int32_t prec, double* flops_per_s, double* ms);
  * n < 0, n > 2^28 or a NULL array with n > 0; PF_ECUDA on a CUDA error. */
 pf_status pf_weight_exp(const double* d, double* w, int64_t n);
 
+/* The propagate kernels' in-tile cumulative weights (Algorithm 2's resampling
+ * needs the prefix sums of the weights, Sec. 3.3), evaluated on the device
+ * for given weights: per tile of 256 consecutive weights, prefix[j] = the sum
+ * of the tile's weights up to j and totals[t] = the tile's sum, as the
+ * windkessel and Lorenz '96 N <= 12 kernels compute them: each weight rounded
+ * to an integer multiple of 2^-55 (nearest, ties to even), those summed
+ * exactly in 64-bit integers, each sum rounded once to the nearest double;
+ * this lets a test compare them with exact rational sums.
+ * w, prefix: HOST arrays of n doubles; totals: HOST array of ceil(n / 256)
+ * doubles; all owned by the caller and not overlapping; n = 0 does nothing.
+ * Synchronous, on the current device; allocates device memory for the call.
+ * PF_EINVAL for n < 0, n > 2^28, a NULL array with n > 0 or a weight outside
+ * [0, 1] (the kernels' weights are exp(ell - M_tile) <= 1); PF_ECUDA on a
+ * CUDA error. */
+pf_status pf_weight_prefix(const double* w, double* prefix, double* totals, int64_t n);
+
 /* The step combine's logarithm of the weight sum (Algorithm 2, likelihood
  * line: log Z_i = M + log S - log P with S = sum_j e^(ell_j - M) >= 1),
  * evaluated on the device for n given arguments: y[i] = log s[i].  A
@@ -535,8 +555,10 @@ pf_status pf_debug_persist_unfilled_slot(int32_t on);
  *   counts[0]  ancestors read outside [0, P) (replaced by the particle's own
  *              index, so every access stays in bounds)
  *   counts[1]  particles whose propagated state is not finite
- *   counts[2]  in-tile cumulative weights that are negative, NaN or decrease
- *              by more than 2^-49 relative (a scan's rounding stays below it)
+ *   counts[2]  in-tile cumulative weights that are negative or NaN, weights
+ *              above 1, and in-tile cumulative weights that decrease (at all
+ *              for the exact fixed-point sums, by more than 2^-49 relative for
+ *              the FP64 tree, whose rounding stays below it)
  *   counts[3]  offspring ranges that end before they start or leave [0, P]
  * counts: host array of 4, owned by the caller, receives the counts since the
  * last call (then zeroed); *checked (may be NULL) receives 1 in a checked

@@ -84,6 +84,7 @@ def lib():
         L.pf_measure_fma_peak.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]
         L.pf_weight_exp.argtypes = [_vp, _vp, ctypes.c_int64]
+        L.pf_weight_prefix.argtypes = [_vp, _vp, _vp, ctypes.c_int64]
         L.pf_weight_sum_log.argtypes = [_vp, _vp, ctypes.c_int64]
         L.pf_debug_fail_allocation.argtypes = [ctypes.c_int32]
         L.pf_debug_fail_server_wait.argtypes = [ctypes.c_int32]
@@ -118,7 +119,8 @@ def lib():
                                     _vp, _vp, _vp]
         for name in ("pf_run", "pf_wait", "pf_destroy", "pf_create", "pf_batch_run",
                      "pf_profile_enable", "pf_profile_read", "pf_measure_fma_peak",
-                     "pf_run_range", "pf_sample_path", "pf_weight_exp", "pf_weight_sum_log",
+                     "pf_run_range", "pf_sample_path", "pf_weight_exp", "pf_weight_prefix",
+                     "pf_weight_sum_log",
                      "pf_debug_step",
                      "pf_debug_fail_allocation", "pf_debug_fail_server_wait",
                      "pf_debug_persist_wait_limit", "pf_debug_persist_unfilled_slot",
@@ -461,6 +463,16 @@ def pf_weight_exp(d):
     w = np.empty_like(d)
     _check(lib().pf_weight_exp(d.ctypes.data, w.ctypes.data, d.size))
     return w
+
+
+def pf_weight_prefix(w):
+    """The propagate kernels' in-tile cumulative weights of the given weights
+    in [0, 1], per tile of 256 (diagnostic): returns (prefix, totals)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    prefix = np.empty_like(w)
+    totals = np.empty((w.size + 255) // 256, dtype=np.float64)
+    _check(lib().pf_weight_prefix(w.ctypes.data, prefix.ctypes.data, totals.ctypes.data, w.size))
+    return prefix, totals
 
 
 def pf_batch_configure(filters, cta_max_particles):

@@ -395,6 +395,7 @@ __device__ __forceinline__ double dunkey(long long k) {
 // Scratch for the canonical block operations (TILE threads).
 struct BlockScratch {
   long long kmax[WARPS];
+  unsigned long long usum[WARPS];  // block_scan_fixed: the warps' totals
   double wsum[WARPS];
   double wsum2[WARPS];
   double wpre[WARPS];
@@ -460,6 +461,85 @@ __device__ __forceinline__ double block_scan(double v, BlockScratch& sm, double*
   __syncthreads();
   *total = sm.wtot;
   return w == 0 ? v : __dadd_rn(sm.wpre[w], v);
+}
+
+// ---------------------------------------------------------------------------
+// The in-tile cumulative weights, exactly.  A weight w = exp(ell - M_t) lies
+// in [0, 1], so w 2^55 rounded to an integer (weight_fixed) and the sum of a
+// tile's 256 of them (at most 2^63) are exact unsigned 64-bit integers: the
+// scan (block_scan_fixed) has no rounding and no order, and each prefix is
+// rounded once to the nearest double (fixed_double).  The resolution, 2^-55
+// of the tile's largest weight, is finer than a double's at the tile total
+// (>= 1); all of it is integer work, none on the FP64 unit (B300: 1/64 of the
+// FP32 rate).
+// ---------------------------------------------------------------------------
+// round(w 2^55) for 0 <= w <= 1, read off the IEEE-754 fields: w = m 2^(e-52)
+// with the 53-bit significand m (no hidden bit for a subnormal), so
+// w 2^55 = m 2^(e+3): a left shift of at most 3 (w <= 1), or a right shift
+// rounded to nearest, ties to even.
+__device__ __forceinline__ unsigned long long weight_fixed(double w) {
+  const unsigned long long b =
+      static_cast<unsigned long long>(__double_as_longlong(w)) & 0x7fffffffffffffffull;  // -0: 0
+  const int E = int(b >> 52);  // biased exponent
+  const unsigned long long m = (b & 0x000fffffffffffffull) | (E ? 0x0010000000000000ull : 0ull);
+  const int sh = (E ? E : 1) - 1023 + 3;
+  if (sh >= 0) return m << sh;
+  const int r = -sh;
+  if (r > 54) return 0ull;  // m 2^-r < 1/2
+  const unsigned long long q = m >> r;
+  const unsigned long long rem = m & ((1ull << r) - 1ull);
+  const unsigned long long half = 1ull << (r - 1);
+  return q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+}
+
+// p 2^-55 rounded to the nearest double (ties to even), for p < 2^64: the
+// leading bit of p sets the exponent; the result is 0 or a normal number.
+__device__ __forceinline__ double fixed_double(unsigned long long p) {
+  if (p == 0ull) return 0.0;
+  const int top = 63 - __clzll(static_cast<long long>(p));  // leading bit of p
+  int e = top - 55;  // unbiased exponent of p 2^-55
+  unsigned long long m;
+  if (top <= 52) {
+    m = p << (52 - top);
+  } else {
+    const int r = top - 52;
+    const unsigned long long q = p >> r;
+    const unsigned long long rem = p & ((1ull << r) - 1ull);
+    const unsigned long long half = 1ull << (r - 1);
+    m = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+    if (m == (1ull << 53)) {
+      m >>= 1;
+      e += 1;
+    }
+  }
+  return __longlong_as_double(static_cast<long long>(
+      (static_cast<unsigned long long>(e + 1023) << 52) | (m & 0x000fffffffffffffull)));
+}
+
+// Inclusive scan of v over the block, exact in unsigned 64-bit integers: a
+// shuffle scan in each warp, then every thread adds the totals of the warps
+// before its own (one barrier).  total receives the block's sum.
+__device__ __forceinline__ unsigned long long block_scan_fixed(unsigned long long v,
+                                                               BlockScratch& sm,
+                                                               unsigned long long* total) {
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  if (lane == 31) sm.usum[w] = v;
+  __syncthreads();
+  unsigned long long before = 0ull, all = 0ull;
+#pragma unroll
+  for (int q = 0; q < WARPS; ++q) {
+    const unsigned long long t = sm.usum[q];
+    if (q < w) before += t;
+    all += t;
+  }
+  *total = all;
+  return v + before;
 }
 
 // Warp-level forms of the three canonical reductions for inputs held by the

@@ -11,6 +11,8 @@ namespace pfb {
 cudaError_t read_checks(unsigned long long* out);
 // The propagate kernels' weight exponential on n device values (diagnostic).
 cudaError_t launch_weight_exp(const double* d, double* w, int64_t n, cudaStream_t st);
+cudaError_t launch_tile_prefix(const double* w, double* prefix, double* total, int64_t n,
+                               cudaStream_t st);
 cudaError_t launch_log_sum(const double* s, double* y, int64_t n, cudaStream_t st);
 
 bool supported(int kind, int N, int prec);

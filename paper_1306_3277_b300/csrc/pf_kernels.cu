@@ -9,7 +9,9 @@
 //                y(t_i) in FP64 (skipped at a step without an observation),
 //                then per tile the max, the inclusive prefix of
 //                exp(ell - M_tile) (exp_weight: double-float on the FP32
-//                unit) and its total.  The last tile of each
+//                unit; for the small states the prefix is an exact
+//                fixed-point integer scan rounded once to FP64) and its
+//                total.  The last tile of each
 //                group of GROUP tiles combines the group; the last group
 //                combines the filter: max, scaled sums, likelihood increment,
 //                ESS test, resampling uniform.
@@ -287,6 +289,16 @@ __device__ __forceinline__ double combine_log(double s) {
 }
 template <int KIND, int N>
 struct OwnCombineMath {
+  static constexpr bool value = !(l96_kind(KIND) && N >= 16);
+};
+// The in-tile cumulative weights of a model class: the exact fixed-point scan
+// (block_scan_fixed) for the small states, whose kernels are bound by the FP64
+// unit; the canonical FP64 scan (block_scan) for Lorenz '96 with N >= 16,
+// bound by FP32 issue, where the scan's integer work measured slower.  Every
+// launch form of a class takes the same one, so its results do not depend on
+// the form.
+template <int KIND, int N>
+struct FixedPrefix {
   static constexpr bool value = !(l96_kind(KIND) && N >= 16);
 };
 
@@ -893,22 +905,33 @@ __device__ __forceinline__ double propagate_ell(const FilterDev& fd, int i, int 
   return ell;
 }
 
+template <bool FIXED>
 __device__ __forceinline__ void tile_epilogue(const FilterDev& fd, int t, int j, double ell,
                                               CombineScratch& cs, TileTriples* tri = nullptr,
                                               int ncopies = 0) {
   const int P = fd.P;
   const int tid = threadIdx.x;
-  // tile partials: max, inclusive prefix of exp(ell - M_t), total
+  // tile partials: max, inclusive prefix of exp(ell - M_t) (FIXED: exact sums
+  // of the weights in 2^-55 fixed point, each rounded once to a double), total
   const double Mt = block_max(ell, cs.b);
   const double w = (Mt == -INFINITY) ? 0.0 : exp_weight(ell - Mt);
-  double St;
-  const double c = block_scan(w, cs.b, &St);
+  double c, St;
+  if constexpr (FIXED) {
+    unsigned long long Ft;
+    c = fixed_double(block_scan_fixed(weight_fixed(w), cs.b, &Ft));
+    St = fixed_double(Ft);
+  } else {
+    c = block_scan(w, cs.b, &St);
+  }
   if constexpr (PF_CHECKED) {
-    // neighbouring prefixes come from different addition trees, so they may
-    // differ by rounding (at most about ten ulp: five levels of sums of
-    // non-negative terms each); a larger decrease is a violation
+    // FIXED: the prefixes are non-decreasing by construction (an exact integer
+    // scan, rounded monotonically).  Otherwise neighbouring prefixes come from
+    // different addition trees and may differ by rounding (at most about ten
+    // ulp: five levels of sums of non-negative terms).  A weight above 1 or a
+    // larger decrease is a violation.
     const double before = __shfl_up_sync(0xffffffffu, c, 1);
-    if (j < P && (!(c >= 0.0) || ((tid & 31) > 0 && c < before * (1.0 - 0x1p-49))))
+    const double floor_ = FIXED ? before : before * (1.0 - 0x1p-49);
+    if (j < P && (!(c >= 0.0) || !(w <= 1.0) || ((tid & 31) > 0 && c < floor_)))
       check_failed(CHK_PREFIX);
   }
   if (j < P) fd.ctil[j] = c;
@@ -936,7 +959,7 @@ __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i
   const int j = t * TILE + int(threadIdx.x);
   const double ell =
       propagate_ell<KIND, N, R>(fd, i, j, j < fd.P, anc_identity, lam_zero, cw, a_spec, ys);
-  tile_epilogue(fd, t, j, ell, cs, tri, ncopies);
+  tile_epilogue<FixedPrefix<KIND, N>::value>(fd, t, j, ell, cs, tri, ncopies);
 }
 
 // The step kernels are launched with programmatic stream serialization: the
@@ -1048,7 +1071,8 @@ __global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value))
   __threadfence();
   if (tid == 0) fd.tp[t].ticket = 0u;  // for the next step (ordered by the launch boundary)
   const int jt = t * TILE + tid;
-  tile_epilogue(fd, t, jt, jt < P ? ldcg(&fd.ctil[jt]) : -INFINITY, cs);
+  tile_epilogue<FixedPrefix<KIND, N>::value>(fd, t, jt, jt < P ? ldcg(&fd.ctil[jt]) : -INFINITY,
+                                              cs);
   if (tid == 0) {
     __threadfence();
     const int g = t / GROUP;
@@ -2278,6 +2302,29 @@ cudaError_t launch_log_sum(const double* s, double* y, int64_t n, cudaStream_t s
   return cudaGetLastError();
 }
 
+// The propagate kernels' in-tile prefix of given weights (tile_epilogue's
+// weight_fixed / block_scan_fixed / fixed_double), one block per tile of
+// TILE weights (past n: 0): prefix[j] for every j < n, total[t] per tile.
+__global__ void __launch_bounds__(TILE) k_tile_prefix(const double* __restrict__ w,
+                                                      double* __restrict__ prefix,
+                                                      double* __restrict__ total, int64_t n) {
+  __shared__ BlockScratch b;
+  const int64_t j = int64_t(blockIdx.x) * TILE + threadIdx.x;
+  const double v = j < n ? w[j] : 0.0;
+  unsigned long long tot;
+  const double c = fixed_double(block_scan_fixed(weight_fixed(v), b, &tot));
+  if (j < n) prefix[j] = c;
+  if (threadIdx.x == 0) total[blockIdx.x] = fixed_double(tot);
+}
+
+cudaError_t launch_tile_prefix(const double* w, double* prefix, double* total, int64_t n,
+                               cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t nb = (n + TILE - 1) / TILE;
+  k_tile_prefix<<<unsigned(nb), TILE, 0, st>>>(w, prefix, total, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_weight_exp(const double* d, double* w, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int64_t nb = (n + TILE - 1) / TILE;
@@ -2285,10 +2332,6 @@ cudaError_t launch_weight_exp(const double* d, double* w, int64_t n, cudaStream_
   return cudaGetLastError();
 }
 
-// Blocks per tile of the sub-tile propagate launch for FP64 tiles of a plan
-// of `ntiles` tiles in all: 4 or 2 when the state is FP64 and that many
-// blocks per tile still fit the GPU's resident blocks at once, else 1
-// (k_propagate).
 // The current device's SM count, queried once per process (a function-local
 // static: its initialisation is thread-safe, so host threads launching at
 // the same time see one value).
@@ -2303,6 +2346,10 @@ static int device_sms() {
   return sms;
 }
 
+// Blocks per tile of the sub-tile propagate launch for FP64 tiles of a plan
+// of `ntiles` tiles in all: 4 or 2 when the state is FP64 and that many
+// blocks per tile still fit the GPU's resident blocks at once, else 1
+// (k_propagate).
 template <int KIND, int N, typename R>
 static int sub_for(int ntiles) {
   if constexpr (sizeof(R) != 8) {

@@ -157,6 +157,30 @@ extern "C" pf_status pf_weight_exp(const double* d, double* w, int64_t n) {
   return PF_OK;
 }
 
+extern "C" pf_status pf_weight_prefix(const double* w, double* prefix, double* totals,
+                                      int64_t n) {
+  if (n < 0) return pfb::fail(PF_EINVAL, "n = %lld < 0", static_cast<long long>(n));
+  if (n == 0) return PF_OK;
+  if (!w || !prefix || !totals) return pfb::fail(PF_EINVAL, "w, prefix or totals is NULL");
+  if (n > (int64_t(1) << 28)) return pfb::fail(PF_EINVAL, "n = %lld > 2^28", static_cast<long long>(n));
+  for (int64_t k = 0; k < n; ++k)
+    if (!(w[k] >= 0.0 && w[k] <= 1.0))
+      return pfb::fail(PF_EINVAL, "w[%lld] is not in [0, 1]", static_cast<long long>(k));
+  const int64_t nt = (n + pfb::TILE - 1) / pfb::TILE;
+  double* buf = nullptr;
+  const size_t bytes = size_t(n) * sizeof(double);
+  cudaError_t e = cudaMalloc(&buf, 2 * bytes + size_t(nt) * sizeof(double));
+  if (e != cudaSuccess) return pfb::fail(PF_ECUDA, "cudaMalloc: %s", cudaGetErrorString(e));
+  e = cudaMemcpy(buf, w, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = pfb::launch_tile_prefix(buf, buf + n, buf + 2 * n, n, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(prefix, buf + n, bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(totals, buf + 2 * n, size_t(nt) * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) return pfb::fail(PF_ECUDA, "tile prefix: %s", cudaGetErrorString(e));
+  return PF_OK;
+}
+
 extern "C" pf_status pf_weight_sum_log(const double* s, double* y, int64_t n) {
   if (n < 0) return pfb::fail(PF_EINVAL, "n = %lld < 0", static_cast<long long>(n));
   if (n == 0) return PF_OK;

@@ -4,8 +4,12 @@ logarithm (likelihood line: log S), evaluated on the GPU through the C ABI and
 compared with correctly rounded values: the exponential within 2.5 units of
 2^-53 relative on -700 < d <= 0, exact at the special points, the library
 exponential below; the logarithm within 4 units of 2^-53 times max(1, log S)
-on 1 <= S <= 2^120, the library logarithm outside."""
+on 1 <= S <= 2^120, the library logarithm outside.  The tile's cumulative
+weights (the prefix sums Sec. 3.3's resampling searches) are the exact
+rational sums of the weights rounded to multiples of 2^-55, each sum rounded
+once to the nearest double."""
 import math
+from fractions import Fraction
 
 import mpmath
 import numpy as np
@@ -116,3 +120,54 @@ def test_weight_sum_log_outside_the_fast_range():
     assert pf.pf_weight_sum_log(np.zeros(0)).size == 0
     assert pf.lib().pf_weight_sum_log(None, None, -1) == pf.PF_EINVAL
     assert pf.lib().pf_weight_sum_log(None, None, 4) == pf.PF_EINVAL
+
+
+def _exact_prefix(w):
+    """Per tile of 256: each weight rounded to the nearest multiple of 2^-55
+    (ties to even: Python's round of a Fraction), exact running sums, each
+    rounded to the nearest double (float of a Fraction)."""
+    pre, tot = [], []
+    for t0 in range(0, len(w), 256):
+        acc = Fraction(0)
+        for v in w[t0:t0 + 256]:
+            acc += Fraction(round(Fraction(float(v)) * 2 ** 55), 2 ** 55)
+            pre.append(float(acc))
+        tot.append(float(acc))
+    return np.array(pre), np.array(tot)
+
+
+def test_tile_prefix_is_the_rounded_exact_sum():
+    import paper_1306_3277_b300 as pf
+    rng = np.random.default_rng(11)
+    ulp55 = 2.0 ** -55
+    w = np.concatenate([
+        rng.uniform(0.0, 1.0, 1024),
+        np.exp(-rng.exponential(5.0, 1024)),               # weights of a spread tile
+        10.0 ** rng.uniform(-320.0, 0.0, 1024),            # down to subnormal weights
+        (rng.integers(0, 2 ** 20, 768) + 0.5) * ulp55,     # ties of the 2^-55 rounding
+        (rng.integers(0, 2 ** 20, 256) + 0.5) * ulp55 * 2 ** 30,
+        np.zeros(100), np.ones(300),                       # exact 0 and 1
+        np.full(256, 1.0), np.full(256, ulp55 / 2),        # a full tile of ones; half ulps
+        np.full(77, 5e-324),                               # the smallest subnormal
+        rng.uniform(0.0, 1.0, 333),                        # ragged last tile
+    ])
+    prefix, totals = pf.pf_weight_prefix(w)
+    ep, et = _exact_prefix(w)
+    assert np.array_equal(prefix, ep)
+    assert np.array_equal(totals, et)
+    # the tile's last prefix is its total, and prefixes never decrease in a tile
+    for t in range(len(totals)):
+        seg = prefix[256 * t:256 * (t + 1)]
+        assert seg[-1] == totals[t]
+        assert np.all(np.diff(seg) >= 0.0)
+
+
+def test_tile_prefix_rejects_weights_outside_unit_interval():
+    import paper_1306_3277_b300 as pf
+    for bad in ([0.5, 1.0000000000000002], [-1e-300], [np.nan], [np.inf]):
+        with pytest.raises(pf.PFError):
+            pf.pf_weight_prefix(np.array(bad))
+    p, t = pf.pf_weight_prefix(np.zeros(0))
+    assert p.size == 0 and t.size == 0
+    p, t = pf.pf_weight_prefix(np.array([-0.0, 0.25, -0.0]))  # -0 counts as 0
+    assert list(p) == [0.0, 0.25, 0.25] and list(t) == [0.25]
