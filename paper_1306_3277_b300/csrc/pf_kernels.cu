@@ -793,16 +793,19 @@ __global__ void __launch_bounds__(TILE) k_init(const FilterDev* __restrict__ fds
   init_tile<KIND, N, R>(fds[ft.x], ft.y);
 }
 
-// Blocks per SM the propagate kernel is compiled for: two wherever the state
-// fits in 128 registers per thread without spilling more than a few words
-// (every FP32 size, FP64 up to N = 12, the windkessel), else one.
 // Blocks per SM the propagate kernel is compiled for (registers per thread =
-// 65536 / (256 x blocks)).  The small states are FP64-latency-bound, so more
-// resident warps pay: windkessel 4 (64 registers), Lorenz '96 in FP32 up to
-// N = 12 3 (85); the N = 40 FP32 state needs its 128 registers (2 blocks).
+// 65536 / (256 x blocks)), as many as the state allows without spilling more
+// than a couple of words: the small states are bound by FP64 latency, so more
+// resident warps pay.  FP32 windkessel 6 (40 registers), FP64 windkessel 4
+// (64); Lorenz '96 in FP32: N = 4 5 (48), N = 8 4 (64), N = 12 3 (85), larger
+// N 2 (the N = 40 state needs its 128 registers); in FP64 2 up to N = 12,
+// else 1.
 template <int KIND, int N, typename R>
 struct PropagateOccupancy {
-  static constexpr int value = wk_kind(KIND)                    ? 4
+  static constexpr int value = (wk_kind(KIND) && sizeof(R) == 4) ? 6
+                               : wk_kind(KIND)                    ? 4
+                               : (sizeof(R) == 4 && N <= 4)      ? 5
+                               : (sizeof(R) == 4 && N <= 8)      ? 4
                                : (sizeof(R) == 4 && N <= 12)     ? 3
                                : (sizeof(R) == 4 || N <= 12)     ? 2
                                                                  : 1;
