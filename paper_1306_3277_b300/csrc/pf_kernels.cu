@@ -794,18 +794,18 @@ __global__ void __launch_bounds__(TILE) k_init(const FilterDev* __restrict__ fds
 }
 
 // Blocks per SM the propagate kernel is compiled for (registers per thread =
-// 65536 / (256 x blocks)), as many as the state allows without spilling more
-// than a couple of words: the small states are bound by FP64 latency, so more
-// resident warps pay.  FP32 windkessel 6 (40 registers), FP64 windkessel 4
-// (64); Lorenz '96 in FP32: N = 4 5 (48), N = 8 4 (64), N = 12 3 (85), larger
-// N 2 (the N = 40 state needs its 128 registers); in FP64 2 up to N = 12,
-// else 1.
+// 65536 / (256 x blocks)).  The small states are bound by FP64 latency, so
+// more resident warps pay, up to a few spilled words (each step measured
+// faster than the one before it): FP32 windkessel 8 (32 registers, 28 bytes
+// spilled), FP64 windkessel 4 (64); Lorenz '96 in FP32: N = 4 and N = 8 5
+// (48; N = 8 spills 32 bytes), N = 12 3 (85), larger N 2 (the N = 40 state
+// needs its 128 registers); in FP64 2 up to N = 12, else 1.
 template <int KIND, int N, typename R>
 struct PropagateOccupancy {
-  static constexpr int value = (wk_kind(KIND) && sizeof(R) == 4) ? 6
+  static constexpr int value = (wk_kind(KIND) && sizeof(R) == 4) ? 8
                                : wk_kind(KIND)                    ? 4
                                : (sizeof(R) == 4 && N <= 4)      ? 5
-                               : (sizeof(R) == 4 && N <= 8)      ? 4
+                               : (sizeof(R) == 4 && N <= 8)      ? 5
                                : (sizeof(R) == 4 && N <= 12)     ? 3
                                : (sizeof(R) == 4 || N <= 12)     ? 2
                                                                  : 1;
