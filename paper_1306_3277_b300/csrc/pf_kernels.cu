@@ -369,17 +369,18 @@ __device__ __forceinline__ void wkx_propagate(const FilterDev& fd, uint32_t j, i
 
 // Windkessel propagation: s Euler substeps x <- x + dt (F_k/C - x/(RC)) +
 // sqrt(q) z_mm (normal number mm of stream (j, i, PROP)).  fc, when given,
-// holds the step's F_k/C, and kc the filter's sqrt(q) and RC (the same
-// operations, made once per block: every particle shares them; in FP64 the
-// square root is a long chain on B300's 1/64-rate FP64 unit).
+// holds the step's F_k/C, and kc the filter's sqrt(q), RC, C and dt in R (the
+// same operations, made once per block: every particle shares them; in FP64
+// the square root is a long chain on B300's 1/64-rate FP64 unit, and in FP32
+// the conversions from FP64 run on that unit too).
 template <typename R>
 __device__ __forceinline__ void wk_propagate(const FilterDev& fd, uint32_t j, int i, R& xv,
                                              const R* fc, const R* kc) {
   const int s = fd.s;
-  const R Cc = from_double<R>(fd.theta[1]);
-  const R dt = from_double<R>(fd.dt);
-  const R sq = kc ? kc[0] : sqrt(from_double<R>(fd.theta[3]));
-  const R RC = kc ? kc[1] : from_double<R>(fd.theta[0]) * Cc;
+  const R Cc = kc[2];
+  const R dt = kc[3];
+  const R sq = kc[0];
+  const R RC = kc[1];
   const double* fl = fd.flow + int64_t(i - 1) * s;
   if constexpr (sizeof(R) == 8) {
     for (int mm = 0; mm < s; mm += 2) {
@@ -848,14 +849,17 @@ __device__ __forceinline__ double propagate_ell(const FilterDev& fd, int i, int 
     __syncthreads();
   }
   // Euler windkessel: F(t_k)/C of the step's substeps, one division each, and
-  // the filter's sqrt(q) and RC
+  // the filter's sqrt(q), RC, C and dt in R, converted by one thread per block
+  // (conversions from FP64 run on the FP64 unit, which bounds this kernel)
   __shared__ R fcs[KIND == KIND_WK ? TILE : 1];
-  __shared__ R wkc[2];
+  __shared__ R wkc[4];
   const R* fc = nullptr;
   if constexpr (KIND == KIND_WK) {
     if (tid == TILE - 2) {
       wkc[0] = sqrt(from_double<R>(fd.theta[3]));
       wkc[1] = from_double<R>(fd.theta[0]) * from_double<R>(fd.theta[1]);
+      wkc[2] = from_double<R>(fd.theta[1]);
+      wkc[3] = from_double<R>(fd.dt);
     }
     if (fd.s <= TILE) {
       if (tid < fd.s)
@@ -901,7 +905,10 @@ __device__ __forceinline__ double propagate_ell(const FilterDev& fd, int i, int 
       else lw = l96_weight<N, R>(fd, x, ys, cw);
     }
     double e = lam_zero ? lw : fd.lam[j] + lw;
-    if (e != e) e = -INFINITY;
+    // NaN -> -inf, tested on the bits (an FP64 compare is FP64-unit work)
+    if ((static_cast<unsigned long long>(__double_as_longlong(e)) & 0x7fffffffffffffffull) >
+        0x7ff0000000000000ull)
+      e = -INFINITY;
     ell = e;
     if (fd.mode != MODE_ALWAYS) fd.ell[j] = e;
   }
@@ -917,7 +924,10 @@ __device__ __forceinline__ void tile_epilogue(const FilterDev& fd, int t, int j,
   // tile partials: max, inclusive prefix of exp(ell - M_t) (FIXED: exact sums
   // of the weights in 2^-55 fixed point, each rounded once to a double), total
   const double Mt = block_max(ell, cs.b);
-  const double w = (Mt == -INFINITY) ? 0.0 : exp_weight(ell - Mt);
+  const double w = (static_cast<unsigned long long>(__double_as_longlong(Mt)) ==
+                    0xfff0000000000000ull)  // Mt == -inf, on the bits
+                       ? 0.0
+                       : exp_weight(ell - Mt);
   double c, St;
   if constexpr (FIXED) {
     unsigned long long Ft;
