@@ -80,6 +80,8 @@ struct alignas(16) Ctl {
   double c_obs;          // -Ny/2 log(2 pi r)
   double logP;           // log P
   double cw;             // -0.5 / r: scale of the residual sum of squares
+  float lf[6];           // FP32 Lorenz '96: F, dt, dt/2, dt/3, dt/6, sqrt(q) of the run
+  float lpad[2];
 };
 
 // Descriptor of one filter (device copy read by every kernel).

@@ -426,14 +426,32 @@ __device__ __forceinline__ double wk_weight(const FilterDev& fd, int i, R xv, do
   return acc * cw;
 }
 
+// The FP32 Lorenz '96 step constants of a run, as l96_propagate derives them
+// from theta and dt: F, dt, dt/2, dt/3, dt/6, sqrt(q).  Computed once per run
+// into the control block (the conversions from FP64 are FP64-unit work, which
+// bounds the small-state kernels) and read back by every block.
+__device__ __forceinline__ void l96_constants32(const FilterDev& fd, float* lf) {
+  const float dt = __double2float_rn(fd.dt);
+  lf[0] = __double2float_rn(fd.theta[0]);
+  lf[1] = dt;
+  lf[2] = 0.5f * dt;
+  lf[3] = dt / 3.0f;
+  lf[4] = dt / 6.0f;
+  lf[5] = sqrtf(__double2float_rn(fd.theta[1]));
+}
+
 // Lorenz '96 propagation: s RK4 substeps, then additive sqrt(q) z_n on every
 // component.  In FP32 the state is integrated as N/2 packed pairs (components
 // p and p + N/2), which issues half the instructions for the same bits.
 template <int N, typename R>
-__device__ __forceinline__ void l96_propagate(const FilterDev& fd, uint32_t j, int i, R (&x)[N]) {
-  const R F = from_double<R>(fd.theta[0]);
-  const R dt = from_double<R>(fd.dt);
-  const R h2 = R(0.5) * dt, h3 = dt / R(3.0), h6 = dt / R(6.0);
+__device__ __forceinline__ void l96_propagate(const FilterDev& fd, uint32_t j, int i, R (&x)[N],
+                                              const float* lf = nullptr) {
+  // lf (FP32 state only): the run's constants from the control block
+  const bool cst = sizeof(R) == 4 && lf != nullptr;
+  const R F = cst ? R(lf[0]) : from_double<R>(fd.theta[0]);
+  const R dt = cst ? R(lf[1]) : from_double<R>(fd.dt);
+  const R h2 = cst ? R(lf[2]) : R(0.5) * dt, h3 = cst ? R(lf[3]) : dt / R(3.0),
+          h6 = cst ? R(lf[4]) : dt / R(6.0);
   if constexpr (sizeof(R) == 4 && N % 2 == 0) {
     constexpr int H = N / 2;
     f32x2 X[H];
@@ -444,7 +462,7 @@ __device__ __forceinline__ void l96_propagate(const FilterDev& fd, uint32_t j, i
     for (int mm = 0; mm < fd.s; ++mm) l96_rk4_step2<H>(X, FF, dt2, h22, h32, h62);
     R z[N];
     normals<N>(z, fd.seed, j, uint32_t(i), PURPOSE_PROP);
-    const R sx = sqrt(from_double<R>(fd.theta[1]));
+    const R sx = cst ? R(lf[5]) : sqrt(from_double<R>(fd.theta[1]));
     const f32x2 sx2 = pk(sx, sx);
 #pragma unroll
     for (int p = 0; p < H; ++p) {
@@ -455,7 +473,7 @@ __device__ __forceinline__ void l96_propagate(const FilterDev& fd, uint32_t j, i
     for (int mm = 0; mm < fd.s; ++mm) l96_rk4_step<N, R>(x, F, dt, h2, h3, h6);
     R z[N];
     normals<N>(z, fd.seed, j, uint32_t(i), PURPOSE_PROP);
-    const R sx = sqrt(from_double<R>(fd.theta[1]));
+    const R sx = cst ? R(lf[5]) : sqrt(from_double<R>(fd.theta[1]));
 #pragma unroll
     for (int n = 0; n < N; ++n) x[n] = fmaR(sx, z[n], x[n]);
   }
@@ -784,6 +802,7 @@ __device__ __forceinline__ void init_tile(const FilterDev& fd, int t) {
     c->S = 0.0;
     c->u = 0.0;
     c->ratio = 0.0;
+    if (l96_kind(KIND)) l96_constants32(fd, c->lf);
   }
 }
 
@@ -838,7 +857,8 @@ __device__ __forceinline__ T* cluster_peer(T* local, unsigned rank) {
 template <int KIND, int N, typename R>
 __device__ __forceinline__ double propagate_ell(const FilterDev& fd, int i, int j, bool valid,
                                                 int anc_identity, int lam_zero, double cw,
-                                                int a_spec, double* ys) {
+                                                int a_spec, double* ys,
+                                                const float* lf = nullptr) {
   const int P = fd.P;
   const int tid = threadIdx.x;
   if (tid < fd.Ny) ys[tid] = fd.y[int64_t(i - 1) * fd.Ny + tid];  // read after the barrier below
@@ -885,7 +905,7 @@ __device__ __forceinline__ double propagate_ell(const FilterDev& fd, int i, int 
     if constexpr (KIND == KIND_WK) wk_propagate<R>(fd, uint32_t(j), i, x[0], fc, wkc);
     else if constexpr (KIND == KIND_WKX) wkx_propagate<R>(fd, uint32_t(j), i, x[0], kc);
     else if constexpr (KIND == KIND_L96W) l96w_propagate<N, R>(fd, uint32_t(j), i, x);
-    else l96_propagate<N, R>(fd, uint32_t(j), i, x);
+    else l96_propagate<N, R>(fd, uint32_t(j), i, x, lf);
     if constexpr (PF_CHECKED) {
       bool bad = false;
 #pragma unroll
@@ -968,10 +988,10 @@ template <int KIND, int N, typename R>
 __device__ __forceinline__ void propagate_tile(const FilterDev& fd, int t, int i, int anc_identity,
                                                int lam_zero, double cw, int a_spec, double* ys,
                                                CombineScratch& cs, TileTriples* tri = nullptr,
-                                               int ncopies = 0) {
+                                               int ncopies = 0, const float* lf = nullptr) {
   const int j = t * TILE + int(threadIdx.x);
-  const double ell =
-      propagate_ell<KIND, N, R>(fd, i, j, j < fd.P, anc_identity, lam_zero, cw, a_spec, ys);
+  const double ell = propagate_ell<KIND, N, R>(fd, i, j, j < fd.P, anc_identity, lam_zero, cw,
+                                               a_spec, ys, lf);
   tile_epilogue<FixedPrefix<KIND, N>::value>(fd, t, j, ell, cs, tri, ncopies);
 }
 
@@ -1004,17 +1024,25 @@ __global__ void __launch_bounds__(TILE, (PropagateOccupancy<KIND, N, R>::value))
   // shares it: every thread reading it would queue on one L2 line
   __shared__ int s_step, s_ok, s_anc_identity, s_lam_zero;
   __shared__ double s_cw;
+  // the FP32 small-state Lorenz '96 constants of the run (see l96_constants32)
+  constexpr bool LF = KIND == KIND_L96 && sizeof(R) == 4 && N <= 12;
+  __shared__ float s_lf[LF ? 6 : 1];
   if (tid == 0) {
     s_step = ldcg(&ctl->step);
     s_ok = ldcg(&ctl->status) == ST_OK;
     s_anc_identity = ldcg(&ctl->anc_identity);
     s_lam_zero = ldcg(&ctl->lam_zero);
     s_cw = ldcg(&ctl->cw);
+    if constexpr (LF) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s_lf[k] = ldcg(&ctl->lf[k]);
+    }
   }
   __syncthreads();
   const int i = s_step;
   if (i > fd.T || !s_ok) return;
-  propagate_tile<KIND, N, R>(fd, t, i, s_anc_identity, s_lam_zero, s_cw, a_spec, ys, cs);
+  propagate_tile<KIND, N, R>(fd, t, i, s_anc_identity, s_lam_zero, s_cw, a_spec, ys, cs, nullptr,
+                             0, LF ? s_lf : nullptr);
   if (tid == 0) {
     __threadfence();
     const int g = t / GROUP;
@@ -2158,6 +2186,7 @@ __global__ void k_debug_ctl(const FilterDev* __restrict__ fds, int step, int anc
     c->S = 0.0;
     c->u = 0.0;
     c->ratio = 0.0;
+    if (l96_kind(fd.kind)) l96_constants32(fd, c->lf);
   }
   for (int g = threadIdx.x; g < fd.ngroups; g += blockDim.x) fd.gp[g].ticket = 0u;
   for (int t = threadIdx.x; t < fd.ntiles; t += blockDim.x) fd.tp[t].ticket = 0u;
